@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""PHOBIC construction + query benchmark on B300.
+
+Workload: 1e8 distinct uniform uint64 keys, lambda = 7, alpha = 0.99 (Elias-Fano
+remap of slots >= n), partition size 2500, interleaved dictionary encoding
+(IC-D); then 1e8 uniform positive queries and 1e8 Zipf(s = 1) positive
+queries.  One step = one build of the resident keys plus both query batches.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`value` is build throughput (Mkeys/s, device-resident inputs, CUDA events on
+the build stream); the query rates, bits/key, per-phase times, roofline,
+end-to-end (host buffers) numbers and the CPU oracle baseline ride along on the
+same JSON line.  Under torchrun each rank builds its own key set (independent
+problems: weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "build Mkeys/s & query Mkeys/s at 1e8 keys; bits/key; serve p50/p99 latency"
+WORKLOAD = ("1e8 distinct uniform uint64 keys, lambda=7, alpha=0.99 with Elias-Fano free-slot remap, partition "
+            "size 2500, interleaved dictionary (IC-D) pilot encoding; 1e8 uniform + 1e8 Zipf(s=1) positive queries")
+SMALL = ("1e6 distinct uniform uint64 keys, lambda=7, alpha=1, partition size 2500, IC-C; 1e7 uniform positive "
+         "queries")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--small", action="store_true", help="the 1e6-key configuration instead")
+    ap.add_argument("--n", type=float, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-target-s", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(a):
+    if a.small:
+        n = int(a.n or 1e6)
+        return dict(name=SMALL, n=n, lam=7.0, alpha=1.0, P=2500, encoder=0, q_uniform=10 * n, q_zipf=0)
+    n = int(a.n or 1e8)
+    return dict(name=WORKLOAD, n=n, lam=7.0, alpha=0.99, P=2500, encoder=1, q_uniform=n, q_zipf=n)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+                power.append(float(c[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# --------------------------------------------------------------- CPU oracle ---
+def oracle_sample_rate(keys: np.ndarray, w: dict, target_s: float):
+    """The oracle as it stands, on a bounded prefix of the same keys, all host
+    cores.  Grows the sample until one build takes about target_s / 3."""
+    from oracle import oracle as o
+
+    o.lib()
+    cores = os.cpu_count() or 1
+    n_s = min(keys.size, 250_000)
+    while True:
+        t = time.perf_counter()
+        h = o.Oracle(keys[:n_s], lam=w["lam"], alpha=w["alpha"], P=w["P"], encoder=w["encoder"], threads=cores)
+        dt = time.perf_counter() - t
+        if dt > target_s / 3 or n_s >= keys.size or n_s >= 20_000_000:
+            break
+        n_s = int(min(keys.size, n_s * max(2.0, (target_s / 3) / max(dt, 1e-3))))
+    builds = [dt]
+    while sum(builds) < target_s * 2 / 3 and len(builds) < 5:
+        t = time.perf_counter()
+        h = o.Oracle(keys[:n_s], lam=w["lam"], alpha=w["alpha"], P=w["P"], encoder=w["encoder"], threads=cores)
+        builds.append(time.perf_counter() - t)
+    qn = min(n_s, 1_000_000)
+    t = time.perf_counter()
+    h.query(keys[:qn])
+    qdt = time.perf_counter() - t
+    return {"value": n_s / min(builds) / 1e6, "unit": "Mkeys/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle build of the first {n_s} keys of the workload (same lambda, alpha, P, encoder), "
+                      f"best of {len(builds)}, OpenMP over partitions on {cores} threads; query of {qn} keys "
+                      f"single-threaded",
+            "query_value": qn / qdt / 1e6, "build_s": min(builds)}
+
+
+def run_reference(a):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2404_18497_b300 import workloads
+
+    w = workload(a)
+    keys = workloads.distinct_u64(min(w["n"], 20_000_000), 2)
+    from oracle import oracle as o
+
+    o.lib()
+    cores = os.cpu_count() or 1
+    n_s = min(keys.size, 1_000_000 if not a.small else keys.size)
+    times = []
+    for i in range(a.warmup + a.steps):
+        t = time.perf_counter()
+        h = o.Oracle(keys[:n_s], lam=w["lam"], alpha=w["alpha"], P=w["P"], encoder=w["encoder"], threads=cores)
+        dt = time.perf_counter() - t
+        del h
+        if i >= a.warmup:
+            times.append(dt)
+    ms = statistics.mean(times) * 1e3
+    v = n_s / (ms / 1e3) / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mkeys/s", "n_gpus": a.gpus, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u64", "data": "synthetic",
+           "config": {"workload": w["name"], "n": w["n"], "lambda": w["lam"], "alpha": w["alpha"], "P": w["P"],
+                      "encoder": "IC-D" if w["encoder"] else "IC-C"},
+           "cpu_baseline": {"value": v, "unit": "Mkeys/s", "cores": cores, "kind": "oracle",
+                            "sample": f"each step: oracle build of the first {n_s} keys of the workload on {cores} "
+                                      f"threads"},
+           "e2e": {"value": v, "unit": "Mkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ ours -----
+def run_ours(a):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2404_18497_b300 import build as libbuild
+
+    libbuild.build()
+    from paper_2404_18497_b300 import phobic, workloads
+
+    w = workload(a)
+    n = w["n"]
+    keys = workloads.distinct_u64(n, 2 + 1000 * rank)
+    qu = workloads.uniform_queries(keys, w["q_uniform"], 3 + 1000 * rank)
+    qz = workloads.zipf_queries(keys, w["q_zipf"], 4 + 1000 * rank) if w["q_zipf"] else None
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dqu = torch.from_numpy(qu.view(np.int64)).cuda()
+    dqz = torch.from_numpy(qz.view(np.int64)).cuda() if qz is not None else None
+    out = torch.empty(max(dqu.numel(), dqz.numel() if dqz is not None else 0), dtype=torch.int64, device="cuda")
+    prm = phobic.make_params(w["lam"], w["alpha"], w["P"], seed=0, encoder=w["encoder"], record_timings=True)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        h = phobic.phobic_build_ex(dk, prm, stream)
+        e[1].record(stream)
+        phobic.phobic_query(h, dqu, out[: dqu.numel()], stream)
+        e[2].record(stream)
+        if dqz is not None:
+            phobic.phobic_query(h, dqz, out[: dqz.numel()], stream)
+        e[3].record(stream)
+        return h, e
+
+    for _ in range(a.warmup):
+        h, _ = step()
+        h.free()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    l0 = phobic.phobic_kernel_launches()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    recs = []
+    t0.record(stream)
+    for _ in range(a.steps):
+        h, e = step()
+        recs.append((h, e))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = phobic.phobic_kernel_launches() - l0
+    total_ms = t0.elapsed_time(t1)
+    build_ms = [e[0].elapsed_time(e[1]) for _, e in recs]
+    qu_ms = [e[1].elapsed_time(e[2]) for _, e in recs]
+    qz_ms = [e[2].elapsed_time(e[3]) for _, e in recs] if dqz is not None else [0.0]
+    phases = [phobic.phobic_get_timings(h) for h, _ in recs]
+    bpk = recs[-1][0].bits_per_key()
+    info = recs[-1][0].info()
+    # check the result on device: the query outputs are a permutation of [0, n)
+    res = recs[-1][0].query(dk)
+    perm_ok = bool(torch.equal(torch.sort(res).values, torch.arange(n, device="cuda")))
+    ref_u = recs[-1][0].query(dqu).cpu().numpy()
+    del res
+    for h, _ in recs:
+        h.free()
+
+    ms_step = reduce_max(total_ms / a.steps, world)
+    b_ms = reduce_max(statistics.mean(build_ms), world)
+    u_ms = reduce_max(statistics.mean(qu_ms), world)
+    z_ms = reduce_max(statistics.mean(qz_ms), world)
+    ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+
+    # ---- roofline of the dominant kernel (CUDA events on the launching stream)
+    hbm, src = peaks()
+    kern = {
+        "k_search (bucketing + pilot search)": ph["search_ms"],
+        "k_sort_pass x2 + k_sort_hist (hash + onesweep partition sort)": ph["sort_ms"],
+        "k_query (uniform batch)": statistics.mean(qu_ms),
+        "k_query (Zipf batch)": statistics.mean(qz_ms),
+        "encode (offsets + IC-D)": ph["encode_ms"],
+        "remap (Elias-Fano)": ph["remap_ms"],
+    }
+    dom = max(kern, key=kern.get)
+    q_bytes = 16.0 * w["q_uniform"]
+    roof_query = {"bound": "hbm", "achieved": q_bytes / (statistics.mean(qu_ms) / 1e3) / 1e9, "peak": hbm,
+                  "unit": "GB/s", "frac": None, "traffic": None, "kernel": "k_query (uniform batch)",
+                  "algorithmic_bytes_per_launch": q_bytes, "peak_source": f"{src} hbm_gbs"}
+    roof_query["frac"] = roof_query["achieved"] / hbm
+    sort_bytes = 40.0 * n  # histogram read 8 B + two passes x (8 B read + 8 B write) per key
+    roof_sort = {"bound": "hbm", "achieved": sort_bytes / (ph["sort_ms"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                 "kernel": "hash + onesweep partition sort", "algorithmic_bytes_per_launch": sort_bytes}
+    roof_sort["frac"] = roof_sort["achieved"] / hbm
+    build_bytes = 8.3 * n
+    roof_build = {"bound": "hbm", "achieved": build_bytes / (b_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                  "kernel": "whole build", "algorithmic_bytes_per_launch": build_bytes}
+    roof_build["frac"] = roof_build["achieved"] / hbm
+    roofline = dict(roof_query)
+    roofline["dominant_kernel_by_time"] = dom
+    roofline["per_kernel_ms"] = kern
+    roofline["sort"] = roof_sort
+    roofline["build"] = roof_build
+
+    # ---- end to end through the host-buffer entry points
+    e2e = None
+    if not a.no_e2e:
+        hk_pin = torch.from_numpy(keys.view(np.int64)).pin_memory()
+        hq_pin = torch.from_numpy(qu.view(np.int64)).pin_memory()
+        ho_pin = torch.empty_like(hq_pin).pin_memory()
+        hkn, hqn, hon = hk_pin.numpy(), hq_pin.numpy(), ho_pin.numpy()
+        prm2 = phobic.make_params(w["lam"], w["alpha"], w["P"], seed=0, encoder=w["encoder"])
+        bt, qt = [], []
+        for i in range(2 + min(a.steps, 5)):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            h = phobic.phobic_build_host(hkn, prm2, stream)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            phobic.phobic_query_host(h, hqn, hon.view(np.uint64), stream)
+            t3 = time.perf_counter()
+            if i >= 2:
+                bt.append(t2 - t)
+                qt.append(t3 - t2)
+            h.free()
+        ok = bool(np.array_equal(hon, ref_u))
+        e2e = {"value": world * n / reduce_max(statistics.mean(bt), world) / 1e6, "unit": "Mkeys/s",
+               "h2d_bytes_per_step": 8 * n + 8 * w["q_uniform"], "d2h_bytes_per_step": 8 * w["q_uniform"],
+               "query_value": world * w["q_uniform"] / reduce_max(statistics.mean(qt), world) / 1e6,
+               "note": "phobic_build_host (pinned keys, H2D inside) + phobic_query_host (H2D keys, D2H results)",
+               "check": ok}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not a.no_cpu_baseline:
+        cpu = oracle_sample_rate(keys, w, a.cpu_target_s)
+    gpu_name = torch.cuda.get_device_name(local)
+    res_line = {
+        "metric": METRIC,
+        "value": world * n / (b_ms / 1e3) / 1e6,
+        "unit": "Mkeys/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "n": n, "lambda": w["lam"], "alpha": w["alpha"], "P": w["P"],
+                   "encoder": "IC-D" if w["encoder"] else "IC-C", "queries_uniform": w["q_uniform"],
+                   "queries_zipf": w["q_zipf"], "parallelism": f"independent key set per GPU x{world}",
+                   "l2": "inputs larger than L2 (8e8-byte key and query arrays vs 126 MB L2)", "gpu": gpu_name},
+        "build_ms": b_ms,
+        "build_mkeys_s": world * n / (b_ms / 1e3) / 1e6,
+        "query_mkeys_s": world * w["q_uniform"] / (u_ms / 1e3) / 1e6,
+        "query_zipf_mkeys_s": (world * w["q_zipf"] / (z_ms / 1e3) / 1e6) if w["q_zipf"] else None,
+        "bits_per_key": bpk,
+        "phase_ms": ph,
+        "structure": {k: info[k] for k in ("M", "num_partitions", "num_buckets", "max_partition", "bits_pilots",
+                                           "bits_offsets", "bits_remap", "device_bytes")},
+        "result_is_permutation": perm_ok,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "gpu_launches_per_step": launches / a.steps,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(res_line))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

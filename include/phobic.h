@@ -1,0 +1,208 @@
+/*
+ * phobic.h -- C ABI of libphobic, a B300 (sm_103a) implementation of PHOBIC's
+ * data-parallel hot path: partitioned pilot-search construction of a minimal
+ * perfect hash function (MPHF) and its query.
+ *
+ * Paper: Hermann, Lehmann, Pibiri, Sanders, Walzer, "PHOBIC: Perfect Hashing
+ * with Optimized Bucket Sizes and Interleaved Coding", arXiv 2404.18497.
+ *
+ * Problem (Section 1): n distinct keys are mapped one-to-one onto [0, n).
+ * Output values are 0-based here; the paper writes [n] = {1..n}.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are CUDA device pointers on the current device; h_* are
+ *    host pointers.  Sizes are element counts unless named *_bytes.
+ *  - `stream` is a cudaStream_t (passed as phobic_stream_t so that this header
+ *    needs no CUDA headers); NULL means the legacy default stream.
+ *  - Entry points return a phobic_status.  No exception crosses the ABI and
+ *    nothing is printed.  On error, *out handles are set to NULL and all
+ *    temporaries are released.
+ *  - The library allocates its own device memory (stream-ordered, from the
+ *    device's default memory pool).  Inputs are borrowed, never freed.
+ *  - Every step of construction and query runs in this library's CUDA kernels;
+ *    there is no CPU fallback.
+ */
+#ifndef PHOBIC_H
+#define PHOBIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* phobic_stream_t; /* same type as cudaStream_t */
+typedef struct phobic_handle phobic_handle;   /* opaque: one built MPHF */
+
+typedef enum {
+    PHOBIC_OK = 0,
+    PHOBIC_ERR_INVALID_ARG = 1,          /* bad size, pointer or parameter */
+    PHOBIC_ERR_OOM = 2,                  /* device or host allocation failed */
+    PHOBIC_ERR_DUP_HASH = 3,             /* two keys share a 64-bit master hash (duplicate keys) */
+    PHOBIC_ERR_SEARCH_LIMIT = 4,         /* a bucket found no pilot below s_max, or holds > 1023 keys */
+    PHOBIC_ERR_PARTITION_TOO_LARGE = 5,  /* a partition does not fit the search kernel's shared memory */
+    PHOBIC_ERR_CUDA = 6,                 /* a CUDA runtime call failed */
+    PHOBIC_ERR_TIMEOUT = 7,              /* a bounded device-side wait gave up */
+    PHOBIC_ERR_FORMAT = 8                /* phobic_import: bytes are not a valid structure */
+} phobic_status;
+
+/* pilot encoders (Section 4.1, interleaved coding) */
+typedef enum {
+    PHOBIC_ENC_IC_C = 0, /* interleaved Compact: column width = bit length of its largest pilot */
+    PHOBIC_ENC_IC_D = 1  /* interleaved Dictionary: sorted distinct pilots + compact ranks */
+} phobic_encoder;
+
+/* pilot hash (Section 4, "Hash Function") */
+typedef enum {
+    PHOBIC_PILOT_ADDITIVE = 0, /* p = s m + d; position (h(x, s) + d) mod m  (the paper's PHOBIC) */
+    PHOBIC_PILOT_XOR = 1       /* PTHash: position h(x xor h(p)) reduced onto [0, m) */
+} phobic_pilot_mode;
+
+typedef struct {
+    double lambda;                /* average bucket size, > 0 (Section 3) */
+    double alpha;                 /* load factor in (0, 1]; < 1 builds on M = sum ceil(n_j/alpha) slots
+                                     and remaps slots >= n with Elias-Fano (Section 5, Further Remarks) */
+    uint32_t partition_size;      /* expected partition size P, 1..16384 (Section 4) */
+    uint32_t encoder;             /* phobic_encoder */
+    uint32_t pilot_mode;          /* phobic_pilot_mode */
+    uint32_t s_max;               /* search limit: s < s_max (ADDITIVE), p < s_max*m (XOR); 0 = default */
+    uint64_t seed;                /* master-hash seed */
+    uint32_t warps_per_partition; /* search kernel tuning: 0 = default; results do not depend on it */
+    uint32_t keep_pilots;         /* nonzero: keep the raw pilot matrix for phobic_copy_pilots */
+    uint32_t record_timings;      /* nonzero: time the build phases with CUDA events on `stream` */
+} phobic_params;
+
+/* Device time of each build phase (CUDA events recorded on the build stream
+ * around each phase's kernels; host gaps between phases are excluded). */
+typedef struct {
+    float sort_ms;     /* master hash + onesweep partition sort + partition starts */
+    float sizes_ms;    /* table sizes m_j and offsets T */
+    float search_ms;   /* bucketing + pilot search (one warp per partition) */
+    float encode_ms;   /* offsets + interleaved pilot encoding */
+    float remap_ms;    /* Elias-Fano remap of slots >= n (alpha < 1) */
+    float total_ms;    /* first to last event, host synchronisations included */
+} phobic_timings;
+
+/* Structure sizes and space breakdown of a built MPHF. */
+typedef struct {
+    uint64_t n;             /* keys */
+    uint64_t M;             /* slots = sum of table sizes m_j (M = n when alpha = 1) */
+    uint64_t num_partitions;/* N_P = max(1, ceil(n / P)) */
+    uint32_t num_buckets;   /* B = ceil(P / lambda) per partition */
+    uint32_t partition_size;
+    double lambda, alpha, epsilon;
+    uint32_t encoder, pilot_mode;
+    uint64_t seed;
+    uint64_t max_partition; /* largest n_j */
+    uint64_t bits_header, bits_offsets, bits_pilots, bits_remap, bits_total;
+    uint64_t device_bytes;  /* device memory owned by the handle */
+} phobic_info;
+
+/* Fills *p with the defaults: lambda 7, alpha 1, P 2500, IC-C, ADDITIVE,
+ * s_max 65536 (capped so that pilots fit 32 bits), seed 0. */
+void phobic_params_init(phobic_params* p);
+
+/*
+ * Construction (Section 4 pipeline + Section 3 bucket function):
+ *   hash keys -> radix-sort by partition -> per partition: bucket, order buckets by
+ *   (size desc, expected size asc), pilot search -> offsets, interleaved encoding,
+ *   Elias-Fano remap (alpha < 1).
+ * d_keys: n distinct 64-bit keys (device), borrowed for the call.
+ * The call returns after the device work finishes (the structure's sizes
+ * depend on device results), so it synchronises `stream`.
+ * Errors: INVALID_ARG for n = 0, NULL pointers, lambda <= 0, alpha outside (0,1],
+ * P = 0 or P > 16384; DUP_HASH for duplicate keys; SEARCH_LIMIT; OOM; CUDA.
+ */
+phobic_status phobic_build(const uint64_t* d_keys, uint64_t n, double lambda, double alpha,
+                           uint32_t partition_size, uint64_t seed, phobic_stream_t stream,
+                           phobic_handle** out);
+
+/* Same, with every parameter of phobic_params. */
+phobic_status phobic_build_ex(const uint64_t* d_keys, uint64_t n, const phobic_params* params,
+                              phobic_stream_t stream, phobic_handle** out);
+
+/* Same, from host memory: the keys are copied in chunks through pinned staging
+ * buffers and hashed on the device as they arrive. */
+phobic_status phobic_build_host(const uint64_t* h_keys, uint64_t n, const phobic_params* params,
+                                phobic_stream_t stream, phobic_handle** out);
+
+/*
+ * Query (Section 4 "Hash Function"): per key, partition j, offsets T_j, T_{j+1},
+ * bucket b, decoded pilot p, local position (h(x, floor(p/m)) + p) mod m, global
+ * position T_j + local, remapped through Elias-Fano when >= n.
+ * d_keys [m] in, d_out [m] out (uint64, values in [0, n)).  Asynchronous and
+ * stream-ordered: the caller keeps both buffers alive until `stream` is done.
+ * A key outside the built set gets an unspecified value in [0, n).
+ * m = 0 is a no-op.  Errors: INVALID_ARG (NULL handle/pointers), CUDA.
+ */
+phobic_status phobic_query(const phobic_handle* h, const uint64_t* d_keys, uint64_t* d_out, uint64_t m,
+                           phobic_stream_t stream);
+
+/* Query from host memory: copies keys in, results out, on `stream`; returns
+ * after the results are in h_out. */
+phobic_status phobic_query_host(const phobic_handle* h, const uint64_t* h_keys, uint64_t* h_out,
+                                uint64_t m, phobic_stream_t stream);
+
+/* Space of the structure in bits per key (fixed accounting: header, offsets,
+ * pilot encoders with their metadata, Elias-Fano remap).  NaN for NULL. */
+double phobic_bits_per_key(const phobic_handle* h);
+
+/* Structure sizes; INVALID_ARG for NULL. */
+phobic_status phobic_get_info(const phobic_handle* h, phobic_info* info);
+
+/*
+ * Serialization (exact words).  With h_buf NULL, *len receives the byte size.
+ * Otherwise *len is the buffer capacity on input and the bytes written on
+ * output.  Format: a versioned header followed by the packed arrays, all
+ * little-endian u64 words.  Synchronises the device.
+ */
+phobic_status phobic_export(const phobic_handle* h, void* h_buf, size_t* len);
+
+/* Rebuilds a handle from phobic_export bytes (FORMAT on malformed input). */
+phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t stream, phobic_handle** out);
+
+/* Copies the raw pilot matrix [B x N_P] (pilot of bucket b of partition j at
+ * b * N_P + j) to d_out; needs params.keep_pilots at build time (else INVALID_ARG). */
+phobic_status phobic_copy_pilots(const phobic_handle* h, uint32_t* d_out, phobic_stream_t stream);
+
+/* Phase timings of the build that produced h (needs params.record_timings;
+ * else INVALID_ARG). */
+phobic_status phobic_get_timings(const phobic_handle* h, phobic_timings* t);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (diagnostic; counts every launch of every entry point). */
+uint64_t phobic_kernel_launches(void);
+
+/* Releases every device buffer of h (synchronises the device).  NULL is a no-op. */
+void phobic_free(phobic_handle* h);
+
+/* Static string naming a status. */
+const char* phobic_status_str(phobic_status s);
+
+/* ---- stage entry points (each runs one kernel of the pipeline) ---- */
+
+/* Master hash codes of 64-bit keys (Section 5: keys first become 64-bit hashes):
+ * d_hk[i] = mix64(d_keys[i] xor mix64(seed xor C)); a bijection. */
+phobic_status phobic_hash_u64(const uint64_t* d_keys, uint64_t n, uint64_t seed, uint64_t* d_hk,
+                              phobic_stream_t stream);
+
+/* Master hash codes of n byte strings: string i is d_bytes[d_offsets[i] ..
+ * d_offsets[i+1]) (d_offsets has n+1 entries); 64-bit XXH64 with `seed`. */
+phobic_status phobic_hash_strings(const uint8_t* d_bytes, const uint64_t* d_offsets, uint64_t n,
+                                  uint64_t seed, uint64_t* d_hk, phobic_stream_t stream);
+
+/* Radix sort (onesweep) of the master hashes d_hk[n] by partition id
+ * j = floor(hk * num_partitions / 2^64) into d_sorted[n] (keys of partition j
+ * contiguous, partitions ascending, order inside a partition unspecified), and
+ * the partition starts d_start[num_partitions + 1].  Allocates its scratch. */
+phobic_status phobic_partition_sort(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions,
+                                    uint64_t* d_sorted, uint64_t* d_start, phobic_stream_t stream);
+
+/* Writes the 2049-entry fixed-point bucket table (Appendix C) to h_table. */
+phobic_status phobic_bucket_table(double lambda, double alpha, uint32_t partition_size, uint64_t* h_table);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHOBIC_H */

@@ -1,0 +1,117 @@
+// K8: query.  For each key (Section 4, "Hash Function", and Section 4.1):
+//   hk = master hash; j = partition; T_j and T_{j+1} decoded from the offsets
+//   stored as differences to their expectation; m = T_{j+1} - T_j;
+//   b = bucket of hk; p = pilot of bucket b in partition j (interleaved
+//   Compact or Dictionary column b, entry j);
+//   additive: local = (h(x, floor(p/m)) + p) mod m;  XOR: local = h(x xor h(p));
+//   g = T_j + local, remapped through Elias-Fano when g >= n.
+// Keys are read and results written coalesced (two keys per thread through
+// 16-byte accesses when aligned); the structure (offsets, column metadata,
+// packed pilots, remap) is a few tens of MB and stays L2-resident, read through
+// the read-only path.
+#include "phobic_dev.cuh"
+#include "phobic_kernels.cuh"
+
+namespace phobic {
+
+namespace {
+
+constexpr uint64_t kMeta = (1ull << 56) - 1;
+
+__device__ __forceinline__ uint64_t expectation(uint64_t j, uint64_t Q) {
+    uint64_t lo = j * Q, hi = __umul64hi(j, Q);
+    return (hi << 32) | (lo >> 32);
+}
+
+__device__ __forceinline__ uint64_t offset_of(const QueryView& v, uint64_t j) {
+    return expectation(j, v.off_Q) + (uint64_t)v.off_dmin + read_bits(v.off_words, j * v.off_w, v.off_w);
+}
+
+// i-th value of the Elias-Fano sequence
+__device__ __forceinline__ uint64_t ef_access(const QueryView& v, uint64_t i) {
+    uint64_t pos = __ldg(v.ef_samples + (i >> 6));
+    uint32_t need = (uint32_t)(i & 63);  // ones to pass after the sampled one
+    uint64_t wi = pos >> 6;
+    uint64_t w = __ldg(v.ef_high + wi) & (~0ull << (pos & 63));
+    for (;;) {
+        uint32_t c = __popcll(w);
+        if (need < c) break;
+        need -= c;
+        w = __ldg(v.ef_high + ++wi);
+    }
+    for (uint32_t t = 0; t < need; t++) w &= w - 1;
+    uint64_t one = wi * 64 + (__ffsll((long long)w) - 1);
+    uint64_t low = read_bits(v.ef_low, i * v.ef_l, v.ef_l);
+    return ((one - i) << v.ef_l) | low;
+}
+
+__device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key) {
+    const uint64_t hk = key_hash(key, v.kseed);
+    const uint64_t j = partition_of(hk, v.NP);
+    const uint64_t Tj = offset_of(v, j);
+    const uint32_t m = (uint32_t)(offset_of(v, j + 1) - Tj);
+    if (m == 0) return 0;  // only a key outside the set can land in an empty partition
+    const uint32_t b = bucket_of(bucket_hash(hk), v.table, v.B);
+    uint32_t p;
+    if (v.encoder == 0) {
+        uint64_t meta = __ldg(v.col_meta + b);
+        uint32_t w = (uint32_t)(meta >> 56);
+        p = (uint32_t)read_bits(v.pil_words, (meta & kMeta) + j * w, w);
+    } else {
+        uint64_t rm = __ldg(v.col_meta + 2 * b), dm = __ldg(v.col_meta + 2 * b + 1);
+        uint32_t rw = (uint32_t)(rm >> 56), dw = (uint32_t)(dm >> 56);
+        uint64_t r = read_bits(v.pil_words, (rm & kMeta) + j * rw, rw);
+        p = (uint32_t)read_bits(v.dict_words, (dm & kMeta) + r * dw, dw);
+    }
+    uint32_t local;
+    if (v.pilot_mode == 0) {
+        uint32_t s = p / m;
+        uint32_t d = p - s * m;
+        local = position_hash(hk, pilot_seed(s), m) + d;
+        if (local >= m) local -= m;
+    } else {
+        local = position_hash(hk, pilot_seed(p), m);
+    }
+    uint64_t g = Tj + local;
+    if (g >= v.n) g = ef_access(v, g - v.n);
+    return g;
+}
+
+__global__ void __launch_bounds__(256) k_query(const QueryView v, const uint64_t* __restrict__ keys,
+                                               uint64_t* __restrict__ out, uint64_t m) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    if (vec) {
+        const uint64_t pairs = m >> 1;
+        const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(keys);
+        ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out);
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < pairs; i += stride) {
+            ulonglong2 k = __ldcs(k2 + i);
+            ulonglong2 r;
+            r.x = query_one(v, k.x);
+            r.y = query_one(v, k.y);
+            __stcs(o2 + i, r);
+        }
+        if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[m - 1] = query_one(v, keys[m - 1]);
+    } else {
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += stride)
+            out[i] = query_one(v, keys[i]);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_query(const QueryView& v, const uint64_t* keys, uint64_t* out, uint64_t m, cudaStream_t stream) {
+    if (m == 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t want = (m / 2 + 255) / 256;
+    uint64_t cap = (uint64_t)sms * 8;  // 8 resident blocks of 256 threads per SM
+    unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
+    k_query<<<grid, 256, 0, stream>>>(v, keys, out, m);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace phobic

@@ -1,0 +1,536 @@
+// K3 + K4: per-partition bucketing, bucket ordering and pilot search.
+//
+// One warp owns one partition (Section 4.2: one workgroup per partition; the
+// search runs in shared memory).  For each partition:
+//   1. Load the partition's master hashes.  Compute every key's bucket with the
+//      tabulated gamma (Section 3.1, Appendix C), and counting-sort the keys by
+//      bucket in shared memory.
+//   2. Order the non-empty buckets by size descending, then by index descending.
+//      Index descending means increasing expected size (Section 1; Section 5,
+//      "Further Remarks").  Equal sizes are split with __match_any_sync, so the
+//      order is deterministic.
+//   3. Place the buckets one after another.  Each bucket takes the smallest pilot
+//      that puts its keys on distinct free slots (Section 4.2: "smallest working
+//      seed").
+//      ADDITIVE mode (Section 4, "Hash Function"): p = s m + d.  For each s the
+//      warp computes h(x, s) once per key.  Equal values among the keys rule
+//      out this s (a shift by d moves them together).  Otherwise d is found by
+//      scanning 32-slot windows of the free-slot bitmap.  The bitmap is stored
+//      twice in a row, so (h + d) mod m reads linearly.  A window is the AND,
+//      over the bucket's keys, of 32 free bits starting at h + 32w.  Lanes
+//      split into groups: each group covers one window and its lanes cover the
+//      keys.  A ballot picks the first window with a set bit, and __ffs picks
+//      its smallest d.  That is the smallest valid d, so p matches a sequential
+//      scan exactly.
+//      XOR mode (PTHash): groups of lanes test consecutive pilots p, one key
+//      per lane.  A slot must be free and unshared within its group.
+//   4. Write the pilots (column-major, i.e. interleaved order) and, when a
+//      global occupancy bitmap is requested (alpha < 1), the partition's taken
+//      slots at bit offset T_j.
+// Bounded work: a bucket that needs s >= s_max, or holds more than 1023 keys,
+// stops its partition with SEARCH_LIMIT.  Equal master hashes inside a bucket
+// (duplicate keys) are detected and reported as DUP_HASH.
+#include "phobic_dev.cuh"
+#include "phobic_kernels.cuh"
+
+namespace phobic {
+
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr int kSizeHist = 1024;  // bucket sizes 1..1023
+
+struct SmemLayout {
+    uint32_t off_hk, off_bend, off_order, off_fw, off_scr, off_aux, total;
+    uint32_t fw_words, scr_words;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(uint32_t cap_n, uint32_t cap_m, uint32_t B) {
+    SmemLayout L;
+    uint32_t o = 0;
+    L.off_hk = o;
+    o += ((cap_n + 1) & ~1u) * 8;
+    L.off_bend = o;
+    o += (B + 1) * 4;
+    L.off_order = o;
+    o += B * 4;
+    L.fw_words = (2 * cap_m + 64) / 32 + 2;
+    L.off_fw = o;
+    o += L.fw_words * 4;
+    L.scr_words = (cap_m + 31) / 32 + 1;
+    L.off_scr = o;
+    o += L.scr_words * 4;
+    o = (o + 7) & ~7u;
+    L.off_aux = o;  // size histogram (u16[1024]) / h buffer of large buckets (u16[1024])
+    o += kSizeHist * 2;
+    L.total = (o + 15) & ~15u;
+    return L;
+}
+
+__device__ __forceinline__ uint32_t pow2ceil(uint32_t k) { return k <= 1 ? 1u : 1u << (32 - __clz(k - 1)); }
+
+// 32 free bits starting at bit q of the doubled free bitmap
+__device__ __forceinline__ uint32_t window32(const uint32_t* fw, uint32_t q) {
+    return __funnelshift_r(fw[q >> 5], fw[(q >> 5) + 1], q & 31);
+}
+
+__device__ __forceinline__ void take_slot(uint32_t* fw, uint32_t pos, uint32_t m) {
+    atomicAnd(&fw[pos >> 5], ~(1u << (pos & 31)));
+    uint32_t q = pos + m;
+    atomicAnd(&fw[q >> 5], ~(1u << (q & 31)));
+}
+
+// any two equal master hashes among keys[0..k)?
+__device__ bool bucket_has_dup(const uint64_t* keys, uint32_t k, uint32_t lane) {
+    bool dup = false;
+    for (uint32_t i = lane; i < k && !dup; i += 32) {
+        uint64_t x = keys[i];
+        for (uint32_t i2 = i + 1; i2 < k; i2++)
+            if (keys[i2] == x) {
+                dup = true;
+                break;
+            }
+    }
+    return __any_sync(kFull, dup);
+}
+
+__global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemLayout L = smem_layout(a.cap_n, a.cap_m, a.B);
+    uint64_t* hk = reinterpret_cast<uint64_t*>(smem + L.off_hk);
+    uint32_t* bend = reinterpret_cast<uint32_t*>(smem + L.off_bend);
+    uint32_t* order = reinterpret_cast<uint32_t*>(smem + L.off_order);
+    uint32_t* fw = reinterpret_cast<uint32_t*>(smem + L.off_fw);
+    uint32_t* scr = reinterpret_cast<uint32_t*>(smem + L.off_scr);
+    uint16_t* aux = reinterpret_cast<uint16_t*>(smem + L.off_aux);
+
+    const uint32_t lane = threadIdx.x;
+    const uint64_t j = blockIdx.x;
+    const uint64_t s0 = a.start[j];
+    const uint32_t nj = (uint32_t)(a.start[j + 1] - s0);
+    const uint64_t Tj = a.T[j];
+    const uint32_t m = (uint32_t)(a.T[j + 1] - Tj);
+    const uint32_t B = a.B;
+    if (nj == 0) return;
+
+    // ---- init: counts, doubled free bitmap, scratch, size histogram
+    for (uint32_t b = lane; b <= B; b += 32) bend[b] = 0;
+    const uint32_t fwn = (2 * m + 64) / 32 + 2;
+    for (uint32_t w = lane; w < fwn; w += 32) {
+        uint32_t lo = w * 32, v;
+        if (lo + 32 <= 2 * m)
+            v = kFull;
+        else if (lo >= 2 * m)
+            v = 0;
+        else
+            v = (1u << (2 * m - lo)) - 1;
+        fw[w] = v;
+    }
+    for (uint32_t w = lane; w < (m + 31) / 32 + 1; w += 32) scr[w] = 0;
+    for (uint32_t i = lane; i < kSizeHist; i += 32) aux[i] = 0;
+    __syncwarp();
+
+    // ---- 1. bucket counts, then counting sort of the keys by bucket
+    for (uint32_t i = lane; i < nj; i += 32) {
+        uint64_t x = __ldg(a.sorted + s0 + i);
+        atomicAdd(&bend[bucket_of(bucket_hash(x), a.table, B)], 1u);
+    }
+    __syncwarp();
+    uint32_t local_err = kDevOk;
+    {
+        uint32_t carry = 0;
+        for (uint32_t b0 = 0; b0 < B; b0 += 32) {
+            uint32_t b = b0 + lane;
+            uint32_t c = b < B ? bend[b] : 0;
+            if (c > kMaxBucket) local_err = kDevSearchLimit;
+            uint32_t x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(kFull, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            if (b < B) bend[b] = carry + x - c;  // start of bucket b (cursor)
+            carry += __shfl_sync(kFull, x, 31);
+        }
+    }
+    local_err = __reduce_max_sync(kFull, local_err);
+    __syncwarp();
+    for (uint32_t i = lane; i < nj; i += 32) {
+        uint64_t x = __ldg(a.sorted + s0 + i);
+        uint32_t b = bucket_of(bucket_hash(x), a.table, B);
+        hk[atomicAdd(&bend[b], 1u)] = x;
+    }
+    __syncwarp();
+    // now bend[b] = end of bucket b; start of b = b ? bend[b-1] : 0
+
+    // ---- 2. bucket order: size descending, index descending
+    uint32_t nb = 0;
+    if (local_err == kDevOk) {
+        for (uint32_t b = lane; b < B; b += 32) {
+            uint32_t sz = bend[b] - (b ? bend[b - 1] : 0);
+            if (sz) atomicAdd(reinterpret_cast<unsigned int*>(aux + (sz & ~1u)), 1u << ((sz & 1) * 16));
+        }
+        __syncwarp();
+        // cum[s] = number of buckets larger than s, computed from the top
+        {
+            uint32_t carry = 0;
+            for (int s0i = kSizeHist - 32; s0i >= 0; s0i -= 32) {
+                uint32_t s = (uint32_t)s0i + (31 - lane);  // lane 0 takes the largest size of the chunk
+                uint32_t c = aux[s];
+                uint32_t x = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(kFull, x, o);
+                    if (lane >= (uint32_t)o) x += y;
+                }
+                __syncwarp();
+                aux[s] = (uint16_t)(carry + x - c);
+                carry += __shfl_sync(kFull, x, 31);
+            }
+        }
+        __syncwarp();
+        for (uint32_t c0 = 0; c0 < B; c0 += 32) {
+            uint32_t idx = c0 + lane;
+            uint32_t b = idx < B ? B - 1 - idx : 0;
+            uint32_t sz = idx < B ? bend[b] - (b ? bend[b - 1] : 0) : 0;
+            uint32_t peers = __match_any_sync(kFull, sz);
+            if (sz) {
+                uint32_t base = aux[sz];
+                uint32_t r = __popc(peers & ((1u << lane) - 1));
+                order[base + r] = b;
+            }
+            __syncwarp();
+            if (sz && lane == (uint32_t)(__ffs(peers) - 1)) aux[sz] = (uint16_t)(aux[sz] + __popc(peers));
+            nb += __popc(__ballot_sync(kFull, sz != 0));
+            __syncwarp();
+        }
+    }
+
+    // ---- 3. placement
+    unsigned long long s_tries = 0, steps = 0;
+    const uint32_t nw = (m + 31) / 32;
+    for (uint32_t r = 0; r < nb && local_err == kDevOk; r++) {
+        const uint32_t b = order[r];
+        const uint32_t bs = b ? bend[b - 1] : 0;
+        const uint32_t k = bend[b] - bs;
+        const uint64_t* keys = hk + bs;
+        bool found = false;
+        uint32_t p = 0;
+        if (a.mode == 0) {
+            // ===== additive displacement =====
+            const uint32_t Lw = k <= 32 ? pow2ceil(k) : 32u;  // lanes per window
+            const uint32_t G = 32 / Lw;                        // windows per step
+            const uint32_t g = lane / Lw, rr = lane & (Lw - 1);
+            const uint64_t mykey = lane < k ? keys[lane] : 0;
+            uint32_t h = 0;
+            uint32_t d = 0;
+            uint32_t s = 0;
+            for (; s < a.s_max; s++) {
+                s_tries++;
+                const uint64_t ps = pilot_seed(s);
+                bool coll;
+                if (k <= 32) {
+                    h = lane < k ? position_hash(mykey, ps, m) : (0x80000000u | lane);
+                    uint32_t peers = __match_any_sync(kFull, h);
+                    coll = __any_sync(kFull, __popc(peers) > 1);
+                } else {
+                    uint16_t* hb = aux;
+                    bool c = false;
+                    for (uint32_t i = lane; i < k; i += 32) {
+                        uint32_t hi = position_hash(keys[i], ps, m);
+                        hb[i] = (uint16_t)hi;
+                        uint32_t bit = 1u << (hi & 31);
+                        if (atomicOr(&scr[hi >> 5], bit) & bit) c = true;
+                    }
+                    coll = __any_sync(kFull, c);
+                    for (uint32_t i = lane; i < k; i += 32) scr[hb[i] >> 5] = 0;
+                    __syncwarp();
+                }
+                if (coll) {
+                    if (s == 8 && bucket_has_dup(keys, k, lane)) {
+                        local_err = kDevDupHash;
+                        break;
+                    }
+                    continue;
+                }
+                if (k <= 32) {
+                    const uint32_t hr = __shfl_sync(kFull, h, rr);
+                    for (uint32_t w0 = 0; w0 < nw; w0 += G) {
+                        steps++;
+                        const uint32_t w = w0 + g;
+                        uint32_t acc = 0;
+                        if (w < nw) {
+                            uint32_t valid = (32 * w + 32 <= m) ? kFull : ((1u << (m - 32 * w)) - 1);
+                            acc = rr < k ? (window32(fw, hr + 32 * w) & valid) : valid;
+                        }
+                        for (uint32_t o = 1; o < Lw; o <<= 1) acc &= __shfl_xor_sync(kFull, acc, o);
+                        uint32_t win = __ballot_sync(kFull, acc != 0 && rr == 0);
+                        if (win) {
+                            uint32_t fl = __ffs(win) - 1;
+                            uint32_t av = __shfl_sync(kFull, acc, fl);
+                            d = 32 * (w0 + fl / Lw) + __ffs(av) - 1;
+                            found = true;
+                            break;
+                        }
+                    }
+                } else {
+                    const uint16_t* hb = aux;
+                    for (uint32_t w = 0; w < nw; w++) {
+                        steps++;
+                        uint32_t acc = (32 * w + 32 <= m) ? kFull : ((1u << (m - 32 * w)) - 1);
+                        for (uint32_t i = lane; i < k && acc; i += 32) acc &= window32(fw, (uint32_t)hb[i] + 32 * w);
+                        acc = __reduce_and_sync(kFull, acc);
+                        if (acc) {
+                            d = 32 * w + __ffs(acc) - 1;
+                            found = true;
+                            break;
+                        }
+                    }
+                }
+                if (found) break;
+            }
+            if (local_err != kDevOk) break;
+            if (!found) {
+                local_err = kDevSearchLimit;
+                break;
+            }
+            p = s * m + d;
+            if (k <= 32) {
+                if (lane < k) {
+                    uint32_t pos = h + d;
+                    if (pos >= m) pos -= m;
+                    take_slot(fw, pos, m);
+                }
+            } else {
+                const uint16_t* hb = aux;
+                for (uint32_t i = lane; i < k; i += 32) {
+                    uint32_t pos = (uint32_t)hb[i] + d;
+                    if (pos >= m) pos -= m;
+                    take_slot(fw, pos, m);
+                }
+            }
+        } else {
+            // ===== PTHash XOR form: p = 0, 1, 2, ... =====
+            const uint64_t limit = (uint64_t)a.s_max * m;
+            uint32_t mypos = 0;
+            if (k <= 32) {
+                const uint32_t Lc = pow2ceil(k), G = 32 / Lc;
+                const uint32_t g = lane / Lc, rr = lane & (Lc - 1);
+                const uint64_t mykey = rr < k ? keys[rr] : 0;
+                const uint32_t gmask = Lc == 32 ? kFull : ((1u << Lc) - 1);
+                bool dup_checked = false;
+                for (uint64_t p0 = 0; p0 < limit; p0 += G) {
+                    steps++;
+                    if (!dup_checked && p0 >= 8ull * m) {
+                        dup_checked = true;
+                        if (bucket_has_dup(keys, k, lane)) {
+                            local_err = kDevDupHash;
+                            break;
+                        }
+                    }
+                    const uint64_t pc = p0 + g;
+                    uint32_t pos = 0;
+                    bool ok = true;
+                    uint32_t key = 0xFFFFFFFFu - lane;  // unique, never a slot
+                    if (rr < k && pc < limit) {
+                        pos = position_hash(mykey, pilot_seed(pc), m);
+                        ok = (fw[pos >> 5] >> (pos & 31)) & 1;
+                        key = (g << 20) | pos;
+                    } else if (pc >= limit) {
+                        ok = false;
+                    }
+                    uint32_t peers = __match_any_sync(kFull, key);
+                    ok = ok && __popc(peers) == 1;
+                    uint32_t bad = __ballot_sync(kFull, !ok);
+                    bool gok = ((bad >> (g * Lc)) & gmask) == 0;
+                    uint32_t win = __ballot_sync(kFull, gok && rr == 0);
+                    if (win) {
+                        uint32_t gi = (__ffs(win) - 1) / Lc;
+                        p = (uint32_t)(p0 + gi);
+                        mypos = __shfl_sync(kFull, pos, (lane & (Lc - 1)) + gi * Lc);
+                        found = true;
+                        break;
+                    }
+                }
+                if (local_err != kDevOk) break;
+                if (!found) {
+                    local_err = kDevSearchLimit;
+                    break;
+                }
+                if (lane < k) take_slot(fw, mypos, m);
+            } else {
+                uint16_t* hb = aux;
+                bool dup_checked = false;
+                for (uint64_t pc = 0; pc < limit; pc++) {
+                    steps++;
+                    if (!dup_checked && pc >= 8ull * m) {
+                        dup_checked = true;
+                        if (bucket_has_dup(keys, k, lane)) {
+                            local_err = kDevDupHash;
+                            break;
+                        }
+                    }
+                    const uint64_t ps = pilot_seed(pc);
+                    bool bad = false;
+                    for (uint32_t i = lane; i < k; i += 32) {
+                        uint32_t pos = position_hash(keys[i], ps, m);
+                        hb[i] = (uint16_t)pos;
+                        uint32_t bit = 1u << (pos & 31);
+                        if (!((fw[pos >> 5] >> (pos & 31)) & 1)) bad = true;
+                        if (atomicOr(&scr[pos >> 5], bit) & bit) bad = true;
+                    }
+                    bool anybad = __any_sync(kFull, bad);
+                    for (uint32_t i = lane; i < k; i += 32) scr[hb[i] >> 5] = 0;
+                    __syncwarp();
+                    if (!anybad) {
+                        p = (uint32_t)pc;
+                        found = true;
+                        break;
+                    }
+                }
+                if (local_err != kDevOk) break;
+                if (!found) {
+                    local_err = kDevSearchLimit;
+                    break;
+                }
+                for (uint32_t i = lane; i < k; i += 32) take_slot(fw, hb[i], m);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) a.pilots[(uint64_t)b * a.np + j] = p;
+    }
+
+    if (local_err != kDevOk) {
+        // a duplicate anywhere in the partition takes precedence over other errors
+        if (local_err != kDevDupHash) {
+            for (uint32_t b = 0; b < B; b++) {
+                uint32_t bs = b ? bend[b - 1] : 0, k = bend[b] - bs;
+                if (k > 1 && bucket_has_dup(hk + bs, k, lane)) {
+                    local_err = kDevDupHash;
+                    break;
+                }
+            }
+        }
+        if (lane == 0) atomicMax(a.status, local_err);
+        return;
+    }
+    if (a.work && lane == 0) {
+        atomicAdd(a.work, s_tries);
+        atomicAdd(a.work + 1, steps);
+    }
+
+    // ---- 4. taken slots into the global occupancy bitmap at bit offset T_j
+    if (a.taken_bits && m) {
+        const uint64_t o0 = Tj >> 5, o1 = (Tj + m - 1) >> 5;
+        for (uint64_t o = o0 + lane; o <= o1; o += 32) {
+            int64_t t0 = (int64_t)(o * 32) - (int64_t)Tj;
+            uint32_t v;
+            if (t0 >= 0) {
+                uint32_t tt = (uint32_t)t0;
+                v = ~window32(fw, tt);
+                if (tt + 32 > m) v &= (m - tt >= 32) ? kFull : ((1u << (m - tt)) - 1);
+            } else {
+                uint32_t sh = (uint32_t)(-t0);
+                v = ~(fw[0] << sh) & ~((1u << sh) - 1);
+                if (m + sh < 32) v &= (1u << (m + sh)) - 1;
+            }
+            if (v) atomicOr(a.taken_bits + o, v);
+        }
+    }
+}
+
+// one block: n_j from the partition starts, m_j, exclusive scan into T, maxima
+__global__ void __launch_bounds__(1024) k_sizes(const uint64_t* __restrict__ start, uint64_t np, double alpha,
+                                                uint64_t* __restrict__ T, uint64_t* __restrict__ stats) {
+    __shared__ unsigned long long warp_sums[32];
+    __shared__ unsigned long long carry_s;
+    __shared__ unsigned long long maxn_s, maxm_s;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        carry_s = 0;
+        maxn_s = 0;
+        maxm_s = 0;
+    }
+    __syncthreads();
+    for (uint64_t c0 = 0; c0 < np; c0 += 1024) {
+        uint64_t j = c0 + tid;
+        uint64_t nj = 0, mj = 0;
+        if (j < np) {
+            nj = start[j + 1] - start[j];
+            if (alpha == 1.0) {
+                mj = nj;
+            } else {
+                mj = (uint64_t)ceil((double)nj / alpha);
+                if (mj < nj) mj = nj;
+            }
+        }
+        unsigned long long x = mj;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(kFull, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        unsigned long long mn = nj, mm = mj;
+        for (int o = 16; o; o >>= 1) {
+            mn = max(mn, __shfl_xor_sync(kFull, mn, o));
+            mm = max(mm, __shfl_xor_sync(kFull, mm, o));
+        }
+        if (lane == 0) {
+            atomicMax(&maxn_s, mn);
+            atomicMax(&maxm_s, mm);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long s = warp_sums[lane], z = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long y = __shfl_up_sync(kFull, z, o);
+                if (lane >= (uint32_t)o) z += y;
+            }
+            warp_sums[lane] = z - s;
+        }
+        __syncthreads();
+        unsigned long long carry = carry_s;
+        if (j < np) T[j] = carry + warp_sums[warp] + x - mj;
+        __syncthreads();
+        if (tid == 1023) carry_s = carry + warp_sums[31] + x;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        T[np] = carry_s;
+        stats[0] = carry_s;
+        stats[1] = maxn_s;
+        stats[2] = maxm_s;
+    }
+}
+
+}  // namespace
+
+size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B) { return smem_layout(cap_n, cap_m, B).total; }
+
+size_t search_smem_limit() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return (size_t)v;
+}
+
+cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream) {
+    size_t smem = search_smem_bytes(a.cap_n, a.cap_m, a.B);
+    cudaError_t e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (a.np > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    k_search<<<(unsigned)a.np, 32, smem, stream>>>(a);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sizes(const uint64_t* start, uint64_t np, double alpha, uint64_t* T, uint64_t* stats,
+                         cudaStream_t stream) {
+    k_sizes<<<1, 1024, 0, stream>>>(start, np, alpha, T, stats);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace phobic

@@ -1,0 +1,320 @@
+// K1 + K2: master hashing fused into an LSD onesweep radix sort by partition id.
+//
+// Section 4 splits the keys into partitions of expected size P.  Partition
+// j = floor(hk * N_P / 2^64) is a monotone function of the 64-bit master hash
+// hk.  Sorting by j therefore needs only ceil(log2 N_P) bits.  The sort is a
+// least-significant-digit radix sort in the onesweep style (Adinets & Merrill
+// 2022): one upfront pass computes every digit histogram, then each digit pass
+// ranks a tile in shared memory.  It finds the tile's global offset by decoupled
+// look-back over its predecessors and writes the tile out in digit order.  When
+// the input is raw 64-bit keys, the upfront pass and the first digit pass hash
+// them on the fly, so no separate array of hashes is written.
+#include "phobic_dev.cuh"
+#include "phobic_kernels.cuh"
+
+namespace phobic {
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kItems = 12;
+constexpr int kTile = kThreads * kItems;  // 6144 keys per tile
+constexpr int kWarps = kThreads / 32;
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPre = 2ull << 62;
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint64_t load_hk(const uint64_t* in, uint64_t i, uint64_t kseed, int hash_input) {
+    uint64_t v = __ldg(in + i);
+    return hash_input ? key_hash(v, kseed) : v;
+}
+
+__global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ in, uint64_t n, uint64_t np,
+                                                   uint64_t kseed, int hash_input, uint32_t passes,
+                                                   uint32_t bits, unsigned long long* __restrict__ hist) {
+    extern __shared__ uint32_t sh_hist[];
+    const uint32_t R = 1u << bits, mask = R - 1;
+    for (uint32_t i = threadIdx.x; i < passes * R; i += blockDim.x) sh_hist[i] = 0;
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t j = partition_of(load_hk(in, i, kseed, hash_input), np);
+        for (uint32_t p = 0; p < passes; p++) atomicAdd(&sh_hist[p * R + ((j >> (p * bits)) & mask)], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < passes * R; i += blockDim.x)
+        if (sh_hist[i]) atomicAdd(hist + i, (unsigned long long)sh_hist[i]);
+}
+
+// exclusive scan of each pass's digit histogram (one block per pass)
+__global__ void k_sort_hist_scan(unsigned long long* hist, uint32_t bits) {
+    const uint32_t R = 1u << bits;
+    if (threadIdx.x == 0) {
+        unsigned long long* h = hist + (uint64_t)blockIdx.x * R;
+        unsigned long long run = 0;
+        for (uint32_t d = 0; d < R; d++) {
+            unsigned long long c = h[d];
+            h[d] = run;
+            run += c;
+        }
+    }
+}
+
+struct PassArgs {
+    const uint64_t* in;
+    uint64_t* out;
+    uint64_t n, np, kseed;
+    int hash_input;
+    uint32_t shift, bits;
+    const unsigned long long* digit_base; // R entries: exclusive scan of the pass histogram
+    unsigned long long* status;            // [tiles x R]: flag | value
+    uint32_t* tile_counter;
+    uint32_t* error;
+};
+
+__global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t R = 1u << a.bits, mask = R - 1;
+    uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);                      // kTile
+    uint32_t* wh = reinterpret_cast<uint32_t*>(keys_s + kTile);                // kWarps x R
+    uint32_t* tile_start = wh + kWarps * R;                                    // R
+    unsigned long long* gbase = reinterpret_cast<unsigned long long*>(tile_start + R + (R & 1)); // R
+    __shared__ uint32_t tile_s;
+
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) tile_s = atomicAdd(a.tile_counter, 1u);
+    for (uint32_t i = tid; i < kWarps * R; i += kThreads) wh[i] = 0;
+    __syncthreads();
+    const uint64_t tile = tile_s;
+    const uint64_t base = tile * kTile;
+    const uint64_t wbase = base + (uint64_t)warp * 32 * kItems;
+
+    // blocked load: warp w owns keys [wbase, wbase + 32*kItems), coalesced per item
+    uint64_t k[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; i++) {
+        uint64_t idx = wbase + (uint64_t)i * 32 + lane;
+        k[i] = idx < a.n ? load_hk(a.in, idx, a.kseed, a.hash_input) : 0;
+    }
+    // stable warp-level ranking (order = warp, item, lane); dr = digit << 16 | rank
+    uint32_t dr[kItems];
+    const uint32_t lt = (1u << lane) - 1;
+    uint32_t* myh = wh + warp * R;
+#pragma unroll
+    for (int i = 0; i < kItems; i++) {
+        const bool valid = wbase + (uint64_t)i * 32 + lane < a.n;
+        const uint32_t dg = valid ? (uint32_t)((partition_of(k[i], a.np) >> a.shift) & mask) : R;  // R: not placed
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
+        uint32_t before = dg < R ? myh[dg] : 0;
+        __syncwarp();
+        if (dg < R && lane == (uint32_t)(__ffs(peers) - 1)) myh[dg] = before + __popc(peers);
+        __syncwarp();
+        dr[i] = (dg << 16) | (before + __popc(peers & lt));
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, tile totals
+    for (uint32_t d = tid; d < R; d += kThreads) {
+        uint32_t run = 0;
+        for (uint32_t w = 0; w < kWarps; w++) {
+            uint32_t c = wh[w * R + d];
+            wh[w * R + d] = run;
+            run += c;
+        }
+        tile_start[d] = run;  // tile count for now
+    }
+    __syncthreads();
+    // decoupled look-back per digit
+    for (uint32_t d = tid; d < R; d += kThreads) {
+        uint64_t cnt = tile_start[d];
+        volatile unsigned long long* st = a.status;
+        uint64_t excl = 0;
+        if (tile == 0) {
+            st[d] = kFlagPre | cnt;
+        } else {
+            st[tile * R + d] = kFlagAgg | cnt;
+            int64_t t = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            while (t >= 0) {
+                unsigned long long v = st[(uint64_t)t * R + d];
+                uint64_t flag = v & ~kValMask;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicMax(a.error, kDevTimeout);
+                        break;
+                    }
+                    if (spins > 32) __nanosleep(64);
+                    continue;
+                }
+                excl += v & kValMask;
+                if (flag == kFlagPre) break;
+                t--;
+            }
+            st[tile * R + d] = kFlagPre | (excl + cnt);
+        }
+        gbase[d] = a.digit_base[d] + excl;
+    }
+    __syncthreads();
+    // exclusive scan of the tile counts over digits (single warp, R <= 512)
+    if (warp == 0) {
+        uint32_t carry = 0;
+        for (uint32_t d0 = 0; d0 < R; d0 += 32) {
+            uint32_t d = d0 + lane;
+            uint32_t c = d < R ? tile_start[d] : 0;
+            uint32_t x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            if (d < R) tile_start[d] = carry + x - c;
+            carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+        }
+    }
+    __syncthreads();
+    for (uint32_t d = tid; d < R; d += kThreads) gbase[d] -= tile_start[d];
+    // scatter into shared memory in digit order
+#pragma unroll
+    for (int i = 0; i < kItems; i++) {
+        uint32_t d = dr[i] >> 16;
+        if (d < R) keys_s[tile_start[d] + wh[warp * R + d] + (dr[i] & 0xFFFFu)] = k[i];
+    }
+    __syncthreads();
+    // coalesced write-out: consecutive slots of one digit go to consecutive addresses
+    uint64_t valid = a.n - base < (uint64_t)kTile ? a.n - base : (uint64_t)kTile;
+    for (uint32_t i = tid; i < valid; i += kThreads) {
+        uint64_t v = keys_s[i];
+        uint32_t d = (uint32_t)((partition_of(v, a.np) >> a.shift) & mask);
+        uint64_t dst = gbase[d] + i;
+        if (dst < a.n) a.out[dst] = v;  // only a timed-out look-back could leave the range
+    }
+}
+
+__global__ void k_hash_copy(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t n, uint64_t kseed,
+                            int hash_input) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = load_hk(in, i, kseed, hash_input);
+}
+
+// start[j] = first index of partition j in the sorted array (binary search)
+__global__ void k_partition_starts(const uint64_t* __restrict__ sorted, uint64_t n, uint64_t np,
+                                   uint64_t* __restrict__ start) {
+    uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (j > np) return;
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint64_t mid = (lo + hi) >> 1;
+        if (partition_of(__ldg(sorted + mid), np) < j)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    start[j] = lo;
+}
+
+}  // namespace
+
+size_t sort_pass_smem(uint32_t bits) {
+    uint32_t R = 1u << bits;
+    return (size_t)kTile * 8 + (size_t)kWarps * R * 4 + (size_t)(R + (R & 1)) * 4 + (size_t)R * 8;
+}
+
+void sort_plan(uint64_t np, uint32_t* passes, uint32_t* bits) {
+    uint32_t total = np > 1 ? bitlen64(np - 1) : 0;
+    uint32_t p = (total + 8) / 9;  // at most 9 bits (512 digits) per pass
+    *passes = p;
+    *bits = p ? (total + p - 1) / p : 0;
+}
+
+size_t sort_scratch_bytes(uint64_t n, uint64_t np) {
+    uint32_t passes, bits;
+    sort_plan(np, &passes, &bits);
+    uint64_t tiles = (n + kTile - 1) / kTile;
+    uint32_t R = 1u << bits;
+    size_t s = 0;
+    s += (size_t)n * 8;                              // ping-pong buffer
+    s += (size_t)passes * R * 8 + 64;                // histograms
+    s += (size_t)tiles * R * 8 + 64;                 // look-back status
+    s += 64 * 4;                                     // tile counters + error
+    return s;
+}
+
+cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t kseed, uint64_t n, uint64_t np,
+                                  uint64_t* sorted, uint64_t* start, void* scratch, uint32_t* d_error,
+                                  cudaStream_t stream) {
+    uint32_t passes, bits;
+    sort_plan(np, &passes, &bits);
+    const uint32_t R = 1u << bits;
+    const uint64_t tiles = (n + kTile - 1) / kTile;
+    unsigned char* p = static_cast<unsigned char*>(scratch);
+    uint64_t* alt = reinterpret_cast<uint64_t*>(p);
+    p += (size_t)n * 8;
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(p);
+    p += (size_t)passes * R * 8 + 64;
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(p);
+    p += (size_t)tiles * R * 8 + 64;
+    uint32_t* counters = reinterpret_cast<uint32_t*>(p);
+    cudaError_t e;
+
+    if (passes == 0) {
+        k_hash_copy<<<(unsigned)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, stream>>>(
+            in, sorted, n, kseed, hash_input);
+        note_launches(1);
+    } else {
+        if ((e = cudaMemsetAsync(hist, 0, (size_t)passes * R * 8, stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(counters, 0, 64 * 4, stream)) != cudaSuccess) return e;
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        uint64_t hblocks = (n + 256 * 16 - 1) / (256 * 16);
+        if (hblocks > (uint64_t)sms * 8) hblocks = (uint64_t)sms * 8;
+        if (hblocks == 0) hblocks = 1;
+        k_sort_hist<<<(unsigned)hblocks, 256, passes * R * 4, stream>>>(in, n, np, kseed, hash_input, passes, bits,
+                                                                        hist);
+        note_launches(1);
+        k_sort_hist_scan<<<passes, 32, 0, stream>>>(hist, bits);
+        note_launches(1);
+        size_t smem = sort_pass_smem(bits);
+        if ((e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        const uint64_t* src = in;
+        int hash_now = hash_input;
+        // ping-pong so that the last pass lands in `sorted`
+        uint64_t* dst = (passes & 1) ? sorted : alt;
+        for (uint32_t ps = 0; ps < passes; ps++) {
+            if ((e = cudaMemsetAsync(status, 0, (size_t)tiles * R * 8, stream)) != cudaSuccess) return e;
+            PassArgs a;
+            a.in = src;
+            a.out = dst;
+            a.n = n;
+            a.np = np;
+            a.kseed = kseed;
+            a.hash_input = hash_now;
+            a.shift = ps * bits;
+            a.bits = bits;
+            a.digit_base = hist + (uint64_t)ps * R;
+            a.status = status;
+            a.tile_counter = counters + ps;
+            a.error = d_error;
+            k_sort_pass<<<(unsigned)tiles, kThreads, smem, stream>>>(a);
+            note_launches(1);
+            src = dst;
+            hash_now = 0;
+            dst = (dst == sorted) ? alt : sorted;
+        }
+    }
+    k_partition_starts<<<(unsigned)((np + 1 + 255) / 256), 256, 0, stream>>>(sorted, n, np, start);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hash_u64(const uint64_t* keys, uint64_t n, uint64_t kseed, uint64_t* out, cudaStream_t stream) {
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 16384) blocks = 16384;
+    if (blocks == 0) return cudaSuccess;
+    k_hash_copy<<<(unsigned)blocks, 256, 0, stream>>>(keys, out, n, kseed, 1);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace phobic

@@ -1,0 +1,116 @@
+// Device-side building blocks shared by the libphobic kernels.
+//
+// The hash functions restate this library's fixed spec for the quantities the
+// paper leaves open: the master hash (Section 5 names xxHash; 64-bit keys use a
+// bijective finaliser), the bucket hash, and the pilot hash h(x, s) of Section 4
+// ("Hash Function").
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace phobic {
+
+// spec constants
+constexpr uint64_t kSeedMix = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kBucketMix = 0x5851F42D4C957F2Dull;
+constexpr uint64_t kPilotMix = 0x2545F4914F6CDD1Dull;
+constexpr int kTablePoints = 2048;   // Appendix C: gamma tabulated at 2048 points
+constexpr uint32_t kMaxBucket = 1023; // larger buckets are rejected as unplaceable
+constexpr uint32_t kMaxPartitionSize = 16384;
+
+// status codes written by kernels into a device status word (priority order:
+// a larger code wins when several partitions fail)
+constexpr uint32_t kDevOk = 0;
+constexpr uint32_t kDevTimeout = 1;
+constexpr uint32_t kDevSearchLimit = 2;
+constexpr uint32_t kDevDupHash = 3;
+
+// SplitMix64 output function (Steele, Lea, Flood 2014), a 64-bit bijection.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// floor(a * b / 2^64)
+__device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+
+// floor(h * m / 2^64) for m < 2^32: fastrange onto [0, m)
+__device__ __forceinline__ uint32_t fastrange32(uint64_t h, uint32_t m) {
+    return (uint32_t)__umul64hi(h, (uint64_t)m);
+}
+
+__host__ __device__ __forceinline__ uint64_t key_seed(uint64_t seed) { return mix64(seed ^ kSeedMix); }
+__host__ __device__ __forceinline__ uint64_t key_hash(uint64_t key, uint64_t kseed) { return mix64(key ^ kseed); }
+__device__ __forceinline__ uint64_t bucket_hash(uint64_t hk) { return mix64(hk ^ kBucketMix); }
+__device__ __forceinline__ uint64_t pilot_seed(uint64_t s) { return mix64(s ^ kPilotMix); }
+__device__ __forceinline__ uint32_t position_hash(uint64_t hk, uint64_t ps, uint32_t m) {
+    return fastrange32(mix64(hk ^ ps), m);
+}
+
+// partition of a master hash
+__device__ __forceinline__ uint64_t partition_of(uint64_t hk, uint64_t np) { return mulhi64(hk, np); }
+
+// Section 3.1 / Appendix C: bucket of normalised hash x from the fixed-point
+// table of gamma, by linear interpolation between table[k] and table[k+1].
+__device__ __forceinline__ uint32_t bucket_of(uint64_t x, const uint64_t* __restrict__ table, uint32_t B) {
+    uint32_t k = (uint32_t)(x >> 53);
+    uint64_t f = (x >> 21) & 0xFFFFFFFFull;
+    uint64_t lo = __ldg(table + k), hi = __ldg(table + k + 1);
+    uint64_t v = lo + (((hi - lo) * f) >> 32);
+    uint64_t b = (v * (uint64_t)B) >> 32;
+    return b > B - 1 ? B - 1 : (uint32_t)b;
+}
+
+// number of bits of v (0 for 0)
+__host__ __device__ __forceinline__ uint32_t bitlen64(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return 64 - __clzll((long long)v);
+#else
+    return v ? 64 - __builtin_clzll(v) : 0;
+#endif
+}
+
+// Read `w` (<= 64) bits at bit offset `o` of little-endian packed words.  The
+// packed arrays carry one zero word of padding so that reading words o/64 and
+// o/64+1 never leaves the buffer.
+__device__ __forceinline__ uint64_t read_bits(const uint64_t* __restrict__ words, uint64_t o, uint32_t w) {
+    if (w == 0) return 0;
+    uint64_t i = o >> 6;
+    uint32_t sh = (uint32_t)(o & 63);
+    uint64_t lo = __ldg(words + i);
+    uint64_t v = lo >> sh;
+    if (sh + w > 64) v |= __ldg(words + i + 1) << (64 - sh);
+    return w == 64 ? v : (v & ((1ull << w) - 1));
+}
+
+// words needed for `nbits` bits, including one padding word
+__host__ __device__ __forceinline__ uint64_t packed_words(uint64_t nbits) { return (nbits + 63) / 64 + 1; }
+
+// Per-structure view passed by value to the query kernel.
+struct QueryView {
+    uint64_t n, M, NP;
+    uint32_t B;
+    uint32_t encoder;    // 0 IC-C, 1 IC-D
+    uint32_t pilot_mode; // 0 additive, 1 xor
+    uint32_t off_w;
+    uint64_t kseed;      // mix64(seed ^ kSeedMix)
+    uint64_t off_Q;
+    int64_t off_dmin;
+    const uint64_t* table;     // 2049
+    const uint64_t* off_words; // offsets, packed
+    // IC-C: col_meta[b] = base | (width << 56); IC-D: col_meta[2b] = rank base | (rank width << 56),
+    // col_meta[2b+1] = dict base | (dict width << 56)
+    const uint64_t* col_meta;
+    const uint64_t* pil_words;  // IC-C data, or IC-D ranks
+    const uint64_t* dict_words; // IC-D dictionary
+    // Elias-Fano remap of slots >= n
+    uint64_t ef_N;
+    uint32_t ef_l;
+    const uint64_t* ef_low;
+    const uint64_t* ef_high;
+    const uint64_t* ef_samples;
+};
+
+}  // namespace phobic

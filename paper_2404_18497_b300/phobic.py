@@ -1,0 +1,340 @@
+"""Python binding of libphobic (argument marshalling only).
+
+Every function mirrors one C entry point of include/phobic.h under the same
+name.  Device buffers are torch CUDA tensors: 64-bit keys as int64 or uint64
+(bit patterns are passed through unchanged), outputs as int64.  Streams are
+torch.cuda streams; the default is torch's current stream.  All computation
+happens in the library's CUDA kernels: if libphobic.so is missing, importing
+this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libphobic.so")
+
+OK = 0
+STATUS_NAMES = {
+    0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "DUP_HASH", 4: "SEARCH_LIMIT",
+    5: "PARTITION_TOO_LARGE", 6: "CUDA", 7: "TIMEOUT", 8: "FORMAT",
+}
+ENC_IC_C, ENC_IC_D = 0, 1
+PILOT_ADDITIVE, PILOT_XOR = 0, 1
+_ENC = {"IC-C": ENC_IC_C, "IC-D": ENC_IC_D, ENC_IC_C: ENC_IC_C, ENC_IC_D: ENC_IC_D}
+_MODE = {"additive": PILOT_ADDITIVE, "xor": PILOT_XOR, PILOT_ADDITIVE: PILOT_ADDITIVE, PILOT_XOR: PILOT_XOR}
+
+
+class PhobicError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)}")
+        self.code = code
+        self.status = STATUS_NAMES.get(code, str(code))
+
+
+class phobic_params(ctypes.Structure):
+    _fields_ = [
+        ("lambda_", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("partition_size", ctypes.c_uint32),
+        ("encoder", ctypes.c_uint32),
+        ("pilot_mode", ctypes.c_uint32),
+        ("s_max", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64),
+        ("warps_per_partition", ctypes.c_uint32),
+        ("keep_pilots", ctypes.c_uint32),
+        ("record_timings", ctypes.c_uint32),
+    ]
+
+
+class phobic_timings(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in
+                ("sort_ms", "sizes_ms", "search_ms", "encode_ms", "remap_ms", "total_ms")]
+
+
+class phobic_info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64), ("M", ctypes.c_uint64), ("num_partitions", ctypes.c_uint64),
+        ("num_buckets", ctypes.c_uint32), ("partition_size", ctypes.c_uint32),
+        ("lambda_", ctypes.c_double), ("alpha", ctypes.c_double), ("epsilon", ctypes.c_double),
+        ("encoder", ctypes.c_uint32), ("pilot_mode", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+        ("max_partition", ctypes.c_uint64),
+        ("bits_header", ctypes.c_uint64), ("bits_offsets", ctypes.c_uint64), ("bits_pilots", ctypes.c_uint64),
+        ("bits_remap", ctypes.c_uint64), ("bits_total", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+    ]
+
+
+_lib = None
+# (name, restype, argtypes): the C ABI, in header order
+_VP, _U64, _U32, _DBL, _INT = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_int
+_PP = ctypes.POINTER(phobic_params)
+_SIGS = [
+    ("phobic_params_init", None, [_PP]),
+    ("phobic_build", _INT, [_VP, _U64, _DBL, _DBL, _U32, _U64, _VP, ctypes.POINTER(_VP)]),
+    ("phobic_build_ex", _INT, [_VP, _U64, _PP, _VP, ctypes.POINTER(_VP)]),
+    ("phobic_build_host", _INT, [_VP, _U64, _PP, _VP, ctypes.POINTER(_VP)]),
+    ("phobic_query", _INT, [_VP, _VP, _VP, _U64, _VP]),
+    ("phobic_query_host", _INT, [_VP, _VP, _VP, _U64, _VP]),
+    ("phobic_bits_per_key", _DBL, [_VP]),
+    ("phobic_get_info", _INT, [_VP, ctypes.POINTER(phobic_info)]),
+    ("phobic_export", _INT, [_VP, _VP, ctypes.POINTER(ctypes.c_size_t)]),
+    ("phobic_import", _INT, [_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    ("phobic_copy_pilots", _INT, [_VP, _VP, _VP]),
+    ("phobic_get_timings", _INT, [_VP, ctypes.POINTER(phobic_timings)]),
+    ("phobic_kernel_launches", _U64, []),
+    ("phobic_free", None, [_VP]),
+    ("phobic_status_str", ctypes.c_char_p, [_INT]),
+    ("phobic_hash_u64", _INT, [_VP, _U64, _U64, _VP, _VP]),
+    ("phobic_hash_strings", _INT, [_VP, _VP, _U64, _U64, _VP, _VP]),
+    ("phobic_partition_sort", _INT, [_VP, _U64, _U64, _VP, _VP, _VP]),
+    ("phobic_bucket_table", _INT, [_DBL, _DBL, _U32, _VP]),
+]
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libphobic.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libphobic.so is not built ({LIB_PATH}); run python -m paper_2404_18497_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_names():
+    return [s[0] for s in _SIGS]
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise PhobicError(code, what)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev_u64(t: torch.Tensor, what: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype not in (torch.int64, torch.uint64):
+        raise TypeError(f"{what} must be int64 or uint64")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t
+
+
+def make_params(lam=7.0, alpha=1.0, P=2500, seed=0, encoder="IC-C", mode="additive", s_max=0,
+                keep_pilots=False, warps_per_partition=0, record_timings=False) -> phobic_params:
+    p = phobic_params()
+    lib().phobic_params_init(ctypes.byref(p))
+    p.lambda_ = float(lam)
+    p.alpha = float(alpha)
+    p.partition_size = int(P)
+    p.seed = int(seed) & ((1 << 64) - 1)
+    p.encoder = _ENC[encoder]
+    p.pilot_mode = _MODE[mode]
+    if s_max:
+        p.s_max = int(s_max)
+    p.keep_pilots = 1 if keep_pilots else 0
+    p.warps_per_partition = int(warps_per_partition)
+    p.record_timings = 1 if record_timings else 0
+    return p
+
+
+class Handle:
+    """One built MPHF (owns the C handle)."""
+
+    def __init__(self, ptr: int):
+        self._h = ctypes.c_void_p(ptr)
+
+    @property
+    def ptr(self) -> ctypes.c_void_p:
+        if not self._h.value:
+            raise ValueError("handle was freed")
+        return self._h
+
+    def free(self):
+        if self._h.value:
+            lib().phobic_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # conveniences over the entry points below
+    def query(self, keys: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        return phobic_query(self, keys, out, stream)
+
+    def bits_per_key(self) -> float:
+        return phobic_bits_per_key(self)
+
+    def info(self) -> dict:
+        return phobic_get_info(self)
+
+    def export(self) -> bytes:
+        return phobic_export(self)
+
+    def pilots(self, stream=None) -> torch.Tensor:
+        return phobic_copy_pilots(self, stream)
+
+
+# ---------------------------------------------------------------- entry points
+def phobic_build(keys: torch.Tensor, lam=7.0, alpha=1.0, P=2500, seed=0, stream=None) -> Handle:
+    k = _dev_u64(keys, "keys")
+    h = ctypes.c_void_p()
+    _check(lib().phobic_build(k.data_ptr(), k.numel(), float(lam), float(alpha), int(P), int(seed),
+                              _stream(stream), ctypes.byref(h)), "phobic_build")
+    return Handle(h.value)
+
+
+def phobic_build_ex(keys: torch.Tensor, params: phobic_params, stream=None) -> Handle:
+    k = _dev_u64(keys, "keys")
+    h = ctypes.c_void_p()
+    _check(lib().phobic_build_ex(k.data_ptr(), k.numel(), ctypes.byref(params), _stream(stream), ctypes.byref(h)),
+           "phobic_build_ex")
+    return Handle(h.value)
+
+
+def phobic_build_host(keys: np.ndarray, params: phobic_params, stream=None) -> Handle:
+    k = np.ascontiguousarray(keys).view(np.uint64)
+    h = ctypes.c_void_p()
+    _check(lib().phobic_build_host(k.ctypes.data, k.size, ctypes.byref(params), _stream(stream), ctypes.byref(h)),
+           "phobic_build_host")
+    return Handle(h.value)
+
+
+def phobic_query(h: Handle, keys: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    k = _dev_u64(keys, "keys")
+    if out is None:
+        out = torch.empty(k.numel(), dtype=torch.int64, device=k.device)
+    _dev_u64(out, "out")
+    if out.numel() < k.numel():
+        raise ValueError("out is too small")
+    _check(lib().phobic_query(h.ptr, k.data_ptr(), out.data_ptr(), k.numel(), _stream(stream)), "phobic_query")
+    return out
+
+
+def phobic_query_host(h: Handle, keys: np.ndarray, out: Optional[np.ndarray] = None, stream=None) -> np.ndarray:
+    k = np.ascontiguousarray(keys).view(np.uint64)
+    if out is None:
+        out = np.empty(k.size, dtype=np.uint64)
+    _check(lib().phobic_query_host(h.ptr, k.ctypes.data, out.ctypes.data, k.size, _stream(stream)),
+           "phobic_query_host")
+    return out
+
+
+def phobic_bits_per_key(h: Handle) -> float:
+    return float(lib().phobic_bits_per_key(h.ptr))
+
+
+def phobic_get_info(h: Handle) -> dict:
+    i = phobic_info()
+    _check(lib().phobic_get_info(h.ptr, ctypes.byref(i)), "phobic_get_info")
+    return {f[0].rstrip("_"): getattr(i, f[0]) for f in phobic_info._fields_}
+
+
+def phobic_export(h: Handle) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib().phobic_export(h.ptr, None, ctypes.byref(n)), "phobic_export")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().phobic_export(h.ptr, buf, ctypes.byref(n)), "phobic_export")
+    return buf.raw[: n.value]
+
+
+def phobic_import(data: bytes, stream=None) -> Handle:
+    buf = ctypes.create_string_buffer(data, len(data))
+    h = ctypes.c_void_p()
+    _check(lib().phobic_import(buf, len(data), _stream(stream), ctypes.byref(h)), "phobic_import")
+    return Handle(h.value)
+
+
+def phobic_copy_pilots(h: Handle, stream=None) -> torch.Tensor:
+    info = phobic_get_info(h)
+    out = torch.empty((info["num_buckets"], info["num_partitions"]), dtype=torch.int32, device="cuda")
+    _check(lib().phobic_copy_pilots(h.ptr, out.data_ptr(), _stream(stream)), "phobic_copy_pilots")
+    return out
+
+
+def phobic_get_timings(h: Handle) -> dict:
+    t = phobic_timings()
+    _check(lib().phobic_get_timings(h.ptr, ctypes.byref(t)), "phobic_get_timings")
+    return {f[0]: float(getattr(t, f[0])) for f in phobic_timings._fields_}
+
+
+def phobic_kernel_launches() -> int:
+    return int(lib().phobic_kernel_launches())
+
+
+def phobic_hash_u64(keys: torch.Tensor, seed: int = 0, out: Optional[torch.Tensor] = None, stream=None):
+    k = _dev_u64(keys, "keys")
+    if out is None:
+        out = torch.empty_like(k, dtype=torch.int64)
+    _check(lib().phobic_hash_u64(k.data_ptr(), k.numel(), int(seed), out.data_ptr(), _stream(stream)),
+           "phobic_hash_u64")
+    return out
+
+
+def phobic_hash_strings(data: torch.Tensor, offsets: torch.Tensor, seed: int = 0, stream=None) -> torch.Tensor:
+    if data.dtype != torch.uint8 or not data.is_cuda:
+        raise TypeError("data must be a CUDA uint8 tensor")
+    o = _dev_u64(offsets, "offsets")
+    n = o.numel() - 1
+    out = torch.empty(max(n, 0), dtype=torch.int64, device=o.device)
+    _check(lib().phobic_hash_strings(data.data_ptr(), o.data_ptr(), n, int(seed), out.data_ptr(), _stream(stream)),
+           "phobic_hash_strings")
+    return out
+
+
+def phobic_partition_sort(hk: torch.Tensor, num_partitions: int, stream=None):
+    h = _dev_u64(hk, "hk")
+    sorted_ = torch.empty_like(h, dtype=torch.int64)
+    start = torch.empty(num_partitions + 1, dtype=torch.int64, device=h.device)
+    _check(lib().phobic_partition_sort(h.data_ptr(), h.numel(), int(num_partitions), sorted_.data_ptr(),
+                                       start.data_ptr(), _stream(stream)), "phobic_partition_sort")
+    return sorted_, start
+
+
+def phobic_bucket_table(lam: float, alpha: float, P: int) -> np.ndarray:
+    t = np.zeros(2049, dtype=np.uint64)
+    _check(lib().phobic_bucket_table(float(lam), float(alpha), int(P), t.ctypes.data), "phobic_bucket_table")
+    return t
+
+
+def phobic_status_str(code: int) -> str:
+    return lib().phobic_status_str(int(code)).decode()
+
+
+# the structure's arrays, parsed from phobic_export bytes (used by the parity tests)
+HEADER_FIELDS = ["magic", "version", "n", "M", "NP", "B", "P", "lambda_bits", "alpha_bits", "seed", "encoder",
+                 "pilot_mode", "off_w", "off_Q", "off_dmin", "ef_l", "n_off_words", "n_col_meta", "n_pil_words",
+                 "n_dict_words", "n_ef_low", "n_ef_high", "n_ef_samples", "bits_header", "bits_offsets",
+                 "bits_pilots", "bits_remap", "bits_total"]
+ARRAYS = ["off_words", "col_meta", "pil_words", "dict_words", "ef_low", "ef_high", "ef_samples"]
+
+
+def parse_export(data: bytes) -> dict:
+    w = np.frombuffer(data, dtype=np.uint64)
+    hdr = {k: int(w[i]) for i, k in enumerate(HEADER_FIELDS)}
+    hdr["off_dmin"] = int(np.uint64(hdr["off_dmin"]).astype(np.int64))
+    at = len(HEADER_FIELDS)
+    for name in ARRAYS:
+        c = hdr["n_" + name]
+        hdr[name] = w[at: at + c].copy()
+        at += c
+    return hdr

@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path against the CPU oracle, element by element, on the
+same seeded inputs.  Integer work throughout, so everything must be bit-exact:
+master hashes, partition order, pilots, every packed word of the structure,
+bits/key and every query output."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ph():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_18497_b300 import build, phobic
+
+    build.build()
+    phobic.lib()
+    return phobic
+
+
+def _dev(a: np.ndarray) -> torch.Tensor:
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def _host(t: torch.Tensor) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+def _keys(n, seed):
+    from paper_2404_18497_b300 import workloads
+
+    return workloads.distinct_u64(n, seed)
+
+
+def compare_structure(ph, orc_h, h, encoder):
+    """Every array of the exported structure equals the oracle's."""
+    ex = ph.parse_export(ph.phobic_export(h))
+    o = orc_h
+    assert ex["n"] == o.u64("n") and ex["M"] == o.u64("M") and ex["NP"] == o.u64("NP") and ex["B"] == o.u64("B")
+    assert ex["off_w"] == o.u64("off_w") and ex["off_Q"] == o.u64("off_Q") and ex["off_dmin"] == o.u64("off_dmin")
+    assert (ex["off_words"] == o.array("off_words")).all()
+    meta = ex["col_meta"]
+    mask = np.uint64((1 << 56) - 1)
+    if encoder == 0:
+        assert ((meta >> np.uint64(56)).astype(np.uint32) == o.array("col_w")).all()
+        assert ((meta & mask) == o.array("col_base")).all()
+        assert (ex["pil_words"] == o.array("pil_words")).all()
+    else:
+        assert ((meta[0::2] >> np.uint64(56)).astype(np.uint32) == o.array("col_rw")).all()
+        assert ((meta[0::2] & mask) == o.array("col_rbase")).all()
+        assert ((meta[1::2] >> np.uint64(56)).astype(np.uint32) == o.array("col_dw")).all()
+        assert ((meta[1::2] & mask) == o.array("col_dbase")).all()
+        assert (ex["pil_words"] == o.array("rank_words")).all()
+        assert (ex["dict_words"] == o.array("dict_words")).all()
+    if o.u64("ef_N"):
+        assert ex["ef_l"] == o.u64("ef_l")
+        assert (ex["ef_low"] == o.array("ef_low")).all()
+        assert (ex["ef_high"] == o.array("ef_high")).all()
+        assert (ex["ef_samples"] == o.array("ef_samples")).all()
+    else:
+        assert ex["n_ef_low"] == 0 and ex["n_ef_high"] == 0
+    for k in ["bits_header", "bits_offsets", "bits_pilots", "bits_remap", "bits_total"]:
+        assert ex[k] == o.u64(k), k
+
+
+def test_master_hash_parity(ph, orc):
+    keys = _keys(1_000_003, 1)
+    for seed in (0, 1, 0xDEADBEEF):
+        got = _host(ph.phobic_hash_u64(_dev(keys), seed))
+        assert (got == orc.key_hash(keys, seed)).all()
+
+
+def test_string_hash_parity(ph, orc):
+    from paper_2404_18497_b300 import workloads
+
+    data, off = workloads.random_strings(200_001, 5, 0, 70)
+    got = _host(ph.phobic_hash_strings(torch.from_numpy(data).cuda(), _dev(off), 7))
+    assert (got == orc.string_hashes(data, off, 7)).all()
+
+
+@pytest.mark.parametrize("n,P", [(1, 2500), (100, 2500), (2500, 2500), (1_000_000, 2500), (1_234_567, 1000),
+                                 (300_000, 37), (5_000_000, 2500), (65_536, 1), (3_000_000, 24)])
+def test_partition_sort_parity(ph, orc, n, P):
+    """Section 4: keys grouped by partition j = floor(hk N_P / 2^64), partitions
+    ascending.  j is monotone in hk, so sorting each partition's segment must give
+    the globally sorted hashes."""
+    keys = _keys(n, n)
+    hk = orc.key_hash(keys, 3)
+    NP = orc.lib().or_num_partitions(n, P)
+    srt, start = ph.phobic_partition_sort(_dev(hk), NP)
+    srt, start = _host(srt), start.cpu().numpy()
+    sizes = orc.partition_sizes(hk, 7.0, 1.0, P)
+    assert (start == np.concatenate([[0], np.cumsum(sizes)])).all()
+    seg = np.repeat(np.arange(NP), sizes.astype(np.int64))
+    assert np.array_equal(srt[np.lexsort((srt, seg))], np.sort(hk))
+
+
+CASES = [
+    # n, lam, alpha, P, encoder, mode
+    (1, 7.0, 1.0, 2500, 0, 0),
+    (2, 7.0, 0.99, 2500, 1, 0),
+    (100, 3.0, 1.0, 8, 0, 0),
+    (2500, 7.0, 1.0, 2500, 0, 0),
+    (2501, 7.0, 0.99, 2500, 1, 0),
+    (10_007, 5.0, 0.9, 300, 1, 0),
+    (20_000, 4.0, 1.0, 3, 0, 0),
+    (50_000, 6.0, 0.7, 2500, 0, 0),
+    (100_000, 7.0, 1.0, 2500, 0, 1),
+    (100_000, 7.0, 0.99, 2500, 1, 1),
+    (200_000, 8.0, 1.0, 4096, 1, 0),
+    (300_000, 7.0, 0.99, 1024, 0, 0),
+    (1_000_000, 7.0, 1.0, 2500, 0, 0),   # the 1M-key configuration (IC-C, alpha = 1)
+    (1_000_000, 7.0, 0.99, 2500, 1, 0),  # the 1e8-key configuration's parameters at 1M keys
+]
+
+
+@pytest.mark.parametrize("n,lam,alpha,P,enc,mode", CASES)
+def test_build_and_query_parity(ph, orc, n, lam, alpha, P, enc, mode):
+    keys = _keys(n, 17 + n)
+    seed = 11
+    o = orc.Oracle(keys, lam=lam, alpha=alpha, P=P, encoder=enc, mode=mode, seed=seed, threads=0)
+    prm = ph.make_params(lam, alpha, P, seed=seed, encoder=enc, mode=mode, keep_pilots=True)
+    dk = _dev(keys)
+    h = ph.phobic_build_ex(dk, prm)
+    info = h.info()
+    assert info["n"] == n and info["M"] == o.u64("M") and info["num_partitions"] == o.u64("NP")
+    # pilots
+    gp = h.pilots().cpu().numpy().view(np.uint32)
+    assert np.array_equal(gp, o.pilots)
+    # packed structure and space
+    compare_structure(ph, o, h, enc)
+    assert h.bits_per_key() == o.bits_per_key()
+    # every query, positive and negative
+    got = _host(h.query(dk))
+    ref = o.query(keys)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint64))
+    neg = np.random.default_rng(n).integers(0, 2**64, size=min(n, 50_000), dtype=np.uint64)
+    assert np.array_equal(_host(h.query(_dev(neg))), o.query(neg))
+    h.free()
+
+
+def test_query_unaligned_and_odd_lengths(ph, orc):
+    keys = _keys(30_001, 4)
+    o = orc.Oracle(keys, lam=6.0, P=500, threads=0)
+    h = ph.phobic_build(_dev(keys), 6.0, 1.0, 500, 0)
+    buf = torch.zeros(30_002, dtype=torch.int64, device="cuda")
+    buf[1:] = _dev(keys)
+    out = torch.zeros(30_002, dtype=torch.int64, device="cuda")
+    ph.phobic_query(h, buf[1:], out[1:])  # 8-byte but not 16-byte aligned
+    assert np.array_equal(_host(out[1:]), o.query(keys))
+    for m in (0, 1, 2, 3, 31):
+        assert np.array_equal(_host(h.query(_dev(keys[:m]))) if m else np.zeros(0, np.uint64), o.query(keys[:m]))
+
+
+def test_export_import_roundtrip(ph, orc):
+    keys = _keys(123_457, 8)
+    for enc, alpha in [(0, 1.0), (1, 0.95)]:
+        h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, alpha, 2500, encoder=enc))
+        data = ph.phobic_export(h)
+        h2 = ph.phobic_import(data)
+        assert ph.phobic_export(h2) == data
+        assert torch.equal(h.query(_dev(keys)), h2.query(_dev(keys)))
+        assert h2.bits_per_key() == h.bits_per_key()
+        bad = bytearray(data)
+        bad[0] ^= 1
+        with pytest.raises(ph.PhobicError) as e:
+            ph.phobic_import(bytes(bad))
+        assert e.value.status == "FORMAT"
+        with pytest.raises(ph.PhobicError):
+            ph.phobic_import(data[:-8])
+
+
+def test_errors(ph):
+    keys = _keys(10_000, 9)
+    dup = np.concatenate([keys, keys[5:6]])
+    with pytest.raises(ph.PhobicError) as e:
+        ph.phobic_build(_dev(dup), 7.0, 1.0, 2500, 0)
+    assert e.value.status == "DUP_HASH"
+    with pytest.raises(ph.PhobicError) as e:
+        ph.phobic_build_ex(_dev(keys), ph.make_params(12.0, 1.0, 2500, s_max=1))
+    assert e.value.status == "SEARCH_LIMIT"
+    for kw in [dict(lam=0.0), dict(alpha=0.0), dict(alpha=1.5), dict(P=0), dict(P=100_000)]:
+        args = dict(lam=7.0, alpha=1.0, P=2500)
+        args.update(kw)
+        with pytest.raises(ph.PhobicError) as e:
+            ph.phobic_build_ex(_dev(keys), ph.make_params(**args))
+        assert e.value.status == "INVALID_ARG"
+    # the context is still usable after the errors
+    h = ph.phobic_build(_dev(keys), 7.0, 1.0, 2500, 0)
+    assert torch.unique(h.query(_dev(keys))).numel() == keys.size
+
+
+def test_search_limit_matches_oracle(ph, orc):
+    """With a small s_max both sides fail (or succeed) on the same inputs."""
+    keys = _keys(50_000, 10)
+    for s_max in (1, 2, 4, 64):
+        try:
+            orc.Oracle(keys, lam=9.0, P=2500, s_max=s_max, threads=0)
+            o_ok = True
+        except orc.OracleError as e:
+            assert e.code == orc.SEARCH_LIMIT
+            o_ok = False
+        try:
+            ph.phobic_build_ex(_dev(keys), ph.make_params(9.0, 1.0, 2500, s_max=s_max)).free()
+            g_ok = True
+        except ph.PhobicError as e:
+            assert e.status == "SEARCH_LIMIT"
+            g_ok = False
+        assert o_ok == g_ok, s_max
+
+
+def test_host_entry_points(ph, orc):
+    keys = _keys(77_777, 12)
+    prm = ph.make_params(7.0, 0.99, 2500, encoder=1)
+    h1 = ph.phobic_build_host(keys, prm)
+    h2 = ph.phobic_build_ex(_dev(keys), prm)
+    assert ph.phobic_export(h1) == ph.phobic_export(h2)
+    out = ph.phobic_query_host(h1, keys)
+    assert np.array_equal(out, _host(h2.query(_dev(keys))))
