@@ -45,11 +45,11 @@ struct SmemLayout {
     uint32_t fw_words, scr_words;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(uint32_t cap_n, uint32_t cap_m, uint32_t B) {
+__host__ __device__ inline SmemLayout smem_layout(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem) {
     SmemLayout L;
     uint32_t o = 0;
     L.off_hk = o;
-    o += ((cap_n + 1) & ~1u) * 8;
+    if (keys_in_smem) o += ((cap_n + 1) & ~1u) * 8;
     L.off_bend = o;
     o += (B + 1) * 4;
     L.off_order = o;
@@ -80,6 +80,34 @@ __device__ __forceinline__ void take_slot(uint32_t* fw, uint32_t pos, uint32_t m
     atomicAnd(&fw[q >> 5], ~(1u << (q & 31)));
 }
 
+// Lanes per window for a bucket of k keys when `free_slots` of m are free.
+// Expected cost model (uniform across the warp, so no divergence): a candidate
+// displacement is valid with probability q^k, q = free fraction, so about
+// C = min(q^-k, 32 nw) candidates are scanned; with L lanes per window one step
+// covers 1024 / L candidates and costs about min(ceil(k/L), e) window ops plus
+// log2(L) shuffles, where e ~ 1 + ln 32 / -ln q keys empty a window on average.
+// The choice only changes speed: the smallest valid displacement is found for
+// every L.
+__device__ __forceinline__ uint32_t choose_lanes_per_window(uint32_t k, uint32_t free_slots, uint32_t m,
+                                                            uint32_t nw) {
+    const float q = (float)free_slots / (float)m;
+    const float lq = __logf(fmaxf(q, 1e-6f));
+    const float cand = fminf(__expf(-(float)k * lq), 32.0f * (float)nw);
+    const float e = lq < -1e-6f ? 1.0f + 3.4657f / -lq : (float)k;
+    float best = 3.0e38f;
+    uint32_t bestL = 1;
+    for (uint32_t L = 1, lg = 0; L <= 32; L <<= 1, lg++) {
+        const float steps = ceilf(cand * (float)L / 1024.0f);
+        const float ops = fminf(ceilf((float)k / (float)L), e);
+        const float cost = steps * (4.0f * ops + 6.0f * (float)lg + 24.0f);
+        if (cost < best) {
+            best = cost;
+            bestL = L;
+        }
+    }
+    return bestL;
+}
+
 // any two equal master hashes among keys[0..k)?
 __device__ bool bucket_has_dup(const uint64_t* keys, uint32_t k, uint32_t lane) {
     bool dup = false;
@@ -94,10 +122,16 @@ __device__ bool bucket_has_dup(const uint64_t* keys, uint32_t k, uint32_t lane) 
     return __any_sync(kFull, dup);
 }
 
+// kKeysInSmem: the partition's bucket-sorted master hashes live in shared
+// memory (fewest latency, ~8 B/key of shared memory per partition); otherwise
+// they are written to a global scratch region (the same index range as the
+// sorted input, L2-resident while the partition is active).  Each bucket's keys
+// are prefetched into registers one bucket ahead, and shared memory shrinks to
+// the bitmaps and counters, so several times more partitions fit on an SM.
+template <bool kKeysInSmem>
 __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout L = smem_layout(a.cap_n, a.cap_m, a.B);
-    uint64_t* hk = reinterpret_cast<uint64_t*>(smem + L.off_hk);
+    const SmemLayout L = smem_layout(a.cap_n, a.cap_m, a.B, kKeysInSmem);
     uint32_t* bend = reinterpret_cast<uint32_t*>(smem + L.off_bend);
     uint32_t* order = reinterpret_cast<uint32_t*>(smem + L.off_order);
     uint32_t* fw = reinterpret_cast<uint32_t*>(smem + L.off_fw);
@@ -112,6 +146,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
     const uint32_t m = (uint32_t)(a.T[j + 1] - Tj);
     const uint32_t B = a.B;
     if (nj == 0) return;
+    uint64_t* hk = kKeysInSmem ? reinterpret_cast<uint64_t*>(smem + L.off_hk) : a.bkeys + s0;
 
     // ---- init: counts, doubled free bitmap, scratch, size histogram
     for (uint32_t b = lane; b <= B; b += 32) bend[b] = 0;
@@ -209,32 +244,45 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
     // ---- 3. placement
     unsigned long long s_tries = 0, steps = 0;
     const uint32_t nw = (m + 31) / 32;
+    uint32_t placed = 0;  // keys placed so far in this partition
+    // one key per lane of the next bucket, loaded a bucket ahead
+    uint64_t pre = 0;
+    if (nb) {
+        const uint32_t b = order[0], bs = b ? bend[b - 1] : 0;
+        if (lane < bend[b] - bs) pre = hk[bs + lane];
+    }
     for (uint32_t r = 0; r < nb && local_err == kDevOk; r++) {
         const uint32_t b = order[r];
         const uint32_t bs = b ? bend[b - 1] : 0;
         const uint32_t k = bend[b] - bs;
         const uint64_t* keys = hk + bs;
+        const uint64_t mykey = pre;
+        if (r + 1 < nb) {
+            const uint32_t bn = order[r + 1], bsn = bn ? bend[bn - 1] : 0;
+            pre = lane < bend[bn] - bsn ? hk[bsn + lane] : 0;
+        }
         bool found = false;
         uint32_t p = 0;
         if (a.mode == 0) {
             // ===== additive displacement =====
-            const uint32_t Lw = k <= 32 ? pow2ceil(k) : 32u;  // lanes per window
-            const uint32_t G = 32 / Lw;                        // windows per step
-            const uint32_t g = lane / Lw, rr = lane & (Lw - 1);
-            const uint64_t mykey = lane < k ? keys[lane] : 0;
+            uint16_t* hb = aux;  // h(x, s) of the bucket's keys
             uint32_t h = 0;
             uint32_t d = 0;
             uint32_t s = 0;
+            // lanes per window: chosen once per bucket from the current load
+            const uint32_t Lw = choose_lanes_per_window(k, m - placed, m, nw);
+            const uint32_t G = 32 / Lw;  // windows per step
+            const uint32_t g = lane / Lw, rr = lane & (Lw - 1);
             for (; s < a.s_max; s++) {
                 s_tries++;
                 const uint64_t ps = pilot_seed(s);
                 bool coll;
                 if (k <= 32) {
                     h = lane < k ? position_hash(mykey, ps, m) : (0x80000000u | lane);
+                    if (lane < k) hb[lane] = (uint16_t)h;
                     uint32_t peers = __match_any_sync(kFull, h);
                     coll = __any_sync(kFull, __popc(peers) > 1);
                 } else {
-                    uint16_t* hb = aux;
                     bool c = false;
                     for (uint32_t i = lane; i < k; i += 32) {
                         uint32_t hi = position_hash(keys[i], ps, m);
@@ -244,8 +292,8 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                     }
                     coll = __any_sync(kFull, c);
                     for (uint32_t i = lane; i < k; i += 32) scr[hb[i] >> 5] = 0;
-                    __syncwarp();
                 }
+                __syncwarp();
                 if (coll) {
                     if (s == 8 && bucket_has_dup(keys, k, lane)) {
                         local_err = kDevDupHash;
@@ -253,38 +301,31 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                     }
                     continue;
                 }
-                if (k <= 32) {
-                    const uint32_t hr = __shfl_sync(kFull, h, rr);
-                    for (uint32_t w0 = 0; w0 < nw; w0 += G) {
-                        steps++;
-                        const uint32_t w = w0 + g;
-                        uint32_t acc = 0;
-                        if (w < nw) {
-                            uint32_t valid = (32 * w + 32 <= m) ? kFull : ((1u << (m - 32 * w)) - 1);
-                            acc = rr < k ? (window32(fw, hr + 32 * w) & valid) : valid;
+                // G windows of 32 displacements per step; lane rr of group g ANDs
+                // the windows of keys rr, rr + Lw, ... for window w0 + g
+                for (uint32_t w0 = 0; w0 < nw; w0 += G) {
+                    steps++;
+                    const uint32_t w = w0 + g;
+                    uint32_t acc = 0;
+                    if (w < nw) {
+                        acc = (32 * w + 32 <= m) ? kFull : ((1u << (m - 32 * w)) - 1);
+                        const uint32_t q0 = 32 * w;
+                        uint32_t i = rr;
+                        for (; i + Lw < k && acc; i += 2 * Lw) {
+                            uint32_t x0 = window32(fw, (uint32_t)hb[i] + q0);
+                            uint32_t x1 = window32(fw, (uint32_t)hb[i + Lw] + q0);
+                            acc &= x0 & x1;
                         }
-                        for (uint32_t o = 1; o < Lw; o <<= 1) acc &= __shfl_xor_sync(kFull, acc, o);
-                        uint32_t win = __ballot_sync(kFull, acc != 0 && rr == 0);
-                        if (win) {
-                            uint32_t fl = __ffs(win) - 1;
-                            uint32_t av = __shfl_sync(kFull, acc, fl);
-                            d = 32 * (w0 + fl / Lw) + __ffs(av) - 1;
-                            found = true;
-                            break;
-                        }
+                        if (i < k && acc) acc &= window32(fw, (uint32_t)hb[i] + q0);
                     }
-                } else {
-                    const uint16_t* hb = aux;
-                    for (uint32_t w = 0; w < nw; w++) {
-                        steps++;
-                        uint32_t acc = (32 * w + 32 <= m) ? kFull : ((1u << (m - 32 * w)) - 1);
-                        for (uint32_t i = lane; i < k && acc; i += 32) acc &= window32(fw, (uint32_t)hb[i] + 32 * w);
-                        acc = __reduce_and_sync(kFull, acc);
-                        if (acc) {
-                            d = 32 * w + __ffs(acc) - 1;
-                            found = true;
-                            break;
-                        }
+                    for (uint32_t o = 1; o < Lw; o <<= 1) acc &= __shfl_xor_sync(kFull, acc, o);
+                    uint32_t win = __ballot_sync(kFull, acc != 0 && rr == 0);
+                    if (win) {
+                        uint32_t fl = __ffs(win) - 1;
+                        uint32_t av = __shfl_sync(kFull, acc, fl);
+                        d = 32 * (w0 + fl / Lw) + __ffs(av) - 1;
+                        found = true;
+                        break;
                     }
                 }
                 if (found) break;
@@ -295,20 +336,12 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                 break;
             }
             p = s * m + d;
-            if (k <= 32) {
-                if (lane < k) {
-                    uint32_t pos = h + d;
-                    if (pos >= m) pos -= m;
-                    take_slot(fw, pos, m);
-                }
-            } else {
-                const uint16_t* hb = aux;
-                for (uint32_t i = lane; i < k; i += 32) {
-                    uint32_t pos = (uint32_t)hb[i] + d;
-                    if (pos >= m) pos -= m;
-                    take_slot(fw, pos, m);
-                }
+            for (uint32_t i = lane; i < k; i += 32) {
+                uint32_t pos = (uint32_t)hb[i] + d;
+                if (pos >= m) pos -= m;
+                take_slot(fw, pos, m);
             }
+            placed += k;
         } else {
             // ===== PTHash XOR form: p = 0, 1, 2, ... =====
             const uint64_t limit = (uint64_t)a.s_max * m;
@@ -316,7 +349,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
             if (k <= 32) {
                 const uint32_t Lc = pow2ceil(k), G = 32 / Lc;
                 const uint32_t g = lane / Lc, rr = lane & (Lc - 1);
-                const uint64_t mykey = rr < k ? keys[rr] : 0;
+                const uint64_t gkey = rr < k ? keys[rr] : 0;
                 const uint32_t gmask = Lc == 32 ? kFull : ((1u << Lc) - 1);
                 bool dup_checked = false;
                 for (uint64_t p0 = 0; p0 < limit; p0 += G) {
@@ -333,7 +366,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                     bool ok = true;
                     uint32_t key = 0xFFFFFFFFu - lane;  // unique, never a slot
                     if (rr < k && pc < limit) {
-                        pos = position_hash(mykey, pilot_seed(pc), m);
+                        pos = position_hash(gkey, pilot_seed(pc), m);
                         ok = (fw[pos >> 5] >> (pos & 31)) & 1;
                         key = (g << 20) | pos;
                     } else if (pc >= limit) {
@@ -358,6 +391,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                     break;
                 }
                 if (lane < k) take_slot(fw, mypos, m);
+                placed += k;
             } else {
                 uint16_t* hb = aux;
                 bool dup_checked = false;
@@ -394,6 +428,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                     break;
                 }
                 for (uint32_t i = lane; i < k; i += 32) take_slot(fw, hb[i], m);
+                placed += k;
             }
         }
         __syncwarp();
@@ -507,7 +542,9 @@ __global__ void __launch_bounds__(1024) k_sizes(const uint64_t* __restrict__ sta
 
 }  // namespace
 
-size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B) { return smem_layout(cap_n, cap_m, B).total; }
+size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem) {
+    return smem_layout(cap_n, cap_m, B, keys_in_smem).total;
+}
 
 size_t search_smem_limit() {
     int dev = 0, v = 0;
@@ -517,11 +554,13 @@ size_t search_smem_limit() {
 }
 
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream) {
-    size_t smem = search_smem_bytes(a.cap_n, a.cap_m, a.B);
-    cudaError_t e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool in_smem = a.keys_in_smem != 0;
+    size_t smem = search_smem_bytes(a.cap_n, a.cap_m, a.B, in_smem);
+    auto kern = in_smem ? k_search<true> : k_search<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (a.np > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-    k_search<<<(unsigned)a.np, 32, smem, stream>>>(a);
+    kern<<<(unsigned)a.np, 32, smem, stream>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }

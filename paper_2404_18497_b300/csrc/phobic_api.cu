@@ -308,7 +308,11 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
     if (reinterpret_cast<uint32_t*>(hst + 4)[0] == kDevTimeout) return PHOBIC_ERR_TIMEOUT;
     h->info.M = M;
     h->info.max_partition = max_n;
-    if (max_m >= 65536 || search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, B) > search_smem_limit())
+    // keys in shared memory only on request (debug / comparison); default: global scratch
+    const char* ks = std::getenv("PHOBIC_KEYS_IN_SMEM");
+    const bool keys_in_smem = ks && ks[0] == '1';
+    if (max_m >= 65536 || max_n >= (1u << 31) ||
+        search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, B, keys_in_smem) > search_smem_limit())
         return PHOBIC_ERR_PARTITION_TOO_LARGE;
     uint32_t s_max = prm.s_max ? prm.s_max : 65536u;
     if (max_m > 0 && (uint64_t)s_max * max_m > 0xFFFFFFFFull) s_max = (uint32_t)(0xFFFFFFFFull / max_m);
@@ -323,7 +327,11 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
         CK(tmp.alloc(&taken, ((M + 31) / 32 + 1) * 4));
         CK(cudaMemsetAsync(taken, 0, ((M + 31) / 32 + 1) * 4, st));
     }
+    uint64_t* bkeys = nullptr;
+    if (!keys_in_smem) CK(tmp.alloc(&bkeys, n * 8));
     SearchLaunch sl;
+    sl.bkeys = bkeys;
+    sl.keys_in_smem = keys_in_smem ? 1 : 0;
     sl.sorted = sorted;
     sl.start = start;
     sl.T = T;
@@ -342,6 +350,7 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
     CK(launch_search(sl, st));
     CK(ev.mark(4, st));
     tmp.release(sorted);
+    if (bkeys) tmp.release(bkeys);
 
     // ---- K5: offsets; K6: column maxima
     const uint64_t Q = (uint64_t)((((unsigned __int128)M) << 32) / NP);

@@ -38,12 +38,14 @@ struct SearchLaunch {
     uint32_t s_max;
     uint32_t cap_n; // largest n_j
     uint32_t cap_m; // largest m_j
+    uint64_t* bkeys;       // [n] scratch for the bucket-sorted keys (used unless keys_in_smem)
+    uint32_t keys_in_smem; // 1: keep each partition's keys in shared memory
     uint32_t* pilots;      // [B x np], zero-filled by the caller
     uint32_t* taken_bits;  // global occupancy bitmap over [0, M) in u32 words, zero-filled; may be null
     uint32_t* status;      // device status word (kDev* codes, atomicMax)
     unsigned long long* work; // [2]: s tries, window steps (may be null)
 };
-size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B);
+size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem);
 size_t search_smem_limit();
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream);
 
