@@ -199,6 +199,31 @@ phobic_status phobic_hash_strings(const uint8_t* d_bytes, const uint64_t* d_offs
 phobic_status phobic_partition_sort(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions,
                                     uint64_t* d_sorted, uint64_t* d_start, phobic_stream_t stream);
 
+/* Largest n accepted by phobic_partition_sort_noalloc. */
+#define PHOBIC_NOALLOC_MAX_KEYS 1048576u
+
+/*
+ * phobic_partition_sort without any device allocation.  The paper has no
+ * counterpart: this serves callers that may not allocate device memory while
+ * they run, such as a process whose device budget is fully reserved up front
+ * (an extra cudaMalloc could fail or push out other data) or a host framework
+ * that owns every allocation and forbids libraries from calling the CUDA
+ * allocator themselves.  The caller still owns d_hk, d_sorted and d_start;
+ * the sort's temporary space comes from one fixed array of about 9 MiB inside
+ * this library, which every GPU that loads the library holds until the
+ * process exits.
+ * Same inputs, outputs and results as phobic_partition_sort, for
+ * n <= PHOBIC_NOALLOC_MAX_KEYS; a larger n (or a partition count whose digit
+ * tables would not fit) returns PHOBIC_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls whose work overlaps on the GPU (on different streams or threads)
+ * race with each other: the caller must serialise them.  Synchronises
+ * `stream`; calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+phobic_status phobic_partition_sort_noalloc(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions,
+                                            uint64_t* d_sorted, uint64_t* d_start, phobic_stream_t stream);
+
 /* Writes the 2049-entry fixed-point bucket table (Appendix C) to h_table. */
 phobic_status phobic_bucket_table(double lambda, double alpha, uint32_t partition_size, uint64_t* h_table);
 

@@ -92,6 +92,7 @@ _SIGS = [
     ("phobic_hash_u64", _INT, [_VP, _U64, _U64, _VP, _VP]),
     ("phobic_hash_strings", _INT, [_VP, _VP, _U64, _U64, _VP, _VP]),
     ("phobic_partition_sort", _INT, [_VP, _U64, _U64, _VP, _VP, _VP]),
+    ("phobic_partition_sort_noalloc", _INT, [_VP, _U64, _U64, _VP, _VP, _VP]),
     ("phobic_bucket_table", _INT, [_DBL, _DBL, _U32, _VP]),
 ]
 
@@ -308,6 +309,23 @@ def phobic_partition_sort(hk: torch.Tensor, num_partitions: int, stream=None):
     _check(lib().phobic_partition_sort(h.data_ptr(), h.numel(), int(num_partitions), sorted_.data_ptr(),
                                        start.data_ptr(), _stream(stream)), "phobic_partition_sort")
     return sorted_, start
+
+
+NOALLOC_MAX_KEYS = 1048576
+
+
+def phobic_partition_sort_noalloc(hk: torch.Tensor, num_partitions: int, sorted_out: torch.Tensor,
+                                  start_out: torch.Tensor, stream=None):
+    """Same as phobic_partition_sort, but the caller provides both outputs and
+    the library uses its fixed internal scratch (no device allocation)."""
+    h = _dev_u64(hk, "hk")
+    _dev_u64(sorted_out, "sorted_out")
+    _dev_u64(start_out, "start_out")
+    if sorted_out.numel() < h.numel() or start_out.numel() < num_partitions + 1:
+        raise ValueError("output buffers are too small")
+    _check(lib().phobic_partition_sort_noalloc(h.data_ptr(), h.numel(), int(num_partitions), sorted_out.data_ptr(),
+                                               start_out.data_ptr(), _stream(stream)), "phobic_partition_sort_noalloc")
+    return sorted_out, start_out
 
 
 def phobic_bucket_table(lam: float, alpha: float, P: int) -> np.ndarray:
