@@ -82,6 +82,8 @@ typedef struct {
     float encode_ms;   /* offsets + interleaved pilot encoding */
     float remap_ms;    /* Elias-Fano remap of slots >= n (alpha < 1) */
     float total_ms;    /* first to last event, host synchronisations included */
+    uint64_t search_s_tries; /* pilot-search work: (bucket, s) pairs tried */
+    uint64_t search_steps;   /* pilot-search work: warp steps of the displacement scan */
 } phobic_timings;
 
 /* Structure sizes and space breakdown of a built MPHF. */
@@ -209,7 +211,7 @@ phobic_status phobic_partition_sort(const uint64_t* d_hk, uint64_t n, uint64_t n
  * (an extra cudaMalloc could fail or push out other data) or a host framework
  * that owns every allocation and forbids libraries from calling the CUDA
  * allocator themselves.  The caller still owns d_hk, d_sorted and d_start;
- * the sort's temporary space comes from one fixed array of about 9 MiB inside
+ * the sort's temporary space comes from one fixed array of about 9.1 MiB inside
  * this library, which every GPU that loads the library holds until the
  * process exits.
  * Same inputs, outputs and results as phobic_partition_sort, for

@@ -81,31 +81,20 @@ __device__ __forceinline__ void take_slot(uint32_t* fw, uint32_t pos, uint32_t m
 }
 
 // Lanes per window for a bucket of k keys when `free_slots` of m are free.
-// Expected cost model (uniform across the warp, so no divergence): a candidate
-// displacement is valid with probability q^k, q = free fraction, so about
-// C = min(q^-k, 32 nw) candidates are scanned; with L lanes per window one step
-// covers 1024 / L candidates and costs about min(ceil(k/L), e) window ops plus
-// log2(L) shuffles, where e ~ 1 + ln 32 / -ln q keys empty a window on average.
-// The choice only changes speed: the smallest valid displacement is found for
-// every L.
-__device__ __forceinline__ uint32_t choose_lanes_per_window(uint32_t k, uint32_t free_slots, uint32_t m,
-                                                            uint32_t nw) {
+// A displacement is valid with probability about q^k (q = free fraction), so
+// about C = q^-k candidates are scanned.  With L lanes per window one warp step
+// covers 1024 / L candidates; while C L <= 1024 one step suffices and a larger
+// L splits the k keys over more lanes, so take the largest such L (at most
+// pow2ceil(k)); when C > 1024, L = 1 (every lane scans its own window).  The
+// choice only changes speed: every L finds the smallest valid displacement.
+__device__ __forceinline__ uint32_t choose_lanes_per_window(uint32_t k, uint32_t free_slots, uint32_t m) {
+    const uint32_t lk = k <= 1 ? 0u : 32u - __clz(k - 1);  // log2 pow2ceil(k)
     const float q = (float)free_slots / (float)m;
-    const float lq = __logf(fmaxf(q, 1e-6f));
-    const float cand = fminf(__expf(-(float)k * lq), 32.0f * (float)nw);
-    const float e = lq < -1e-6f ? 1.0f + 3.4657f / -lq : (float)k;
-    float best = 3.0e38f;
-    uint32_t bestL = 1;
-    for (uint32_t L = 1, lg = 0; L <= 32; L <<= 1, lg++) {
-        const float steps = ceilf(cand * (float)L / 1024.0f);
-        const float ops = fminf(ceilf((float)k / (float)L), e);
-        const float cost = steps * (4.0f * ops + 6.0f * (float)lg + 24.0f);
-        if (cost < best) {
-            best = cost;
-            bestL = L;
-        }
-    }
-    return bestL;
+    const float lc = (float)k * -__log2f(q);                // log2 C
+    const float lg = 10.0f - lc;
+    uint32_t l = lg <= 0.0f ? 0u : (uint32_t)lg;
+    l = min(l, min(lk, 5u));
+    return 1u << l;
 }
 
 // any two equal master hashes among keys[0..k)?
@@ -245,6 +234,8 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
     unsigned long long s_tries = 0, steps = 0;
     const uint32_t nw = (m + 31) / 32;
     uint32_t placed = 0;  // keys placed so far in this partition
+    // pilot seeds mix64(s ^ C) for s < 32, one per lane (most buckets need s < 32)
+    const uint64_t ps_lane = pilot_seed(lane);
     // one key per lane of the next bucket, loaded a bucket ahead
     uint64_t pre = 0;
     if (nb) {
@@ -266,22 +257,63 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
         if (a.mode == 0) {
             // ===== additive displacement =====
             uint16_t* hb = aux;  // h(x, s) of the bucket's keys
+            if (k == 1) {
+                // one key: s = 0 always works (free slots remain); d is the
+                // distance from h to the first free slot at or after it
+                // only lane 0 holds the key; every lane scans from its h
+                const uint32_t h1 =
+                    __shfl_sync(kFull, position_hash(mykey, __shfl_sync(kFull, ps_lane, 0), m), 0);
+                s_tries++;
+                uint32_t d1 = 0;
+                for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
+                    steps++;
+                    const uint32_t w = w0 + lane;
+                    uint32_t acc = 0;
+                    if (w < nw) {
+                        acc = (32 * w + 32 <= m) ? kFull : ((1u << (m - 32 * w)) - 1);
+                        acc &= window32(fw, h1 + 32 * w);
+                    }
+                    uint32_t win = __ballot_sync(kFull, acc != 0);
+                    if (win) {
+                        uint32_t fl = __ffs(win) - 1;
+                        d1 = 32 * (w0 + fl) + __ffs(__shfl_sync(kFull, acc, fl)) - 1;
+                        found = true;
+                        break;
+                    }
+                }
+                if (!found) {  // unreachable while the counts are consistent
+                    local_err = kDevSearchLimit;
+                    break;
+                }
+                p = d1;
+                if (lane == 0) {
+                    uint32_t pos = h1 + d1;
+                    if (pos >= m) pos -= m;
+                    take_slot(fw, pos, m);
+                }
+                placed += 1;
+                __syncwarp();
+                if (lane == 0) a.pilots[(uint64_t)b * a.np + j] = p;
+                continue;
+            }
             uint32_t h = 0;
             uint32_t d = 0;
             uint32_t s = 0;
             // lanes per window: chosen once per bucket from the current load
-            const uint32_t Lw = choose_lanes_per_window(k, m - placed, m, nw);
+            const uint32_t Lw = choose_lanes_per_window(k, m - placed, m);
             const uint32_t G = 32 / Lw;  // windows per step
             const uint32_t g = lane / Lw, rr = lane & (Lw - 1);
             for (; s < a.s_max; s++) {
                 s_tries++;
-                const uint64_t ps = pilot_seed(s);
-                bool coll;
+                const uint64_t ps = s < 32 ? __shfl_sync(kFull, ps_lane, s) : pilot_seed(s);
+                bool coll = false;
                 if (k <= 32) {
                     h = lane < k ? position_hash(mykey, ps, m) : (0x80000000u | lane);
                     if (lane < k) hb[lane] = (uint16_t)h;
-                    uint32_t peers = __match_any_sync(kFull, h);
-                    coll = __any_sync(kFull, __popc(peers) > 1);
+                    if (k > 1) {
+                        uint32_t peers = __match_any_sync(kFull, h);
+                        coll = __any_sync(kFull, __popc(peers) > 1);
+                    }
                 } else {
                     bool c = false;
                     for (uint32_t i = lane; i < k; i += 32) {

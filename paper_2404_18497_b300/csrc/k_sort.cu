@@ -16,34 +16,57 @@ namespace phobic {
 
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kItems = 12;
-constexpr int kTile = kThreads * kItems;  // 6144 keys per tile
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // keys per tile
+static_assert(kTile == (int)kSortTileKeys, "tile size");
 constexpr int kWarps = kThreads / 32;
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPre = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 __device__ __forceinline__ uint64_t load_hk(const uint64_t* in, uint64_t i, uint64_t kseed, int hash_input) {
     uint64_t v = __ldg(in + i);
     return hash_input ? key_hash(v, kseed) : v;
 }
 
+// Digit histograms of every pass in one read of the input.  Each warp counts
+// into its own sub-histogram (fewer shared-atomic collisions); 16-byte loads.
 __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ in, uint64_t n, uint64_t np,
                                                    uint64_t kseed, int hash_input, uint32_t passes,
                                                    uint32_t bits, unsigned long long* __restrict__ hist) {
-    extern __shared__ uint32_t sh_hist[];
-    const uint32_t R = 1u << bits, mask = R - 1;
-    for (uint32_t i = threadIdx.x; i < passes * R; i += blockDim.x) sh_hist[i] = 0;
+    extern __shared__ uint32_t sh_hist[];  // [kWarpsH][passes * R]
+    constexpr int kWarpsH = 8;
+    const uint32_t R = 1u << bits, mask = R - 1, PR = passes * R;
+    for (uint32_t i = threadIdx.x; i < kWarpsH * PR; i += blockDim.x) sh_hist[i] = 0;
     __syncthreads();
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t j = partition_of(load_hk(in, i, kseed, hash_input), np);
-        for (uint32_t p = 0; p < passes; p++) atomicAdd(&sh_hist[p * R + ((j >> (p * bits)) & mask)], 1u);
+    uint32_t* mine = sh_hist + (threadIdx.x >> 5) * PR;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t pairs = n >> 1;
+    const ulonglong2* in2 = reinterpret_cast<const ulonglong2*>(in);
+    const bool vec = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+    auto count = [&](uint64_t v) {
+        uint64_t j = partition_of(hash_input ? key_hash(v, kseed) : v, np);
+        for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
+    };
+    if (vec) {
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < pairs; i += stride) {
+            ulonglong2 v = __ldcs(in2 + i);
+            count(v.x);
+            count(v.y);
+        }
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) count(__ldg(in + n - 1));
+    } else {
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) count(__ldg(in + i));
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < passes * R; i += blockDim.x)
-        if (sh_hist[i]) atomicAdd(hist + i, (unsigned long long)sh_hist[i]);
+    for (uint32_t i = threadIdx.x; i < PR; i += blockDim.x) {
+        uint32_t c = 0;
+        for (int w = 0; w < kWarpsH; w++) c += sh_hist[w * PR + i];
+        if (c) atomicAdd(hist + i, (unsigned long long)c);
+    }
 }
 
 // exclusive scan of each pass's digit histogram (one block per pass)
@@ -72,7 +95,14 @@ struct PassArgs {
     uint32_t* error;
 };
 
-__global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
+// One digit pass.  Tile = kTile consecutive keys.  Warp w ranks its 32 x kItems
+// keys (order: item, lane) with __match_any_sync: the leader of each group of
+// equal digits adds the group size to the warp's counter with one shared
+// atomicAdd and hands the old value to its peers, so ranks are stable.  Then
+// per digit: prefix over warps, decoupled look-back for the tile's global
+// offset, a block scan for the tile-local digit starts, a shared-memory
+// reorder and a coalesced write-out.
+__global__ void __launch_bounds__(kThreads, 4) k_sort_pass(PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t R = 1u << a.bits, mask = R - 1;
     uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);                      // kTile
@@ -80,6 +110,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     uint32_t* tile_start = wh + kWarps * R;                                    // R
     unsigned long long* gbase = reinterpret_cast<unsigned long long*>(tile_start + R + (R & 1)); // R
     __shared__ uint32_t tile_s;
+    __shared__ uint32_t warp_tot[kWarps];
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) tile_s = atomicAdd(a.tile_counter, 1u);
@@ -89,43 +120,42 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     const uint64_t base = tile * kTile;
     const uint64_t wbase = base + (uint64_t)warp * 32 * kItems;
 
-    // blocked load: warp w owns keys [wbase, wbase + 32*kItems), coalesced per item
     uint64_t k[kItems];
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
         uint64_t idx = wbase + (uint64_t)i * 32 + lane;
         k[i] = idx < a.n ? load_hk(a.in, idx, a.kseed, a.hash_input) : 0;
     }
-    // stable warp-level ranking (order = warp, item, lane); dr = digit << 16 | rank
-    uint32_t dr[kItems];
+    uint32_t dr[kItems];  // digit << 16 | rank within the warp's digit group
     const uint32_t lt = (1u << lane) - 1;
     uint32_t* myh = wh + warp * R;
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
         const bool valid = wbase + (uint64_t)i * 32 + lane < a.n;
-        const uint32_t dg = valid ? (uint32_t)((partition_of(k[i], a.np) >> a.shift) & mask) : R;  // R: not placed
-        uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
-        uint32_t before = dg < R ? myh[dg] : 0;
-        __syncwarp();
-        if (dg < R && lane == (uint32_t)(__ffs(peers) - 1)) myh[dg] = before + __popc(peers);
-        __syncwarp();
-        dr[i] = (dg << 16) | (before + __popc(peers & lt));
+        const uint32_t dg = valid ? (uint32_t)((partition_of(k[i], a.np) >> a.shift) & mask) : R;
+        const uint32_t peers = __match_any_sync(kFull, dg);
+        const uint32_t leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && dg < R) old = atomicAdd(&myh[dg], (uint32_t)__popc(peers));
+        old = __shfl_sync(kFull, old, leader);
+        dr[i] = (dg << 16) | (old + __popc(peers & lt));
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps, tile totals
+    // per digit: exclusive prefix over warps; tile count into tile_start
     for (uint32_t d = tid; d < R; d += kThreads) {
         uint32_t run = 0;
-        for (uint32_t w = 0; w < kWarps; w++) {
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) {
             uint32_t c = wh[w * R + d];
             wh[w * R + d] = run;
             run += c;
         }
-        tile_start[d] = run;  // tile count for now
+        tile_start[d] = run;
     }
     __syncthreads();
-    // decoupled look-back per digit
+    // decoupled look-back per digit (publish the aggregate first)
     for (uint32_t d = tid; d < R; d += kThreads) {
-        uint64_t cnt = tile_start[d];
+        const uint64_t cnt = tile_start[d];
         volatile unsigned long long* st = a.status;
         uint64_t excl = 0;
         if (tile == 0) {
@@ -153,26 +183,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
         }
         gbase[d] = a.digit_base[d] + excl;
     }
-    __syncthreads();
-    // exclusive scan of the tile counts over digits (single warp, R <= 512)
-    if (warp == 0) {
-        uint32_t carry = 0;
-        for (uint32_t d0 = 0; d0 < R; d0 += 32) {
-            uint32_t d = d0 + lane;
-            uint32_t c = d < R ? tile_start[d] : 0;
-            uint32_t x = c;
+    // block-wide exclusive scan of the tile counts over digits: each thread
+    // owns R / kThreads consecutive digits (1 or 2)
+    {
+        const uint32_t per = (R + kThreads - 1) / kThreads;
+        uint32_t c[2] = {0, 0}, sum = 0;
+        for (uint32_t u = 0; u < per; u++) {
+            uint32_t d = tid * per + u;
+            c[u] = d < R ? tile_start[d] : 0;
+            sum += c[u];
+        }
+        uint32_t x = sum;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-                if (lane >= (uint32_t)o) x += y;
-            }
-            if (d < R) tile_start[d] = carry + x - c;
-            carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        uint32_t woff = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) woff += (w < (int)warp) ? warp_tot[w] : 0;
+        uint32_t run = woff + x - sum;
+        for (uint32_t u = 0; u < per; u++) {
+            uint32_t d = tid * per + u;
+            if (d < R) tile_start[d] = run;
+            run += c[u];
         }
     }
     __syncthreads();
     for (uint32_t d = tid; d < R; d += kThreads) gbase[d] -= tile_start[d];
-    // scatter into shared memory in digit order
+    // reorder in shared memory by digit
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
         uint32_t d = dr[i] >> 16;
@@ -180,7 +221,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     }
     __syncthreads();
     // coalesced write-out: consecutive slots of one digit go to consecutive addresses
-    uint64_t valid = a.n - base < (uint64_t)kTile ? a.n - base : (uint64_t)kTile;
+    const uint64_t valid = a.n - base < (uint64_t)kTile ? a.n - base : (uint64_t)kTile;
+#pragma unroll 4
     for (uint32_t i = tid; i < valid; i += kThreads) {
         uint64_t v = keys_s[i];
         uint32_t d = (uint32_t)((partition_of(v, a.np) >> a.shift) & mask);
@@ -268,7 +310,10 @@ cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t k
         uint64_t hblocks = (n + 256 * 16 - 1) / (256 * 16);
         if (hblocks > (uint64_t)sms * 8) hblocks = (uint64_t)sms * 8;
         if (hblocks == 0) hblocks = 1;
-        k_sort_hist<<<(unsigned)hblocks, 256, passes * R * 4, stream>>>(in, n, np, kseed, hash_input, passes, bits,
+        if ((e = cudaFuncSetAttribute(k_sort_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(8 * passes * R * 4))) != cudaSuccess)
+            return e;
+        k_sort_hist<<<(unsigned)hblocks, 256, 8 * passes * R * 4, stream>>>(in, n, np, kseed, hash_input, passes, bits,
                                                                         hist);
         note_launches(1);
         k_sort_hist_scan<<<passes, 32, 0, stream>>>(hist, bits);

@@ -148,11 +148,23 @@ struct PhaseEvents {
     }
 };
 
+// Small pinned host buffer for the scalars a build reads back, kept per host
+// thread and grown on demand (pinned allocation is slow; builds are frequent).
 struct PinnedBuf {
     void* p = nullptr;
-    cudaError_t alloc(size_t bytes) { return cudaMallocHost(&p, bytes); }
-    ~PinnedBuf() {
-        if (p) cudaFreeHost(p);
+    cudaError_t alloc(size_t bytes) {
+        thread_local void* buf = nullptr;
+        thread_local size_t cap = 0;
+        if (cap < bytes) {
+            if (buf) cudaFreeHost(buf);
+            buf = nullptr;
+            cap = 0;
+            cudaError_t e = cudaMallocHost(&buf, bytes);
+            if (e != cudaSuccess) return e;
+            cap = bytes;
+        }
+        p = buf;
+        return cudaSuccess;
     }
 };
 
@@ -345,7 +357,12 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
     sl.pilots = pilots;
     sl.taken_bits = taken;
     sl.status = status;
-    sl.work = nullptr;
+    unsigned long long* work = nullptr;
+    if (prm.record_timings) {
+        CK(tmp.alloc(&work, 16));
+        CK(cudaMemsetAsync(work, 0, 16, st));
+    }
+    sl.work = work;
     CK(ev.mark(3, st));
     CK(launch_search(sl, st));
     CK(ev.mark(4, st));
@@ -365,6 +382,7 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
     uint32_t* hcolmax = reinterpret_cast<uint32_t*>(hst + 16);
     CK(d2h(hmm, mm, 2, st));
     CK(d2h(hcolmax, colmax, B, st));
+    if (work) CK(d2h(hst + 12, reinterpret_cast<uint64_t*>(work), 2, st));
     CK(d2h(reinterpret_cast<uint32_t*>(hst + 4), status, 1, st));
     CK(cudaStreamSynchronize(st));
     switch (reinterpret_cast<uint32_t*>(hst + 4)[0]) {
@@ -402,7 +420,6 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
         CK(h2d(dwb, wbegin.data(), B + 1, st));
         CK(cudaMemsetAsync(h->pil_words, 0, h->n_pil_words * 8, st));
         CK(launch_compact_pack(pilots, NP, B, h->col_meta, dwb, h->pil_words, wbegin[B], st));
-        CK(cudaStreamSynchronize(st));  // host vectors above are read by async copies
     } else {
         // presence bitmaps over [0, max_b] per column
         std::vector<uint64_t> bm_base(B + 1, 0);
@@ -446,7 +463,6 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
         CK(cudaMemsetAsync(h->dict_words, 0, h->n_dict_words * 8, st));
         CK(launch_dict_pack(pilots, NP, B, dbm_base, bitmaps, brank, h->col_meta, dwb, h->pil_words, wbegin[B],
                             nullptr, h->dict_words, bm_base[B], st));
-        CK(cudaStreamSynchronize(st));
     }
 
     CK(ev.mark(6, st));
@@ -510,6 +526,8 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
         h->timings.encode_ms = ev.between(5, 6);
         h->timings.remap_ms = ev.between(6, 7);
         h->timings.total_ms = ev.between(0, 7);
+        h->timings.search_s_tries = hst[12];
+        h->timings.search_steps = hst[13];
     }
 
     // the handle takes the permanent buffers

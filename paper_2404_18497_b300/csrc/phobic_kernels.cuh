@@ -13,6 +13,7 @@ namespace phobic {
 void note_launches(uint64_t k);
 
 // ---- k_sort.cu: master hash + onesweep sort by partition id ----
+constexpr uint32_t kSortTileKeys = 4096;  // keys per onesweep tile
 void sort_plan(uint64_t np, uint32_t* passes, uint32_t* bits);
 size_t sort_scratch_bytes(uint64_t n, uint64_t np);
 cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t kseed, uint64_t n, uint64_t np,

@@ -54,7 +54,8 @@ class phobic_params(ctypes.Structure):
 
 class phobic_timings(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in
-                ("sort_ms", "sizes_ms", "search_ms", "encode_ms", "remap_ms", "total_ms")]
+                ("sort_ms", "sizes_ms", "search_ms", "encode_ms", "remap_ms", "total_ms")] + [
+        ("search_s_tries", ctypes.c_uint64), ("search_steps", ctypes.c_uint64)]
 
 
 class phobic_info(ctypes.Structure):
@@ -275,7 +276,7 @@ def phobic_copy_pilots(h: Handle, stream=None) -> torch.Tensor:
 def phobic_get_timings(h: Handle) -> dict:
     t = phobic_timings()
     _check(lib().phobic_get_timings(h.ptr, ctypes.byref(t)), "phobic_get_timings")
-    return {f[0]: float(getattr(t, f[0])) for f in phobic_timings._fields_}
+    return {f[0]: (float if f[1] is ctypes.c_float else int)(getattr(t, f[0])) for f in phobic_timings._fields_}
 
 
 def phobic_kernel_launches() -> int:
