@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-target-s", type=float, default=12.0)
+    ap.add_argument("--candidate-width", type=int, default=0, help="search window width (32/64; 0 = default)")
     return ap.parse_args()
 
 
@@ -57,6 +58,36 @@ def workload(a):
         return dict(name=SMALL, n=n, lam=7.0, alpha=1.0, P=2500, encoder=0, q_uniform=10 * n, q_zipf=0)
     n = int(a.n or 1e8)
     return dict(name=WORKLOAD, n=n, lam=7.0, alpha=0.99, P=2500, encoder=1, q_uniform=n, q_zipf=n)
+
+
+# Per-key counters from the ncu captures summarised in profiles/ (3e7-key case of
+# this workload), valid only for the kernel sources they were taken on: each
+# entry names the source files and the sha256 (first 16 hex digits) of their
+# concatenation.  When a source changes, the counters are reported as null.
+NCU_CAPTURES = {
+    "k_search": {"files": ["paper_2404_18497_b300/csrc/k_search.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
+                 "sha": "db85c4af5ab769cf", "n": 3e7, "warp_inst": 2302259631, "dram_bytes": 537991168 + 301251072,
+                 "profile": "profiles/k_search_3e7.md"},
+    "k_query": {"files": ["paper_2404_18497_b300/csrc/k_query.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
+                "sha": "5c5cf41cc31d5a6f", "n": 3e7, "dram_bytes": 249891840 + 198090496,
+                "profile": "profiles/k_query_3e7.md"},
+    "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
+               "sha": "811cef033233d6a5", "n": 3e7, "dram_bytes": 246039808 + 199315200 + 245927424 + 198025216,
+               "profile": "profiles/k_sort_pass_3e7.md"},
+}
+ISSUE_SLOTS_PER_CLOCK = 148 * 4  # B300: 148 SMs x 4 warp schedulers, one warp instruction per clock each
+SM_MAX_MHZ = 2032.0
+
+
+def capture(name):
+    import hashlib
+
+    c = NCU_CAPTURES[name]
+    h = hashlib.sha256()
+    for f in c["files"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return c if h.hexdigest()[:16] == c["sha"] else None
 
 
 def peaks():
@@ -236,7 +267,8 @@ def run_ours(a):
     dqu = torch.from_numpy(qu.view(np.int64)).cuda()
     dqz = torch.from_numpy(qz.view(np.int64)).cuda() if qz is not None else None
     out = torch.empty(max(dqu.numel(), dqz.numel() if dqz is not None else 0), dtype=torch.int64, device="cuda")
-    prm = phobic.make_params(w["lam"], w["alpha"], w["P"], seed=0, encoder=w["encoder"], record_timings=True)
+    prm = phobic.make_params(w["lam"], w["alpha"], w["P"], seed=0, encoder=w["encoder"], record_timings=True,
+                             candidate_width=a.candidate_width)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -297,31 +329,49 @@ def run_ours(a):
     hbm, src = peaks()
     kern = {
         "k_search (bucketing + pilot search)": ph["search_ms"],
-        "k_sort_pass x2 + k_sort_hist (hash + onesweep partition sort)": ph["sort_ms"],
+        "k_sort_hist + 2 x k_sort_pass (hash + onesweep partition sort)": ph["sort_ms"],
         "k_query (uniform batch)": statistics.mean(qu_ms),
         "k_query (Zipf batch)": statistics.mean(qz_ms),
         "encode (offsets + IC-D)": ph["encode_ms"],
         "remap (Elias-Fano)": ph["remap_ms"],
     }
     dom = max(kern, key=kern.get)
+    sm_mhz = (clocks.get("sm_mhz") or SM_MAX_MHZ) if isinstance(clocks, dict) else SM_MAX_MHZ
+    # k_search: integer ALU + shared memory, no dense contraction; its ceiling is
+    # the issue rate (warp instructions per second) at the SM clock
+    cs = capture("k_search")
+    peak_issue = ISSUE_SLOTS_PER_CLOCK * SM_MAX_MHZ * 1e6 / 1e9  # G warp-inst/s at the maximum clock
+    if cs:
+        inst = cs["warp_inst"] / cs["n"] * n
+        achieved = inst / (ph["search_ms"] / 1e3) / 1e9
+        traffic = cs["dram_bytes"] / cs["n"] * n
+    else:
+        inst = achieved = traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_issue, "unit": "G warp-inst/s",
+                "frac": (achieved / peak_issue) if achieved else None, "traffic": traffic,
+                "kernel": "k_search", "launch_ms": ph["search_ms"], "warp_inst_per_launch": inst,
+                "peak_source": "148 SMs x 4 schedulers x 1 warp-inst/clock x 2032 MHz (unit counts and max clock)",
+                "sm_mhz_measured": sm_mhz,
+                "counters": cs["profile"] if cs else "stale: kernel source changed since the ncu capture",
+                "dominant_kernel_by_time": dom, "per_kernel_ms": kern}
+    cq = capture("k_query")
     q_bytes = 16.0 * w["q_uniform"]
-    roof_query = {"bound": "hbm", "achieved": q_bytes / (statistics.mean(qu_ms) / 1e3) / 1e9, "peak": hbm,
-                  "unit": "GB/s", "frac": None, "traffic": None, "kernel": "k_query (uniform batch)",
-                  "algorithmic_bytes_per_launch": q_bytes, "peak_source": f"{src} hbm_gbs"}
-    roof_query["frac"] = roof_query["achieved"] / hbm
+    roofline["query"] = {"bound": "hbm", "achieved": q_bytes / (statistics.mean(qu_ms) / 1e3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "kernel": "k_query (uniform batch)", "algorithmic_bytes_per_launch": q_bytes,
+                         "traffic": (cq["dram_bytes"] / cq["n"] * w["q_uniform"]) if cq else None,
+                         "peak_source": f"{src} hbm_gbs"}
+    roofline["query"]["frac"] = roofline["query"]["achieved"] / hbm
+    cso = capture("k_sort")
     sort_bytes = 40.0 * n  # histogram read 8 B + two passes x (8 B read + 8 B write) per key
-    roof_sort = {"bound": "hbm", "achieved": sort_bytes / (ph["sort_ms"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                 "kernel": "hash + onesweep partition sort", "algorithmic_bytes_per_launch": sort_bytes}
-    roof_sort["frac"] = roof_sort["achieved"] / hbm
+    roofline["sort"] = {"bound": "hbm", "achieved": sort_bytes / (ph["sort_ms"] / 1e3) / 1e9, "peak": hbm,
+                        "unit": "GB/s", "kernel": "hash + onesweep partition sort",
+                        "algorithmic_bytes_per_launch": sort_bytes,
+                        "traffic": (cso["dram_bytes"] / cso["n"] * n) if cso else None}
+    roofline["sort"]["frac"] = roofline["sort"]["achieved"] / hbm
     build_bytes = 8.3 * n
-    roof_build = {"bound": "hbm", "achieved": build_bytes / (b_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                  "kernel": "whole build", "algorithmic_bytes_per_launch": build_bytes}
-    roof_build["frac"] = roof_build["achieved"] / hbm
-    roofline = dict(roof_query)
-    roofline["dominant_kernel_by_time"] = dom
-    roofline["per_kernel_ms"] = kern
-    roofline["sort"] = roof_sort
-    roofline["build"] = roof_build
+    roofline["build"] = {"bound": "hbm", "achieved": build_bytes / (b_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "kernel": "whole build", "algorithmic_bytes_per_launch": build_bytes}
+    roofline["build"]["frac"] = roofline["build"]["achieved"] / hbm
 
     # ---- end to end through the host-buffer entry points
     e2e = None

@@ -71,6 +71,8 @@ typedef struct {
     uint32_t warps_per_partition; /* search kernel tuning: 0 = default; results do not depend on it */
     uint32_t keep_pilots;         /* nonzero: keep the raw pilot matrix for phobic_copy_pilots */
     uint32_t record_timings;      /* nonzero: time the build phases with CUDA events on `stream` */
+    uint32_t candidate_width;     /* search tuning: displacements per lane-window, 32 or 64 (0 = default 64);
+                                     results do not depend on it */
 } phobic_params;
 
 /* Device time of each build phase (CUDA events recorded on the build stream

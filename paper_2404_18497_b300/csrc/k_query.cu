@@ -23,8 +23,43 @@ __device__ __forceinline__ uint64_t expectation(uint64_t j, uint64_t Q) {
     return (hi << 32) | (lo >> 32);
 }
 
+// T_j and T_{j+1}: the two stored differences are adjacent (2w <= 62 bits), so
+// one 128-bit window of the packed words holds both
+__device__ __forceinline__ void offsets_of(const QueryView& v, uint64_t j, uint64_t* Tj, uint64_t* Tj1) {
+    const uint32_t w = v.off_w;
+    uint64_t d0 = 0, d1 = 0;
+    if (w) {
+        const uint64_t o = j * w;
+        const uint64_t i = o >> 6;
+        const uint32_t sh = (uint32_t)(o & 63);
+        const uint64_t lo = __ldg(v.off_words + i);
+        const uint64_t x = sh ? (lo >> sh) | (__ldg(v.off_words + i + 1) << (64 - sh)) : lo;
+        const uint64_t mask = (1ull << w) - 1;
+        d0 = x & mask;
+        d1 = (x >> w) & mask;
+    }
+    *Tj = expectation(j, v.off_Q) + (uint64_t)v.off_dmin + d0;
+    *Tj1 = expectation(j + 1, v.off_Q) + (uint64_t)v.off_dmin + d1;
+}
+
 __device__ __forceinline__ uint64_t offset_of(const QueryView& v, uint64_t j) {
     return expectation(j, v.off_Q) + (uint64_t)v.off_dmin + read_bits(v.off_words, j * v.off_w, v.off_w);
+}
+
+// floor(p / m) for m >= 1 through a float reciprocal and an exact integer
+// correction (the estimate is within one of the quotient for p < 2^32)
+__device__ __forceinline__ uint32_t div_u32(uint32_t p, uint32_t m) {
+    uint32_t q = __float2uint_rz(__fmul_rz((float)p, __frcp_rz((float)m)));
+    int64_t r = (int64_t)p - (int64_t)q * m;
+    while (r < 0) {
+        q--;
+        r += m;
+    }
+    while (r >= (int64_t)m) {
+        q++;
+        r -= m;
+    }
+    return q;
 }
 
 // i-th value of the Elias-Fano sequence
@@ -45,15 +80,35 @@ __device__ __forceinline__ uint64_t ef_access(const QueryView& v, uint64_t i) {
     return ((one - i) << v.ef_l) | low;
 }
 
-__device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key) {
+constexpr int kSeedTable = 64;  // pilot seeds mix64(s ^ C) for s < 64, per block
+
+__device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key, const uint64_t* seeds) {
     const uint64_t hk = key_hash(key, v.kseed);
     const uint64_t j = partition_of(hk, v.NP);
-    const uint64_t Tj = offset_of(v, j);
-    const uint32_t m = (uint32_t)(offset_of(v, j + 1) - Tj);
+    uint64_t Tj, Tj1;
+    if (v.off_w <= 31) {
+        offsets_of(v, j, &Tj, &Tj1);
+    } else {
+        Tj = offset_of(v, j);
+        Tj1 = offset_of(v, j + 1);
+    }
+    const uint32_t m = (uint32_t)(Tj1 - Tj);
     if (m == 0) return 0;  // only a key outside the set can land in an empty partition
     const uint32_t b = bucket_of(bucket_hash(hk), v.table, v.B);
     uint32_t p;
-    if (v.encoder == 0) {
+    if (v.small_bits) {
+        const uint32_t jj = (uint32_t)j;
+        if (v.encoder == 0) {
+            const uint64_t meta = __ldg(v.col_meta + b);
+            const uint32_t w = (uint32_t)(meta >> 56);
+            p = read_bits32(v.pil_words, (uint32_t)meta + jj * w, w);
+        } else {
+            const uint64_t rm = __ldg(v.col_meta + 2 * b), dm = __ldg(v.col_meta + 2 * b + 1);
+            const uint32_t rw = (uint32_t)(rm >> 56), dw = (uint32_t)(dm >> 56);
+            const uint32_t r = read_bits32(v.pil_words, (uint32_t)rm + jj * rw, rw);
+            p = read_bits32(v.dict_words, (uint32_t)dm + r * dw, dw);
+        }
+    } else if (v.encoder == 0) {
         uint64_t meta = __ldg(v.col_meta + b);
         uint32_t w = (uint32_t)(meta >> 56);
         p = (uint32_t)read_bits(v.pil_words, (meta & kMeta) + j * w, w);
@@ -65,12 +120,14 @@ __device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key) 
     }
     uint32_t local;
     if (v.pilot_mode == 0) {
-        uint32_t s = p / m;
-        uint32_t d = p - s * m;
-        local = position_hash(hk, pilot_seed(s), m) + d;
+        const uint32_t s = div_u32(p, m);
+        const uint32_t d = p - s * m;
+        const uint64_t ps = s < kSeedTable ? seeds[s] : pilot_seed(s);
+        local = position_hash(hk, ps, m) + d;
         if (local >= m) local -= m;
     } else {
-        local = position_hash(hk, pilot_seed(p), m);
+        const uint64_t ps = p < kSeedTable ? seeds[p] : pilot_seed(p);
+        local = position_hash(hk, ps, m);
     }
     uint64_t g = Tj + local;
     if (g >= v.n) g = ef_access(v, g - v.n);
@@ -79,6 +136,9 @@ __device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key) 
 
 __global__ void __launch_bounds__(256) k_query(const QueryView v, const uint64_t* __restrict__ keys,
                                                uint64_t* __restrict__ out, uint64_t m) {
+    __shared__ uint64_t seeds[kSeedTable];
+    if (threadIdx.x < kSeedTable) seeds[threadIdx.x] = pilot_seed(threadIdx.x);
+    __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const bool vec = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     if (vec) {
@@ -88,14 +148,14 @@ __global__ void __launch_bounds__(256) k_query(const QueryView v, const uint64_t
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < pairs; i += stride) {
             ulonglong2 k = __ldcs(k2 + i);
             ulonglong2 r;
-            r.x = query_one(v, k.x);
-            r.y = query_one(v, k.y);
+            r.x = query_one(v, k.x, seeds);
+            r.y = query_one(v, k.y, seeds);
             __stcs(o2 + i, r);
         }
-        if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[m - 1] = query_one(v, keys[m - 1]);
+        if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[m - 1] = query_one(v, keys[m - 1], seeds);
     } else {
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += stride)
-            out[i] = query_one(v, keys[i]);
+            out[i] = query_one(v, keys[i], seeds);
     }
 }
 

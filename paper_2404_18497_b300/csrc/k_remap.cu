@@ -21,9 +21,7 @@ namespace phobic {
 
 namespace {
 
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr uint64_t kScanTile = kScanTileItems;
 
 // count of bits in word w of the region [lo, hi) of a u32 bitmap; `want_zero`
 // counts free slots instead of occupied ones
@@ -37,88 +35,11 @@ __device__ __forceinline__ uint32_t region_bits(const uint32_t* bm, uint64_t w, 
     return v & mask;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_count_words(const uint32_t* __restrict__ bm, uint64_t w0, uint64_t nw,
+__global__ void __launch_bounds__(256) k_count_words(const uint32_t* __restrict__ bm, uint64_t w0, uint64_t nw,
                                                               uint64_t lo, uint64_t hi, int want_zero,
                                                               uint32_t* __restrict__ cnt) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nw; i += (uint64_t)gridDim.x * blockDim.x)
         cnt[i] = __popc(region_bits(bm, w0 + i, lo, hi, want_zero != 0));
-}
-
-__device__ __forceinline__ unsigned long long block_scan_excl(unsigned long long v, unsigned long long* total) {
-    __shared__ unsigned long long ws[32];
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= (uint32_t)o) x += y;
-    }
-    if (lane == 31) ws[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        unsigned long long s = ws[lane], z = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, z, o);
-            if (lane >= (uint32_t)o) z += y;
-        }
-        ws[lane] = z - s;
-        if (lane == 31) *total = z;
-    }
-    __syncthreads();
-    unsigned long long r = ws[warp] + x - v;
-    __syncthreads();
-    return r;
-}
-
-// phase 1: per-tile sums
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t* __restrict__ in, uint64_t n,
-                                                             unsigned long long* __restrict__ tile_sum) {
-    __shared__ unsigned long long tot;
-    uint64_t base = (uint64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
-    unsigned long long s = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; i++)
-        if (base + i < n) s += in[base + i];
-    block_scan_excl(s, &tot);
-    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
-}
-
-// phase 2: exclusive scan of the tile sums (one block); grand total at [ntiles]
-__global__ void __launch_bounds__(kScanThreads) k_scan_sums(unsigned long long* __restrict__ tile_sum, uint64_t ntiles) {
-    __shared__ unsigned long long tot;
-    unsigned long long carry = 0;
-    for (uint64_t c = 0; c < ntiles; c += kScanThreads) {
-        uint64_t i = c + threadIdx.x;
-        unsigned long long v = i < ntiles ? tile_sum[i] : 0;
-        unsigned long long e = block_scan_excl(v, &tot);
-        if (i < ntiles) tile_sum[i] = carry + e;
-        carry += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) tile_sum[ntiles] = carry;
-}
-
-// phase 3: exclusive scan within tiles plus the tile offset
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ in, uint64_t n,
-                                                             const unsigned long long* __restrict__ tile_sum,
-                                                             unsigned long long* __restrict__ out) {
-    __shared__ unsigned long long tot;
-    uint64_t base = (uint64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
-    uint32_t v[kScanItems];
-    unsigned long long s = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; i++) {
-        v[i] = base + i < n ? in[base + i] : 0;
-        s += v[i];
-    }
-    unsigned long long run = tile_sum[blockIdx.x] + block_scan_excl(s, &tot);
-#pragma unroll
-    for (int i = 0; i < kScanItems; i++)
-        if (base + i < n) {
-            out[base + i] = run;
-            run += v[i];
-        }
 }
 
 // F: free slots below n, in order (only the first cap entries are needed)
@@ -185,24 +106,6 @@ unsigned grid_for(uint64_t work, unsigned threads) {
     return (unsigned)(g ? g : 1);
 }
 
-struct ScanBufs {
-    unsigned long long* tiles;
-    uint64_t ntiles;
-};
-
-cudaError_t exclusive_scan(const uint32_t* in, uint64_t n, unsigned long long* out, unsigned long long* tiles,
-                           cudaStream_t st) {
-    uint64_t nt = (n + kScanTile - 1) / kScanTile;
-    if (nt == 0) nt = 1;
-    k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, st>>>(in, n, tiles);
-    note_launches(1);
-    k_scan_sums<<<1, kScanThreads, 0, st>>>(tiles, nt);
-    note_launches(1);
-    k_scan_apply<<<(unsigned)nt, kScanThreads, 0, st>>>(in, n, tiles, out);
-    note_launches(1);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 size_t remap_scratch_bytes(uint64_t n, uint64_t M) {
@@ -236,18 +139,17 @@ cudaError_t launch_remap(const uint32_t* taken_bits, uint64_t n, uint64_t M, uin
     unsigned long long* ztiles = (unsigned long long*)take(((nw0 + kScanTile - 1) / kScanTile + 2) * 8);
     unsigned long long* ttiles = (unsigned long long*)take(((nw1 + kScanTile - 1) / kScanTile + 2) * 8);
     uint64_t* F = (uint64_t*)take((N + 1) * 8);
-    const uint64_t nt1 = (nw1 + kScanTile - 1) / kScanTile;
 
     k_count_words<<<grid_for(nw0, 256), 256, 0, st>>>(taken_bits, 0, nw0, 0, n, 1, zc);
     note_launches(1);
     k_count_words<<<grid_for(nw1, 256), 256, 0, st>>>(taken_bits, w0, nw1, n, M, 0, tc);
     note_launches(1);
     cudaError_t e;
-    if ((e = exclusive_scan(zc, nw0, zoff, ztiles, st)) != cudaSuccess) return e;
-    if ((e = exclusive_scan(tc, nw1, toff, ttiles, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan_u32(zc, nw0, zoff, ztiles, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan_u32(tc, nw1, toff, ttiles, st)) != cudaSuccess) return e;
     k_free_list<<<grid_for(nw0, 256), 256, 0, st>>>(taken_bits, nw0, n, zoff, F, N);
     note_launches(1);
-    k_fill_fs<<<grid_for(N, 256), 256, 0, st>>>(taken_bits, n, M, w0, toff, ttiles + (nt1 ? nt1 : 1), F, fs);
+    k_fill_fs<<<grid_for(N, 256), 256, 0, st>>>(taken_bits, n, M, w0, toff, scan_total(ttiles, nw1), F, fs);
     note_launches(1);
     if ((e = cudaMemsetAsync(ef_high, 0, high_nwords * 8, st)) != cudaSuccess) return e;
     k_ef_low<<<grid_for(low_nwords, 256), 256, 0, st>>>(fs, N, l, ef_low, low_nwords);

@@ -39,6 +39,7 @@ namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr int kSizeHist = 1024;  // bucket sizes 1..1023
+constexpr int kBigRegs = 4;      // keys per lane kept in registers for buckets of 33..128 keys
 
 struct SmemLayout {
     uint32_t off_hk, off_bend, off_order, off_fw, off_scr, off_aux, total;
@@ -54,7 +55,7 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t cap_n, uint32_t cap_m
     o += (B + 1) * 4;
     L.off_order = o;
     o += B * 4;
-    L.fw_words = (2 * cap_m + 64) / 32 + 2;
+    L.fw_words = (2 * cap_m + 128) / 32 + 3;
     L.off_fw = o;
     o += L.fw_words * 4;
     L.scr_words = (cap_m + 31) / 32 + 1;
@@ -67,12 +68,42 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t cap_n, uint32_t cap_m
     return L;
 }
 
-__device__ __forceinline__ uint32_t pow2ceil(uint32_t k) { return k <= 1 ? 1u : 1u << (32 - __clz(k - 1)); }
 
 // 32 free bits starting at bit q of the doubled free bitmap
 __device__ __forceinline__ uint32_t window32(const uint32_t* fw, uint32_t q) {
     return __funnelshift_r(fw[q >> 5], fw[(q >> 5) + 1], q & 31);
 }
+
+// W free bits (W = 32 or 64 displacements) starting at bit q, with the mask of
+// displacements d = W w .. W w + W - 1 that lie below m, and helpers on them.
+template <int W>
+struct Win;
+template <>
+struct Win<32> {
+    using T = uint32_t;
+    static __device__ __forceinline__ T load(const uint32_t* fw, uint32_t q) { return window32(fw, q); }
+    static __device__ __forceinline__ T valid(uint32_t w, uint32_t m) {
+        return (32 * w + 32 <= m) ? 0xFFFFFFFFu : ((1u << (m - 32 * w)) - 1);
+    }
+    static __device__ __forceinline__ uint32_t first(T x) { return __ffs(x) - 1; }
+    static __device__ __forceinline__ T shfl(T x, uint32_t l) { return __shfl_sync(0xFFFFFFFFu, x, l); }
+    static __device__ __forceinline__ T shfl_xor(T x, uint32_t o) { return __shfl_xor_sync(0xFFFFFFFFu, x, o); }
+};
+template <>
+struct Win<64> {
+    using T = uint64_t;
+    static __device__ __forceinline__ T load(const uint32_t* fw, uint32_t q) {
+        const uint32_t i = q >> 5, sh = q & 31;
+        const uint32_t a = fw[i], b = fw[i + 1], c = fw[i + 2];
+        return (uint64_t)__funnelshift_r(a, b, sh) | ((uint64_t)__funnelshift_r(b, c, sh) << 32);
+    }
+    static __device__ __forceinline__ T valid(uint32_t w, uint32_t m) {
+        return (64 * w + 64 <= m) ? ~0ull : ((1ull << (m - 64 * w)) - 1);
+    }
+    static __device__ __forceinline__ uint32_t first(T x) { return __ffsll((long long)x) - 1; }
+    static __device__ __forceinline__ T shfl(T x, uint32_t l) { return __shfl_sync(0xFFFFFFFFu, x, l); }
+    static __device__ __forceinline__ T shfl_xor(T x, uint32_t o) { return __shfl_xor_sync(0xFFFFFFFFu, x, o); }
+};
 
 __device__ __forceinline__ void take_slot(uint32_t* fw, uint32_t pos, uint32_t m) {
     atomicAnd(&fw[pos >> 5], ~(1u << (pos & 31)));
@@ -83,18 +114,62 @@ __device__ __forceinline__ void take_slot(uint32_t* fw, uint32_t pos, uint32_t m
 // Lanes per window for a bucket of k keys when `free_slots` of m are free.
 // A displacement is valid with probability about q^k (q = free fraction), so
 // about C = q^-k candidates are scanned.  With L lanes per window one warp step
-// covers 1024 / L candidates; while C L <= 1024 one step suffices and a larger
-// L splits the k keys over more lanes, so take the largest such L (at most
-// pow2ceil(k)); when C > 1024, L = 1 (every lane scans its own window).  The
+// covers 32 W / L candidates (W displacements per window); while C L <= 32 W one
+// step suffices and a larger L splits the k keys over more lanes, so take the
+// largest such L (at most pow2ceil(k)); otherwise L = 1 (every lane scans its
+// own window).  The
 // choice only changes speed: every L finds the smallest valid displacement.
-__device__ __forceinline__ uint32_t choose_lanes_per_window(uint32_t k, uint32_t free_slots, uint32_t m) {
+template <int W>
+__device__ __forceinline__ uint32_t choose_lanes_log2(uint32_t k, uint32_t free_slots, uint32_t m) {
     const uint32_t lk = k <= 1 ? 0u : 32u - __clz(k - 1);  // log2 pow2ceil(k)
-    const float q = (float)free_slots / (float)m;
+    const float q = __fdividef((float)free_slots, (float)m);
     const float lc = (float)k * -__log2f(q);                // log2 C
-    const float lg = 10.0f - lc;
-    uint32_t l = lg <= 0.0f ? 0u : (uint32_t)lg;
-    l = min(l, min(lk, 5u));
-    return 1u << l;
+    const float lg = (W == 64 ? 11.0f : 10.0f) - lc;        // log2(32 W) - log2 C
+    const uint32_t l = lg <= 0.0f ? 0u : (uint32_t)lg;
+    return min(l, min(lk, 5u));
+}
+
+// One sweep over the displacement windows for the current s with 2^LG lanes
+// per window (32 >> LG windows per warp step): lane rr of group g ANDs the
+// windows of keys rr, rr + 2^LG, ... for window w0 + g, the group reduces by
+// AND, and a ballot over the group leaders takes the first window that still
+// has a set bit; its lowest bit is the smallest valid displacement.
+template <int W, int LG>
+__device__ __forceinline__ bool scan_windows(const uint32_t* fw, const uint16_t* hb, uint32_t k, uint32_t m,
+                                             uint32_t nw, uint32_t lane, uint32_t& d, unsigned long long& steps) {
+    using Wn = Win<W>;
+    using WT = typename Wn::T;
+    constexpr uint32_t Lw = 1u << LG, G = 32u >> LG;
+    const uint32_t g = lane >> LG, rr = lane & (Lw - 1);
+    for (uint32_t w0 = 0; w0 < nw; w0 += G) {
+        steps++;
+        const uint32_t w = w0 + g;
+        WT acc = 0;
+        if (w < nw) {
+            acc = Wn::valid(w, m);
+            const uint32_t q0 = W * w;
+            uint32_t i = rr;
+            for (; i + Lw < k && acc; i += 2 * Lw) {
+                const WT x0 = Wn::load(fw, (uint32_t)hb[i] + q0);
+                const WT x1 = Wn::load(fw, (uint32_t)hb[i + Lw] + q0);
+                acc &= x0 & x1;
+            }
+            if (i < k && acc) acc &= Wn::load(fw, (uint32_t)hb[i] + q0);
+        }
+        if constexpr (LG == 5 && W == 32) {
+            acc = __reduce_and_sync(kFull, acc);
+        } else {
+#pragma unroll
+            for (uint32_t o = 1; o < Lw; o <<= 1) acc &= Wn::shfl_xor(acc, o);
+        }
+        const uint32_t win = __ballot_sync(kFull, acc != 0 && rr == 0);
+        if (win) {
+            const uint32_t fl = __ffs(win) - 1;
+            d = W * (w0 + (fl >> LG)) + Wn::first(Wn::shfl(acc, fl));
+            return true;
+        }
+    }
+    return false;
 }
 
 // any two equal master hashes among keys[0..k)?
@@ -117,8 +192,10 @@ __device__ bool bucket_has_dup(const uint64_t* keys, uint32_t k, uint32_t lane) 
 // sorted input, L2-resident while the partition is active).  Each bucket's keys
 // are prefetched into registers one bucket ahead, and shared memory shrinks to
 // the bitmaps and counters, so several times more partitions fit on an SM.
-template <bool kKeysInSmem>
+template <bool kKeysInSmem, int kW>
 __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
+    using Wn = Win<kW>;
+    using WT = typename Wn::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemLayout L = smem_layout(a.cap_n, a.cap_m, a.B, kKeysInSmem);
     uint32_t* bend = reinterpret_cast<uint32_t*>(smem + L.off_bend);
@@ -139,7 +216,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
 
     // ---- init: counts, doubled free bitmap, scratch, size histogram
     for (uint32_t b = lane; b <= B; b += 32) bend[b] = 0;
-    const uint32_t fwn = (2 * m + 64) / 32 + 2;
+    const uint32_t fwn = (2 * m + 128) / 32 + 3;
     for (uint32_t w = lane; w < fwn; w += 32) {
         uint32_t lo = w * 32, v;
         if (lo + 32 <= 2 * m)
@@ -232,7 +309,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
 
     // ---- 3. placement
     unsigned long long s_tries = 0, steps = 0;
-    const uint32_t nw = (m + 31) / 32;
+    const uint32_t nw = (m + kW - 1) / kW;  // windows of kW displacements
     uint32_t placed = 0;  // keys placed so far in this partition
     // pilot seeds mix64(s ^ C) for s < 32, one per lane (most buckets need s < 32)
     const uint64_t ps_lane = pilot_seed(lane);
@@ -268,15 +345,12 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                 for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
                     steps++;
                     const uint32_t w = w0 + lane;
-                    uint32_t acc = 0;
-                    if (w < nw) {
-                        acc = (32 * w + 32 <= m) ? kFull : ((1u << (m - 32 * w)) - 1);
-                        acc &= window32(fw, h1 + 32 * w);
-                    }
+                    WT acc = 0;
+                    if (w < nw) acc = Wn::valid(w, m) & Wn::load(fw, h1 + kW * w);
                     uint32_t win = __ballot_sync(kFull, acc != 0);
                     if (win) {
                         uint32_t fl = __ffs(win) - 1;
-                        d1 = 32 * (w0 + fl) + __ffs(__shfl_sync(kFull, acc, fl)) - 1;
+                        d1 = kW * (w0 + fl) + Wn::first(Wn::shfl(acc, fl));
                         found = true;
                         break;
                     }
@@ -300,12 +374,22 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
             uint32_t d = 0;
             uint32_t s = 0;
             // lanes per window: chosen once per bucket from the current load
-            const uint32_t Lw = choose_lanes_per_window(k, m - placed, m);
-            const uint32_t G = 32 / Lw;  // windows per step
-            const uint32_t g = lane / Lw, rr = lane & (Lw - 1);
+            const uint32_t lg = choose_lanes_log2<kW>(k, m - placed, m);  // lanes per window: 2^lg
+            uint64_t bigkey[kBigRegs];
+            if (k > 32) {
+#pragma unroll
+                for (int t = 0; t < kBigRegs; t++) {
+                    const uint32_t i = lane + 32 * t;
+                    bigkey[t] = i < k ? keys[i] : 0;
+                }
+            }
             for (; s < a.s_max; s++) {
                 s_tries++;
-                const uint64_t ps = s < 32 ? __shfl_sync(kFull, ps_lane, s) : pilot_seed(s);
+                uint64_t ps;
+                if (s < 32)  // warp-uniform branch: never evaluate both sides
+                    ps = __shfl_sync(kFull, ps_lane, s);
+                else
+                    ps = pilot_seed(s);
                 bool coll = false;
                 if (k <= 32) {
                     h = lane < k ? position_hash(mykey, ps, m) : (0x80000000u | lane);
@@ -315,8 +399,25 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                         coll = __any_sync(kFull, __popc(peers) > 1);
                     }
                 } else {
+                    // large bucket: up to kBigRegs keys per lane stay in registers
+                    // across s values; the rest are re-read from the key store
                     bool c = false;
-                    for (uint32_t i = lane; i < k; i += 32) {
+                    uint32_t hv[kBigRegs];
+#pragma unroll
+                    for (int t = 0; t < kBigRegs; t++) {
+                        const uint32_t i = lane + 32 * t;
+                        hv[t] = i < k ? position_hash(bigkey[t], ps, m) : 0;
+                    }
+#pragma unroll
+                    for (int t = 0; t < kBigRegs; t++) {
+                        const uint32_t i = lane + 32 * t;
+                        if (i < k) {
+                            hb[i] = (uint16_t)hv[t];
+                            const uint32_t bit = 1u << (hv[t] & 31);
+                            if (atomicOr(&scr[hv[t] >> 5], bit) & bit) c = true;
+                        }
+                    }
+                    for (uint32_t i = lane + 32 * kBigRegs; i < k; i += 32) {
                         uint32_t hi = position_hash(keys[i], ps, m);
                         hb[i] = (uint16_t)hi;
                         uint32_t bit = 1u << (hi & 31);
@@ -333,32 +434,13 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                     }
                     continue;
                 }
-                // G windows of 32 displacements per step; lane rr of group g ANDs
-                // the windows of keys rr, rr + Lw, ... for window w0 + g
-                for (uint32_t w0 = 0; w0 < nw; w0 += G) {
-                    steps++;
-                    const uint32_t w = w0 + g;
-                    uint32_t acc = 0;
-                    if (w < nw) {
-                        acc = (32 * w + 32 <= m) ? kFull : ((1u << (m - 32 * w)) - 1);
-                        const uint32_t q0 = 32 * w;
-                        uint32_t i = rr;
-                        for (; i + Lw < k && acc; i += 2 * Lw) {
-                            uint32_t x0 = window32(fw, (uint32_t)hb[i] + q0);
-                            uint32_t x1 = window32(fw, (uint32_t)hb[i + Lw] + q0);
-                            acc &= x0 & x1;
-                        }
-                        if (i < k && acc) acc &= window32(fw, (uint32_t)hb[i] + q0);
-                    }
-                    for (uint32_t o = 1; o < Lw; o <<= 1) acc &= __shfl_xor_sync(kFull, acc, o);
-                    uint32_t win = __ballot_sync(kFull, acc != 0 && rr == 0);
-                    if (win) {
-                        uint32_t fl = __ffs(win) - 1;
-                        uint32_t av = __shfl_sync(kFull, acc, fl);
-                        d = 32 * (w0 + fl / Lw) + __ffs(av) - 1;
-                        found = true;
-                        break;
-                    }
+                switch (lg) {
+                    case 0: found = scan_windows<kW, 0>(fw, hb, k, m, nw, lane, d, steps); break;
+                    case 1: found = scan_windows<kW, 1>(fw, hb, k, m, nw, lane, d, steps); break;
+                    case 2: found = scan_windows<kW, 2>(fw, hb, k, m, nw, lane, d, steps); break;
+                    case 3: found = scan_windows<kW, 3>(fw, hb, k, m, nw, lane, d, steps); break;
+                    case 4: found = scan_windows<kW, 4>(fw, hb, k, m, nw, lane, d, steps); break;
+                    default: found = scan_windows<kW, 5>(fw, hb, k, m, nw, lane, d, steps); break;
                 }
                 if (found) break;
             }
@@ -379,8 +461,9 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
             const uint64_t limit = (uint64_t)a.s_max * m;
             uint32_t mypos = 0;
             if (k <= 32) {
-                const uint32_t Lc = pow2ceil(k), G = 32 / Lc;
-                const uint32_t g = lane / Lc, rr = lane & (Lc - 1);
+                const uint32_t lc = k <= 1 ? 0u : 32u - __clz(k - 1);  // log2 pow2ceil(k)
+                const uint32_t Lc = 1u << lc, G = 32u >> lc;
+                const uint32_t g = lane >> lc, rr = lane & (Lc - 1);
                 const uint64_t gkey = rr < k ? keys[rr] : 0;
                 const uint32_t gmask = Lc == 32 ? kFull : ((1u << Lc) - 1);
                 bool dup_checked = false;
@@ -410,7 +493,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                     bool gok = ((bad >> (g * Lc)) & gmask) == 0;
                     uint32_t win = __ballot_sync(kFull, gok && rr == 0);
                     if (win) {
-                        uint32_t gi = (__ffs(win) - 1) / Lc;
+                        uint32_t gi = (__ffs(win) - 1) >> lc;
                         p = (uint32_t)(p0 + gi);
                         mypos = __shfl_sync(kFull, pos, (lane & (Lc - 1)) + gi * Lc);
                         found = true;
@@ -506,69 +589,31 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
     }
 }
 
-// one block: n_j from the partition starts, m_j, exclusive scan into T, maxima
-__global__ void __launch_bounds__(1024) k_sizes(const uint64_t* __restrict__ start, uint64_t np, double alpha,
-                                                uint64_t* __restrict__ T, uint64_t* __restrict__ stats) {
-    __shared__ unsigned long long warp_sums[32];
-    __shared__ unsigned long long carry_s;
-    __shared__ unsigned long long maxn_s, maxm_s;
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        carry_s = 0;
-        maxn_s = 0;
-        maxm_s = 0;
+// m_j from the partition starts (alpha = 1: m_j = n_j; else ceil(n_j / alpha) in
+// IEEE double), plus the largest n_j and m_j
+__global__ void __launch_bounds__(256) k_table_sizes(const uint64_t* __restrict__ start, uint64_t np, double alpha,
+                                                     uint32_t* __restrict__ m_out,
+                                                     unsigned long long* __restrict__ maxima) {
+    unsigned long long mn = 0, mm = 0;
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < np; j += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t nj = start[j + 1] - start[j], mj;
+        if (alpha == 1.0) {
+            mj = nj;
+        } else {
+            mj = (uint64_t)ceil((double)nj / alpha);
+            if (mj < nj) mj = nj;
+        }
+        m_out[j] = (uint32_t)(mj < 0xFFFFFFFFull ? mj : 0xFFFFFFFFull);
+        mn = max(mn, (unsigned long long)nj);
+        mm = max(mm, (unsigned long long)mj);
     }
-    __syncthreads();
-    for (uint64_t c0 = 0; c0 < np; c0 += 1024) {
-        uint64_t j = c0 + tid;
-        uint64_t nj = 0, mj = 0;
-        if (j < np) {
-            nj = start[j + 1] - start[j];
-            if (alpha == 1.0) {
-                mj = nj;
-            } else {
-                mj = (uint64_t)ceil((double)nj / alpha);
-                if (mj < nj) mj = nj;
-            }
-        }
-        unsigned long long x = mj;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(kFull, x, o);
-            if (lane >= (uint32_t)o) x += y;
-        }
-        if (lane == 31) warp_sums[warp] = x;
-        unsigned long long mn = nj, mm = mj;
-        for (int o = 16; o; o >>= 1) {
-            mn = max(mn, __shfl_xor_sync(kFull, mn, o));
-            mm = max(mm, __shfl_xor_sync(kFull, mm, o));
-        }
-        if (lane == 0) {
-            atomicMax(&maxn_s, mn);
-            atomicMax(&maxm_s, mm);
-        }
-        __syncthreads();
-        if (warp == 0) {
-            unsigned long long s = warp_sums[lane], z = s;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long y = __shfl_up_sync(kFull, z, o);
-                if (lane >= (uint32_t)o) z += y;
-            }
-            warp_sums[lane] = z - s;
-        }
-        __syncthreads();
-        unsigned long long carry = carry_s;
-        if (j < np) T[j] = carry + warp_sums[warp] + x - mj;
-        __syncthreads();
-        if (tid == 1023) carry_s = carry + warp_sums[31] + x;
-        __syncthreads();
+    for (int o = 16; o; o >>= 1) {
+        mn = max(mn, __shfl_xor_sync(kFull, mn, o));
+        mm = max(mm, __shfl_xor_sync(kFull, mm, o));
     }
-    if (tid == 0) {
-        T[np] = carry_s;
-        stats[0] = carry_s;
-        stats[1] = maxn_s;
-        stats[2] = maxm_s;
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(maxima, mn);
+        atomicMax(maxima + 1, mm);
     }
 }
 
@@ -588,7 +633,11 @@ size_t search_smem_limit() {
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream) {
     const bool in_smem = a.keys_in_smem != 0;
     size_t smem = search_smem_bytes(a.cap_n, a.cap_m, a.B, in_smem);
-    auto kern = in_smem ? k_search<true> : k_search<false>;
+    void (*kern)(SearchLaunch);
+    if (a.window_bits == 64)
+        kern = in_smem ? k_search<true, 64> : k_search<false, 64>;
+    else
+        kern = in_smem ? k_search<true, 32> : k_search<false, 32>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (a.np > 0x7FFFFFFFull) return cudaErrorInvalidValue;
@@ -598,10 +647,26 @@ cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream) {
 }
 
 cudaError_t launch_sizes(const uint64_t* start, uint64_t np, double alpha, uint64_t* T, uint64_t* stats,
-                         cudaStream_t stream) {
-    k_sizes<<<1, 1024, 0, stream>>>(start, np, alpha, T, stats);
+                         void* scratch, cudaStream_t stream) {
+    // scratch: m_j (u32, np) | scan tile sums; stats[0] = M, stats[1] = max n_j, stats[2] = max m_j
+    uint32_t* m = static_cast<uint32_t*>(scratch);
+    unsigned long long* tiles = reinterpret_cast<unsigned long long*>(
+        static_cast<unsigned char*>(scratch) + ((np * 4 + 15) & ~uint64_t(15)));
+    cudaError_t e = cudaMemsetAsync(stats, 0, 3 * sizeof(uint64_t), stream);
+    if (e != cudaSuccess) return e;
+    uint64_t blocks = (np + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_table_sizes<<<(unsigned)blocks, 256, 0, stream>>>(start, np, alpha, m,
+                                                        reinterpret_cast<unsigned long long*>(stats + 1));
     note_launches(1);
-    return cudaGetLastError();
+    e = exclusive_scan_u32(m, np, reinterpret_cast<unsigned long long*>(T), tiles, stream);
+    if (e != cudaSuccess) return e;
+    // T[np] = M = grand total; stats[0] = M
+    e = cudaMemcpyAsync(T + np, scan_total(tiles, np), sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(stats, T + np, sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream);
 }
+
+size_t sizes_scratch_bytes(uint64_t np) { return ((np * 4 + 15) & ~uint64_t(15)) + scan_tiles_bytes(np); }
 
 }  // namespace phobic

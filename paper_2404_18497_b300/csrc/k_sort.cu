@@ -52,7 +52,14 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ 
         for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
     };
     if (vec) {
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < pairs; i += stride) {
+        uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+        for (; i + 3 * stride < pairs; i += 4 * stride) {  // four 16-byte loads in flight
+            ulonglong2 v0 = __ldcs(in2 + i), v1 = __ldcs(in2 + i + stride);
+            ulonglong2 v2 = __ldcs(in2 + i + 2 * stride), v3 = __ldcs(in2 + i + 3 * stride);
+            count(v0.x); count(v0.y); count(v1.x); count(v1.y);
+            count(v2.x); count(v2.y); count(v3.x); count(v3.y);
+        }
+        for (; i < pairs; i += stride) {
             ulonglong2 v = __ldcs(in2 + i);
             count(v.x);
             count(v.y);
@@ -69,18 +76,23 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ 
     }
 }
 
-// exclusive scan of each pass's digit histogram (one block per pass)
-__global__ void k_sort_hist_scan(unsigned long long* hist, uint32_t bits) {
-    const uint32_t R = 1u << bits;
-    if (threadIdx.x == 0) {
-        unsigned long long* h = hist + (uint64_t)blockIdx.x * R;
-        unsigned long long run = 0;
-        for (uint32_t d = 0; d < R; d++) {
-            unsigned long long c = h[d];
-            h[d] = run;
-            run += c;
-        }
+// exclusive scan of each pass's digit histogram (one block of 512 threads per pass)
+__global__ void __launch_bounds__(512) k_sort_hist_scan(unsigned long long* hist, uint32_t bits) {
+    __shared__ unsigned long long ws[16];
+    const uint32_t R = 1u << bits, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long* h = hist + (uint64_t)blockIdx.x * R;
+    const unsigned long long v = tid < R ? h[tid] : 0;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= (uint32_t)o) x += y;
     }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    unsigned long long off = 0;
+    for (uint32_t w = 0; w < warp; w++) off += ws[w];
+    if (tid < R) h[tid] = off + x - v;
 }
 
 struct PassArgs {
@@ -102,7 +114,7 @@ struct PassArgs {
 // per digit: prefix over warps, decoupled look-back for the tile's global
 // offset, a block scan for the tile-local digit starts, a shared-memory
 // reorder and a coalesced write-out.
-__global__ void __launch_bounds__(kThreads, 4) k_sort_pass(PassArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_sort_pass(PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t R = 1u << a.bits, mask = R - 1;
     uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);                      // kTile
@@ -153,7 +165,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(PassArgs a) {
         tile_start[d] = run;
     }
     __syncthreads();
-    // decoupled look-back per digit (publish the aggregate first)
+    // decoupled look-back per digit (publish the aggregate first); each thread
+    // reads up to 8 predecessors' states at once, so a long chain of
+    // aggregates costs one L2 round trip per 8 tiles instead of one per tile
     for (uint32_t d = tid; d < R; d += kThreads) {
         const uint64_t cnt = tile_start[d];
         volatile unsigned long long* st = a.status;
@@ -162,22 +176,32 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(PassArgs a) {
             st[d] = kFlagPre | cnt;
         } else {
             st[tile * R + d] = kFlagAgg | cnt;
-            int64_t t = (int64_t)tile - 1;
+            int64_t t = (int64_t)tile - 1;  // next predecessor to account for
             uint32_t spins = 0;
-            while (t >= 0) {
-                unsigned long long v = st[(uint64_t)t * R + d];
-                uint64_t flag = v & ~kValMask;
-                if (flag == 0) {
+            bool done = false;
+            while (!done) {
+                unsigned long long v[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) v[u] = (t - u >= 0) ? st[(uint64_t)(t - u) * R + d] : (kFlagPre | 0ull);
+                int u = 0;
+                for (; u < 8; u++) {
+                    const uint64_t flag = v[u] & ~kValMask;
+                    if (flag == 0) break;  // not published yet: poll again from here
+                    excl += v[u] & kValMask;
+                    if (flag == kFlagPre) {
+                        done = true;
+                        break;
+                    }
+                }
+                if (done) break;
+                t -= u;
+                if (u == 0) {
                     if (++spins > kSpinLimit) {
                         atomicMax(a.error, kDevTimeout);
                         break;
                     }
                     if (spins > 32) __nanosleep(64);
-                    continue;
                 }
-                excl += v & kValMask;
-                if (flag == kFlagPre) break;
-                t--;
             }
             st[tile * R + d] = kFlagPre | (excl + cnt);
         }
@@ -316,7 +340,7 @@ cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t k
         k_sort_hist<<<(unsigned)hblocks, 256, 8 * passes * R * 4, stream>>>(in, n, np, kseed, hash_input, passes, bits,
                                                                         hist);
         note_launches(1);
-        k_sort_hist_scan<<<passes, 32, 0, stream>>>(hist, bits);
+        k_sort_hist_scan<<<passes, 512, 0, stream>>>(hist, bits);
         note_launches(1);
         size_t smem = sort_pass_smem(bits);
         if ((e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=

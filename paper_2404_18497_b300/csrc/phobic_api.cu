@@ -207,6 +207,7 @@ phobic_status check_params(uint64_t n, const phobic_params& p) {
     if (p.partition_size == 0 || p.partition_size > kMaxPartitionSize) return PHOBIC_ERR_INVALID_ARG;
     if (p.encoder > PHOBIC_ENC_IC_D || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
     if (p.warps_per_partition > 1) return PHOBIC_ERR_INVALID_ARG;  // one warp per partition
+    if (p.candidate_width != 0 && p.candidate_width != 32 && p.candidate_width != 64) return PHOBIC_ERR_INVALID_ARG;
     return PHOBIC_OK;
 }
 
@@ -311,7 +312,9 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
     CK(launch_partition_sort(in, hash_input, kseed, n, NP, sorted, start, sort_scratch, status, st));
     CK(ev.mark(1, st));
     tmp.release(sort_scratch);
-    CK(launch_sizes(start, NP, prm.alpha, T, stats, st));
+    void* sizes_scratch;
+    CK(tmp.alloc(&sizes_scratch, sizes_scratch_bytes(NP)));
+    CK(launch_sizes(start, NP, prm.alpha, T, stats, sizes_scratch, st));
     CK(ev.mark(2, st));
     CK(d2h(hst, stats, 3, st));
     CK(d2h(reinterpret_cast<uint32_t*>(hst + 4), status, 1, st));
@@ -344,6 +347,7 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
     SearchLaunch sl;
     sl.bkeys = bkeys;
     sl.keys_in_smem = keys_in_smem ? 1 : 0;
+    sl.window_bits = prm.candidate_width == 32 ? 32 : 64;
     sl.sorted = sorted;
     sl.start = start;
     sl.T = T;
@@ -515,6 +519,7 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
     v.ef_low = h->ef_low;
     v.ef_high = h->ef_high;
     v.ef_samples = h->ef_samples;
+    v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
     account(h, w1, w2, K);
     if (ev.on) {
         h->has_timings = true;
@@ -833,6 +838,7 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     v.ef_low = h->ef_low;
     v.ef_high = h->ef_high;
     v.ef_samples = h->ef_samples;
+    v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
     I.device_bytes = (kTablePoints + 1) * 8 + 8 * (words - kHeaderWords);
     *out = h;
     return PHOBIC_OK;

@@ -53,14 +53,18 @@ __device__ __forceinline__ uint32_t position_hash(uint64_t hk, uint64_t ps, uint
 __device__ __forceinline__ uint64_t partition_of(uint64_t hk, uint64_t np) { return mulhi64(hk, np); }
 
 // Section 3.1 / Appendix C: bucket of normalised hash x from the fixed-point
-// table of gamma, by linear interpolation between table[k] and table[k+1].
+// table of gamma, by linear interpolation between table[k] and table[k+1]:
+// v = T_k + ((T_{k+1} - T_k) f >> 32), bucket = min(B - 1, v B >> 32).
+// The increments T_{k+1} - T_k are below 2^32, so the products are formed with
+// 32-bit multiplies; v >= 2^32 can only give bucket B - 1.
 __device__ __forceinline__ uint32_t bucket_of(uint64_t x, const uint64_t* __restrict__ table, uint32_t B) {
-    uint32_t k = (uint32_t)(x >> 53);
-    uint64_t f = (x >> 21) & 0xFFFFFFFFull;
-    uint64_t lo = __ldg(table + k), hi = __ldg(table + k + 1);
-    uint64_t v = lo + (((hi - lo) * f) >> 32);
-    uint64_t b = (v * (uint64_t)B) >> 32;
-    return b > B - 1 ? B - 1 : (uint32_t)b;
+    const uint32_t k = (uint32_t)(x >> 53);
+    const uint32_t f = (uint32_t)(x >> 21);
+    const uint64_t lo = __ldg(table + k), hi = __ldg(table + k + 1);
+    const uint64_t v = lo + __umulhi((uint32_t)(hi - lo), f);
+    if (v >> 32) return B - 1;
+    const uint32_t b = __umulhi((uint32_t)v, B);
+    return b > B - 1 ? B - 1 : b;
 }
 
 // number of bits of v (0 for 0)
@@ -83,6 +87,16 @@ __device__ __forceinline__ uint64_t read_bits(const uint64_t* __restrict__ words
     uint64_t v = lo >> sh;
     if (sh + w > 64) v |= __ldg(words + i + 1) << (64 - sh);
     return w == 64 ? v : (v & ((1ull << w) - 1));
+}
+
+// Read w <= 32 bits at bit offset o (o < 2^32 bits into the array) through the
+// 32-bit view of the little-endian packed words: one funnel shift of two
+// adjacent 32-bit words (the padding word keeps the second read in bounds).
+__device__ __forceinline__ uint32_t read_bits32(const uint64_t* __restrict__ words, uint32_t o, uint32_t w) {
+    const uint32_t* w32 = reinterpret_cast<const uint32_t*>(words);
+    const uint32_t i = o >> 5;
+    const uint32_t x = __funnelshift_r(__ldg(w32 + i), __ldg(w32 + i + 1), o & 31);
+    return w >= 32 ? x : (x & ((1u << w) - 1));
 }
 
 // words needed for `nbits` bits, including one padding word
@@ -111,6 +125,7 @@ struct QueryView {
     const uint64_t* ef_low;
     const uint64_t* ef_high;
     const uint64_t* ef_samples;
+    uint32_t small_bits;  // 1: every packed array has < 2^32 bits (32-bit offsets)
 };
 
 }  // namespace phobic

@@ -23,10 +23,19 @@ cudaError_t launch_hash_u64(const uint64_t* keys, uint64_t n, uint64_t kseed, ui
 cudaError_t launch_hash_strings(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint64_t seed,
                                 uint64_t* out, cudaStream_t stream);
 
+// ---- k_scan.cu: exclusive scan of u32 counts into u64 offsets ----
+constexpr uint32_t kScanTileItems = 4096;
+uint64_t scan_num_tiles(uint64_t n);
+size_t scan_tiles_bytes(uint64_t n);
+const unsigned long long* scan_total(const unsigned long long* tiles, uint64_t n);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint64_t n, unsigned long long* out, unsigned long long* tiles,
+                               cudaStream_t st);
+
 // ---- k_search.cu: partition sizes, table sizes, offsets T; bucketing + pilot search ----
-// stats[0] = M, stats[1] = max n_j, stats[2] = max m_j
+// T[0..np] = exclusive scan of m_j with T[np] = M; stats[0] = M, stats[1] = max n_j, stats[2] = max m_j
+size_t sizes_scratch_bytes(uint64_t np);
 cudaError_t launch_sizes(const uint64_t* start, uint64_t np, double alpha, uint64_t* T, uint64_t* stats,
-                         cudaStream_t stream);
+                         void* scratch, cudaStream_t stream);
 
 struct SearchLaunch {
     const uint64_t* sorted;
@@ -41,6 +50,7 @@ struct SearchLaunch {
     uint32_t cap_m; // largest m_j
     uint64_t* bkeys;       // [n] scratch for the bucket-sorted keys (used unless keys_in_smem)
     uint32_t keys_in_smem; // 1: keep each partition's keys in shared memory
+    uint32_t window_bits;  // displacements per lane-window: 32 or 64 (speed only)
     uint32_t* pilots;      // [B x np], zero-filled by the caller
     uint32_t* taken_bits;  // global occupancy bitmap over [0, M) in u32 words, zero-filled; may be null
     uint32_t* status;      // device status word (kDev* codes, atomicMax)

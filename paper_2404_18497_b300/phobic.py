@@ -49,6 +49,7 @@ class phobic_params(ctypes.Structure):
         ("warps_per_partition", ctypes.c_uint32),
         ("keep_pilots", ctypes.c_uint32),
         ("record_timings", ctypes.c_uint32),
+        ("candidate_width", ctypes.c_uint32),
     ]
 
 
@@ -139,7 +140,8 @@ def _dev_u64(t: torch.Tensor, what: str) -> torch.Tensor:
 
 
 def make_params(lam=7.0, alpha=1.0, P=2500, seed=0, encoder="IC-C", mode="additive", s_max=0,
-                keep_pilots=False, warps_per_partition=0, record_timings=False) -> phobic_params:
+                keep_pilots=False, warps_per_partition=0, record_timings=False,
+                candidate_width=0) -> phobic_params:
     p = phobic_params()
     lib().phobic_params_init(ctypes.byref(p))
     p.lambda_ = float(lam)
@@ -153,6 +155,7 @@ def make_params(lam=7.0, alpha=1.0, P=2500, seed=0, encoder="IC-C", mode="additi
     p.keep_pilots = 1 if keep_pilots else 0
     p.warps_per_partition = int(warps_per_partition)
     p.record_timings = 1 if record_timings else 0
+    p.candidate_width = int(candidate_width)
     return p
 
 

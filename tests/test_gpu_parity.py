@@ -221,3 +221,18 @@ def test_host_entry_points(ph, orc):
     assert ph.phobic_export(h1) == ph.phobic_export(h2)
     out = ph.phobic_query_host(h1, keys)
     assert np.array_equal(out, _host(h2.query(_dev(keys))))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_search_variants_agree(ph, orc, mode, monkeypatch):
+    """Window width (32 or 64 displacements per lane) and key placement (shared
+    memory or global scratch) change speed only: pilots equal the oracle's."""
+    keys = _keys(200_000, 31)
+    o = orc.Oracle(keys, lam=7.0, alpha=0.99, P=2500, mode=mode, threads=0)
+    for in_smem in ("0", "1"):
+        monkeypatch.setenv("PHOBIC_KEYS_IN_SMEM", in_smem)
+        for width in (32, 64):
+            h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, 0.99, 2500, mode=mode, keep_pilots=True,
+                                                              candidate_width=width))
+            assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots), (in_smem, width)
+            h.free()
