@@ -148,6 +148,20 @@ phobic_status phobic_query(const phobic_handle* h, const uint64_t* d_keys, uint6
 phobic_status phobic_query_host(const phobic_handle* h, const uint64_t* h_keys, uint64_t* h_out,
                                 uint64_t m, phobic_stream_t stream);
 
+/*
+ * String keys (Section 5: strings of 10-50 characters, reduced to 64-bit master
+ * hash codes with xxHash).  String i is d_bytes[d_offsets[i] .. d_offsets[i+1]);
+ * d_offsets has n+1 (m+1) entries and d_bytes must be readable for
+ * d_offsets[n] bytes.  The master hash is XXH64 with params->seed.  Two
+ * distinct strings with equal XXH64 give DUP_HASH (rebuild with another seed).
+ * Query semantics and errors as for 64-bit keys; a handle built from strings
+ * only answers phobic_query_strings, and a 64-bit handle only phobic_query.
+ */
+phobic_status phobic_build_strings(const uint8_t* d_bytes, const uint64_t* d_offsets, uint64_t n,
+                                   const phobic_params* params, phobic_stream_t stream, phobic_handle** out);
+phobic_status phobic_query_strings(const phobic_handle* h, const uint8_t* d_bytes, const uint64_t* d_offsets,
+                                   uint64_t* d_out, uint64_t m, phobic_stream_t stream);
+
 /* Space of the structure in bits per key (fixed accounting: header, offsets,
  * pilot encoders with their metadata, Elias-Fano remap).  NaN for NULL. */
 double phobic_bits_per_key(const phobic_handle* h);

@@ -11,6 +11,7 @@
 // the read-only path.
 #include "phobic_dev.cuh"
 #include "phobic_kernels.cuh"
+#include "phobic_xxh64.cuh"
 
 namespace phobic {
 
@@ -82,8 +83,13 @@ __device__ __forceinline__ uint64_t ef_access(const QueryView& v, uint64_t i) {
 
 constexpr int kSeedTable = 64;  // pilot seeds mix64(s ^ C) for s < 64, per block
 
+__device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds);
+
 __device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key, const uint64_t* seeds) {
-    const uint64_t hk = key_hash(key, v.kseed);
+    return query_hashed(v, key_hash(key, v.kseed), seeds);
+}
+
+__device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds) {
     const uint64_t j = partition_of(hk, v.NP);
     uint64_t Tj, Tj1;
     if (v.off_w <= 31) {
@@ -159,7 +165,33 @@ __global__ void __launch_bounds__(256) k_query(const QueryView v, const uint64_t
     }
 }
 
+// string keys: XXH64 master hash of each string (Section 5), then the same query
+__global__ void __launch_bounds__(256) k_query_strings(const QueryView v, const uint8_t* __restrict__ bytes,
+                                                       const uint64_t* __restrict__ offsets, uint64_t* __restrict__ out,
+                                                       uint64_t m) {
+    __shared__ uint64_t seeds[kSeedTable];
+    if (threadIdx.x < kSeedTable) seeds[threadIdx.x] = pilot_seed(threadIdx.x);
+    __syncthreads();
+    const uint64_t total = __ldg(offsets + m);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = query_hashed(v, string_master_hash(bytes, offsets, total, i, v.string_seed), seeds);
+}
+
 }  // namespace
+
+cudaError_t launch_query_strings(const QueryView& v, const uint8_t* bytes, const uint64_t* offsets, uint64_t* out,
+                                 uint64_t m, cudaStream_t stream) {
+    if (m == 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t want = (m + 255) / 256;
+    uint64_t cap = (uint64_t)sms * 8;
+    unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
+    k_query_strings<<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_query(const QueryView& v, const uint64_t* keys, uint64_t* out, uint64_t m, cudaStream_t stream) {
     if (m == 0) return cudaSuccess;

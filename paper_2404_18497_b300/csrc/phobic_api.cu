@@ -254,7 +254,7 @@ cudaError_t h2d(T* dev, const T* host, size_t count, cudaStream_t st) {
 // Builds from master hashes (already sorted by the caller's choice of path):
 // `in` holds raw keys (hash_input = 1) or master hashes (hash_input = 0).
 phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const phobic_params& prm, cudaStream_t st,
-                         phobic_handle** out) {
+                         phobic_handle** out, uint32_t key_kind = 0) {
     ensure_pool();
     const uint64_t NP = num_partitions(n, prm.partition_size);
     const uint32_t B = num_buckets(prm.lambda, prm.partition_size);
@@ -520,6 +520,8 @@ phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const p
     v.ef_high = h->ef_high;
     v.ef_samples = h->ef_samples;
     v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
+    v.key_kind = key_kind;
+    v.string_seed = prm.seed;
     account(h, w1, w2, K);
     if (ev.on) {
         h->has_timings = true;
@@ -608,7 +610,7 @@ phobic_status phobic_build_host(const uint64_t* h_keys, uint64_t n, const phobic
 
 phobic_status phobic_query(const phobic_handle* h, const uint64_t* d_keys, uint64_t* d_out, uint64_t m,
                            phobic_stream_t stream) {
-    if (!h) return PHOBIC_ERR_INVALID_ARG;
+    if (!h || h->view.key_kind != 0) return PHOBIC_ERR_INVALID_ARG;
     if (m == 0) return PHOBIC_OK;
     if (!d_keys || !d_out) return PHOBIC_ERR_INVALID_ARG;
     return from_cuda(launch_query(h->view, d_keys, d_out, m, (cudaStream_t)stream));
@@ -616,7 +618,7 @@ phobic_status phobic_query(const phobic_handle* h, const uint64_t* d_keys, uint6
 
 phobic_status phobic_query_host(const phobic_handle* h, const uint64_t* h_keys, uint64_t* h_out, uint64_t m,
                                 phobic_stream_t stream) {
-    if (!h) return PHOBIC_ERR_INVALID_ARG;
+    if (!h || h->view.key_kind != 0) return PHOBIC_ERR_INVALID_ARG;
     if (m == 0) return PHOBIC_OK;
     if (!h_keys || !h_out) return PHOBIC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -701,7 +703,7 @@ phobic_status phobic_export(const phobic_handle* h, void* h_buf, size_t* len) {
     std::memcpy(&lam, &I.lambda, 8);
     std::memcpy(&alp, &I.alpha, 8);
     uint64_t hdr[kHeaderWords] = {kMagic, kFormatVersion, I.n, I.M, I.num_partitions, I.num_buckets,
-                                  I.partition_size, lam, alp, I.seed, I.encoder, I.pilot_mode, h->view.off_w,
+                                  I.partition_size, lam, alp, I.seed, I.encoder, (uint64_t)I.pilot_mode | ((uint64_t)h->view.key_kind << 32), h->view.off_w,
                                   h->view.off_Q, (uint64_t)h->view.off_dmin, h->view.ef_l};
     for (int i = 0; i < 7; i++) hdr[16 + i] = counts[i];
     hdr[23] = I.bits_header;
@@ -737,6 +739,8 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     p.seed = w[9];
     p.encoder = (uint32_t)w[10];
     p.pilot_mode = (uint32_t)w[11];
+    const uint32_t key_kind = (uint32_t)(w[11] >> 32);
+    if (key_kind > 1) return PHOBIC_ERR_FORMAT;
     if (P != p.partition_size || check_params(n, p) != PHOBIC_OK) return PHOBIC_ERR_FORMAT;
     if (NP != num_partitions(n, p.partition_size) || B != num_buckets(p.lambda, p.partition_size) || M < n)
         return PHOBIC_ERR_FORMAT;
@@ -839,6 +843,8 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     v.ef_high = h->ef_high;
     v.ef_samples = h->ef_samples;
     v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
+    v.key_kind = key_kind;
+    v.string_seed = p.seed;
     I.device_bytes = (kTablePoints + 1) * 8 + 8 * (words - kHeaderWords);
     *out = h;
     return PHOBIC_OK;
@@ -878,6 +884,35 @@ phobic_status phobic_bucket_table(double lambda, double alpha, uint32_t partitio
 }
 
 }  // extern "C"
+
+extern "C" phobic_status phobic_build_strings(const uint8_t* d_bytes, const uint64_t* d_offsets, uint64_t n,
+                                              const phobic_params* params, phobic_stream_t stream,
+                                              phobic_handle** out) {
+    if (!out) return PHOBIC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!d_bytes || !d_offsets || !params) return PHOBIC_ERR_INVALID_ARG;
+    phobic_status s = check_params(n, *params);
+    if (s != PHOBIC_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    ensure_pool();
+    uint64_t* hk = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&hk, n * 8, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    e = launch_hash_strings(d_bytes, d_offsets, n, params->seed, hk, st);
+    if (e == cudaSuccess) s = build_impl(hk, 0, n, *params, st, out, 1);
+    else s = from_cuda(e);
+    cudaFreeAsync(hk, st);
+    return s;
+}
+
+extern "C" phobic_status phobic_query_strings(const phobic_handle* h, const uint8_t* d_bytes,
+                                              const uint64_t* d_offsets, uint64_t* d_out, uint64_t m,
+                                              phobic_stream_t stream) {
+    if (!h || h->view.key_kind != 1) return PHOBIC_ERR_INVALID_ARG;
+    if (m == 0) return PHOBIC_OK;
+    if (!d_bytes || !d_offsets || !d_out) return PHOBIC_ERR_INVALID_ARG;
+    return from_cuda(launch_query_strings(h->view, d_bytes, d_offsets, d_out, m, (cudaStream_t)stream));
+}
 
 extern "C" phobic_status phobic_hash_strings(const uint8_t* d_bytes, const uint64_t* d_offsets, uint64_t n,
                                              uint64_t seed, uint64_t* d_hk, phobic_stream_t stream) {

@@ -126,6 +126,9 @@ struct QueryView {
     const uint64_t* ef_high;
     const uint64_t* ef_samples;
     uint32_t small_bits;  // 1: every packed array has < 2^32 bits (32-bit offsets)
+    uint32_t key_kind;    // 0: 64-bit keys, 1: byte strings (XXH64 with string_seed)
+    uint64_t string_seed;
 };
+
 
 }  // namespace phobic

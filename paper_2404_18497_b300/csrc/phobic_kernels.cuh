@@ -92,5 +92,7 @@ cudaError_t launch_remap(const uint32_t* taken_bits, uint64_t n, uint64_t M, uin
 
 // ---- k_query.cu ----
 cudaError_t launch_query(const QueryView& v, const uint64_t* keys, uint64_t* out, uint64_t m, cudaStream_t stream);
+cudaError_t launch_query_strings(const QueryView& v, const uint8_t* bytes, const uint64_t* offsets, uint64_t* out,
+                                 uint64_t m, cudaStream_t stream);
 
 }  // namespace phobic

@@ -81,6 +81,8 @@ _SIGS = [
     ("phobic_build_ex", _INT, [_VP, _U64, _PP, _VP, ctypes.POINTER(_VP)]),
     ("phobic_build_host", _INT, [_VP, _U64, _PP, _VP, ctypes.POINTER(_VP)]),
     ("phobic_query", _INT, [_VP, _VP, _VP, _U64, _VP]),
+    ("phobic_build_strings", _INT, [_VP, _VP, _U64, _PP, _VP, ctypes.POINTER(_VP)]),
+    ("phobic_query_strings", _INT, [_VP, _VP, _VP, _VP, _U64, _VP]),
     ("phobic_query_host", _INT, [_VP, _VP, _VP, _U64, _VP]),
     ("phobic_bits_per_key", _DBL, [_VP]),
     ("phobic_get_info", _INT, [_VP, ctypes.POINTER(phobic_info)]),
@@ -235,6 +237,33 @@ def phobic_query(h: Handle, keys: torch.Tensor, out: Optional[torch.Tensor] = No
     return out
 
 
+def _dev_bytes(t: torch.Tensor, what: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.uint8 or not t.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous CUDA uint8 tensor")
+    return t
+
+
+def phobic_build_strings(data: torch.Tensor, offsets: torch.Tensor, params: phobic_params, stream=None) -> Handle:
+    d = _dev_bytes(data, "data")
+    o = _dev_u64(offsets, "offsets")
+    h = ctypes.c_void_p()
+    _check(lib().phobic_build_strings(d.data_ptr(), o.data_ptr(), o.numel() - 1, ctypes.byref(params),
+                                      _stream(stream), ctypes.byref(h)), "phobic_build_strings")
+    return Handle(h.value)
+
+
+def phobic_query_strings(h: Handle, data: torch.Tensor, offsets: torch.Tensor, out: Optional[torch.Tensor] = None,
+                         stream=None) -> torch.Tensor:
+    d = _dev_bytes(data, "data")
+    o = _dev_u64(offsets, "offsets")
+    m = o.numel() - 1
+    if out is None:
+        out = torch.empty(max(m, 0), dtype=torch.int64, device=o.device)
+    _check(lib().phobic_query_strings(h.ptr, d.data_ptr(), o.data_ptr(), out.data_ptr(), m, _stream(stream)),
+           "phobic_query_strings")
+    return out
+
+
 def phobic_query_host(h: Handle, keys: np.ndarray, out: Optional[np.ndarray] = None, stream=None) -> np.ndarray:
     k = np.ascontiguousarray(keys).view(np.uint64)
     if out is None:
@@ -353,6 +382,8 @@ ARRAYS = ["off_words", "col_meta", "pil_words", "dict_words", "ef_low", "ef_high
 def parse_export(data: bytes) -> dict:
     w = np.frombuffer(data, dtype=np.uint64)
     hdr = {k: int(w[i]) for i, k in enumerate(HEADER_FIELDS)}
+    hdr["key_kind"] = hdr["pilot_mode"] >> 32
+    hdr["pilot_mode"] &= 0xFFFFFFFF
     hdr["off_dmin"] = int(np.uint64(hdr["off_dmin"]).astype(np.int64))
     at = len(HEADER_FIELDS)
     for name in ARRAYS:

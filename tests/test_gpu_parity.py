@@ -236,3 +236,44 @@ def test_search_variants_agree(ph, orc, mode, monkeypatch):
                                                               candidate_width=width))
             assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots), (in_smem, width)
             h.free()
+
+
+@pytest.mark.parametrize("n,lam,alpha,enc", [(1, 7.5, 0.99, 0), (50_000, 7.5, 0.99, 1), (1_000_000, 7.5, 0.99, 1),
+                                             (300_000, 7.0, 1.0, 0)])
+def test_string_build_and_query_parity(ph, orc, n, lam, alpha, enc):
+    """Section 5's input: random strings of length 10-50 over [A-Za-z0-9],
+    reduced to XXH64 master hashes on the device; then the same construction."""
+    from paper_2404_18497_b300 import workloads
+
+    data, off = workloads.random_strings(n, 40 + n)
+    hk = orc.string_hashes(data, off, 9)
+    o = orc.Oracle(hashed=hk, lam=lam, alpha=alpha, P=2500, encoder=enc, seed=9, threads=0)
+    dd, do = torch.from_numpy(data).cuda(), _dev(off)
+    h = ph.phobic_build_strings(dd, do, ph.make_params(lam, alpha, 2500, seed=9, encoder=enc, keep_pilots=True))
+    assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots)
+    compare_structure(ph, o, h, enc)
+    got = _host(ph.phobic_query_strings(h, dd, do))
+    assert np.array_equal(got, o.query_hashed(hk))
+    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint64))
+    # a string handle refuses 64-bit queries, and the other way round
+    with pytest.raises(ph.PhobicError):
+        ph.phobic_query(h, _dev(np.arange(4, dtype=np.uint64)))
+    # export / import keeps the key kind
+    h2 = ph.phobic_import(ph.phobic_export(h))
+    assert np.array_equal(_host(ph.phobic_query_strings(h2, dd, do)), got)
+
+
+def test_string_hash_unaligned_and_tails(ph, orc):
+    """Strings at every byte alignment and every tail length, including the last
+    bytes of the buffer (no read past offsets[n])."""
+    rng = np.random.default_rng(77)
+    lens = np.concatenate([np.arange(0, 80), rng.integers(0, 80, size=5000)])
+    off = np.zeros(lens.size + 1, dtype=np.uint64)
+    np.cumsum(lens, out=off[1:])
+    data = rng.integers(0, 256, size=int(off[-1]), dtype=np.uint8)
+    for shift in (0, 1, 3, 7):
+        buf = torch.zeros(data.size + 8, dtype=torch.uint8, device="cuda")
+        view = buf[shift:shift + data.size]
+        view.copy_(torch.from_numpy(data))
+        got = _host(ph.phobic_hash_strings(view, _dev(off), 123))
+        assert np.array_equal(got, orc.string_hashes(data, off, 123))
