@@ -73,6 +73,8 @@ typedef struct {
     uint32_t record_timings;      /* nonzero: time the build phases with CUDA events on `stream` */
     uint32_t candidate_width;     /* search tuning: displacements per lane-window, 32 or 64 (0 = default 64);
                                      results do not depend on it */
+    uint32_t search_schedule;     /* search tuning: 0 auto, 1 one CTA per partition, 2 persistent CTAs taking
+                                     partitions from a device work queue; results do not depend on it */
 } phobic_params;
 
 /* Device time of each build phase (CUDA events recorded on the build stream
@@ -125,6 +127,23 @@ phobic_status phobic_build(const uint64_t* d_keys, uint64_t n, double lambda, do
 /* Same, with every parameter of phobic_params. */
 phobic_status phobic_build_ex(const uint64_t* d_keys, uint64_t n, const phobic_params* params,
                               phobic_stream_t stream, phobic_handle** out);
+
+/*
+ * Batched construction: n_sets independent key sets stored back to back in
+ * d_keys, set s being d_keys[h_set_offsets[s] .. h_set_offsets[s+1]) (host array
+ * of n_sets + 1 entries, strictly increasing: every set non-empty).  Each set
+ * gets its own MPHF, exactly as phobic_build_ex would build it alone, with
+ * partition size h_partition_sizes[s] (host array; NULL = params->partition_size
+ * for all).  One segmented partition sort, one persistent search launch over the
+ * partitions of all sets (device work queue) and one launch per encoding step
+ * serve the whole batch.  out_handles[s] receives set s's handle; the handles
+ * share one device allocation, released when the last of them is freed (each
+ * must still be passed to phobic_free).  Errors as phobic_build_ex, for the
+ * whole batch (no handle is returned on error).
+ */
+phobic_status phobic_build_batch(const uint64_t* d_keys, const uint64_t* h_set_offsets, uint32_t n_sets,
+                                 const uint32_t* h_partition_sizes, const phobic_params* params,
+                                 phobic_stream_t stream, phobic_handle** out_handles);
 
 /* Same, from host memory: the keys are copied in chunks through pinned staging
  * buffers and hashed on the device as they arrive. */

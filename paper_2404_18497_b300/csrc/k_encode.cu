@@ -1,4 +1,5 @@
-// K5 + K6: partition offsets and interleaved pilot encoders.
+// K5 + K6: partition offsets and interleaved pilot encoders, for every key set
+// of a build in one launch per step.
 //
 // Offsets (Section 4, "Encoding the offsets of the partitions"): partition
 // sizes are implicit as differences of consecutive offsets T_j, and each T_j is
@@ -7,7 +8,7 @@
 // bit-packed at a common width.
 //
 // Interleaved coding (Section 4.1): encoder b stores the pilot of bucket b of
-// every partition.  The pilot matrix is already column-major, so column b is
+// every partition.  The pilot matrix of a set is column-major, so column b is
 // one contiguous run of N_P values.
 //   IC-C (Compact): width = bit length of the column's largest pilot.
 //   IC-D (Dictionary): the column's sorted distinct pilots, bit-packed at the
@@ -15,8 +16,9 @@
 //   bit-packed at the bit length of (#distinct - 1).  The distinct values are
 //   found by marking a presence bitmap over [0, max]; a rank is a prefix
 //   popcount over that bitmap.
-// Packing is a gather: each thread assembles one 64-bit output word from the
-// values that overlap it.  Words shared by two columns use atomicOr.
+// Columns of all sets are described by ColDesc records; packing is a gather in
+// which each thread assembles one 64-bit output word from the values that
+// overlap it (atomicOr where two columns share a word).
 #include "phobic_dev.cuh"
 #include "phobic_kernels.cuh"
 
@@ -24,46 +26,14 @@ namespace phobic {
 
 namespace {
 
-constexpr uint64_t kMeta = (1ull << 56) - 1;
-
 __device__ __forceinline__ uint64_t expectation(uint64_t j, uint64_t Q) {
     uint64_t lo = j * Q, hi = __umul64hi(j, Q);
     return (hi << 32) | (lo >> 32);
 }
 
-__global__ void __launch_bounds__(1024) k_offset_minmax(const uint64_t* __restrict__ T, uint64_t np, uint64_t Q,
-                                                        long long* mm) {
-    __shared__ long long smin[32], smax[32];
-    long long lo = LLONG_MAX, hi = LLONG_MIN;
-    for (uint64_t j = threadIdx.x; j <= np; j += blockDim.x) {
-        long long d = (long long)(T[j] - expectation(j, Q));
-        lo = min(lo, d);
-        hi = max(hi, d);
-    }
-    for (int o = 16; o; o >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
-        hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        smin[threadIdx.x >> 5] = lo;
-        smax[threadIdx.x >> 5] = hi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
-            lo = min(lo, smin[w]);
-            hi = max(hi, smax[w]);
-        }
-        lo = min(lo, smin[0]);
-        hi = max(hi, smax[0]);
-        mm[0] = lo;
-        mm[1] = hi;
-    }
-}
-
-// Assemble output word `word` (absolute word index) from values i in [0, count)
-// placed at bit base + i*w; value(i) supplies the value.  Only bits of this
-// column are produced; the caller combines columns.
+// Assemble output word `word` (index inside the array) from values i in
+// [0, count) placed at bit base + i*w; value(i) supplies the value.  Only this
+// column's bits are produced.
 template <class F>
 __device__ __forceinline__ uint64_t gather_word(uint64_t word, uint64_t base, uint32_t w, uint64_t count, F value) {
     if (w == 0 || count == 0) return 0;
@@ -78,48 +48,19 @@ __device__ __forceinline__ uint64_t gather_word(uint64_t word, uint64_t base, ui
     for (uint64_t i = i0; i <= i1; i++) {
         uint64_t v = value(i) & vmask;
         uint64_t o = base + i * w;  // first bit of value i
-        if (o >= wlo) {
-            uint64_t sh = o - wlo;
-            acc |= v << sh;  // sh < 64
-        } else {
-            uint64_t sh = wlo - o;  // 0 < sh < w <= 64
-            acc |= v >> sh;
-        }
+        if (o >= wlo)
+            acc |= v << (o - wlo);  // shift < 64
+        else
+            acc |= v >> (wlo - o);  // 0 < shift < w <= 64
     }
-    // keep only the bits of [lo, hi)
     uint64_t a = lo - wlo, b = hi - wlo;  // 0 <= a < b <= 64
     uint64_t keep = (b == 64 ? ~0ull : ((1ull << b) - 1)) & ~((1ull << a) - 1);
     return acc & keep;
 }
 
-__global__ void k_offset_pack(const uint64_t* __restrict__ T, uint64_t np, uint64_t Q, int64_t dmin, uint32_t w,
-                              uint64_t* __restrict__ words, uint64_t nwords) {
-    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < nwords; k += (uint64_t)gridDim.x * blockDim.x) {
-        words[k] = gather_word(k, 0, w, np + 1, [&](uint64_t j) {
-            return (uint64_t)((long long)(T[j] - expectation(j, Q)) - dmin);
-        });
-    }
-}
-
-__global__ void __launch_bounds__(256) k_column_max(const uint32_t* __restrict__ pilots, uint64_t np,
-                                                    uint32_t* __restrict__ colmax) {
-    __shared__ uint32_t sm[8];
-    const uint32_t* col = pilots + (uint64_t)blockIdx.x * np;
-    uint32_t mx = 0;
-    for (uint64_t j = threadIdx.x; j < np; j += blockDim.x) mx = max(mx, __ldg(col + j));
-    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < 8; i++) mx = max(mx, sm[i]);
-        colmax[blockIdx.x] = mx;
-    }
-}
-
-// column of flat thread index t: col_word_begin is a prefix sum over columns of
-// the number of output words each column touches
-__device__ __forceinline__ uint32_t find_column(const uint64_t* __restrict__ begin, uint32_t ncols, uint64_t t) {
-    uint32_t lo = 0, hi = ncols;  // answer in [0, ncols)
+// largest index c in [0, n) with begin[c] <= t (begin non-decreasing, begin[0] = 0)
+__device__ __forceinline__ uint32_t find_item(const uint64_t* __restrict__ begin, uint32_t n, uint64_t t) {
+    uint32_t lo = 0, hi = n;
     while (hi - lo > 1) {
         uint32_t mid = (lo + hi) >> 1;
         if (__ldg(begin + mid) <= t) lo = mid; else hi = mid;
@@ -127,128 +68,191 @@ __device__ __forceinline__ uint32_t find_column(const uint64_t* __restrict__ beg
     return lo;
 }
 
-__global__ void k_compact_pack(const uint32_t* __restrict__ pilots, uint64_t np, uint32_t B,
-                               const uint64_t* __restrict__ col_meta, const uint64_t* __restrict__ col_word_begin,
-                               uint64_t* __restrict__ words) {
-    const uint64_t total = col_word_begin[B];
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t b = find_column(col_word_begin, B, t);
-        uint64_t meta = __ldg(col_meta + b);
-        uint64_t base = meta & kMeta;
-        uint32_t w = (uint32_t)(meta >> 56);
-        uint64_t word = (base >> 6) + (t - col_word_begin[b]);
-        const uint32_t* col = pilots + (uint64_t)b * np;
-        uint64_t v = gather_word(word, base, w, np, [&](uint64_t j) { return (uint64_t)__ldg(col + j); });
-        uint64_t cend = base + np * w;
-        bool interior = word * 64 >= base && word * 64 + 64 <= cend;
-        if (interior) words[word] = v;
-        else if (v) atomicOr((unsigned long long*)(words + word), (unsigned long long)v);
-    }
+__device__ __forceinline__ void put_word(uint64_t* words, uint64_t word, uint64_t v, bool interior) {
+    if (interior)
+        words[word] = v;
+    else if (v)
+        atomicOr((unsigned long long*)(words + word), (unsigned long long)v);
 }
 
-__global__ void k_dict_mark(const uint32_t* __restrict__ pilots, uint64_t np, uint32_t B,
-                            const uint64_t* __restrict__ bm_base, uint64_t* __restrict__ bitmaps) {
-    const uint64_t total = np * B;
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t b = (uint32_t)(t / np);
-        uint32_t v = __ldg(pilots + t);
-        atomicOr((unsigned long long*)(bitmaps + bm_base[b] + (v >> 6)), 1ull << (v & 63));
-    }
-}
-
-// one block per column: exclusive popcount prefix of its bitmap words
-__global__ void __launch_bounds__(1024) k_dict_rank(const uint64_t* __restrict__ bm_base,
-                                                    uint64_t* __restrict__ bitmaps_rank,
-                                                    const uint64_t* __restrict__ bitmaps, uint64_t* __restrict__ K) {
-    __shared__ uint32_t warp_sums[32];
-    __shared__ unsigned long long carry_s;
-    const uint32_t b = blockIdx.x;
-    const uint64_t w0 = bm_base[b], w1 = bm_base[b + 1];
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry_s = 0;
-    __syncthreads();
-    for (uint64_t c = w0; c < w1; c += 1024) {
-        uint64_t i = c + tid;
-        uint32_t v = i < w1 ? __popcll(bitmaps[i]) : 0;
-        uint32_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if (lane >= (uint32_t)o) x += y;
+// ---------------------------------------------------------------- offsets ---
+__global__ void __launch_bounds__(256) k_offset_minmax(const uint64_t* __restrict__ T,
+                                                       const OffDesc* __restrict__ sets, uint32_t nsets,
+                                                       long long* __restrict__ mm) {
+    __shared__ long long smin[8], smax[8];
+    for (uint32_t s = blockIdx.x; s < nsets; s += gridDim.x) {
+        const OffDesc d = sets[s];
+        const uint64_t T0 = T[d.part_base];
+        long long lo = LLONG_MAX, hi = LLONG_MIN;
+        for (uint64_t j = threadIdx.x; j <= d.np; j += blockDim.x) {
+            long long v = (long long)(T[d.part_base + j] - T0 - expectation(j, d.Q));
+            lo = min(lo, v);
+            hi = max(hi, v);
         }
-        if (lane == 31) warp_sums[warp] = x;
+        for (int o = 16; o; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            smin[threadIdx.x >> 5] = lo;
+            smax[threadIdx.x >> 5] = hi;
+        }
         __syncthreads();
-        if (warp == 0) {
-            uint32_t s = warp_sums[lane], z = s;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
-                if (lane >= (uint32_t)o) z += y;
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < 8; w++) {
+                lo = min(lo, smin[w]);
+                hi = max(hi, smax[w]);
             }
-            warp_sums[lane] = z - s;
+            mm[2 * s] = lo;
+            mm[2 * s + 1] = hi;
         }
         __syncthreads();
-        unsigned long long carry = carry_s;
-        if (i < w1) bitmaps_rank[i] = carry + warp_sums[warp] + x - v;
+    }
+}
+
+__global__ void k_offset_pack(const uint64_t* __restrict__ T, const OffDesc* __restrict__ sets, uint32_t nsets,
+                              const uint64_t* __restrict__ word_begin, uint64_t* __restrict__ arena) {
+    const uint64_t total = word_begin[nsets];
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = find_item(word_begin, nsets, t);
+        const OffDesc d = sets[s];
+        const uint64_t word = t - word_begin[s];
+        const uint64_t T0 = T[d.part_base];
+        arena[d.dst_word + word] = gather_word(word, 0, d.width, d.np + 1, [&](uint64_t j) {
+            return (uint64_t)((long long)(T[d.part_base + j] - T0 - expectation(j, d.Q)) - d.dmin);
+        });
+    }
+}
+
+// ---------------------------------------------------------------- columns ---
+__global__ void __launch_bounds__(256) k_column_max(const uint32_t* __restrict__ pilots,
+                                                    const ColDesc* __restrict__ cols, uint32_t ncols,
+                                                    uint32_t* __restrict__ colmax) {
+    __shared__ uint32_t sm[8];
+    for (uint32_t c = blockIdx.x; c < ncols; c += gridDim.x) {
+        const ColDesc d = cols[c];
+        uint32_t mx = 0;
+        for (uint64_t j = threadIdx.x; j < d.count; j += blockDim.x) mx = max(mx, __ldg(pilots + d.src + j));
+        mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
         __syncthreads();
-        if (tid == 1023) carry_s = carry + warp_sums[31] + x;
+        if (threadIdx.x == 0) {
+            for (int i = 1; i < 8; i++) mx = max(mx, sm[i]);
+            colmax[c] = mx;
+        }
         __syncthreads();
     }
-    if (tid == 0) K[b] = carry_s;
 }
 
 __device__ __forceinline__ uint64_t dict_rank_of(uint32_t v, uint64_t wbase, const uint64_t* __restrict__ bitmaps,
                                                  const uint64_t* __restrict__ bitmaps_rank) {
-    uint64_t wi = wbase + (v >> 6);
-    uint64_t below = (v & 63) ? (__ldg(bitmaps + wi) & ((1ull << (v & 63)) - 1)) : 0;
+    const uint64_t wi = wbase + (v >> 6);
+    const uint64_t below = (v & 63) ? (__ldg(bitmaps + wi) & ((1ull << (v & 63)) - 1)) : 0;
     return __ldg(bitmaps_rank + wi) + __popcll(below);
 }
 
-__global__ void k_dict_pack_ranks(const uint32_t* __restrict__ pilots, uint64_t np, uint32_t B,
-                                  const uint64_t* __restrict__ bm_base, const uint64_t* __restrict__ bitmaps,
-                                  const uint64_t* __restrict__ bitmaps_rank, const uint64_t* __restrict__ col_meta,
-                                  const uint64_t* __restrict__ word_begin, uint64_t* __restrict__ words) {
-    const uint64_t total = word_begin[B];
+// IC-C data (kRanks = false) or IC-D ranks (kRanks = true) of every column
+template <bool kRanks>
+__global__ void k_pack_columns(const uint32_t* __restrict__ pilots, const ColDesc* __restrict__ cols, uint32_t ncols,
+                               const uint64_t* __restrict__ word_begin, const uint64_t* __restrict__ bitmaps,
+                               const uint64_t* __restrict__ bitmaps_rank, uint64_t* __restrict__ arena) {
+    const uint64_t total = word_begin[ncols];
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t b = find_column(word_begin, B, t);
-        uint64_t meta = __ldg(col_meta + 2 * b);
-        uint64_t base = meta & kMeta;
-        uint32_t w = (uint32_t)(meta >> 56);
-        uint64_t word = (base >> 6) + (t - word_begin[b]);
-        const uint32_t* col = pilots + (uint64_t)b * np;
-        const uint64_t wb = bm_base[b];
-        uint64_t v = gather_word(word, base, w, np,
-                                 [&](uint64_t j) { return dict_rank_of(__ldg(col + j), wb, bitmaps, bitmaps_rank); });
-        uint64_t cend = base + np * w;
-        bool interior = word * 64 >= base && word * 64 + 64 <= cend;
-        if (interior) words[word] = v;
-        else if (v) atomicOr((unsigned long long*)(words + word), (unsigned long long)v);
+        const uint32_t c = find_item(word_begin, ncols, t);
+        const ColDesc d = cols[c];
+        const uint64_t word = (d.base >> 6) + (t - word_begin[c]);
+        const uint32_t* col = pilots + d.src;
+        uint64_t v;
+        if (kRanks)
+            v = gather_word(word, d.base, d.width, d.count,
+                            [&](uint64_t j) { return dict_rank_of(__ldg(col + j), d.bm_base, bitmaps, bitmaps_rank); });
+        else
+            v = gather_word(word, d.base, d.width, d.count, [&](uint64_t j) { return (uint64_t)__ldg(col + j); });
+        const uint64_t cend = d.base + d.count * d.width;
+        put_word(arena + d.dst_word, word, v, word * 64 >= d.base && word * 64 + 64 <= cend);
     }
 }
 
-// dictionary entries: thread per bitmap word; each set bit v with rank r writes
-// v at bit dbase + r * dw
-__global__ void k_dict_pack_values(uint32_t B, const uint64_t* __restrict__ bm_base,
-                                   const uint64_t* __restrict__ bitmaps, const uint64_t* __restrict__ bitmaps_rank,
-                                   const uint64_t* __restrict__ col_meta, uint64_t* __restrict__ words) {
-    const uint64_t total = bm_base[B];
+// IC-D presence bitmaps: bit v of column c's bitmap is set when v occurs
+__global__ void __launch_bounds__(256) k_dict_mark(const uint32_t* __restrict__ pilots,
+                                                   const ColDesc* __restrict__ cols, uint32_t ncols,
+                                                   uint64_t* __restrict__ bitmaps) {
+    for (uint32_t c = blockIdx.x; c < ncols; c += gridDim.x) {
+        const ColDesc d = cols[c];
+        for (uint64_t j = threadIdx.x; j < d.count; j += blockDim.x) {
+            const uint32_t v = __ldg(pilots + d.src + j);
+            atomicOr((unsigned long long*)(bitmaps + d.bm_base + (v >> 6)), 1ull << (v & 63));
+        }
+    }
+}
+
+// one block per column: exclusive popcount prefix of its bitmap words, and the
+// number of distinct values K
+__global__ void __launch_bounds__(1024) k_dict_rank(const ColDesc* __restrict__ cols, uint32_t ncols,
+                                                    uint64_t* __restrict__ bitmaps_rank,
+                                                    const uint64_t* __restrict__ bitmaps, uint64_t* __restrict__ K) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ unsigned long long carry_s;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t c = blockIdx.x; c < ncols; c += gridDim.x) {
+        const uint64_t w0 = cols[c].bm_base, w1 = w0 + cols[c].bm_words;
+        if (tid == 0) carry_s = 0;
+        __syncthreads();
+        for (uint64_t cc = w0; cc < w1; cc += 1024) {
+            uint64_t i = cc + tid;
+            uint32_t v = i < w1 ? __popcll(bitmaps[i]) : 0;
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            if (lane == 31) warp_sums[warp] = x;
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t s = warp_sums[lane], z = s;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+                    if (lane >= (uint32_t)o) z += y;
+                }
+                warp_sums[lane] = z - s;
+            }
+            __syncthreads();
+            unsigned long long carry = carry_s;
+            if (i < w1) bitmaps_rank[i] = carry + warp_sums[warp] + x - v;
+            __syncthreads();
+            if (tid == 1023) carry_s = carry + warp_sums[31] + x;
+            __syncthreads();
+        }
+        if (tid == 0) K[c] = carry_s;
+        __syncthreads();
+    }
+}
+
+// IC-D dictionaries: thread per bitmap word; each set bit v with rank r writes
+// v at bit dict_base + r * dict_width of its set's dictionary array
+__global__ void k_dict_pack_values(const ColDesc* __restrict__ cols, uint32_t ncols,
+                                   const uint64_t* __restrict__ bm_begin, const uint64_t* __restrict__ bitmaps,
+                                   const uint64_t* __restrict__ bitmaps_rank, uint64_t* __restrict__ arena) {
+    const uint64_t total = bm_begin[ncols];
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t bits = bitmaps[t];
         if (!bits) continue;
-        uint32_t b = find_column(bm_base, B, t);
-        uint64_t meta = __ldg(col_meta + 2 * b + 1);
-        uint64_t base = meta & kMeta;
-        uint32_t w = (uint32_t)(meta >> 56);
+        const uint32_t c = find_item(bm_begin, ncols, t);
+        const ColDesc d = cols[c];
+        const uint32_t w = d.dict_width;
+        uint64_t* words = arena + d.dict_dst_word;
         uint64_t r = bitmaps_rank[t];
-        uint64_t v0 = (t - bm_base[b]) * 64;
+        const uint64_t v0 = (t - d.bm_base) * 64;
         while (bits) {
-            uint32_t bit = __ffsll((long long)bits) - 1;
+            const uint32_t bit = __ffsll((long long)bits) - 1;
             bits &= bits - 1;
-            uint64_t v = v0 + bit;
+            const uint64_t v = v0 + bit;
             if (w) {
-                uint64_t o = base + r * w;
-                uint64_t wi = o >> 6;
-                uint32_t sh = (uint32_t)(o & 63);
+                const uint64_t o = d.dict_base + r * w;
+                const uint64_t wi = o >> 6;
+                const uint32_t sh = (uint32_t)(o & 63);
                 atomicOr((unsigned long long*)(words + wi), (unsigned long long)(v << sh));
                 if (sh + w > 64) atomicOr((unsigned long long*)(words + wi + 1), (unsigned long long)(v >> (64 - sh)));
             }
@@ -263,59 +267,63 @@ unsigned grid_for(uint64_t work, unsigned threads) {
     return (unsigned)(g ? g : 1);
 }
 
+unsigned grid_items(uint64_t items) { return (unsigned)(items < 65535ull * 4 ? (items ? items : 1) : 65535ull * 4); }
+
 }  // namespace
 
-cudaError_t launch_offset_minmax(const uint64_t* T, uint64_t np, uint64_t Q, long long* mm, cudaStream_t stream) {
-    k_offset_minmax<<<1, 1024, 0, stream>>>(T, np, Q, mm);
+cudaError_t launch_offset_minmax(const uint64_t* T, const OffDesc* sets, uint32_t nsets, long long* mm,
+                                 cudaStream_t stream) {
+    k_offset_minmax<<<grid_items(nsets), 256, 0, stream>>>(T, sets, nsets, mm);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_offset_pack(const uint64_t* T, uint64_t np, uint64_t Q, int64_t dmin, uint32_t w, uint64_t* words,
-                               uint64_t nwords, cudaStream_t stream) {
-    k_offset_pack<<<grid_for(nwords, 256), 256, 0, stream>>>(T, np, Q, dmin, w, words, nwords);
+cudaError_t launch_offset_pack(const uint64_t* T, const OffDesc* sets, uint32_t nsets, const uint64_t* word_begin,
+                               uint64_t total_words, uint64_t* arena, cudaStream_t stream) {
+    k_offset_pack<<<grid_for(total_words, 256), 256, 0, stream>>>(T, sets, nsets, word_begin, arena);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_column_max(const uint32_t* pilots, uint64_t np, uint32_t B, uint32_t* colmax, cudaStream_t stream) {
-    k_column_max<<<B, 256, 0, stream>>>(pilots, np, colmax);
+cudaError_t launch_column_max(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint32_t* colmax,
+                              cudaStream_t stream) {
+    k_column_max<<<grid_items(ncols), 256, 0, stream>>>(pilots, cols, ncols, colmax);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_pack(const uint32_t* pilots, uint64_t np, uint32_t B, const uint64_t* col_meta,
-                                const uint64_t* col_word_begin, uint64_t* words, uint64_t total_colwords,
-                                cudaStream_t stream) {
-    k_compact_pack<<<grid_for(total_colwords, 256), 256, 0, stream>>>(pilots, np, B, col_meta, col_word_begin, words);
+cudaError_t launch_pack_columns(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, const uint64_t* word_begin,
+                                uint64_t total_words, bool ranks, const uint64_t* bitmaps,
+                                const uint64_t* bitmaps_rank, uint64_t* arena, cudaStream_t stream) {
+    if (ranks)
+        k_pack_columns<true><<<grid_for(total_words, 256), 256, 0, stream>>>(pilots, cols, ncols, word_begin, bitmaps,
+                                                                             bitmaps_rank, arena);
+    else
+        k_pack_columns<false><<<grid_for(total_words, 256), 256, 0, stream>>>(pilots, cols, ncols, word_begin,
+                                                                              bitmaps, bitmaps_rank, arena);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_dict_mark(const uint32_t* pilots, uint64_t np, uint32_t B, const uint64_t* bm_base,
-                             uint64_t* bitmaps, cudaStream_t stream) {
-    k_dict_mark<<<grid_for(np * B, 256), 256, 0, stream>>>(pilots, np, B, bm_base, bitmaps);
-    note_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_dict_rank(const uint64_t* bm_base, uint32_t B, uint64_t* bitmaps_rank, const uint64_t* bitmaps,
-                             uint64_t* K, cudaStream_t stream) {
-    k_dict_rank<<<B, 1024, 0, stream>>>(bm_base, bitmaps_rank, bitmaps, K);
-    note_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_dict_pack(const uint32_t* pilots, uint64_t np, uint32_t B, const uint64_t* bm_base,
-                             const uint64_t* bitmaps, const uint64_t* bitmaps_rank, const uint64_t* col_meta,
-                             const uint64_t* rank_word_begin, uint64_t* rank_words, uint64_t rank_colwords,
-                             const uint64_t* /*dict_word_begin*/, uint64_t* dict_words, uint64_t bitmap_words,
+cudaError_t launch_dict_mark(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* bitmaps,
                              cudaStream_t stream) {
-    k_dict_pack_ranks<<<grid_for(rank_colwords, 256), 256, 0, stream>>>(pilots, np, B, bm_base, bitmaps, bitmaps_rank,
-                                                                        col_meta, rank_word_begin, rank_words);
+    k_dict_mark<<<grid_items(ncols), 256, 0, stream>>>(pilots, cols, ncols, bitmaps);
     note_launches(1);
-    k_dict_pack_values<<<grid_for(bitmap_words, 256), 256, 0, stream>>>(B, bm_base, bitmaps, bitmaps_rank, col_meta,
-                                                                        dict_words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dict_rank(const ColDesc* cols, uint32_t ncols, uint64_t* bitmaps_rank, const uint64_t* bitmaps,
+                             uint64_t* K, cudaStream_t stream) {
+    k_dict_rank<<<grid_items(ncols), 1024, 0, stream>>>(cols, ncols, bitmaps_rank, bitmaps, K);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dict_pack_values(const ColDesc* cols, uint32_t ncols, const uint64_t* bm_begin,
+                                    uint64_t total_bm_words, const uint64_t* bitmaps, const uint64_t* bitmaps_rank,
+                                    uint64_t* arena, cudaStream_t stream) {
+    k_dict_pack_values<<<grid_for(total_bm_words, 256), 256, 0, stream>>>(cols, ncols, bm_begin, bitmaps, bitmaps_rank,
+                                                                          arena);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -1,4 +1,5 @@
-// K7: remap of slots >= n onto free slots < n (alpha < 1).
+// K7: remap of slots >= n onto free slots < n (alpha < 1), for every key set of
+// a build in one launch per step.
 //
 // Section 5 ("Further Remarks") names PTHash's non-minimal trick.  The search
 // runs on M = sum m_j > n slots.  Afterwards every occupied slot q >= n is sent
@@ -10,10 +11,11 @@
 // value; the high part in unary, with bit (fs_i >> l) + i set; and the position
 // of every 64th one kept as a select sample.
 //
-// Device steps: popcounts per 32-bit word of the occupancy bitmap, exclusive
-// scans (three-phase: block sums, scan of the sums, block scan with carry),
-// then compaction of F and the per-slot gather of fs.  The Elias-Fano words
-// are built last.
+// Each set's slots occupy bits [g0, g0 + M) of one global occupancy bitmap.
+// Device steps: popcounts of the 32-bit words covering each set's [g0, g0 + n)
+// (free slots) and [g0 + n, g0 + M) (occupied), flattened over all sets; two
+// exclusive scans; compaction of F; the per-slot gather of fs; then the
+// Elias-Fano words, written into each set's arrays.
 #include "phobic_dev.cuh"
 #include "phobic_kernels.cuh"
 
@@ -21,82 +23,127 @@ namespace phobic {
 
 namespace {
 
-constexpr uint64_t kScanTile = kScanTileItems;
-
-// count of bits in word w of the region [lo, hi) of a u32 bitmap; `want_zero`
-// counts free slots instead of occupied ones
+// bits of word w of a u32 bitmap inside the global bit range [lo, hi);
+// `want_zero` selects free slots instead of occupied ones
 __device__ __forceinline__ uint32_t region_bits(const uint32_t* bm, uint64_t w, uint64_t lo, uint64_t hi, bool want_zero) {
     uint32_t v = bm[w];
     if (want_zero) v = ~v;
-    uint64_t b0 = w * 32;
+    const uint64_t b0 = w * 32;
     uint32_t mask = 0xFFFFFFFFu;
-    if (b0 < lo) mask &= 0xFFFFFFFFu << (uint32_t)(lo - b0);
-    if (b0 + 32 > hi) mask &= (hi - b0 >= 32) ? 0xFFFFFFFFu : ((1u << (uint32_t)(hi - b0)) - 1);
+    if (b0 < lo) mask &= (lo - b0 >= 32) ? 0u : (0xFFFFFFFFu << (uint32_t)(lo - b0));
+    if (b0 + 32 > hi) mask &= (hi <= b0) ? 0u : ((hi - b0 >= 32) ? 0xFFFFFFFFu : ((1u << (uint32_t)(hi - b0)) - 1));
     return v & mask;
 }
 
-__global__ void __launch_bounds__(256) k_count_words(const uint32_t* __restrict__ bm, uint64_t w0, uint64_t nw,
-                                                              uint64_t lo, uint64_t hi, int want_zero,
-                                                              uint32_t* __restrict__ cnt) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nw; i += (uint64_t)gridDim.x * blockDim.x)
-        cnt[i] = __popc(region_bits(bm, w0 + i, lo, hi, want_zero != 0));
+__device__ __forceinline__ uint32_t find_set(const uint64_t* __restrict__ begin, uint32_t n, uint64_t t) {
+    uint32_t lo = 0, hi = n;  // largest s with begin[s] <= t
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(begin + mid) <= t) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
-// F: free slots below n, in order (only the first cap entries are needed)
-__global__ void k_free_list(const uint32_t* __restrict__ bm, uint64_t nw, uint64_t n,
-                            const unsigned long long* __restrict__ zoff, uint64_t* __restrict__ F, uint64_t cap) {
-    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nw; w += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t z = region_bits(bm, w, 0, n, true);
-        unsigned long long r = zoff[w];
+// kind 0: free slots of [g0, g0 + n); kind 1: occupied slots of [g0 + n, g0 + M)
+template <int kind>
+__global__ void k_count_words(const uint32_t* __restrict__ bm, const RemapDesc* __restrict__ sets, uint32_t nsets,
+                              const uint64_t* __restrict__ begin, uint32_t* __restrict__ cnt) {
+    const uint64_t total = begin[nsets];
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = find_set(begin, nsets, t);
+        const RemapDesc d = sets[s];
+        const uint64_t lo = kind == 0 ? d.g0 : d.g0 + d.n;
+        const uint64_t hi = kind == 0 ? d.g0 + d.n : d.g0 + d.M;
+        const uint64_t w = (lo >> 5) + (t - begin[s]);
+        cnt[t] = __popc(region_bits(bm, w, lo, hi, kind == 0));
+    }
+}
+
+__device__ __forceinline__ unsigned long long scan_at(const unsigned long long* off, uint64_t i, uint64_t n,
+                                                      const unsigned long long* total) {
+    return i < n ? off[i] : *total;
+}
+
+// F: free slots below n (set-local positions), in order; only the first N are needed
+__global__ void k_free_list(const uint32_t* __restrict__ bm, const RemapDesc* __restrict__ sets, uint32_t nsets,
+                            const uint64_t* __restrict__ zbegin, const unsigned long long* __restrict__ zoff,
+                            uint64_t* __restrict__ F) {
+    const uint64_t total = zbegin[nsets];
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = find_set(zbegin, nsets, t);
+        const RemapDesc d = sets[s];
+        const uint64_t w = (d.g0 >> 5) + (t - zbegin[s]);
+        uint32_t z = region_bits(bm, w, d.g0, d.g0 + d.n, true);
+        unsigned long long r = zoff[t] - zoff[zbegin[s]];
+        const uint64_t cap = d.M - d.n;
         while (z && r < cap) {
-            uint32_t b = __ffs(z) - 1;
+            const uint32_t b = __ffs(z) - 1;
             z &= z - 1;
-            F[r++] = w * 32 + b;
+            F[d.f_base + r++] = w * 32 + b - d.g0;
         }
     }
 }
 
-// fs[q - n] for q in [n, M)
-__global__ void k_fill_fs(const uint32_t* __restrict__ bm, uint64_t n, uint64_t M, uint64_t w0,
+// fs[q - n] for q in [n, M) of every set (flattened: entry f_base + i of set s)
+__global__ void k_fill_fs(const uint32_t* __restrict__ bm, const RemapDesc* __restrict__ sets, uint32_t nsets,
+                          const uint64_t* __restrict__ fbegin, const uint64_t* __restrict__ tbegin,
                           const unsigned long long* __restrict__ toff, const unsigned long long* __restrict__ ttotal,
                           const uint64_t* __restrict__ F, uint64_t* __restrict__ fs) {
-    const unsigned long long nF = *ttotal;
-    for (uint64_t q = n + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < M; q += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t w = q >> 5;
-        uint32_t below = region_bits(bm, w, n, q, false);
-        unsigned long long r = toff[w - w0] + __popc(below);
-        fs[q - n] = nF ? F[r < nF ? r : nF - 1] : 0;
+    const uint64_t total = fbegin[nsets];
+    const uint64_t tw_total = tbegin[nsets];
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = find_set(fbegin, nsets, t);
+        const RemapDesc d = sets[s];
+        const uint64_t q = d.n + (t - d.f_base);  // set-local slot
+        const uint64_t gb = d.g0 + q;             // global bit
+        const uint64_t w = gb >> 5;
+        const uint64_t lo = d.g0 + d.n;
+        const uint64_t widx = tbegin[s] + (w - (lo >> 5));
+        const unsigned long long base = scan_at(toff, tbegin[s], tw_total, ttotal);
+        const unsigned long long nF = scan_at(toff, tbegin[s + 1], tw_total, ttotal) - base;
+        const unsigned long long r = toff[widx] - base + __popc(region_bits(bm, w, lo, gb, false));
+        fs[t] = nF ? F[d.f_base + (r < nF ? r : nF - 1)] : 0;
     }
 }
 
-__global__ void k_ef_low(const uint64_t* __restrict__ fs, uint64_t N, uint32_t l, uint64_t* __restrict__ low,
-                         uint64_t nwords) {
-    const uint64_t lmask = l ? ((1ull << l) - 1) : 0;
-    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < nwords; k += (uint64_t)gridDim.x * blockDim.x) {
+__global__ void k_ef_low(const RemapDesc* __restrict__ sets, uint32_t nsets, const uint64_t* __restrict__ lbegin,
+                         const uint64_t* __restrict__ fs, uint64_t* __restrict__ arena) {
+    const uint64_t total = lbegin[nsets];
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = find_set(lbegin, nsets, t);
+        const RemapDesc d = sets[s];
+        const uint64_t k = t - lbegin[s];
+        const uint32_t l = d.l;
+        const uint64_t N = d.M - d.n;
         uint64_t acc = 0;
         if (l) {
-            uint64_t wlo = k * 64, whi = wlo + 64, end = N * l;
+            const uint64_t lmask = (1ull << l) - 1;
+            const uint64_t wlo = k * 64, whi = wlo + 64, end = N * l;
             if (wlo < end) {
-                uint64_t hi = whi < end ? whi : end;
-                uint64_t i0 = wlo / l, i1 = (hi - 1) / l;
+                const uint64_t hi = whi < end ? whi : end;
+                const uint64_t i0 = wlo / l, i1 = (hi - 1) / l;
                 for (uint64_t i = i0; i <= i1; i++) {
-                    uint64_t v = fs[i] & lmask, o = i * l;
+                    const uint64_t v = fs[d.f_base + i] & lmask, o = i * l;
                     acc |= o >= wlo ? (v << (o - wlo)) : (v >> (wlo - o));
                 }
-                uint64_t b = hi - wlo;
+                const uint64_t b = hi - wlo;
                 if (b < 64) acc &= (1ull << b) - 1;
             }
         }
-        low[k] = acc;
+        arena[d.low_dst + k] = acc;
     }
 }
 
-__global__ void k_ef_high(const uint64_t* __restrict__ fs, uint64_t N, uint32_t l, uint64_t* __restrict__ high,
-                          uint64_t* __restrict__ samples) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t pos = (fs[i] >> l) + i;
-        atomicOr((unsigned long long*)(high + (pos >> 6)), 1ull << (pos & 63));
-        if ((i & 63) == 0) samples[i >> 6] = pos;
+__global__ void k_ef_high(const RemapDesc* __restrict__ sets, uint32_t nsets, const uint64_t* __restrict__ fbegin,
+                          const uint64_t* __restrict__ fs, uint64_t* __restrict__ arena) {
+    const uint64_t total = fbegin[nsets];
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = find_set(fbegin, nsets, t);
+        const RemapDesc d = sets[s];
+        const uint64_t i = t - d.f_base;
+        const uint64_t pos = (fs[t] >> d.l) + i;
+        atomicOr((unsigned long long*)(arena + d.high_dst + (pos >> 6)), 1ull << (pos & 63));
+        if ((i & 63) == 0) arena[d.samp_dst + (i >> 6)] = pos;
     }
 }
 
@@ -108,53 +155,50 @@ unsigned grid_for(uint64_t work, unsigned threads) {
 
 }  // namespace
 
-size_t remap_scratch_bytes(uint64_t n, uint64_t M) {
-    uint64_t nw0 = (n + 31) / 32;                       // words of [0, n)
-    uint64_t w0 = n >> 5, nw1 = ((M - 1) >> 5) - w0 + 1; // words of [n, M)
-    uint64_t N = M - n;
+size_t remap_scratch_bytes(uint64_t zwords, uint64_t twords, uint64_t ntotal) {
     size_t s = 0;
-    s += (nw0 + nw1) * 4 + 16;                          // counts
-    s += (nw0 + nw1) * 8 + 16;                          // scans
-    s += 2 * ((nw0 + kScanTile - 1) / kScanTile + (nw1 + kScanTile - 1) / kScanTile + 4) * 8; // tile sums
-    s += (N + 1) * 8;                                   // F
+    s += (zwords + twords) * 4 + 32;  // counts
+    s += (zwords + twords) * 8 + 32;  // scans
+    s += scan_tiles_bytes(zwords) + scan_tiles_bytes(twords) + 32;
+    s += (ntotal + 1) * 8;            // F
+    s += (ntotal + 1) * 8;            // fs
     return s + 256;
 }
 
-cudaError_t launch_remap(const uint32_t* taken_bits, uint64_t n, uint64_t M, uint32_t l, uint64_t* fs,
-                         uint64_t* ef_low, uint64_t low_nwords, uint64_t* ef_high, uint64_t high_nwords,
-                         uint64_t* ef_samples, void* scratch, cudaStream_t st) {
-    const uint64_t N = M - n;
-    const uint64_t nw0 = (n + 31) / 32;
-    const uint64_t w0 = n >> 5, nw1 = ((M - 1) >> 5) - w0 + 1;
+cudaError_t launch_remap(const uint32_t* bm, const RemapDesc* d_sets, uint32_t nsets, const uint64_t* d_zbegin,
+                         uint64_t zwords, const uint64_t* d_tbegin, uint64_t twords, const uint64_t* d_fbegin,
+                         uint64_t ntotal, const uint64_t* d_lbegin, uint64_t lwords, uint64_t* arena, void* scratch,
+                         cudaStream_t st) {
     unsigned char* p = static_cast<unsigned char*>(scratch);
     auto take = [&](size_t bytes) {
         void* r = p;
         p += (bytes + 15) & ~size_t(15);
         return r;
     };
-    uint32_t* zc = (uint32_t*)take(nw0 * 4);
-    uint32_t* tc = (uint32_t*)take(nw1 * 4);
-    unsigned long long* zoff = (unsigned long long*)take(nw0 * 8);
-    unsigned long long* toff = (unsigned long long*)take(nw1 * 8);
-    unsigned long long* ztiles = (unsigned long long*)take(((nw0 + kScanTile - 1) / kScanTile + 2) * 8);
-    unsigned long long* ttiles = (unsigned long long*)take(((nw1 + kScanTile - 1) / kScanTile + 2) * 8);
-    uint64_t* F = (uint64_t*)take((N + 1) * 8);
+    uint32_t* zc = (uint32_t*)take(zwords * 4 + 4);
+    uint32_t* tc = (uint32_t*)take(twords * 4 + 4);
+    unsigned long long* zoff = (unsigned long long*)take(zwords * 8 + 8);
+    unsigned long long* toff = (unsigned long long*)take(twords * 8 + 8);
+    unsigned long long* ztiles = (unsigned long long*)take(scan_tiles_bytes(zwords));
+    unsigned long long* ttiles = (unsigned long long*)take(scan_tiles_bytes(twords));
+    uint64_t* F = (uint64_t*)take((ntotal + 1) * 8);
+    uint64_t* fs = (uint64_t*)take((ntotal + 1) * 8);
 
-    k_count_words<<<grid_for(nw0, 256), 256, 0, st>>>(taken_bits, 0, nw0, 0, n, 1, zc);
+    k_count_words<0><<<grid_for(zwords, 256), 256, 0, st>>>(bm, d_sets, nsets, d_zbegin, zc);
     note_launches(1);
-    k_count_words<<<grid_for(nw1, 256), 256, 0, st>>>(taken_bits, w0, nw1, n, M, 0, tc);
+    k_count_words<1><<<grid_for(twords, 256), 256, 0, st>>>(bm, d_sets, nsets, d_tbegin, tc);
     note_launches(1);
     cudaError_t e;
-    if ((e = exclusive_scan_u32(zc, nw0, zoff, ztiles, st)) != cudaSuccess) return e;
-    if ((e = exclusive_scan_u32(tc, nw1, toff, ttiles, st)) != cudaSuccess) return e;
-    k_free_list<<<grid_for(nw0, 256), 256, 0, st>>>(taken_bits, nw0, n, zoff, F, N);
+    if ((e = exclusive_scan_u32(zc, zwords, zoff, ztiles, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan_u32(tc, twords, toff, ttiles, st)) != cudaSuccess) return e;
+    k_free_list<<<grid_for(zwords, 256), 256, 0, st>>>(bm, d_sets, nsets, d_zbegin, zoff, F);
     note_launches(1);
-    k_fill_fs<<<grid_for(N, 256), 256, 0, st>>>(taken_bits, n, M, w0, toff, scan_total(ttiles, nw1), F, fs);
+    k_fill_fs<<<grid_for(ntotal, 256), 256, 0, st>>>(bm, d_sets, nsets, d_fbegin, d_tbegin, toff,
+                                                     scan_total(ttiles, twords), F, fs);
     note_launches(1);
-    if ((e = cudaMemsetAsync(ef_high, 0, high_nwords * 8, st)) != cudaSuccess) return e;
-    k_ef_low<<<grid_for(low_nwords, 256), 256, 0, st>>>(fs, N, l, ef_low, low_nwords);
+    k_ef_low<<<grid_for(lwords, 256), 256, 0, st>>>(d_sets, nsets, d_lbegin, fs, arena);
     note_launches(1);
-    k_ef_high<<<grid_for(N, 256), 256, 0, st>>>(fs, N, l, ef_high, ef_samples);
+    k_ef_high<<<grid_for(ntotal, 256), 256, 0, st>>>(d_sets, nsets, d_fbegin, fs, arena);
     note_launches(1);
     return cudaGetLastError();
 }

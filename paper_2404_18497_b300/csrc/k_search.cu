@@ -192,12 +192,11 @@ __device__ bool bucket_has_dup(const uint64_t* keys, uint32_t k, uint32_t lane) 
 // sorted input, L2-resident while the partition is active).  Each bucket's keys
 // are prefetched into registers one bucket ahead, and shared memory shrinks to
 // the bitmaps and counters, so several times more partitions fit on an SM.
-template <bool kKeysInSmem, int kW>
-__global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
+template <bool kKeysInSmem, int kW, int kMode>
+__device__ __forceinline__ void search_partition(const SearchLaunch& a, const SearchSet& S, const uint64_t gid,
+                                                 const uint64_t j, unsigned char* smem, const SmemLayout& L) {
     using Wn = Win<kW>;
     using WT = typename Wn::T;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout L = smem_layout(a.cap_n, a.cap_m, a.B, kKeysInSmem);
     uint32_t* bend = reinterpret_cast<uint32_t*>(smem + L.off_bend);
     uint32_t* order = reinterpret_cast<uint32_t*>(smem + L.off_order);
     uint32_t* fw = reinterpret_cast<uint32_t*>(smem + L.off_fw);
@@ -205,12 +204,13 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
     uint16_t* aux = reinterpret_cast<uint16_t*>(smem + L.off_aux);
 
     const uint32_t lane = threadIdx.x;
-    const uint64_t j = blockIdx.x;
-    const uint64_t s0 = a.start[j];
-    const uint32_t nj = (uint32_t)(a.start[j + 1] - s0);
-    const uint64_t Tj = a.T[j];
-    const uint32_t m = (uint32_t)(a.T[j + 1] - Tj);
-    const uint32_t B = a.B;
+    const uint64_t s0 = a.start[gid];
+    const uint32_t nj = (uint32_t)(a.start[gid + 1] - s0);
+    const uint64_t Tj = a.T[gid];
+    const uint32_t m = (uint32_t)(a.T[gid + 1] - Tj);
+    const uint32_t B = S.B;
+    const uint64_t* const table = S.table;
+    uint32_t* const pil = a.pilots + S.pilot_base + j;  // pilot of bucket b at pil[b * S.np]
     if (nj == 0) return;
     uint64_t* hk = kKeysInSmem ? reinterpret_cast<uint64_t*>(smem + L.off_hk) : a.bkeys + s0;
 
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
     // ---- 1. bucket counts, then counting sort of the keys by bucket
     for (uint32_t i = lane; i < nj; i += 32) {
         uint64_t x = __ldg(a.sorted + s0 + i);
-        atomicAdd(&bend[bucket_of(bucket_hash(x), a.table, B)], 1u);
+        atomicAdd(&bend[bucket_of(bucket_hash(x), table, B)], 1u);
     }
     __syncwarp();
     uint32_t local_err = kDevOk;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
     __syncwarp();
     for (uint32_t i = lane; i < nj; i += 32) {
         uint64_t x = __ldg(a.sorted + s0 + i);
-        uint32_t b = bucket_of(bucket_hash(x), a.table, B);
+        uint32_t b = bucket_of(bucket_hash(x), table, B);
         hk[atomicAdd(&bend[b], 1u)] = x;
     }
     __syncwarp();
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
         }
         bool found = false;
         uint32_t p = 0;
-        if (a.mode == 0) {
+        if (kMode == 0) {
             // ===== additive displacement =====
             uint16_t* hb = aux;  // h(x, s) of the bucket's keys
             if (k == 1) {
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
                 }
                 placed += 1;
                 __syncwarp();
-                if (lane == 0) a.pilots[(uint64_t)b * a.np + j] = p;
+                if (lane == 0) pil[(uint64_t)b * S.np] = p;
                 continue;
             }
             uint32_t h = 0;
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
             }
         }
         __syncwarp();
-        if (lane == 0) a.pilots[(uint64_t)b * a.np + j] = p;
+        if (lane == 0) pil[(uint64_t)b * S.np] = p;
     }
 
     if (local_err != kDevOk) {
@@ -589,6 +589,34 @@ __global__ void __launch_bounds__(32) k_search(SearchLaunch a) {
     }
 }
 
+// One warp per CTA.  kQueue = true: persistent kernel, every CTA takes the next
+// partition (a global partition id over every key set of the launch) from a
+// device work queue until none are left.  kQueue = false: CTA g processes
+// partition g.  The order in which partitions are processed does not change any
+// result.
+template <bool kKeysInSmem, int kW, int kMode, bool kQueue>
+__global__ void __launch_bounds__(32, 32) k_search(SearchLaunch a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemLayout L = smem_layout(a.cap_n, a.cap_m, a.cap_B, kKeysInSmem);
+    unsigned long long gid = blockIdx.x;
+    for (;;) {
+        if (kQueue) {
+            if (threadIdx.x == 0) gid = atomicAdd(a.queue, 1ull);
+            gid = __shfl_sync(kFull, gid, 0);
+            if (gid >= a.total_parts) break;
+        }
+        uint32_t lo = 0, hi = a.nsets;  // key set: largest s with part_base <= gid
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.sets[mid].part_base <= gid) lo = mid; else hi = mid;
+        }
+        const SearchSet S = a.sets[lo];
+        search_partition<kKeysInSmem, kW, kMode>(a, S, gid, gid - S.part_base, smem, L);
+        if (!kQueue) break;
+        __syncwarp();
+    }
+}
+
 // m_j from the partition starts (alpha = 1: m_j = n_j; else ceil(n_j / alpha) in
 // IEEE double), plus the largest n_j and m_j
 __global__ void __launch_bounds__(256) k_table_sizes(const uint64_t* __restrict__ start, uint64_t np, double alpha,
@@ -617,7 +645,23 @@ __global__ void __launch_bounds__(256) k_table_sizes(const uint64_t* __restrict_
     }
 }
 
+__global__ void k_gather_u64(const uint64_t* __restrict__ src, const uint64_t* __restrict__ idx,
+                             uint64_t* __restrict__ out, uint64_t count) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = src[idx[i]];
+}
+
 }  // namespace
+
+cudaError_t launch_gather_u64(const uint64_t* src, const uint64_t* idx, uint64_t* out, uint64_t count,
+                              cudaStream_t stream) {
+    if (count == 0) return cudaSuccess;
+    uint64_t blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_gather_u64<<<(unsigned)blocks, 256, 0, stream>>>(src, idx, out, count);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem) {
     return smem_layout(cap_n, cap_m, B, keys_in_smem).total;
@@ -632,16 +676,34 @@ size_t search_smem_limit() {
 
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream) {
     const bool in_smem = a.keys_in_smem != 0;
-    size_t smem = search_smem_bytes(a.cap_n, a.cap_m, a.B, in_smem);
+    size_t smem = search_smem_bytes(a.cap_n, a.cap_m, a.cap_B, in_smem);
     void (*kern)(SearchLaunch);
-    if (a.window_bits == 64)
-        kern = in_smem ? k_search<true, 64> : k_search<false, 64>;
-    else
-        kern = in_smem ? k_search<true, 32> : k_search<false, 32>;
+    const bool q = a.use_queue != 0;
+#define PICK(SM, W, MD) kern = q ? k_search<SM, W, MD, true> : k_search<SM, W, MD, false>
+    if (a.mode != 0) {  // PTHash XOR pilots: the window width does not apply
+        if (in_smem) PICK(true, 32, 1); else PICK(false, 32, 1);
+    } else if (a.window_bits == 64) {
+        if (in_smem) PICK(true, 64, 0); else PICK(false, 64, 0);
+    } else {
+        if (in_smem) PICK(true, 32, 0); else PICK(false, 32, 0);
+    }
+#undef PICK
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (a.np > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-    kern<<<(unsigned)a.np, 32, smem, stream>>>(a);
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = a.total_parts;
+    if (q) {
+        grid = (uint64_t)sms * per_sm;  // persistent: every CTA resident, work from the queue
+        if (grid > a.total_parts) grid = a.total_parts;
+        if ((e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream)) != cudaSuccess) return e;
+    }
+    if (grid == 0) return cudaSuccess;
+    if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    kern<<<(unsigned)grid, 32, smem, stream>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }

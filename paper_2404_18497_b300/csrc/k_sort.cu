@@ -9,6 +9,12 @@
 // look-back over its predecessors and writes the tile out in digit order.  When
 // the input is raw 64-bit keys, the upfront pass and the first digit pass hash
 // them on the fly, so no separate array of hashes is written.
+//
+// Segments: the input may hold several independent key sets back to back (a
+// batched build).  Each set is a segment with its own partition count; tiles
+// never cross segments, digit offsets are per segment and the look-back stops
+// at the segment's first tile, so every set comes out grouped by its own
+// partition ids in place.  A single build is one segment.
 #include "phobic_dev.cuh"
 #include "phobic_kernels.cuh"
 
@@ -32,54 +38,70 @@ __device__ __forceinline__ uint64_t load_hk(const uint64_t* in, uint64_t i, uint
     return hash_input ? key_hash(v, kseed) : v;
 }
 
-// Digit histograms of every pass in one read of the input.  Each warp counts
-// into its own sub-histogram (fewer shared-atomic collisions); 16-byte loads.
-__global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ in, uint64_t n, uint64_t np,
-                                                   uint64_t kseed, int hash_input, uint32_t passes,
-                                                   uint32_t bits, unsigned long long* __restrict__ hist) {
+// Digit histograms of every pass in one read of the input, per segment.  Each
+// block walks a contiguous range of tiles; each warp counts into its own
+// sub-histogram, which is flushed to the segment's global histogram when the
+// segment changes and at the end.
+__device__ __forceinline__ uint32_t seg_of_tile(const SortSeg* __restrict__ segs, uint32_t nseg, uint64_t t) {
+    uint32_t lo = 0, hi = nseg;  // largest s with first_tile[s] <= t
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (segs[mid].first_tile <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ in, const SortSeg* __restrict__ segs,
+                                                   uint32_t nseg, uint64_t tiles, uint64_t kseed, int hash_input,
+                                                   uint32_t passes, uint32_t bits,
+                                                   unsigned long long* __restrict__ hist) {
     extern __shared__ uint32_t sh_hist[];  // [kWarpsH][passes * R]
     constexpr int kWarpsH = 8;
     const uint32_t R = 1u << bits, mask = R - 1, PR = passes * R;
+    const uint64_t per = (tiles + gridDim.x - 1) / gridDim.x;
+    const uint64_t t0 = (uint64_t)blockIdx.x * per;
+    const uint64_t t1 = t0 + per < tiles ? t0 + per : tiles;
+    if (t0 >= t1) return;
     for (uint32_t i = threadIdx.x; i < kWarpsH * PR; i += blockDim.x) sh_hist[i] = 0;
     __syncthreads();
     uint32_t* mine = sh_hist + (threadIdx.x >> 5) * PR;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t pairs = n >> 1;
-    const ulonglong2* in2 = reinterpret_cast<const ulonglong2*>(in);
-    const bool vec = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
-    auto count = [&](uint64_t v) {
-        uint64_t j = partition_of(hash_input ? key_hash(v, kseed) : v, np);
-        for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
-    };
-    if (vec) {
-        uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-        for (; i + 3 * stride < pairs; i += 4 * stride) {  // four 16-byte loads in flight
-            ulonglong2 v0 = __ldcs(in2 + i), v1 = __ldcs(in2 + i + stride);
-            ulonglong2 v2 = __ldcs(in2 + i + 2 * stride), v3 = __ldcs(in2 + i + 3 * stride);
-            count(v0.x); count(v0.y); count(v1.x); count(v1.y);
-            count(v2.x); count(v2.y); count(v3.x); count(v3.y);
+    uint32_t sg = seg_of_tile(segs, nseg, t0);
+    uint64_t t = t0;
+    while (t < t1) {
+        const SortSeg S = segs[sg];
+        const uint64_t tend = S.first_tile + (S.n + kTile - 1) / kTile;  // this segment's tiles
+        const uint64_t ta = t, tb = tend < t1 ? tend : t1;
+        const uint64_t k0 = S.key_base + (ta - S.first_tile) * kTile;
+        uint64_t k1 = S.key_base + (tb - S.first_tile) * kTile;
+        if (k1 > S.key_base + S.n) k1 = S.key_base + S.n;
+        for (uint64_t i = k0 + threadIdx.x; i < k1; i += blockDim.x) {
+            const uint64_t v = __ldg(in + i);
+            const uint64_t j = partition_of(hash_input ? key_hash(v, kseed) : v, S.np);
+            for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
         }
-        for (; i < pairs; i += stride) {
-            ulonglong2 v = __ldcs(in2 + i);
-            count(v.x);
-            count(v.y);
+        __syncthreads();
+        unsigned long long* gh = hist + (uint64_t)sg * PR;
+        for (uint32_t i = threadIdx.x; i < PR; i += blockDim.x) {
+            uint32_t c = 0;
+            for (int w = 0; w < kWarpsH; w++) {
+                c += sh_hist[w * PR + i];
+                sh_hist[w * PR + i] = 0;
+            }
+            if (c) atomicAdd(gh + i, (unsigned long long)c);
         }
-        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) count(__ldg(in + n - 1));
-    } else {
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) count(__ldg(in + i));
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < PR; i += blockDim.x) {
-        uint32_t c = 0;
-        for (int w = 0; w < kWarpsH; w++) c += sh_hist[w * PR + i];
-        if (c) atomicAdd(hist + i, (unsigned long long)c);
+        __syncthreads();
+        t = tb;
+        sg++;
     }
 }
 
-// exclusive scan of each pass's digit histogram (one block of 512 threads per pass)
-__global__ void __launch_bounds__(512) k_sort_hist_scan(unsigned long long* hist, uint32_t bits) {
+// exclusive scan of each (segment, pass) digit histogram, plus the segment's
+// first key index (one block of 512 threads each)
+__global__ void __launch_bounds__(512) k_sort_hist_scan(unsigned long long* hist, const SortSeg* __restrict__ segs,
+                                                        uint32_t passes, uint32_t bits) {
     __shared__ unsigned long long ws[16];
     const uint32_t R = 1u << bits, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t sg = blockIdx.x / passes;
     unsigned long long* h = hist + (uint64_t)blockIdx.x * R;
     const unsigned long long v = tid < R ? h[tid] : 0;
     unsigned long long x = v;
@@ -90,7 +112,7 @@ __global__ void __launch_bounds__(512) k_sort_hist_scan(unsigned long long* hist
     }
     if (lane == 31) ws[warp] = x;
     __syncthreads();
-    unsigned long long off = 0;
+    unsigned long long off = segs[sg].key_base;
     for (uint32_t w = 0; w < warp; w++) off += ws[w];
     if (tid < R) h[tid] = off + x - v;
 }
@@ -98,10 +120,12 @@ __global__ void __launch_bounds__(512) k_sort_hist_scan(unsigned long long* hist
 struct PassArgs {
     const uint64_t* in;
     uint64_t* out;
-    uint64_t n, np, kseed;
+    const SortSeg* segs;
+    uint32_t nseg, passes, pass;
+    uint64_t kseed;
     int hash_input;
     uint32_t shift, bits;
-    const unsigned long long* digit_base; // R entries: exclusive scan of the pass histogram
+    const unsigned long long* digit_base; // [seg][pass][R]: exclusive scans of the histograms
     unsigned long long* status;            // [tiles x R]: flag | value
     uint32_t* tile_counter;
     uint32_t* error;
@@ -129,22 +153,26 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(PassArgs a) {
     for (uint32_t i = tid; i < kWarps * R; i += kThreads) wh[i] = 0;
     __syncthreads();
     const uint64_t tile = tile_s;
-    const uint64_t base = tile * kTile;
+    const uint32_t sg = seg_of_tile(a.segs, a.nseg, tile);
+    const SortSeg S = a.segs[sg];
+    const uint64_t first = S.first_tile;
+    const uint64_t seg_end = S.key_base + S.n;
+    const uint64_t base = S.key_base + (tile - first) * kTile;
     const uint64_t wbase = base + (uint64_t)warp * 32 * kItems;
 
     uint64_t k[kItems];
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
         uint64_t idx = wbase + (uint64_t)i * 32 + lane;
-        k[i] = idx < a.n ? load_hk(a.in, idx, a.kseed, a.hash_input) : 0;
+        k[i] = idx < seg_end ? load_hk(a.in, idx, a.kseed, a.hash_input) : 0;
     }
     uint32_t dr[kItems];  // digit << 16 | rank within the warp's digit group
     const uint32_t lt = (1u << lane) - 1;
     uint32_t* myh = wh + warp * R;
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
-        const bool valid = wbase + (uint64_t)i * 32 + lane < a.n;
-        const uint32_t dg = valid ? (uint32_t)((partition_of(k[i], a.np) >> a.shift) & mask) : R;
+        const bool valid = wbase + (uint64_t)i * 32 + lane < seg_end;
+        const uint32_t dg = valid ? (uint32_t)((partition_of(k[i], S.np) >> a.shift) & mask) : R;
         const uint32_t peers = __match_any_sync(kFull, dg);
         const uint32_t leader = __ffs(peers) - 1;
         uint32_t old = 0;
@@ -172,8 +200,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(PassArgs a) {
         const uint64_t cnt = tile_start[d];
         volatile unsigned long long* st = a.status;
         uint64_t excl = 0;
-        if (tile == 0) {
-            st[d] = kFlagPre | cnt;
+        if (tile == first) {
+            st[tile * R + d] = kFlagPre | cnt;
         } else {
             st[tile * R + d] = kFlagAgg | cnt;
             int64_t t = (int64_t)tile - 1;  // next predecessor to account for
@@ -182,7 +210,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(PassArgs a) {
             while (!done) {
                 unsigned long long v[8];
 #pragma unroll
-                for (int u = 0; u < 8; u++) v[u] = (t - u >= 0) ? st[(uint64_t)(t - u) * R + d] : (kFlagPre | 0ull);
+                for (int u = 0; u < 8; u++)
+                    v[u] = (t - u >= (int64_t)first) ? st[(uint64_t)(t - u) * R + d] : (kFlagPre | 0ull);
                 int u = 0;
                 for (; u < 8; u++) {
                     const uint64_t flag = v[u] & ~kValMask;
@@ -205,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(PassArgs a) {
             }
             st[tile * R + d] = kFlagPre | (excl + cnt);
         }
-        gbase[d] = a.digit_base[d] + excl;
+        gbase[d] = a.digit_base[((uint64_t)sg * a.passes + a.pass) * R + d] + excl;
     }
     // block-wide exclusive scan of the tile counts over digits: each thread
     // owns R / kThreads consecutive digits (1 or 2)
@@ -245,13 +274,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(PassArgs a) {
     }
     __syncthreads();
     // coalesced write-out: consecutive slots of one digit go to consecutive addresses
-    const uint64_t valid = a.n - base < (uint64_t)kTile ? a.n - base : (uint64_t)kTile;
+    const uint64_t valid = seg_end - base < (uint64_t)kTile ? seg_end - base : (uint64_t)kTile;
 #pragma unroll 4
     for (uint32_t i = tid; i < valid; i += kThreads) {
         uint64_t v = keys_s[i];
-        uint32_t d = (uint32_t)((partition_of(v, a.np) >> a.shift) & mask);
+        uint32_t d = (uint32_t)((partition_of(v, S.np) >> a.shift) & mask);
         uint64_t dst = gbase[d] + i;
-        if (dst < a.n) a.out[dst] = v;  // only a timed-out look-back could leave the range
+        if (dst >= S.key_base && dst < seg_end) a.out[dst] = v;  // only a timed-out look-back could leave the range
     }
 }
 
@@ -261,20 +290,32 @@ __global__ void k_hash_copy(const uint64_t* __restrict__ in, uint64_t* __restric
         out[i] = load_hk(in, i, kseed, hash_input);
 }
 
-// start[j] = first index of partition j in the sorted array (binary search)
-__global__ void k_partition_starts(const uint64_t* __restrict__ sorted, uint64_t n, uint64_t np,
-                                   uint64_t* __restrict__ start) {
-    uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (j > np) return;
-    uint64_t lo = 0, hi = n;
+// start[part_base_s + j] = first index of partition j of segment s in the
+// sorted array (binary search inside the segment); start[total partitions] = n
+__global__ void k_partition_starts(const uint64_t* __restrict__ sorted, const SortSeg* __restrict__ segs, uint32_t nseg,
+                                   uint64_t total_parts, uint64_t* __restrict__ start) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g > total_parts) return;
+    uint32_t lo_s = 0, hi_s = nseg;  // segment: largest s with part_base <= g (ignoring empty ones at the end)
+    while (hi_s - lo_s > 1) {
+        uint32_t mid = (lo_s + hi_s) >> 1;
+        if (segs[mid].part_base <= g) lo_s = mid; else hi_s = mid;
+    }
+    const SortSeg S = segs[lo_s];
+    const uint64_t j = g - S.part_base;
+    uint64_t lo = S.key_base, hi = S.key_base + S.n;
+    if (j >= S.np) {
+        start[g] = hi;
+        return;
+    }
     while (lo < hi) {
         uint64_t mid = (lo + hi) >> 1;
-        if (partition_of(__ldg(sorted + mid), np) < j)
+        if (partition_of(__ldg(sorted + mid), S.np) < j)
             lo = mid + 1;
         else
             hi = mid;
     }
-    start[j] = lo;
+    start[g] = lo;
 }
 
 }  // namespace
@@ -291,56 +332,62 @@ void sort_plan(uint64_t np, uint32_t* passes, uint32_t* bits) {
     *bits = p ? (total + p - 1) / p : 0;
 }
 
-size_t sort_scratch_bytes(uint64_t n, uint64_t np) {
+uint64_t sort_tiles(uint64_t n) { return (n + kTile - 1) / kTile; }
+
+size_t sort_seg_scratch_bytes(uint64_t n_total, uint64_t tiles, uint32_t nseg, uint64_t max_np) {
     uint32_t passes, bits;
-    sort_plan(np, &passes, &bits);
-    uint64_t tiles = (n + kTile - 1) / kTile;
-    uint32_t R = 1u << bits;
+    sort_plan(max_np, &passes, &bits);
+    const uint64_t R = 1ull << bits;
     size_t s = 0;
-    s += (size_t)n * 8;                              // ping-pong buffer
-    s += (size_t)passes * R * 8 + 64;                // histograms
-    s += (size_t)tiles * R * 8 + 64;                 // look-back status
-    s += 64 * 4;                                     // tile counters + error
+    s += (size_t)n_total * 8;                          // ping-pong buffer
+    s += (size_t)nseg * (passes ? passes : 1) * R * 8 + 64;  // histograms / digit bases
+    s += (size_t)tiles * R * 8 + 64;                   // look-back status
+    s += 64 * 4;                                       // tile counters
     return s;
 }
 
-cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t kseed, uint64_t n, uint64_t np,
-                                  uint64_t* sorted, uint64_t* start, void* scratch, uint32_t* d_error,
-                                  cudaStream_t stream) {
+size_t sort_scratch_bytes(uint64_t n, uint64_t np) {
+    return sort_seg_scratch_bytes(n, sort_tiles(n), 1, np) + 64;  // + one segment record
+}
+
+cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint64_t kseed, const SortSeg* d_segs,
+                                       uint32_t nseg, uint64_t n_total, uint64_t tiles, uint64_t max_np,
+                                       uint64_t total_parts, uint64_t* sorted, uint64_t* start, void* scratch,
+                                       uint32_t* d_error, cudaStream_t stream) {
     uint32_t passes, bits;
-    sort_plan(np, &passes, &bits);
+    sort_plan(max_np, &passes, &bits);
     const uint32_t R = 1u << bits;
-    const uint64_t tiles = (n + kTile - 1) / kTile;
     unsigned char* p = static_cast<unsigned char*>(scratch);
     uint64_t* alt = reinterpret_cast<uint64_t*>(p);
-    p += (size_t)n * 8;
+    p += (size_t)n_total * 8;
     unsigned long long* hist = reinterpret_cast<unsigned long long*>(p);
-    p += (size_t)passes * R * 8 + 64;
+    p += (size_t)nseg * (passes ? passes : 1) * R * 8 + 64;
     unsigned long long* status = reinterpret_cast<unsigned long long*>(p);
     p += (size_t)tiles * R * 8 + 64;
     uint32_t* counters = reinterpret_cast<uint32_t*>(p);
     cudaError_t e;
 
-    if (passes == 0) {
-        k_hash_copy<<<(unsigned)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, stream>>>(
-            in, sorted, n, kseed, hash_input);
-        note_launches(1);
+    if (passes == 0) {  // every segment is a single partition: hash (or copy) only
+        if (n_total) {
+            k_hash_copy<<<(unsigned)((n_total + 255) / 256 < 8192 ? (n_total + 255) / 256 : 8192), 256, 0,
+                          stream>>>(in, sorted, n_total, kseed, hash_input);
+            note_launches(1);
+        }
     } else {
-        if ((e = cudaMemsetAsync(hist, 0, (size_t)passes * R * 8, stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(hist, 0, (size_t)nseg * passes * R * 8, stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(counters, 0, 64 * 4, stream)) != cudaSuccess) return e;
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        uint64_t hblocks = (n + 256 * 16 - 1) / (256 * 16);
-        if (hblocks > (uint64_t)sms * 8) hblocks = (uint64_t)sms * 8;
+        uint64_t hblocks = tiles < (uint64_t)sms * 8 ? tiles : (uint64_t)sms * 8;
         if (hblocks == 0) hblocks = 1;
         if ((e = cudaFuncSetAttribute(k_sort_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(8 * passes * R * 4))) != cudaSuccess)
             return e;
-        k_sort_hist<<<(unsigned)hblocks, 256, 8 * passes * R * 4, stream>>>(in, n, np, kseed, hash_input, passes, bits,
-                                                                        hist);
+        k_sort_hist<<<(unsigned)hblocks, 256, 8 * passes * R * 4, stream>>>(in, d_segs, nseg, tiles, kseed,
+                                                                            hash_input, passes, bits, hist);
         note_launches(1);
-        k_sort_hist_scan<<<passes, 512, 0, stream>>>(hist, bits);
+        k_sort_hist_scan<<<nseg * passes, 512, 0, stream>>>(hist, d_segs, passes, bits);
         note_launches(1);
         size_t smem = sort_pass_smem(bits);
         if ((e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
@@ -355,13 +402,15 @@ cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t k
             PassArgs a;
             a.in = src;
             a.out = dst;
-            a.n = n;
-            a.np = np;
+            a.segs = d_segs;
+            a.nseg = nseg;
+            a.passes = passes;
+            a.pass = ps;
             a.kseed = kseed;
             a.hash_input = hash_now;
             a.shift = ps * bits;
             a.bits = bits;
-            a.digit_base = hist + (uint64_t)ps * R;
+            a.digit_base = hist;
             a.status = status;
             a.tile_counter = counters + ps;
             a.error = d_error;
@@ -372,9 +421,29 @@ cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t k
             dst = (dst == sorted) ? alt : sorted;
         }
     }
-    k_partition_starts<<<(unsigned)((np + 1 + 255) / 256), 256, 0, stream>>>(sorted, n, np, start);
+    k_partition_starts<<<(unsigned)((total_parts + 1 + 255) / 256), 256, 0, stream>>>(sorted, d_segs, nseg,
+                                                                                      total_parts, start);
     note_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t kseed, uint64_t n, uint64_t np,
+                                  uint64_t* sorted, uint64_t* start, void* scratch, uint32_t* d_error,
+                                  cudaStream_t stream) {
+    // one segment; its record sits at the end of the scratch region
+    const uint64_t tiles = sort_tiles(n);
+    SortSeg* d_seg = reinterpret_cast<SortSeg*>(static_cast<unsigned char*>(scratch) +
+                                                sort_seg_scratch_bytes(n, tiles, 1, np));
+    SortSeg hs;
+    hs.key_base = 0;
+    hs.n = n;
+    hs.np = np;
+    hs.part_base = 0;
+    hs.first_tile = 0;
+    cudaError_t e = cudaMemcpyAsync(d_seg, &hs, sizeof(SortSeg), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return e;
+    return launch_partition_sort_segs(in, hash_input, kseed, d_seg, 1, n, tiles, np, np, sorted, start, scratch,
+                                      d_error, stream);
 }
 
 cudaError_t launch_hash_u64(const uint64_t* keys, uint64_t n, uint64_t kseed, uint64_t* out, cudaStream_t stream) {

@@ -112,14 +112,6 @@ struct Arena {
                 return;
             }
     }
-    void disown(void* p) {
-        for (auto& q : ptrs)
-            if (q == p) {
-                q = ptrs.back();
-                ptrs.pop_back();
-                return;
-            }
-    }
 };
 
 // CUDA events around the build phases (only when requested)
@@ -170,11 +162,19 @@ struct PinnedBuf {
 
 }  // namespace
 
+// Device memory shared by the handles of one build (or one import): freed when
+// the last handle that refers to it is freed.
+struct SharedMem {
+    void* ptr = nullptr;
+    std::atomic<int> refs{0};
+    size_t bytes = 0;
+};
+
 struct phobic_handle {
     phobic_params prm;
     phobic_info info;
     QueryView view;
-    // owned device buffers
+    SharedMem* mem = nullptr;  // owns every device array below
     uint64_t* table = nullptr;
     uint64_t* off_words = nullptr;
     uint64_t* col_meta = nullptr;
@@ -188,15 +188,21 @@ struct phobic_handle {
     phobic_timings timings;
     uint64_t n_off_words = 0, n_col_meta = 0, n_pil_words = 0, n_dict_words = 0;
     uint64_t n_ef_low = 0, n_ef_high = 0, n_ef_samples = 0;
-    std::vector<void*> owned;
 };
 
 namespace {
 
+void release_mem(SharedMem* m) {
+    if (m && m->refs.fetch_sub(1) == 1) {
+        cudaDeviceSynchronize();
+        cudaFree(m->ptr);
+        delete m;
+    }
+}
+
 void handle_destroy(phobic_handle* h) {
     if (!h) return;
-    cudaDeviceSynchronize();
-    for (void* p : h->owned) cudaFree(p);
+    release_mem(h->mem);
     delete h;
 }
 
@@ -208,32 +214,8 @@ phobic_status check_params(uint64_t n, const phobic_params& p) {
     if (p.encoder > PHOBIC_ENC_IC_D || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
     if (p.warps_per_partition > 1) return PHOBIC_ERR_INVALID_ARG;  // one warp per partition
     if (p.candidate_width != 0 && p.candidate_width != 32 && p.candidate_width != 64) return PHOBIC_ERR_INVALID_ARG;
+    if (p.search_schedule > 2) return PHOBIC_ERR_INVALID_ARG;
     return PHOBIC_OK;
-}
-
-// space accounting (fixed spec): header, offsets, pilot encoders with their
-// metadata, Elias-Fano remap
-void account(phobic_handle* h, const std::vector<uint32_t>& w1, const std::vector<uint32_t>& w2,
-             const std::vector<uint64_t>& K) {
-    phobic_info& I = h->info;
-    const uint64_t NP = I.num_partitions;
-    I.bits_header = 9 * 64;
-    I.bits_offsets = (NP + 1) * (uint64_t)h->view.off_w + 64 + 64 + 8;
-    uint64_t bp = 0;
-    for (uint32_t b = 0; b < I.num_buckets; b++) {
-        if (I.encoder == PHOBIC_ENC_IC_C)
-            bp += NP * (uint64_t)w1[b] + 64 + 8;
-        else
-            bp += NP * (uint64_t)w1[b] + K[b] * (uint64_t)w2[b] + 64 + 64 + 8 + 8;
-    }
-    I.bits_pilots = bp;
-    I.bits_remap = 0;
-    const uint64_t N = I.M - I.n;
-    if (N) {
-        const uint32_t l = h->view.ef_l;
-        I.bits_remap = N * (uint64_t)l + (N + (I.n >> l) + 1) + 64 * ((N + 63) / 64) + 3 * 64;
-    }
-    I.bits_total = I.bits_header + I.bits_offsets + I.bits_pilots + I.bits_remap;
 }
 
 template <class T>
@@ -251,302 +233,514 @@ cudaError_t h2d(T* dev, const T* host, size_t count, cudaStream_t st) {
         if (_e != cudaSuccess) return from_cuda(_e);  \
     } while (0)
 
-// Builds from master hashes (already sorted by the caller's choice of path):
-// `in` holds raw keys (hash_input = 1) or master hashes (hash_input = 0).
-phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const phobic_params& prm, cudaStream_t st,
-                         phobic_handle** out, uint32_t key_kind = 0) {
+// One key set of a build: keys [key_base, key_base + n) of the input.
+struct SetIn {
+    uint64_t key_base, n;
+    uint32_t P;
+};
+
+// Per-set plan and layout, filled in as the build proceeds.
+struct SetPlan {
+    uint64_t key_base, n, NP, part_base, first_tile, pilot_base, col_base, M, g0;
+    uint32_t P, B, table_idx;
+    double eps;
+    uint64_t Q;
+    int64_t dmin;
+    uint32_t off_w;
+    // arena word offsets and sizes
+    uint64_t a_off, n_off, a_meta, n_meta, a_pil, n_pil, a_dict, n_dict, a_low, n_low, a_high, n_high, a_samp,
+        n_samp, a_pilots;
+    uint32_t ef_l;
+    uint64_t bits_header, bits_offsets, bits_pilots, bits_remap, bits_total;
+};
+
+// Builds the MPHFs of every set of `sets` from one input array.  `in` holds raw
+// 64-bit keys (hash_input = 1) or master hashes (hash_input = 0).  One handle per
+// set is returned in `out`; all of them share one device arena.
+phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<SetIn>& sets, const phobic_params& prm,
+                         cudaStream_t st, uint32_t key_kind, std::vector<phobic_handle*>* out) {
     ensure_pool();
-    const uint64_t NP = num_partitions(n, prm.partition_size);
-    const uint32_t B = num_buckets(prm.lambda, prm.partition_size);
+    const uint32_t S = (uint32_t)sets.size();
     const uint64_t kseed = key_seed(prm.seed);
-    Arena tmp(st), own(st);
-
-    phobic_handle* h = new (std::nothrow) phobic_handle();
-    if (!h) return PHOBIC_ERR_OOM;
-    struct Guard {
-        phobic_handle*& h;
-        Arena& own;
-        ~Guard() {
-            if (h) delete h;
-        }
-    } guard{h, own};
-    h->prm = prm;
-    std::memset(&h->info, 0, sizeof(h->info));
-    h->info.n = n;
-    h->info.num_partitions = NP;
-    h->info.num_buckets = B;
-    h->info.partition_size = prm.partition_size;
-    h->info.lambda = prm.lambda;
-    h->info.alpha = prm.alpha;
-    h->info.epsilon = eps_of(prm.lambda, prm.partition_size);
-    h->info.encoder = prm.encoder;
-    h->info.pilot_mode = prm.pilot_mode;
-    h->info.seed = prm.seed;
-
+    Arena tmp(st);
     PhaseEvents ev;
     CK(ev.init(prm.record_timings != 0));
 
-    // pinned scalars exchanged with the device
+    // ---- host plan
+    std::vector<SetPlan> pl(S);
+    std::vector<uint32_t> table_P;
+    uint64_t n_total = 0, NPT = 0, tiles = 0, pilots_total = 0, cols_total = 0, max_np = 1;
+    uint32_t cap_B = 1;
+    for (uint32_t s = 0; s < S; s++) {
+        SetPlan& p = pl[s];
+        std::memset(&p, 0, sizeof(p));
+        p.key_base = sets[s].key_base;
+        p.n = sets[s].n;
+        p.P = sets[s].P;
+        p.NP = num_partitions(p.n, p.P);
+        p.B = num_buckets(prm.lambda, p.P);
+        p.eps = eps_of(prm.lambda, p.P);
+        uint32_t ti = 0;
+        while (ti < table_P.size() && table_P[ti] != p.P) ti++;
+        if (ti == table_P.size()) table_P.push_back(p.P);
+        p.table_idx = ti;
+        p.part_base = NPT;
+        p.first_tile = tiles;
+        p.pilot_base = pilots_total;
+        p.col_base = cols_total;
+        NPT += p.NP;
+        tiles += sort_tiles(p.n);
+        pilots_total += (uint64_t)p.B * p.NP;
+        cols_total += p.B;
+        n_total += p.n;
+        if (p.NP > max_np) max_np = p.NP;
+        if (p.B > cap_B) cap_B = p.B;
+    }
+    const uint32_t ntab = (uint32_t)table_P.size();
+    std::vector<uint64_t> tables((size_t)ntab * (kTablePoints + 1));
+    for (uint32_t t = 0; t < ntab; t++) make_table(prm.lambda, prm.alpha, table_P[t], tables.data() + (size_t)t * (kTablePoints + 1));
+
     PinnedBuf pin;
-    CK(pin.alloc(4096 + (size_t)B * 16));
+    CK(pin.alloc(4096 + (size_t)S * 48 + (size_t)cols_total * 12));
     uint64_t* hst = static_cast<uint64_t*>(pin.p);
+    uint64_t* hTb = hst + 32;                                       // [S + 1] set slot bases
+    long long* hmm = reinterpret_cast<long long*>(hTb + S + 1);     // [2 S]
+    uint32_t* hcolmax = reinterpret_cast<uint32_t*>(hmm + 2 * S);   // [cols_total]
+    uint64_t* hK = reinterpret_cast<uint64_t*>(hcolmax + cols_total + (cols_total & 1));  // [cols_total]
+    uint32_t* hstatus = reinterpret_cast<uint32_t*>(hst + 4);
 
-    // ---- bucket table
-    std::vector<uint64_t> table(kTablePoints + 1);
-    make_table(prm.lambda, prm.alpha, prm.partition_size, table.data());
-    CK(own.alloc(&h->table, table.size() * 8));
-    CK(h2d(h->table, table.data(), table.size(), st));
-
-    // ---- K1 + K2: hash, partition sort, partition starts
-    uint64_t *sorted, *start, *T, *stats;
+    // ---- K1 + K2: hash, segmented partition sort, partition starts
+    std::vector<SortSeg> segs(S);
+    for (uint32_t s = 0; s < S; s++) segs[s] = SortSeg{pl[s].key_base, pl[s].n, pl[s].NP, pl[s].part_base, pl[s].first_tile};
+    SortSeg* d_segs;
+    uint64_t *d_tables, *sorted, *start, *T, *stats;
     uint32_t* status;
-    void* sort_scratch;
-    CK(tmp.alloc(&sorted, n * 8));
-    CK(tmp.alloc(&start, (NP + 1) * 8));
-    CK(tmp.alloc(&T, (NP + 1) * 8));
+    void *sort_scratch, *sizes_scratch;
+    CK(tmp.alloc(&d_segs, (size_t)S * sizeof(SortSeg)));
+    CK(tmp.alloc(&d_tables, tables.size() * 8));
+    CK(tmp.alloc(&sorted, n_total * 8));
+    CK(tmp.alloc(&start, (NPT + 1) * 8));
+    CK(tmp.alloc(&T, (NPT + 1) * 8));
     CK(tmp.alloc(&stats, 64));
     CK(tmp.alloc(&status, 64));
     CK(cudaMemsetAsync(status, 0, 64, st));
-    CK(tmp.alloc(&sort_scratch, sort_scratch_bytes(n, NP)));
+    CK(h2d(d_segs, segs.data(), S, st));
+    CK(h2d(d_tables, tables.data(), tables.size(), st));
+    CK(tmp.alloc(&sort_scratch, sort_seg_scratch_bytes(n_total, tiles, S, max_np)));
     CK(ev.mark(0, st));
-    CK(launch_partition_sort(in, hash_input, kseed, n, NP, sorted, start, sort_scratch, status, st));
+    CK(launch_partition_sort_segs(in, hash_input, kseed, d_segs, S, n_total, tiles, max_np, NPT, sorted, start,
+                                  sort_scratch, status, st));
     CK(ev.mark(1, st));
     tmp.release(sort_scratch);
-    void* sizes_scratch;
-    CK(tmp.alloc(&sizes_scratch, sizes_scratch_bytes(NP)));
-    CK(launch_sizes(start, NP, prm.alpha, T, stats, sizes_scratch, st));
+    CK(tmp.alloc(&sizes_scratch, sizes_scratch_bytes(NPT)));
+    CK(launch_sizes(start, NPT, prm.alpha, T, stats, sizes_scratch, st));
     CK(ev.mark(2, st));
+    {  // slot base of every set: T[part_base_s], s = 0..S
+        std::vector<uint64_t> idx(S + 1);
+        for (uint32_t s = 0; s < S; s++) idx[s] = pl[s].part_base;
+        idx[S] = NPT;
+        uint64_t *d_idx, *d_out;
+        CK(tmp.alloc(&d_idx, (S + 1) * 8));
+        CK(tmp.alloc(&d_out, (S + 1) * 8));
+        CK(h2d(d_idx, idx.data(), S + 1, st));
+        CK(launch_gather_u64(T, d_idx, d_out, S + 1, st));
+        CK(d2h(hTb, d_out, S + 1, st));
+    }
     CK(d2h(hst, stats, 3, st));
-    CK(d2h(reinterpret_cast<uint32_t*>(hst + 4), status, 1, st));
+    CK(d2h(hstatus, status, 1, st));
     CK(cudaStreamSynchronize(st));
-    const uint64_t M = hst[0], max_n = hst[1], max_m = hst[2];
-    if (reinterpret_cast<uint32_t*>(hst + 4)[0] == kDevTimeout) return PHOBIC_ERR_TIMEOUT;
-    h->info.M = M;
-    h->info.max_partition = max_n;
-    // keys in shared memory only on request (debug / comparison); default: global scratch
+    if (hstatus[0] == kDevTimeout) return PHOBIC_ERR_TIMEOUT;
+    const uint64_t M_total = hst[0], max_n = hst[1], max_m = hst[2];
+    for (uint32_t s = 0; s < S; s++) {
+        pl[s].g0 = hTb[s];
+        pl[s].M = hTb[s + 1] - hTb[s];
+    }
     const char* ks = std::getenv("PHOBIC_KEYS_IN_SMEM");
     const bool keys_in_smem = ks && ks[0] == '1';
     if (max_m >= 65536 || max_n >= (1u << 31) ||
-        search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, B, keys_in_smem) > search_smem_limit())
+        search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, cap_B, keys_in_smem) > search_smem_limit())
         return PHOBIC_ERR_PARTITION_TOO_LARGE;
     uint32_t s_max = prm.s_max ? prm.s_max : 65536u;
     if (max_m > 0 && (uint64_t)s_max * max_m > 0xFFFFFFFFull) s_max = (uint32_t)(0xFFFFFFFFull / max_m);
-    h->prm.s_max = s_max;
 
-    // ---- K3 + K4: bucketing and pilot search
+    // ---- K3 + K4: bucketing and pilot search, one persistent launch over all sets
+    std::vector<SearchSet> ss(S);
+    for (uint32_t s = 0; s < S; s++)
+        ss[s] = SearchSet{pl[s].part_base, pl[s].NP, pl[s].pilot_base,
+                          d_tables + (size_t)pl[s].table_idx * (kTablePoints + 1), pl[s].B, 0};
+    SearchSet* d_ss;
     uint32_t* pilots;
     uint32_t* taken = nullptr;
-    CK(tmp.alloc(&pilots, (uint64_t)B * NP * 4));
-    CK(cudaMemsetAsync(pilots, 0, (uint64_t)B * NP * 4, st));
-    if (M > n) {
-        CK(tmp.alloc(&taken, ((M + 31) / 32 + 1) * 4));
-        CK(cudaMemsetAsync(taken, 0, ((M + 31) / 32 + 1) * 4, st));
-    }
     uint64_t* bkeys = nullptr;
-    if (!keys_in_smem) CK(tmp.alloc(&bkeys, n * 8));
-    SearchLaunch sl;
-    sl.bkeys = bkeys;
-    sl.keys_in_smem = keys_in_smem ? 1 : 0;
-    sl.window_bits = prm.candidate_width == 32 ? 32 : 64;
-    sl.sorted = sorted;
-    sl.start = start;
-    sl.T = T;
-    sl.table = h->table;
-    sl.np = NP;
-    sl.B = B;
-    sl.mode = prm.pilot_mode;
-    sl.s_max = s_max;
-    sl.cap_n = (uint32_t)max_n;
-    sl.cap_m = (uint32_t)max_m;
-    sl.pilots = pilots;
-    sl.taken_bits = taken;
-    sl.status = status;
-    unsigned long long* work = nullptr;
+    unsigned long long *queue, *work = nullptr;
+    CK(tmp.alloc(&d_ss, (size_t)S * sizeof(SearchSet)));
+    CK(h2d(d_ss, ss.data(), S, st));
+    CK(tmp.alloc(&pilots, pilots_total * 4));
+    CK(cudaMemsetAsync(pilots, 0, pilots_total * 4, st));
+    if (M_total > n_total) {
+        CK(tmp.alloc(&taken, ((M_total + 31) / 32 + 1) * 4));
+        CK(cudaMemsetAsync(taken, 0, ((M_total + 31) / 32 + 1) * 4, st));
+    }
+    if (!keys_in_smem) CK(tmp.alloc(&bkeys, n_total * 8));
+    CK(tmp.alloc(&queue, 16));
     if (prm.record_timings) {
         CK(tmp.alloc(&work, 16));
         CK(cudaMemsetAsync(work, 0, 16, st));
     }
+    SearchLaunch sl;
+    sl.sorted = sorted;
+    sl.start = start;
+    sl.T = T;
+    sl.sets = d_ss;
+    sl.nsets = S;
+    sl.total_parts = NPT;
+    sl.cap_B = cap_B;
+    sl.mode = prm.pilot_mode;
+    sl.s_max = s_max;
+    sl.cap_n = (uint32_t)max_n;
+    sl.cap_m = (uint32_t)max_m;
+    sl.bkeys = bkeys;
+    sl.keys_in_smem = keys_in_smem ? 1 : 0;
+    sl.window_bits = prm.candidate_width == 32 ? 32 : 64;
+    sl.pilots = pilots;
+    sl.taken_bits = taken;
+    sl.status = status;
     sl.work = work;
+    sl.queue = queue;
+    // schedule: 1 = one CTA per partition, 2 = persistent CTAs over the work queue;
+    // 0 (auto) = the queue for batches of several key sets
+    sl.use_queue = prm.search_schedule == 2 || (prm.search_schedule == 0 && S > 1) ? 1 : 0;
     CK(ev.mark(3, st));
     CK(launch_search(sl, st));
     CK(ev.mark(4, st));
     tmp.release(sorted);
     if (bkeys) tmp.release(bkeys);
 
-    // ---- K5: offsets; K6: column maxima
-    const uint64_t Q = (uint64_t)((((unsigned __int128)M) << 32) / NP);
+    // ---- K5: offset differences; K6: column maxima (all sets)
+    std::vector<OffDesc> od(S);
+    for (uint32_t s = 0; s < S; s++) {
+        pl[s].Q = (uint64_t)((((unsigned __int128)pl[s].M) << 32) / pl[s].NP);
+        od[s] = OffDesc{pl[s].part_base, pl[s].NP, pl[s].Q, 0, 0, 0, 0};
+    }
+    std::vector<ColDesc> cd(cols_total);
+    for (uint32_t s = 0; s < S; s++)
+        for (uint32_t b = 0; b < pl[s].B; b++) {
+            ColDesc& c = cd[pl[s].col_base + b];
+            std::memset(&c, 0, sizeof(c));
+            c.src = pl[s].pilot_base + (uint64_t)b * pl[s].NP;
+            c.count = pl[s].NP;
+        }
+    OffDesc* d_od;
+    ColDesc* d_cd;
     long long* mm;
     uint32_t* colmax;
-    CK(tmp.alloc(&mm, 16));
-    CK(tmp.alloc(&colmax, (size_t)B * 4));
+    CK(tmp.alloc(&d_od, (size_t)S * sizeof(OffDesc)));
+    CK(tmp.alloc(&d_cd, (size_t)cols_total * sizeof(ColDesc)));
+    CK(tmp.alloc(&mm, (size_t)S * 16));
+    CK(tmp.alloc(&colmax, (size_t)cols_total * 4));
+    CK(h2d(d_od, od.data(), S, st));
+    CK(h2d(d_cd, cd.data(), cols_total, st));
     CK(ev.mark(5, st));
-    CK(launch_offset_minmax(T, NP, Q, mm, st));
-    CK(launch_column_max(pilots, NP, B, colmax, st));
-    long long* hmm = reinterpret_cast<long long*>(hst + 8);
-    uint32_t* hcolmax = reinterpret_cast<uint32_t*>(hst + 16);
-    CK(d2h(hmm, mm, 2, st));
-    CK(d2h(hcolmax, colmax, B, st));
+    CK(launch_offset_minmax(T, d_od, S, mm, st));
+    CK(launch_column_max(pilots, d_cd, (uint32_t)cols_total, colmax, st));
+    CK(d2h(hmm, mm, 2 * (size_t)S, st));
+    CK(d2h(hcolmax, colmax, cols_total, st));
+    CK(d2h(hstatus, status, 1, st));
     if (work) CK(d2h(hst + 12, reinterpret_cast<uint64_t*>(work), 2, st));
-    CK(d2h(reinterpret_cast<uint32_t*>(hst + 4), status, 1, st));
     CK(cudaStreamSynchronize(st));
-    switch (reinterpret_cast<uint32_t*>(hst + 4)[0]) {
+    switch (hstatus[0]) {
         case kDevOk: break;
         case kDevDupHash: return PHOBIC_ERR_DUP_HASH;
         case kDevSearchLimit: return PHOBIC_ERR_SEARCH_LIMIT;
         default: return PHOBIC_ERR_TIMEOUT;
     }
-    const int64_t dmin = hmm[0], dmax = hmm[1];
-    const uint32_t off_w = bitlen64((uint64_t)(dmax - dmin));
-    h->n_off_words = packed_words((NP + 1) * (uint64_t)off_w);
-    CK(own.alloc(&h->off_words, h->n_off_words * 8));
-    CK(launch_offset_pack(T, NP, Q, dmin, off_w, h->off_words, h->n_off_words, st));
 
-    std::vector<uint32_t> w1(B), w2(B);
-    std::vector<uint64_t> K(B, 0);
-    std::vector<uint64_t> meta, wbegin(B + 1, 0);
-    if (prm.encoder == PHOBIC_ENC_IC_C) {
-        meta.resize(B);
-        uint64_t base = 0;
-        for (uint32_t b = 0; b < B; b++) {
-            w1[b] = bitlen64(hcolmax[b]);
-            meta[b] = base | ((uint64_t)w1[b] << 56);
-            uint64_t bits = NP * (uint64_t)w1[b];
-            wbegin[b + 1] = wbegin[b] + (bits ? ((base + bits - 1) >> 6) - (base >> 6) + 1 : 0);
-            base += bits;
+    // ---- IC-D: presence bitmaps, ranks, dictionary sizes
+    uint64_t *bitmaps = nullptr, *brank = nullptr;
+    std::vector<uint64_t> bm_begin(cols_total + 1, 0);
+    if (prm.encoder == PHOBIC_ENC_IC_D) {
+        for (uint64_t c = 0; c < cols_total; c++) {
+            cd[c].bm_base = bm_begin[c];
+            cd[c].bm_words = ((uint64_t)hcolmax[c] + 64) / 64;
+            bm_begin[c + 1] = bm_begin[c] + cd[c].bm_words;
         }
-        h->n_pil_words = packed_words(base);
-        h->n_col_meta = B;
-        uint64_t* dwb;
-        CK(own.alloc(&h->col_meta, (size_t)B * 8));
-        CK(tmp.alloc(&dwb, (size_t)(B + 1) * 8));
-        CK(own.alloc(&h->pil_words, h->n_pil_words * 8));
-        CK(h2d(h->col_meta, meta.data(), B, st));
-        CK(h2d(dwb, wbegin.data(), B + 1, st));
-        CK(cudaMemsetAsync(h->pil_words, 0, h->n_pil_words * 8, st));
-        CK(launch_compact_pack(pilots, NP, B, h->col_meta, dwb, h->pil_words, wbegin[B], st));
-    } else {
-        // presence bitmaps over [0, max_b] per column
-        std::vector<uint64_t> bm_base(B + 1, 0);
-        for (uint32_t b = 0; b < B; b++) bm_base[b + 1] = bm_base[b] + ((uint64_t)hcolmax[b] + 64) / 64;
-        uint64_t *dbm_base, *bitmaps, *brank, *dK;
-        CK(tmp.alloc(&dbm_base, (size_t)(B + 1) * 8));
-        CK(tmp.alloc(&bitmaps, bm_base[B] * 8));
-        CK(tmp.alloc(&brank, bm_base[B] * 8));
-        CK(tmp.alloc(&dK, (size_t)B * 8));
-        CK(h2d(dbm_base, bm_base.data(), B + 1, st));
-        CK(cudaMemsetAsync(bitmaps, 0, bm_base[B] * 8, st));
-        CK(launch_dict_mark(pilots, NP, B, dbm_base, bitmaps, st));
-        CK(launch_dict_rank(dbm_base, B, brank, bitmaps, dK, st));
-        uint64_t* hK = hst + 16 + (B + 1) / 2 + 1;
-        CK(d2h(hK, dK, B, st));
+        uint64_t* dK;
+        CK(tmp.alloc(&bitmaps, bm_begin[cols_total] * 8));
+        CK(tmp.alloc(&brank, bm_begin[cols_total] * 8));
+        CK(tmp.alloc(&dK, cols_total * 8));
+        CK(h2d(d_cd, cd.data(), cols_total, st));
+        CK(cudaMemsetAsync(bitmaps, 0, bm_begin[cols_total] * 8, st));
+        CK(launch_dict_mark(pilots, d_cd, (uint32_t)cols_total, bitmaps, st));
+        CK(launch_dict_rank(d_cd, (uint32_t)cols_total, brank, bitmaps, dK, st));
+        CK(d2h(hK, dK, cols_total, st));
         CK(cudaStreamSynchronize(st));
-        meta.resize(2 * (size_t)B);
-        uint64_t rbase = 0, dbase = 0;
-        for (uint32_t b = 0; b < B; b++) {
-            K[b] = hK[b];
-            w1[b] = bitlen64(K[b] - 1);         // rank width
-            w2[b] = bitlen64(hcolmax[b]);       // dictionary value width
-            meta[2 * b] = rbase | ((uint64_t)w1[b] << 56);
-            meta[2 * b + 1] = dbase | ((uint64_t)w2[b] << 56);
-            uint64_t bits = NP * (uint64_t)w1[b];
-            wbegin[b + 1] = wbegin[b] + (bits ? ((rbase + bits - 1) >> 6) - (rbase >> 6) + 1 : 0);
-            rbase += bits;
-            dbase += K[b] * (uint64_t)w2[b];
-        }
-        h->n_pil_words = packed_words(rbase);
-        h->n_dict_words = packed_words(dbase);
-        h->n_col_meta = 2 * (uint64_t)B;
-        uint64_t* dwb;
-        CK(own.alloc(&h->col_meta, (size_t)B * 16));
-        CK(tmp.alloc(&dwb, (size_t)(B + 1) * 8));
-        CK(own.alloc(&h->pil_words, h->n_pil_words * 8));
-        CK(own.alloc(&h->dict_words, h->n_dict_words * 8));
-        CK(h2d(h->col_meta, meta.data(), 2 * (size_t)B, st));
-        CK(h2d(dwb, wbegin.data(), B + 1, st));
-        CK(cudaMemsetAsync(h->pil_words, 0, h->n_pil_words * 8, st));
-        CK(cudaMemsetAsync(h->dict_words, 0, h->n_dict_words * 8, st));
-        CK(launch_dict_pack(pilots, NP, B, dbm_base, bitmaps, brank, h->col_meta, dwb, h->pil_words, wbegin[B],
-                            nullptr, h->dict_words, bm_base[B], st));
     }
 
+    // ---- layouts and the arena
+    uint64_t aw = (uint64_t)ntab * (kTablePoints + 1);  // tables first
+    std::vector<uint64_t> off_begin(S + 1, 0), col_begin(cols_total + 1, 0), remap_sets;
+    std::vector<std::vector<uint64_t>> metas(S);
+    for (uint32_t s = 0; s < S; s++) {
+        SetPlan& p = pl[s];
+        p.dmin = hmm[2 * s];
+        p.off_w = bitlen64((uint64_t)(hmm[2 * s + 1] - hmm[2 * s]));
+        p.n_off = packed_words((p.NP + 1) * (uint64_t)p.off_w);
+        p.a_off = aw;
+        aw += p.n_off;
+        off_begin[s + 1] = off_begin[s] + p.n_off;
+        const bool icd = prm.encoder == PHOBIC_ENC_IC_D;
+        p.n_meta = icd ? 2 * (uint64_t)p.B : p.B;
+        p.a_meta = aw;
+        aw += p.n_meta;
+        metas[s].resize(p.n_meta);
+        uint64_t rbase = 0, dbase = 0, bp = 0;
+        for (uint32_t b = 0; b < p.B; b++) {
+            ColDesc& c = cd[p.col_base + b];
+            const uint64_t c_id = p.col_base + b;
+            if (!icd) {
+                c.width = bitlen64(hcolmax[c_id]);
+                c.base = rbase;
+                metas[s][b] = rbase | ((uint64_t)c.width << 56);
+                rbase += p.NP * (uint64_t)c.width;
+                bp += p.NP * (uint64_t)c.width + 64 + 8;
+            } else {
+                const uint64_t K = hK[c_id];
+                c.width = bitlen64(K - 1);
+                c.dict_width = bitlen64(hcolmax[c_id]);
+                c.base = rbase;
+                c.dict_base = dbase;
+                metas[s][2 * b] = rbase | ((uint64_t)c.width << 56);
+                metas[s][2 * b + 1] = dbase | ((uint64_t)c.dict_width << 56);
+                rbase += p.NP * (uint64_t)c.width;
+                dbase += K * (uint64_t)c.dict_width;
+                bp += p.NP * (uint64_t)c.width + K * (uint64_t)c.dict_width + 64 + 64 + 8 + 8;
+            }
+            const uint64_t bits = p.NP * (uint64_t)c.width;
+            col_begin[c_id + 1] = col_begin[c_id] + (bits ? ((c.base + bits - 1) >> 6) - (c.base >> 6) + 1 : 0);
+        }
+        p.n_pil = packed_words(rbase);
+        p.a_pil = aw;
+        aw += p.n_pil;
+        p.n_dict = icd ? packed_words(dbase) : 0;
+        p.a_dict = aw;
+        aw += p.n_dict;
+        for (uint32_t b = 0; b < p.B; b++) {
+            cd[p.col_base + b].dst_word = p.a_pil;
+            cd[p.col_base + b].dict_dst_word = p.a_dict;
+        }
+        // Elias-Fano remap of slots >= n
+        const uint64_t N = p.M - p.n;
+        if (N) {
+            p.ef_l = (p.n / N >= 1) ? bitlen64(p.n / N) - 1 : 0;
+            p.n_low = packed_words(N * (uint64_t)p.ef_l);
+            p.n_high = packed_words(N + (p.n >> p.ef_l) + 1);
+            p.n_samp = (N + 63) / 64;
+            p.a_low = aw;
+            aw += p.n_low;
+            p.a_high = aw;
+            aw += p.n_high;
+            p.a_samp = aw;
+            aw += p.n_samp;
+            remap_sets.push_back(s);
+        }
+        if (prm.keep_pilots) {
+            p.a_pilots = aw;
+            aw += ((uint64_t)p.B * p.NP + 1) / 2;
+        }
+        // space accounting (fixed spec)
+        p.bits_header = 9 * 64;
+        p.bits_offsets = (p.NP + 1) * (uint64_t)p.off_w + 64 + 64 + 8;
+        p.bits_pilots = bp;
+        p.bits_remap = N ? N * (uint64_t)p.ef_l + (N + (p.n >> p.ef_l) + 1) + 64 * ((N + 63) / 64) + 3 * 64 : 0;
+        p.bits_total = p.bits_header + p.bits_offsets + p.bits_pilots + p.bits_remap;
+        od[s].dmin = p.dmin;
+        od[s].width = p.off_w;
+        od[s].dst_word = p.a_off;
+    }
+    SharedMem* mem = new (std::nothrow) SharedMem();
+    if (!mem) return PHOBIC_ERR_OOM;
+    {
+        cudaError_t e = cudaMallocAsync(&mem->ptr, aw * 8, st);
+        if (e != cudaSuccess) {
+            delete mem;
+            return from_cuda(e);
+        }
+        mem->bytes = aw * 8;
+    }
+    struct MemGuard {
+        SharedMem*& m;
+        cudaStream_t st;
+        ~MemGuard() {
+            if (m) {
+                cudaFreeAsync(m->ptr, st);
+                delete m;
+            }
+        }
+    } mem_guard{mem, st};
+    uint64_t* arena = static_cast<uint64_t*>(mem->ptr);
+    CK(cudaMemsetAsync(arena, 0, aw * 8, st));
+    CK(h2d(arena, tables.data(), tables.size(), st));
+    for (uint32_t s = 0; s < S; s++) CK(h2d(arena + pl[s].a_meta, metas[s].data(), metas[s].size(), st));
+
+    // ---- K5 / K6 packing (all sets, one launch each)
+    uint64_t *d_obeg, *d_cbeg;
+    CK(tmp.alloc(&d_obeg, (S + 1) * 8));
+    CK(tmp.alloc(&d_cbeg, (cols_total + 1) * 8));
+    CK(h2d(d_od, od.data(), S, st));
+    CK(h2d(d_cd, cd.data(), cols_total, st));
+    CK(h2d(d_obeg, off_begin.data(), S + 1, st));
+    CK(h2d(d_cbeg, col_begin.data(), cols_total + 1, st));
+    CK(launch_offset_pack(T, d_od, S, d_obeg, off_begin[S], arena, st));
+    const bool icd = prm.encoder == PHOBIC_ENC_IC_D;
+    CK(launch_pack_columns(pilots, d_cd, (uint32_t)cols_total, d_cbeg, col_begin[cols_total], icd, bitmaps, brank,
+                           arena, st));
+    if (icd) {
+        uint64_t* d_bmbeg;
+        CK(tmp.alloc(&d_bmbeg, (cols_total + 1) * 8));
+        CK(h2d(d_bmbeg, bm_begin.data(), cols_total + 1, st));
+        CK(launch_dict_pack_values(d_cd, (uint32_t)cols_total, d_bmbeg, bm_begin[cols_total], bitmaps, brank, arena,
+                                   st));
+    }
     CK(ev.mark(6, st));
-    // ---- K7: Elias-Fano remap of slots >= n
-    uint32_t ef_l = 0;
-    if (M > n) {
-        const uint64_t N = M - n;
-        ef_l = (n / N >= 1) ? bitlen64(n / N) - 1 : 0;
-        h->n_ef_low = packed_words(N * (uint64_t)ef_l);
-        h->n_ef_high = packed_words(N + (n >> ef_l) + 1);
-        h->n_ef_samples = (N + 63) / 64;
-        uint64_t* fs;
+
+    // ---- K7: Elias-Fano remap of slots >= n (sets with alpha < 1)
+    if (!remap_sets.empty()) {
+        const uint32_t R = (uint32_t)remap_sets.size();
+        std::vector<RemapDesc> rd(R);
+        std::vector<uint64_t> zb(R + 1, 0), tb(R + 1, 0), fb(R + 1, 0), lb(R + 1, 0);
+        for (uint32_t r = 0; r < R; r++) {
+            const SetPlan& p = pl[remap_sets[r]];
+            rd[r] = RemapDesc{p.g0, p.n, p.M, fb[r], p.a_low, p.a_high, p.a_samp, p.ef_l, 0};
+            zb[r + 1] = zb[r] + (((p.g0 + p.n - 1) >> 5) - (p.g0 >> 5) + 1);
+            tb[r + 1] = tb[r] + (((p.g0 + p.M - 1) >> 5) - ((p.g0 + p.n) >> 5) + 1);
+            fb[r + 1] = fb[r] + (p.M - p.n);
+            lb[r + 1] = lb[r] + p.n_low;
+        }
+        RemapDesc* d_rd;
+        uint64_t* d_beg;
         void* rs;
-        CK(tmp.alloc(&fs, N * 8));
-        CK(tmp.alloc(&rs, remap_scratch_bytes(n, M)));
-        CK(own.alloc(&h->ef_low, h->n_ef_low * 8));
-        CK(own.alloc(&h->ef_high, h->n_ef_high * 8));
-        CK(own.alloc(&h->ef_samples, h->n_ef_samples * 8));
-        CK(launch_remap(taken, n, M, ef_l, fs, h->ef_low, h->n_ef_low, h->ef_high, h->n_ef_high, h->ef_samples, rs,
-                        st));
+        CK(tmp.alloc(&d_rd, (size_t)R * sizeof(RemapDesc)));
+        CK(tmp.alloc(&d_beg, 4 * (size_t)(R + 1) * 8));
+        CK(tmp.alloc(&rs, remap_scratch_bytes(zb[R], tb[R], fb[R])));
+        CK(h2d(d_rd, rd.data(), R, st));
+        CK(h2d(d_beg, zb.data(), R + 1, st));
+        CK(h2d(d_beg + (R + 1), tb.data(), R + 1, st));
+        CK(h2d(d_beg + 2 * (R + 1), fb.data(), R + 1, st));
+        CK(h2d(d_beg + 3 * (R + 1), lb.data(), R + 1, st));
+        CK(launch_remap(taken, d_rd, R, d_beg, zb[R], d_beg + (R + 1), tb[R], d_beg + 2 * (R + 1), fb[R],
+                        d_beg + 3 * (R + 1), lb[R], arena, rs, st));
     }
     CK(ev.mark(7, st));
-    if (prm.keep_pilots) {
-        h->pilots = pilots;
-        tmp.disown(pilots);
-        own.ptrs.push_back(pilots);
-    }
+    if (prm.keep_pilots)
+        for (uint32_t s = 0; s < S; s++)
+            CK(cudaMemcpyAsync(arena + pl[s].a_pilots, pilots + pl[s].pilot_base, (uint64_t)pl[s].B * pl[s].NP * 4,
+                               cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
 
-    // ---- view for the query kernel
-    QueryView& v = h->view;
-    v.n = n;
-    v.M = M;
-    v.NP = NP;
-    v.B = B;
-    v.encoder = prm.encoder;
-    v.pilot_mode = prm.pilot_mode;
-    v.off_w = off_w;
-    v.kseed = kseed;
-    v.off_Q = Q;
-    v.off_dmin = dmin;
-    v.table = h->table;
-    v.off_words = h->off_words;
-    v.col_meta = h->col_meta;
-    v.pil_words = h->pil_words;
-    v.dict_words = h->dict_words;
-    v.ef_N = M - n;
-    v.ef_l = ef_l;
-    v.ef_low = h->ef_low;
-    v.ef_high = h->ef_high;
-    v.ef_samples = h->ef_samples;
-    v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
-    v.key_kind = key_kind;
-    v.string_seed = prm.seed;
-    account(h, w1, w2, K);
-    if (ev.on) {
-        h->has_timings = true;
-        h->timings.sort_ms = ev.between(0, 1);
-        h->timings.sizes_ms = ev.between(1, 2);
-        h->timings.search_ms = ev.between(3, 4);
-        // encode spans host synchronisations (column widths, dictionary sizes);
-        // it is reported as device time between its first and last event
-        h->timings.encode_ms = ev.between(5, 6);
-        h->timings.remap_ms = ev.between(6, 7);
-        h->timings.total_ms = ev.between(0, 7);
-        h->timings.search_s_tries = hst[12];
-        h->timings.search_steps = hst[13];
+    // ---- handles
+    std::vector<phobic_handle*> hs(S, nullptr);
+    for (uint32_t s = 0; s < S; s++) {
+        hs[s] = new (std::nothrow) phobic_handle();
+        if (!hs[s]) {
+            for (auto* h : hs) delete h;
+            return PHOBIC_ERR_OOM;
+        }
     }
-
-    // the handle takes the permanent buffers
-    for (void* p : own.ptrs) h->owned.push_back(p);
-    own.ptrs.clear();
-    uint64_t dev_bytes = (kTablePoints + 1) * 8 + 8 * (h->n_off_words + h->n_col_meta + h->n_pil_words +
-                                                     h->n_dict_words + h->n_ef_low + h->n_ef_high + h->n_ef_samples);
-    if (h->pilots) dev_bytes += (uint64_t)B * NP * 4;  // counted once: pilots was moved into `own`
-    h->info.device_bytes = dev_bytes;
-    *out = h;
-    h = nullptr;  // guard releases nothing
+    mem->refs.store((int)S);
+    for (uint32_t s = 0; s < S; s++) {
+        const SetPlan& p = pl[s];
+        phobic_handle* h = hs[s];
+        h->prm = prm;
+        h->prm.partition_size = p.P;
+        h->prm.s_max = s_max;
+        h->mem = mem;
+        h->table = arena + (size_t)p.table_idx * (kTablePoints + 1);
+        h->off_words = arena + p.a_off;
+        h->n_off_words = p.n_off;
+        h->col_meta = arena + p.a_meta;
+        h->n_col_meta = p.n_meta;
+        h->pil_words = arena + p.a_pil;
+        h->n_pil_words = p.n_pil;
+        h->dict_words = p.n_dict ? arena + p.a_dict : nullptr;
+        h->n_dict_words = p.n_dict;
+        if (p.M > p.n) {
+            h->ef_low = arena + p.a_low;
+            h->ef_high = arena + p.a_high;
+            h->ef_samples = arena + p.a_samp;
+            h->n_ef_low = p.n_low;
+            h->n_ef_high = p.n_high;
+            h->n_ef_samples = p.n_samp;
+        }
+        if (prm.keep_pilots) h->pilots = reinterpret_cast<uint32_t*>(arena + p.a_pilots);
+        phobic_info& I = h->info;
+        std::memset(&I, 0, sizeof(I));
+        I.n = p.n;
+        I.M = p.M;
+        I.num_partitions = p.NP;
+        I.num_buckets = p.B;
+        I.partition_size = p.P;
+        I.lambda = prm.lambda;
+        I.alpha = prm.alpha;
+        I.epsilon = p.eps;
+        I.encoder = prm.encoder;
+        I.pilot_mode = prm.pilot_mode;
+        I.seed = prm.seed;
+        I.max_partition = max_n;
+        I.bits_header = p.bits_header;
+        I.bits_offsets = p.bits_offsets;
+        I.bits_pilots = p.bits_pilots;
+        I.bits_remap = p.bits_remap;
+        I.bits_total = p.bits_total;
+        I.device_bytes = 8 * ((kTablePoints + 1) + p.n_off + p.n_meta + p.n_pil + p.n_dict + p.n_low + p.n_high +
+                              p.n_samp) + (prm.keep_pilots ? (uint64_t)p.B * p.NP * 4 : 0);
+        QueryView& v = h->view;
+        v.n = p.n;
+        v.M = p.M;
+        v.NP = p.NP;
+        v.B = p.B;
+        v.encoder = prm.encoder;
+        v.pilot_mode = prm.pilot_mode;
+        v.off_w = p.off_w;
+        v.kseed = kseed;
+        v.off_Q = p.Q;
+        v.off_dmin = p.dmin;
+        v.table = h->table;
+        v.off_words = h->off_words;
+        v.col_meta = h->col_meta;
+        v.pil_words = h->pil_words;
+        v.dict_words = h->dict_words;
+        v.ef_N = p.M - p.n;
+        v.ef_l = p.ef_l;
+        v.ef_low = h->ef_low;
+        v.ef_high = h->ef_high;
+        v.ef_samples = h->ef_samples;
+        v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
+        v.key_kind = key_kind;
+        v.string_seed = prm.seed;
+        if (ev.on) {
+            h->has_timings = true;
+            h->timings.sort_ms = ev.between(0, 1);
+            h->timings.sizes_ms = ev.between(1, 2);
+            h->timings.search_ms = ev.between(3, 4);
+            h->timings.encode_ms = ev.between(5, 6);
+            h->timings.remap_ms = ev.between(6, 7);
+            h->timings.total_ms = ev.between(0, 7);
+            h->timings.search_s_tries = hst[12];
+            h->timings.search_steps = hst[13];
+        }
+    }
+    mem = nullptr;  // the handles own it now
+    *out = hs;
     return PHOBIC_OK;
+}
+
+phobic_status build_impl(const uint64_t* in, int hash_input, uint64_t n, const phobic_params& prm, cudaStream_t st,
+                         phobic_handle** out, uint32_t key_kind = 0) {
+    std::vector<phobic_handle*> hs;
+    phobic_status s = build_sets(in, hash_input, {SetIn{0, n, prm.partition_size}}, prm, st, key_kind, &hs);
+    if (s == PHOBIC_OK) *out = hs[0];
+    return s;
 }
 
 }  // namespace
@@ -584,6 +778,31 @@ phobic_status phobic_build(const uint64_t* d_keys, uint64_t n, double lambda, do
     p.partition_size = partition_size;
     p.seed = seed;
     return phobic_build_ex(d_keys, n, &p, stream, out);
+}
+
+phobic_status phobic_build_batch(const uint64_t* d_keys, const uint64_t* h_set_offsets, uint32_t n_sets,
+                                 const uint32_t* h_partition_sizes, const phobic_params* params,
+                                 phobic_stream_t stream, phobic_handle** out_handles) {
+    if (!out_handles || n_sets == 0) return PHOBIC_ERR_INVALID_ARG;
+    for (uint32_t s = 0; s < n_sets; s++) out_handles[s] = nullptr;
+    if (!d_keys || !h_set_offsets || !params) return PHOBIC_ERR_INVALID_ARG;
+    std::vector<SetIn> sets(n_sets);
+    for (uint32_t s = 0; s < n_sets; s++) {
+        if (h_set_offsets[s + 1] <= h_set_offsets[s]) return PHOBIC_ERR_INVALID_ARG;  // every set non-empty
+        phobic_params p = *params;
+        if (h_partition_sizes) p.partition_size = h_partition_sizes[s];
+        phobic_status st = check_params(h_set_offsets[s + 1] - h_set_offsets[s], p);
+        if (st != PHOBIC_OK) return st;
+        sets[s] = SetIn{h_set_offsets[s], h_set_offsets[s + 1] - h_set_offsets[s], p.partition_size};
+    }
+    std::vector<phobic_handle*> hs;
+    phobic_status st = build_sets(d_keys + h_set_offsets[0], 1, [&] {
+        for (auto& x : sets) x.key_base -= h_set_offsets[0];
+        return sets;
+    }(), *params, (cudaStream_t)stream, 0, &hs);
+    if (st != PHOBIC_OK) return st;
+    for (uint32_t s = 0; s < n_sets; s++) out_handles[s] = hs[s];
+    return PHOBIC_OK;
 }
 
 phobic_status phobic_build_host(const uint64_t* h_keys, uint64_t n, const phobic_params* params,
@@ -801,21 +1020,32 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
                          &h->n_ef_low,    &h->n_ef_high,  &h->n_ef_samples};
     std::vector<uint64_t> table(kTablePoints + 1);
     make_table(p.lambda, p.alpha, p.partition_size, table.data());
-    cudaError_t e = cudaMalloc(&h->table, table.size() * 8);
-    if (e == cudaSuccess) {
-        h->owned.push_back(h->table);
-        e = cudaMemcpy(h->table, table.data(), table.size() * 8, cudaMemcpyHostToDevice);
+    // one allocation: the table, then the seven arrays in file order
+    SharedMem* mem = new (std::nothrow) SharedMem();
+    if (!mem) {
+        delete h;
+        return PHOBIC_ERR_OOM;
     }
-    uint64_t at = kHeaderWords;
+    cudaError_t e = cudaMalloc(&mem->ptr, ((kTablePoints + 1) + (words - kHeaderWords)) * 8);
+    if (e != cudaSuccess) {
+        delete mem;
+        delete h;
+        return from_cuda(e);
+    }
+    mem->refs.store(1);
+    h->mem = mem;
+    uint64_t* arena = static_cast<uint64_t*>(mem->ptr);
+    h->table = arena;
+    e = cudaMemcpy(h->table, table.data(), table.size() * 8, cudaMemcpyHostToDevice);
+    uint64_t at = kHeaderWords, aw = kTablePoints + 1;
     for (int i = 0; i < 7 && e == cudaSuccess; i++) {
         *cnts[i] = counts[i];
         if (counts[i]) {
-            e = cudaMalloc(dst[i], counts[i] * 8);
-            if (e != cudaSuccess) break;
-            h->owned.push_back(*dst[i]);
+            *dst[i] = arena + aw;
             e = cudaMemcpy(*dst[i], w + at, counts[i] * 8, cudaMemcpyHostToDevice);
         }
         at += counts[i];
+        aw += counts[i];
     }
     if (e != cudaSuccess) {
         handle_destroy(h);

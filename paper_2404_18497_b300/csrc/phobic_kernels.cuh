@@ -14,8 +14,20 @@ void note_launches(uint64_t k);
 
 // ---- k_sort.cu: master hash + onesweep sort by partition id ----
 constexpr uint32_t kSortTileKeys = 4096;  // keys per onesweep tile
+// one independent key set of a (batched) sort: keys [key_base, key_base + n)
+// grouped by partition j = floor(hk np / 2^64) into [key_base, key_base + n);
+// partition starts go to start[part_base + j]; tiles [first_tile, ...)
+struct SortSeg {
+    uint64_t key_base, n, np, part_base, first_tile;
+};
 void sort_plan(uint64_t np, uint32_t* passes, uint32_t* bits);
+uint64_t sort_tiles(uint64_t n);
+size_t sort_seg_scratch_bytes(uint64_t n_total, uint64_t tiles, uint32_t nseg, uint64_t max_np);
 size_t sort_scratch_bytes(uint64_t n, uint64_t np);
+cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint64_t kseed, const SortSeg* d_segs,
+                                       uint32_t nseg, uint64_t n_total, uint64_t tiles, uint64_t max_np,
+                                       uint64_t total_parts, uint64_t* sorted, uint64_t* start, void* scratch,
+                                       uint32_t* d_error, cudaStream_t stream);
 cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t kseed, uint64_t n, uint64_t np,
                                   uint64_t* sorted, uint64_t* start, void* scratch, uint32_t* d_error,
                                   cudaStream_t stream);
@@ -37,13 +49,23 @@ size_t sizes_scratch_bytes(uint64_t np);
 cudaError_t launch_sizes(const uint64_t* start, uint64_t np, double alpha, uint64_t* T, uint64_t* stats,
                          void* scratch, cudaStream_t stream);
 
+// one key set of a search launch: its partitions are [part_base, part_base + np)
+// in the global partition numbering; pilot of bucket b of local partition j at
+// pilots[pilot_base + b * np + j]
+struct SearchSet {
+    uint64_t part_base, np, pilot_base;
+    const uint64_t* table;  // 2049-entry bucket table of this set's (lambda, alpha, P)
+    uint32_t B, pad;
+};
+
 struct SearchLaunch {
-    const uint64_t* sorted;
-    const uint64_t* start;
-    const uint64_t* T;
-    const uint64_t* table;
-    uint64_t np;
-    uint32_t B;
+    const uint64_t* sorted;  // master hashes grouped by global partition
+    const uint64_t* start;   // [total_parts + 1]
+    const uint64_t* T;       // [total_parts + 1] slot offsets (global over all sets)
+    const SearchSet* sets;
+    uint32_t nsets;
+    uint64_t total_parts;
+    uint32_t cap_B;        // largest B over the sets
     uint32_t mode;
     uint32_t s_max;
     uint32_t cap_n; // largest n_j
@@ -51,44 +73,68 @@ struct SearchLaunch {
     uint64_t* bkeys;       // [n] scratch for the bucket-sorted keys (used unless keys_in_smem)
     uint32_t keys_in_smem; // 1: keep each partition's keys in shared memory
     uint32_t window_bits;  // displacements per lane-window: 32 or 64 (speed only)
-    uint32_t* pilots;      // [B x np], zero-filled by the caller
-    uint32_t* taken_bits;  // global occupancy bitmap over [0, M) in u32 words, zero-filled; may be null
+    uint32_t* pilots;      // zero-filled by the caller
+    uint32_t* taken_bits;  // global occupancy bitmap over all slots in u32 words, zero-filled; may be null
     uint32_t* status;      // device status word (kDev* codes, atomicMax)
-    unsigned long long* work; // [2]: s tries, window steps (may be null)
+    unsigned long long* work;  // [2]: s tries, window steps (may be null)
+    unsigned long long* queue; // work-queue counter (the launcher zeroes it)
+    uint32_t use_queue;        // 1: persistent CTAs over a work queue; 0: one CTA per partition
 };
+// out[i] = src[idx[i]]
+cudaError_t launch_gather_u64(const uint64_t* src, const uint64_t* idx, uint64_t* out, uint64_t count,
+                              cudaStream_t stream);
 size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem);
 size_t search_smem_limit();
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream);
 
-// ---- k_encode.cu ----
-// offsets: D_j = T_j - floor(j Q / 2^32); mm[0] = min D (as int64 bits), mm[1] = max D
-cudaError_t launch_offset_minmax(const uint64_t* T, uint64_t np, uint64_t Q, long long* mm, cudaStream_t stream);
-cudaError_t launch_offset_pack(const uint64_t* T, uint64_t np, uint64_t Q, int64_t dmin, uint32_t w,
-                               uint64_t* words, uint64_t nwords, cudaStream_t stream);
-// per column max pilot: colmax[b]
-cudaError_t launch_column_max(const uint32_t* pilots, uint64_t np, uint32_t B, uint32_t* colmax, cudaStream_t stream);
-// IC-C: col_meta[b] = base | width << 56 (device copy made by the caller)
-cudaError_t launch_compact_pack(const uint32_t* pilots, uint64_t np, uint32_t B, const uint64_t* col_meta,
-                                const uint64_t* col_word_begin, uint64_t* words, uint64_t nwords,
-                                cudaStream_t stream);
-// IC-D, step 1: presence bitmaps of the pilot values of each column
-cudaError_t launch_dict_mark(const uint32_t* pilots, uint64_t np, uint32_t B, const uint64_t* bm_base,
-                             uint64_t* bitmaps, cudaStream_t stream);
-// IC-D, step 2: per column, popcount prefix of its bitmap words -> rank base per word, and distinct count K_b
-cudaError_t launch_dict_rank(const uint64_t* bm_base, uint32_t B, uint64_t* bitmaps_rank, const uint64_t* bitmaps,
-                             uint64_t* K, cudaStream_t stream);
-// IC-D, step 3: pack ranks and dictionaries
-cudaError_t launch_dict_pack(const uint32_t* pilots, uint64_t np, uint32_t B, const uint64_t* bm_base,
-                             const uint64_t* bitmaps, const uint64_t* bitmaps_rank, const uint64_t* col_meta,
-                             const uint64_t* rank_word_begin, uint64_t* rank_words, uint64_t rank_nwords,
-                             const uint64_t* dict_word_begin, uint64_t* dict_words, uint64_t dict_nwords,
+// ---- k_encode.cu: offsets and interleaved encoders, all key sets per launch ----
+// offsets of one key set: its T values are T[part_base .. part_base + np]
+struct OffDesc {
+    uint64_t part_base, np, Q;  // Q = floor(M 2^32 / np)
+    int64_t dmin;               // minimum stored difference (subtracted before packing)
+    uint64_t dst_word;          // arena word where the set's packed offsets start
+    uint32_t width, pad;
+};
+// one pilot column (bucket b of one key set)
+struct ColDesc {
+    uint64_t src;       // first pilot of the column in the pilot buffer
+    uint64_t count;     // N_P of the set
+    uint64_t dst_word;  // arena word where the set's packed pilots (IC-C) / ranks (IC-D) start
+    uint64_t base;      // bit offset of this column inside that array
+    uint32_t width;     // bits per value
+    uint32_t dict_width;  // IC-D: bits per dictionary value
+    uint64_t bm_base, bm_words;  // IC-D: the column's presence bitmap (words)
+    uint64_t dict_dst_word, dict_base;  // IC-D: the set's dictionary array, this column's bit offset
+};
+cudaError_t launch_offset_minmax(const uint64_t* T, const OffDesc* sets, uint32_t nsets, long long* mm,
+                                 cudaStream_t stream);
+cudaError_t launch_offset_pack(const uint64_t* T, const OffDesc* sets, uint32_t nsets, const uint64_t* word_begin,
+                               uint64_t total_words, uint64_t* arena, cudaStream_t stream);
+cudaError_t launch_column_max(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint32_t* colmax,
+                              cudaStream_t stream);
+cudaError_t launch_pack_columns(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, const uint64_t* word_begin,
+                                uint64_t total_words, bool ranks, const uint64_t* bitmaps,
+                                const uint64_t* bitmaps_rank, uint64_t* arena, cudaStream_t stream);
+cudaError_t launch_dict_mark(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* bitmaps,
                              cudaStream_t stream);
+cudaError_t launch_dict_rank(const ColDesc* cols, uint32_t ncols, uint64_t* bitmaps_rank, const uint64_t* bitmaps,
+                             uint64_t* K, cudaStream_t stream);
+cudaError_t launch_dict_pack_values(const ColDesc* cols, uint32_t ncols, const uint64_t* bm_begin,
+                                    uint64_t total_bm_words, const uint64_t* bitmaps, const uint64_t* bitmaps_rank,
+                                    uint64_t* arena, cudaStream_t stream);
 
-// ---- k_remap.cu: Elias-Fano remap of slots >= n (alpha < 1) ----
-size_t remap_scratch_bytes(uint64_t n, uint64_t M);
-cudaError_t launch_remap(const uint32_t* taken_bits, uint64_t n, uint64_t M, uint32_t l, uint64_t* fs,
-                         uint64_t* ef_low, uint64_t low_nwords, uint64_t* ef_high, uint64_t high_nwords,
-                         uint64_t* ef_samples, void* scratch, cudaStream_t stream);
+// ---- k_remap.cu: Elias-Fano remap of slots >= n (alpha < 1), all key sets per launch ----
+struct RemapDesc {
+    uint64_t g0, n, M;  // the set's slots are bits [g0, g0 + M) of the global occupancy bitmap
+    uint64_t f_base;    // offset of the set's N = M - n entries in the F and fs buffers
+    uint64_t low_dst, high_dst, samp_dst;  // arena words of the set's Elias-Fano arrays
+    uint32_t l, pad;
+};
+size_t remap_scratch_bytes(uint64_t zwords, uint64_t twords, uint64_t ntotal);
+cudaError_t launch_remap(const uint32_t* bm, const RemapDesc* d_sets, uint32_t nsets, const uint64_t* d_zbegin,
+                         uint64_t zwords, const uint64_t* d_tbegin, uint64_t twords, const uint64_t* d_fbegin,
+                         uint64_t ntotal, const uint64_t* d_lbegin, uint64_t lwords, uint64_t* arena, void* scratch,
+                         cudaStream_t st);
 
 // ---- k_query.cu ----
 cudaError_t launch_query(const QueryView& v, const uint64_t* keys, uint64_t* out, uint64_t m, cudaStream_t stream);

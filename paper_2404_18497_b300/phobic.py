@@ -50,6 +50,7 @@ class phobic_params(ctypes.Structure):
         ("keep_pilots", ctypes.c_uint32),
         ("record_timings", ctypes.c_uint32),
         ("candidate_width", ctypes.c_uint32),
+        ("search_schedule", ctypes.c_uint32),
     ]
 
 
@@ -79,6 +80,7 @@ _SIGS = [
     ("phobic_params_init", None, [_PP]),
     ("phobic_build", _INT, [_VP, _U64, _DBL, _DBL, _U32, _U64, _VP, ctypes.POINTER(_VP)]),
     ("phobic_build_ex", _INT, [_VP, _U64, _PP, _VP, ctypes.POINTER(_VP)]),
+    ("phobic_build_batch", _INT, [_VP, _VP, _U32, _VP, _PP, _VP, ctypes.POINTER(_VP)]),
     ("phobic_build_host", _INT, [_VP, _U64, _PP, _VP, ctypes.POINTER(_VP)]),
     ("phobic_query", _INT, [_VP, _VP, _VP, _U64, _VP]),
     ("phobic_build_strings", _INT, [_VP, _VP, _U64, _PP, _VP, ctypes.POINTER(_VP)]),
@@ -143,7 +145,7 @@ def _dev_u64(t: torch.Tensor, what: str) -> torch.Tensor:
 
 def make_params(lam=7.0, alpha=1.0, P=2500, seed=0, encoder="IC-C", mode="additive", s_max=0,
                 keep_pilots=False, warps_per_partition=0, record_timings=False,
-                candidate_width=0) -> phobic_params:
+                candidate_width=0, search_schedule=0) -> phobic_params:
     p = phobic_params()
     lib().phobic_params_init(ctypes.byref(p))
     p.lambda_ = float(lam)
@@ -158,6 +160,7 @@ def make_params(lam=7.0, alpha=1.0, P=2500, seed=0, encoder="IC-C", mode="additi
     p.warps_per_partition = int(warps_per_partition)
     p.record_timings = 1 if record_timings else 0
     p.candidate_width = int(candidate_width)
+    p.search_schedule = int(search_schedule)
     return p
 
 
@@ -216,6 +219,23 @@ def phobic_build_ex(keys: torch.Tensor, params: phobic_params, stream=None) -> H
     _check(lib().phobic_build_ex(k.data_ptr(), k.numel(), ctypes.byref(params), _stream(stream), ctypes.byref(h)),
            "phobic_build_ex")
     return Handle(h.value)
+
+
+def phobic_build_batch(keys: torch.Tensor, set_offsets, params: phobic_params, partition_sizes=None,
+                       stream=None) -> list:
+    """One handle per key set; set s is keys[set_offsets[s]:set_offsets[s+1]]."""
+    k = _dev_u64(keys, "keys")
+    off = np.ascontiguousarray(np.asarray(set_offsets, dtype=np.uint64))
+    ns = off.size - 1
+    if ns < 1 or int(off[-1]) > k.numel():
+        raise ValueError("bad set offsets")
+    ps = None if partition_sizes is None else np.ascontiguousarray(np.asarray(partition_sizes, dtype=np.uint32))
+    if ps is not None and ps.size != ns:
+        raise ValueError("one partition size per set")
+    outs = (ctypes.c_void_p * ns)()
+    _check(lib().phobic_build_batch(k.data_ptr(), off.ctypes.data, ns, None if ps is None else ps.ctypes.data,
+                                    ctypes.byref(params), _stream(stream), outs), "phobic_build_batch")
+    return [Handle(outs[i]) for i in range(ns)]
 
 
 def phobic_build_host(keys: np.ndarray, params: phobic_params, stream=None) -> Handle:

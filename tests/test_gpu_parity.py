@@ -232,10 +232,11 @@ def test_search_variants_agree(ph, orc, mode, monkeypatch):
     for in_smem in ("0", "1"):
         monkeypatch.setenv("PHOBIC_KEYS_IN_SMEM", in_smem)
         for width in (32, 64):
-            h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, 0.99, 2500, mode=mode, keep_pilots=True,
-                                                              candidate_width=width))
-            assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots), (in_smem, width)
-            h.free()
+            for sched in (1, 2):
+                h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, 0.99, 2500, mode=mode, keep_pilots=True,
+                                                                  candidate_width=width, search_schedule=sched))
+                assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots), (in_smem, width, sched)
+                h.free()
 
 
 @pytest.mark.parametrize("n,lam,alpha,enc", [(1, 7.5, 0.99, 0), (50_000, 7.5, 0.99, 1), (1_000_000, 7.5, 0.99, 1),
@@ -277,3 +278,34 @@ def test_string_hash_unaligned_and_tails(ph, orc):
         view.copy_(torch.from_numpy(data))
         got = _host(ph.phobic_hash_strings(view, _dev(off), 123))
         assert np.array_equal(got, orc.string_hashes(data, off, 123))
+
+
+@pytest.mark.parametrize("alpha,enc", [(0.99, 1), (1.0, 0)])
+def test_batch_build_matches_single_builds(ph, orc, alpha, enc):
+    """Batched construction: every set's structure equals the oracle's build of
+    that set alone (and so the single-set path), for uneven set sizes and mixed
+    partition sizes."""
+    from paper_2404_18497_b300 import workloads
+
+    rng = np.random.default_rng(123)
+    sizes = np.concatenate([[1, 2, 3, 17, 2499, 2500, 2501], workloads.log_uniform_sizes(40, 10, 200_000, 9)])
+    rng.shuffle(sizes)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    keys = _keys(int(off[-1]), 51)
+    Ps = rng.choice([1024, 2500, 4096], size=sizes.size).astype(np.uint32)
+    prm = ph.make_params(7.0, alpha, 2500, seed=3, encoder=enc, keep_pilots=True)
+    hs = ph.phobic_build_batch(_dev(keys), off, prm, partition_sizes=Ps)
+    assert len(hs) == sizes.size
+    for s, h in enumerate(hs):
+        ks = keys[off[s]:off[s + 1]]
+        o = orc.Oracle(ks, lam=7.0, alpha=alpha, P=int(Ps[s]), encoder=enc, seed=3, threads=0)
+        assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots), s
+        compare_structure(ph, o, h, enc)
+        got = _host(h.query(_dev(ks)))
+        assert np.array_equal(got, o.query(ks)), s
+    # handles share one allocation: free in an arbitrary order, the rest stay valid
+    last = hs[-1]
+    for h in hs[:-1]:
+        h.free()
+    ks = keys[off[-2]:off[-1]]
+    assert np.array_equal(np.sort(_host(last.query(_dev(ks)))), np.arange(ks.size, dtype=np.uint64))
