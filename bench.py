@@ -51,11 +51,27 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-target-s", type=float, default=12.0)
     ap.add_argument("--candidate-width", type=int, default=0, help="search window width (32/64; 0 = default)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-build section")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--only", choices=["batch", "serve"], default=None, help="run one extra section alone")
     return ap.parse_args()
 
 
 STRINGS = ("2e8 random strings, lengths uniform in [10, 50] over [A-Za-z0-9], XXH64 master hashes on device, "
            "lambda=7.5, alpha=0.99 with Elias-Fano remap, partition size 2500, IC-D; every key queried once")
+
+
+BATCH = ("batched build: 4096 independent sets of distinct uniform uint64 keys, sizes log-uniform in [1e3, 1e7] "
+         "(seed 2024; about 4.45e9 keys in total), lambda=7, alpha=0.99, IC-D, each its own MPHF; partition size "
+         "per size class, warps per partition and candidate width autotuned; compared with one phobic_build_ex per "
+         "set (P 2500, default knobs)")
+SERVE = ("serving: open-loop Poisson requests for {secs:g} s: builds (uint64 key sets, sizes log-uniform in "
+         "[1e4, 5e7], lambda=7, alpha=0.99, IC-D) at {brate:g}/s and query batches (sizes log-uniform in [1e3, 1e6], "
+         "90% members of a random resident MPHF, 10% random non-member keys) at {qrate:g}/s; 120 GB HBM budget; the "
+         "oldest MPHF is released beyond {cap} resident; continuous batching compared with the same trace served "
+         "one request at a time")
 
 
 def workload(a):
@@ -410,6 +426,16 @@ def run_ours(a):
                "note": "phobic_build_host (pinned keys, H2D inside) + phobic_query_host (H2D keys, D2H results)",
                "check": ok}
 
+    batch = serve = None
+    if world == 1 and not (a.no_batch and a.no_serve):
+        dk = dqu = dqz = out = None
+        torch.cuda.empty_cache()
+        phobic.phobic_trim(0)
+        if not a.no_batch:
+            batch = run_batch(a, phobic, workloads, torch)
+        if not a.no_serve:
+            serve = run_serve(a, phobic, workloads, torch)
+
     if rank != 0:
         return
     cpu = None
@@ -448,8 +474,263 @@ def run_ours(a):
         "gpu_launches_per_step": launches / a.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "batch": batch,
+        "serve": serve,
     }
     print(json.dumps(res_line))
+
+# ------------------------------------------------------- batched build (C4) ---
+def run_batch(a, phobic, workloads, torch):
+    """4096 sets built by one batched launch sequence (autotuned) against one
+    build per set; device-resident keys, CUDA events on the build stream."""
+    stream = torch.cuda.current_stream()
+    off = workloads.batch_sets(4096, 1e3, 1e7, 2024)
+    sizes = np.diff(off).astype(np.int64)
+    total = int(off[-1])
+    prm = phobic.make_params(7.0, 0.99, 2500, encoder=1)
+    t = time.perf_counter()
+    Ps, tuned, tinfo = phobic.phobic_tune_batch(off, prm, stream)
+    tune_s = time.perf_counter() - t
+    t = time.perf_counter()
+    _, _, tinfo2 = phobic.phobic_tune_batch(off, prm, stream)
+    tune_cached_s = time.perf_counter() - t
+    keys = workloads.stream_keys_torch(0, total, 11, "cuda")
+    torch.cuda.synchronize()
+
+    def batched():
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hs = phobic.phobic_build_batch(keys, off, tuned, partition_sizes=Ps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return hs, e0.elapsed_time(e1)
+
+    hs, _ = batched()  # warm-up
+    bits = sum(h.bits_per_key() * int(n) for h, n in zip(hs, sizes)) / total
+    for h in hs:
+        h.free()
+    l0 = phobic.phobic_kernel_launches()
+    ms = []
+    for _ in range(a.batch_steps):
+        hs, dt = batched()
+        ms.append(dt)
+        for h in hs:
+            h.free()
+    launches = (phobic.phobic_kernel_launches() - l0) / a.batch_steps
+    # the plain path: one phobic_build_ex per set, P 2500, default knobs
+    seq = phobic.make_params(7.0, 0.99, 2500, encoder=1)
+    for s in range(16):
+        phobic.phobic_build_ex(keys[int(off[s]):int(off[s + 1])], seq, stream).free()
+    torch.cuda.synchronize()
+    l0 = phobic.phobic_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    seq_bits = 0.0
+    for s in range(sizes.size):
+        h = phobic.phobic_build_ex(keys[int(off[s]):int(off[s + 1])], seq, stream)
+        seq_bits += h.bits_per_key() * int(sizes[s])
+        h.free()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    seq_launches = phobic.phobic_kernel_launches() - l0
+    del keys
+    torch.cuda.empty_cache()
+    phobic.phobic_trim(0)
+    b_ms = statistics.mean(ms)
+    return {
+        "workload": BATCH, "sets": int(sizes.size), "keys": total, "steps": a.batch_steps,
+        "batched_ms": b_ms, "batched_ms_all": ms, "batched_mkeys_s": total / (b_ms / 1e3) / 1e6,
+        "batched_launches": launches, "bits_per_key": bits,
+        "sequential_ms": seq_ms, "sequential_mkeys_s": total / (seq_ms / 1e3) / 1e6,
+        "sequential_launches": seq_launches, "sequential_bits_per_key": seq_bits / total,
+        "speedup_vs_sequential": seq_ms / b_ms,
+        "tuned": {"partition_size_by_decade": {f"1e{c}": ci["partition_size"] for c, ci in tinfo["classes"].items()},
+                  "sets_by_decade": {f"1e{c}": ci["sets"] for c, ci in tinfo["classes"].items()},
+                  "ns_per_key_by_decade": {f"1e{c}": ci["ns_per_key"] for c, ci in tinfo["classes"].items()},
+                  "warps_per_partition": tinfo["warps_per_partition"], "candidate_width": tinfo["candidate_width"],
+                  "launch_ns_per_key": tinfo["launch_ns_per_key"], "total_partitions": tinfo["total_partitions"],
+                  "tune_s": tune_s, "tune_cached_s": tune_cached_s,
+                  "cached_second_call": bool(tinfo2["cached_launch"])},
+        "l2": "inputs larger than L2 (35.6 GB of keys vs 126 MB L2)",
+    }
+
+
+# ------------------------------------------------------------ serving (C5) ---
+def _percentiles(x):
+    if len(x) == 0:
+        return {"p50_ms": None, "p99_ms": None, "mean_ms": None, "max_ms": None}
+    x = np.asarray(x, dtype=np.float64) / 1e6
+    return {"p50_ms": float(np.percentile(x, 50)), "p99_ms": float(np.percentile(x, 99)),
+            "mean_ms": float(x.mean()), "max_ms": float(x.max())}
+
+
+def serve_trace(secs, brate, qrate, seed):
+    """Seeded open-loop trace: (arrival s, kind, size) sorted by arrival."""
+    rng = np.random.default_rng(seed)
+    ev = []
+    for kind, rate, lo, hi in ((0, brate, 1e4, 5e7), (1, qrate, 1e3, 1e6)):
+        t = 0.0
+        while True:
+            t += rng.exponential(1.0 / rate)
+            if t >= secs:
+                break
+            ev.append((t, kind, int(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
+    ev.sort()
+    return ev
+
+
+def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_every=100):
+    """Replays the trace against a server.  Latency is measured from each
+    request's scheduled arrival (open loop: a late submission counts against
+    it) to its completion, on the steady clock the library also uses.
+
+    Every key set is a window [ps, ps + n) of a pool of distinct keys.  A query
+    batch of m keys is one slice of the pool that covers 90% of it inside the
+    set's window and 10% just outside it (keys of the pool that are not in the
+    set: random non-members), so no request needs a copy of its input."""
+    P = keys_pool.numel()
+    margin = 1 << 20
+    rng = np.random.default_rng(seed)
+    prm = phobic.make_params(7.0, 0.99, 2500, encoder=1)
+    srv = phobic.Server(hbm_budget_bytes=120 * 10**9, build_slots=2, serial=serial)
+    ring = 1 << 27
+    qout = torch.empty(ring, dtype=torch.int64, device="cuda")
+    head = 0
+    req = {}        # request id -> (kind, arrival ns, ...)
+    resident = []   # (handle id, pool start, n), oldest first
+    keep = set()    # handles kept for the final checks
+    samples = []    # (handle id, pool start, m, request id)
+    outs = {}
+    lat = {0: [], 1: [], 2: []}
+    lat_srv = {0: [], 1: []}
+    keys_done = {0: 0, 1: 0}
+    batch_sizes = []
+    checked_builds = []
+    torch.cuda.synchronize()
+
+    def handle_completions():
+        comp = srv.poll()
+        for c in comp:
+            kind = int(c["kind"])
+            rid = int(c["request_id"])
+            r = req.pop(rid)
+            lat[kind].append(int(c["t_done_ns"]) - r[1])
+            if kind < 2:
+                lat_srv[kind].append(int(c["t_done_ns"]) - int(c["t_submit_ns"]))
+            if kind == 0:
+                _, _, ps, n = r
+                if int(c["status"]) == 0:
+                    resident.append((int(c["handle_id"]), ps, n))
+                    keys_done[0] += n
+                    if len(checked_builds) < 3 and n < 3_000_000:
+                        checked_builds.append((int(c["handle_id"]), ps, n))
+                        keep.add(int(c["handle_id"]))
+            elif kind == 1:
+                _, _, st, m = r
+                keys_done[1] += m
+                batch_sizes.append(int(c["batch_requests"]))
+                if rid in outs:
+                    outs[rid] = qout[st:st + m].clone()
+        return comp.size
+
+    t0 = time.monotonic_ns()
+    i = 0
+    while i < len(trace):
+        now = time.monotonic_ns()
+        arrival = t0 + int(trace[i][0] * 1e9)
+        if arrival > now:
+            if handle_completions() == 0:
+                time.sleep(min(2e-4, (arrival - now) / 1e9))
+            continue
+        _, kind, size = trace[i]
+        i += 1
+        if kind == 0:
+            n = size
+            ps = int(rng.integers(margin, P - n - margin))
+            rid = srv.submit_build(keys_pool[ps:ps + n], prm)
+            req[rid] = (0, arrival, ps, n)
+        else:
+            if not resident:
+                continue
+            hid, ps, n = resident[int(rng.integers(0, len(resident)))]
+            m = size
+            mp = min(n, (m * 9) // 10)
+            mn = m - mp
+            # members at the head or the tail of the set's window, non-members beside them
+            q0 = ps - mn if rng.integers(0, 2) else ps + n - mp
+            if head + m > ring:
+                head = 0
+            # the output region must be free: wait for older requests that overlap it
+            while any(r[0] == 1 and r[2] < head + m and head < r[2] + r[3] for r in req.values()):
+                handle_completions()
+            rid = srv.submit_query(hid, keys_pool[q0:q0 + m], qout[head:head + m])
+            req[rid] = (1, arrival, head, m)
+            if len(samples) < 400 and rid % check_every == 0:
+                samples.append((hid, q0, m, rid))
+                outs[rid] = None
+                keep.add(hid)
+            head += m
+        if len(resident) > cap:
+            for j, (hid, ps0, n0) in enumerate(resident):
+                if hid not in keep:
+                    resident.pop(j)
+                    rid = srv.submit_release(hid)
+                    req[rid] = (2, time.monotonic_ns())
+                    break
+    submit_s = (time.monotonic_ns() - t0) / 1e9
+    srv.drain(600)
+    handle_completions()
+    wall = (time.monotonic_ns() - t0) / 1e9
+    st = srv.stats()
+    # results in the mix equal the results alone (answered now, nothing else running)
+    ok_q, n_q = True, 0
+    for hid, q0, m, rid in samples:
+        if outs.get(rid) is None:
+            continue
+        n_q += 1
+        ok_q = ok_q and bool(torch.equal(srv.handle(hid).query(keys_pool[q0:q0 + m]), outs[rid]))
+    ok_b, n_b = True, 0
+    for hid, ps, n in checked_builds:
+        h = phobic.phobic_build_ex(keys_pool[ps:ps + n], prm)
+        ok_b = ok_b and (h.export() == srv.handle(hid).export())
+        h.free()
+        n_b += 1
+    srv.close()
+    del qout
+    return {
+        "requests": {"builds": len(lat[0]), "queries": len(lat[1]), "releases": len(lat[2])},
+        "query_latency": _percentiles(lat[1]), "build_latency": _percentiles(lat[0]),
+        "query_latency_from_submit": _percentiles(lat_srv[1]), "build_latency_from_submit": _percentiles(lat_srv[0]),
+        "query_mkeys_s": keys_done[1] / wall / 1e6, "build_mkeys_s": keys_done[0] / wall / 1e6,
+        "wall_s": wall, "submit_s": submit_s,
+        "query_launches": st["query_launches"],
+        "mean_requests_per_launch": float(np.mean(batch_sizes)) if batch_sizes else None,
+        "max_requests_per_launch": st["max_batch_requests_seen"],
+        "peak_accounted_gb": st["peak_accounted_bytes"] / 1e9,
+        "builds_waited_for_memory": st["builds_waited_for_memory"],
+        "check": {"queries_compared": n_q, "queries_equal_alone": ok_q, "builds_compared": n_b,
+                  "builds_equal_alone": ok_b},
+    }
+
+
+def run_serve(a, phobic, workloads, torch):
+    secs, brate, qrate, cap = a.serve_seconds, 40.0, 4000.0, 200
+    trace = serve_trace(secs, brate, qrate, 77)
+    keys_pool = workloads.stream_keys_torch(40_000_000_000, 1 << 28, 13, "cuda")
+    torch.cuda.synchronize()
+    cont = run_serve_mode(phobic, torch, trace, False, keys_pool, cap, 5)
+    phobic.phobic_trim(0)
+    ser = run_serve_mode(phobic, torch, trace, True, keys_pool, cap, 5)
+    del keys_pool
+    torch.cuda.empty_cache()
+    phobic.phobic_trim(0)
+    return {"workload": SERVE.format(secs=secs, brate=brate, qrate=qrate, cap=cap),
+            "offered": {"seconds": secs, "build_per_s": brate, "query_per_s": qrate,
+                        "builds": sum(1 for e in trace if e[1] == 0), "queries": sum(1 for e in trace if e[1] == 1)},
+            "continuous": cont, "serial": ser,
+            "query_p99_speedup": (ser["query_latency"]["p99_ms"] / cont["query_latency"]["p99_ms"])
+            if cont["query_latency"]["p99_ms"] else None}
 
 
 def run_strings(a):
@@ -522,8 +803,25 @@ def run_strings(a):
         "e2e": None, "gpu_launches": None, "cpu_baseline": None}))
 
 
+def run_only(a):
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2404_18497_b300 import build as libbuild
+
+    libbuild.build()
+    from paper_2404_18497_b300 import phobic, workloads
+
+    if a.only == "batch":
+        print(json.dumps({"batch": run_batch(a, phobic, workloads, torch)}))
+    else:
+        print(json.dumps({"serve": run_serve(a, phobic, workloads, torch)}))
+
+
 def main():
     a = parse()
+    if a.only and a.impl != "reference":
+        return run_only(a)
     if a.strings and a.impl != "reference":
         return run_strings(a)
     if a.impl == "reference":

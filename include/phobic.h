@@ -68,7 +68,9 @@ typedef struct {
     uint32_t pilot_mode;          /* phobic_pilot_mode */
     uint32_t s_max;               /* search limit: s < s_max (ADDITIVE), p < s_max*m (XOR); 0 = default */
     uint64_t seed;                /* master-hash seed */
-    uint32_t warps_per_partition; /* search kernel tuning: 0 = default; results do not depend on it */
+    uint32_t warps_per_partition; /* search tuning: warps sharing one partition, 1, 2 or 4 (0 = 1); several
+                                     warps test consecutive candidate ranges of a bucket at once and the first
+                                     success in enumeration order is kept, so results do not depend on it */
     uint32_t keep_pilots;         /* nonzero: keep the raw pilot matrix for phobic_copy_pilots */
     uint32_t record_timings;      /* nonzero: time the build phases with CUDA events on `stream` */
     uint32_t candidate_width;     /* search tuning: displacements per lane-window, 32 or 64 (0 = default 64);
@@ -145,6 +147,46 @@ phobic_status phobic_build_batch(const uint64_t* d_keys, const uint64_t* h_set_o
                                  const uint32_t* h_partition_sizes, const phobic_params* params,
                                  phobic_stream_t stream, phobic_handle** out_handles);
 
+/*
+ * Autotuner for phobic_build_batch (the paper has no counterpart).  From the
+ * set sizes alone it picks, by timing trial batches of synthetic keys on the
+ * current device: the expected partition size of every set, one of 1024, 2500,
+ * 4096, per decade size class (the fastest, or within 3% of it the one with the
+ * fewest bits per key); and warps_per_partition (1, 2, 4) and candidate_width
+ * (32, 64) for the launch.  h_set_offsets as for phobic_build_batch (only the
+ * sizes are read; no key is read).  Outputs: h_partition_sizes_out[n_sets],
+ * *params_out = *params with the two search knobs set and search_schedule = 2;
+ * *info (may be NULL) reports the measurements.  Decisions are cached for the
+ * process per device and (lambda, alpha, encoder, pilot_mode, s_max): per size
+ * class for P, per power of two of the partition count for the search knobs.
+ * The trials allocate device memory (keys for up to about 2^25 + one set) and
+ * synchronize `stream`.  Errors: INVALID_ARG, OOM, CUDA, and any build error of
+ * a trial.  Results of builds made with the outputs are exact PHOBIC
+ * constructions with the chosen partition sizes.
+ */
+#define PHOBIC_TUNE_P_CHOICES 3
+#define PHOBIC_TUNE_MAX_CLASSES 20
+typedef struct {
+    uint32_t sets;           /* sets of the batch in this class (0: none) */
+    uint32_t partition_size; /* chosen expected partition size */
+    float ns_per_key[PHOBIC_TUNE_P_CHOICES];   /* trial time per key for P = 1024, 2500, 4096 */
+    float bits_per_key[PHOBIC_TUNE_P_CHOICES]; /* trial bits per key for the same */
+} phobic_tune_class;
+typedef struct {
+    phobic_tune_class classes[PHOBIC_TUNE_MAX_CLASSES]; /* class c: sizes in [10^c, 10^(c+1)) */
+    uint32_t warps_per_partition;
+    uint32_t candidate_width;
+    float launch_ns_per_key[6]; /* (warps, width) = (1,32) (1,64) (2,32) (2,64) (4,32) (4,64) */
+    uint64_t total_partitions;  /* of the batch with the chosen sizes */
+    uint32_t cached_classes;    /* classes answered from the cache */
+    uint32_t cached_launch;     /* 1: search knobs answered from the cache */
+} phobic_tune_info;
+phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32_t n_sets, const phobic_params* params,
+                                phobic_stream_t stream, uint32_t* h_partition_sizes_out,
+                                phobic_params* params_out, phobic_tune_info* info);
+/* Forget every tuning decision and free the trial keys. */
+void phobic_tune_clear(void);
+
 /* Same, from host memory: the keys are copied in chunks through pinned staging
  * buffers and hashed on the device as they arrive. */
 phobic_status phobic_build_host(const uint64_t* h_keys, uint64_t n, const phobic_params* params,
@@ -161,6 +203,20 @@ phobic_status phobic_build_host(const uint64_t* h_keys, uint64_t n, const phobic
  */
 phobic_status phobic_query(const phobic_handle* h, const uint64_t* d_keys, uint64_t* d_out, uint64_t m,
                            phobic_stream_t stream);
+
+/*
+ * Coalesced query (the paper has no counterpart; a serving convenience):
+ * n_req batches against possibly different handles in one kernel launch.
+ * Batch r: d_keys[r][0 .. counts[r]) against handles[r] into d_outs[r].  The
+ * results equal those of n_req separate phobic_query calls.  The host arrays
+ * are read before the call returns; the device buffers follow phobic_query's
+ * rules.  Handles must be built from 64-bit keys.  Batches with counts[r] = 0
+ * are skipped.  Errors: INVALID_ARG (NULL array, NULL or string handle, NULL
+ * buffer of a non-empty batch), OOM, CUDA.
+ */
+phobic_status phobic_query_multi(const phobic_handle* const* handles, const uint64_t* const* d_keys,
+                                 uint64_t* const* d_outs, const uint64_t* counts, uint32_t n_req,
+                                 phobic_stream_t stream);
 
 /* Query from host memory: copies keys in, results out, on `stream`; returns
  * after the results are in h_out. */
@@ -210,6 +266,14 @@ phobic_status phobic_get_timings(const phobic_handle* h, phobic_timings* t);
 /* Number of CUDA kernels this library has launched in this process so far
  * (diagnostic; counts every launch of every entry point). */
 uint64_t phobic_kernel_launches(void);
+
+/* Device memory: builds take their buffers from the current device's default
+ * stream-ordered pool, which keeps freed memory cached for the next build.
+ * phobic_trim synchronizes the device and returns cached memory above
+ * keep_bytes to the system; phobic_pool_bytes reports the pool's reserved and
+ * in-use bytes (handles and running builds).  Errors: INVALID_ARG, CUDA. */
+phobic_status phobic_trim(uint64_t keep_bytes);
+phobic_status phobic_pool_bytes(uint64_t* reserved, uint64_t* used);
 
 /* Releases every device buffer of h (synchronises the device).  NULL is a no-op. */
 void phobic_free(phobic_handle* h);
@@ -263,6 +327,79 @@ phobic_status phobic_partition_sort_noalloc(const uint64_t* d_hk, uint64_t n, ui
 
 /* Writes the 2049-entry fixed-point bucket table (Appendix C) to h_table. */
 phobic_status phobic_bucket_table(double lambda, double alpha, uint32_t partition_size, uint64_t* h_table);
+
+/*
+ * Serving (the paper has no counterpart; a deployment layer that leaves the
+ * construction and query arithmetic untouched).  A server keeps built MPHFs
+ * resident on the current device and accepts requests from any host thread:
+ *   build:   keys on the device -> a resident MPHF id (in the completion);
+ *   query:   resident id, keys, output on the device -> positions in the output;
+ *   release: resident id -> its memory returned.
+ * Continuous mode (serial = 0): builds are admitted in arrival order while at
+ * most build_slots run and the bytes of resident MPHFs plus the estimated
+ * peak of admitted builds (32 B/key + 64 MiB) stay within hbm_budget_bytes
+ * (0: no limit; a build larger than the budget runs alone); each build slot
+ * has its own host thread and stream.  Pending queries against any resident
+ * MPHFs are coalesced into one launch (at most max_batch_requests requests and
+ * max_batch_keys keys) on a high-priority stream while builds run; up to
+ * launch_slots coalesced launches are in flight.  A release completes once no
+ * submitted query reads the MPHF.  Serial mode (serial = 1): one request at a
+ * time in arrival order, each as its own launch sequence waited for to
+ * completion; the budget is not applied.
+ * Ownership: the caller keeps keys and outputs alive until the request's
+ * completion is polled.  `ready` (may be NULL) is an event that the request's
+ * input waits for; it must not be recorded again before that completion.
+ * Results equal those of phobic_build_ex / phobic_query on the same inputs.
+ * Errors at submission: INVALID_ARG (NULL arguments, unknown or releasing id,
+ * an MPHF of string keys, a stopped server), OOM.  A request's own outcome is
+ * the status of its completion.  phobic_server_destroy waits for every
+ * submitted request, then frees every resident MPHF.
+ */
+typedef struct phobic_server phobic_server;
+typedef struct CUevent_st* phobic_event_t; /* same type as cudaEvent_t */
+enum { PHOBIC_REQ_BUILD = 0, PHOBIC_REQ_QUERY = 1, PHOBIC_REQ_RELEASE = 2 };
+typedef struct {
+    uint64_t hbm_budget_bytes;
+    uint32_t build_slots;        /* 0: 2 */
+    uint32_t max_batch_requests; /* 0: 1024 */
+    uint64_t max_batch_keys;     /* 0: 2^24 */
+    uint32_t launch_slots;       /* 0: 4 */
+    uint32_t serial;
+} phobic_server_config;
+typedef struct {
+    uint64_t request_id;
+    uint32_t kind;             /* PHOBIC_REQ_* */
+    int32_t status;            /* phobic_status of the request */
+    uint64_t handle_id;        /* build: the new MPHF's id (0 on error); query, release: the target */
+    uint64_t keys;             /* keys built or queried */
+    int64_t t_submit_ns;       /* steady clock: submission, start on the device side, completion */
+    int64_t t_start_ns;
+    int64_t t_done_ns;
+    uint32_t batch_requests;   /* query: requests in its launch */
+    uint32_t pad;
+    uint64_t batch_id;         /* query: its launch */
+} phobic_completion;
+typedef struct {
+    uint64_t resident_bytes, reserved_bytes, peak_accounted_bytes, resident_handles;
+    uint64_t builds_done, queries_done, releases_done;
+    uint64_t query_launches, max_batch_requests_seen, builds_waited_for_memory;
+    uint64_t pending;
+} phobic_server_stats;
+void phobic_server_config_init(phobic_server_config* c);
+phobic_status phobic_server_create(const phobic_server_config* cfg, phobic_server** out);
+phobic_status phobic_server_submit_build(phobic_server* s, const uint64_t* d_keys, uint64_t n,
+                                         const phobic_params* params, phobic_event_t ready, uint64_t* request_id);
+phobic_status phobic_server_submit_query(phobic_server* s, uint64_t handle_id, const uint64_t* d_keys,
+                                         uint64_t* d_out, uint64_t m, phobic_event_t ready, uint64_t* request_id);
+phobic_status phobic_server_submit_release(phobic_server* s, uint64_t handle_id, uint64_t* request_id);
+/* Up to cap completions, oldest first; *count receives how many. */
+phobic_status phobic_server_poll(phobic_server* s, phobic_completion* out, uint32_t cap, uint32_t* count);
+/* Waits until every submitted request has completed; TIMEOUT after timeout_s seconds. */
+phobic_status phobic_server_drain(phobic_server* s, double timeout_s);
+/* The resident MPHF with this id (borrowed: valid until its release). */
+phobic_status phobic_server_handle(phobic_server* s, uint64_t handle_id, const phobic_handle** out);
+phobic_status phobic_server_get_stats(phobic_server* s, phobic_server_stats* out);
+void phobic_server_destroy(phobic_server* s);
 
 #ifdef __cplusplus
 }

@@ -177,7 +177,57 @@ __global__ void __launch_bounds__(256) k_query_strings(const QueryView v, const 
         out[i] = query_hashed(v, string_master_hash(bytes, offsets, total, i, v.string_seed), seeds);
 }
 
+// Several query batches against different structures in one launch.  The
+// batches are concatenated into one index space: request r covers indexes
+// [reqs[r].begin, reqs[r + 1].begin).  A block takes chunks of kChunk
+// consecutive indexes; thread 0 finds the request of the chunk's first index by
+// binary search and every thread advances from there (a chunk rarely spans more
+// than two requests).  Loads and stores stay coalesced inside each request.
+constexpr uint32_t kChunk = 1024;
+
+__global__ void __launch_bounds__(256) k_query_multi(const MultiQuery* __restrict__ reqs, uint32_t nreq,
+                                                     uint64_t total) {
+    __shared__ uint64_t seeds[kSeedTable];
+    __shared__ uint32_t r_first[2];
+    if (threadIdx.x < kSeedTable) seeds[threadIdx.x] = pilot_seed(threadIdx.x);
+    uint32_t bank = 0;
+    for (uint64_t c0 = blockIdx.x * (uint64_t)kChunk; c0 < total; c0 += (uint64_t)gridDim.x * kChunk) {
+        if (threadIdx.x == 0) {
+            uint32_t lo = 0, hi = nreq;  // largest r with begin <= c0
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (reqs[mid].begin <= c0) lo = mid; else hi = mid;
+            }
+            r_first[bank] = lo;
+        }
+        __syncthreads();  // (two banks: the next chunk's write never meets this chunk's reads)
+        uint32_t r = r_first[bank];
+        bank ^= 1;
+        for (uint32_t k = 0; k < kChunk / 256; k++) {
+            const uint64_t i = c0 + k * 256 + threadIdx.x;
+            if (i >= total) break;
+            while (r + 1 < nreq && reqs[r + 1].begin <= i) r++;
+            const MultiQuery* q = reqs + r;
+            const uint64_t x = __ldcs(q->keys + (i - q->begin));
+            __stcs(q->out + (i - q->begin), query_one(q->v, x, seeds));
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_query_multi(const MultiQuery* d_reqs, uint32_t nreq, uint64_t total, cudaStream_t stream) {
+    if (total == 0 || nreq == 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t want = (total + kChunk - 1) / kChunk;
+    uint64_t cap = (uint64_t)sms * 8;
+    unsigned grid = (unsigned)(want < cap ? want : cap);
+    k_query_multi<<<grid, 256, 0, stream>>>(d_reqs, nreq, total);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_query_strings(const QueryView& v, const uint8_t* bytes, const uint64_t* offsets, uint64_t* out,
                                  uint64_t m, cudaStream_t stream) {

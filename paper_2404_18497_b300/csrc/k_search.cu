@@ -42,11 +42,16 @@ constexpr int kSizeHist = 1024;  // bucket sizes 1..1023
 constexpr int kBigRegs = 4;      // keys per lane kept in registers for buckets of 33..128 keys
 
 struct SmemLayout {
-    uint32_t off_hk, off_bend, off_order, off_fw, off_scr, off_aux, total;
+    uint32_t off_hk, off_bend, off_order, off_fw, off_scr, off_aux, off_ctl, total;
     uint32_t fw_words, scr_words;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem) {
+// Shared memory of one partition's CTA: keys (optional), bucket ends, bucket
+// order, the doubled free bitmap, then per warp a collision scratch bitmap and a
+// u16[1024] buffer of h values (warp 0's also serves as the size histogram),
+// then the control words through which the warps of a CTA agree on a result.
+__host__ __device__ inline SmemLayout smem_layout(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem,
+                                                  uint32_t warps) {
     SmemLayout L;
     uint32_t o = 0;
     L.off_hk = o;
@@ -60,14 +65,23 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t cap_n, uint32_t cap_m
     o += L.fw_words * 4;
     L.scr_words = (cap_m + 31) / 32 + 1;
     L.off_scr = o;
-    o += L.scr_words * 4;
+    o += warps * L.scr_words * 4;
     o = (o + 7) & ~7u;
-    L.off_aux = o;  // size histogram (u16[1024]) / h buffer of large buckets (u16[1024])
-    o += kSizeHist * 2;
+    L.off_aux = o;
+    o += warps * kSizeHist * 2;
+    L.off_ctl = o;
+    o += (warps > 1 ? 4 * warps + 4 : 0) * 4;
     L.total = (o + 15) & ~15u;
     return L;
 }
 
+template <int kWarps>
+__device__ __forceinline__ void cta_sync() {
+    if constexpr (kWarps == 1)
+        __syncwarp();
+    else
+        __syncthreads();
+}
 
 // 32 free bits starting at bit q of the doubled free bitmap
 __device__ __forceinline__ uint32_t window32(const uint32_t* fw, uint32_t q) {
@@ -186,24 +200,66 @@ __device__ bool bucket_has_dup(const uint64_t* keys, uint32_t k, uint32_t lane) 
     return __any_sync(kFull, dup);
 }
 
+// Outcomes of one candidate range (one s, or one run of XOR pilots) for one warp;
+// the first range, in enumeration order, with a nonzero outcome decides.
+constexpr uint32_t kOutNone = 0, kOutFound = 1, kOutDup = 2, kOutLimit = 3;
+
+// Agreement among the warps of a CTA after each of them tested its own
+// candidate range: publish (outcome, value), wait, and return the first warp in
+// enumeration order whose outcome is final (or kWarps when none is).  The slots
+// alternate between two banks so that the next round never overwrites a bank
+// that another warp may still be reading.
+template <int kWarps>
+__device__ __forceinline__ uint32_t first_final(uint32_t* ctl, uint32_t& bank, uint32_t warp, uint32_t lane,
+                                                uint32_t out, uint32_t val, uint32_t& w_out, uint32_t& w_val) {
+    uint32_t* slot = ctl + bank * 2 * kWarps;
+    if (lane == 0) {
+        slot[2 * warp] = out;
+        slot[2 * warp + 1] = val;
+    }
+    __syncthreads();
+    uint32_t w = kWarps;
+#pragma unroll
+    for (int i = kWarps - 1; i >= 0; i--)
+        if (slot[2 * i] != kOutNone) w = (uint32_t)i;
+    if (w < kWarps) {
+        w_out = slot[2 * w];
+        w_val = slot[2 * w + 1];
+    }
+    bank ^= 1u;
+    return w;
+}
+
 // kKeysInSmem: the partition's bucket-sorted master hashes live in shared
 // memory (fewest latency, ~8 B/key of shared memory per partition); otherwise
 // they are written to a global scratch region (the same index range as the
 // sorted input, L2-resident while the partition is active).  Each bucket's keys
 // are prefetched into registers one bucket ahead, and shared memory shrinks to
 // the bitmaps and counters, so several times more partitions fit on an SM.
-template <bool kKeysInSmem, int kW, int kMode>
+//
+// kWarps > 1 warps share one partition.  Bucketing and ordering are split over
+// the CTA (scans by warp 0).  In the placement of a bucket, warp w tests the
+// (w+1)-th next candidate range: s = s0 + w in ADDITIVE mode, pilots
+// p0 + w G .. p0 + w G + G - 1 in XOR mode.  The CTA then takes the first range
+// in enumeration order with a final outcome (placed, duplicate or limit), which
+// is the outcome a single sequential search reaches first.  The singleton
+// buckets come last in the order and are placed by warp 0 alone.
+template <bool kKeysInSmem, int kW, int kMode, int kWarps>
 __device__ __forceinline__ void search_partition(const SearchLaunch& a, const SearchSet& S, const uint64_t gid,
                                                  const uint64_t j, unsigned char* smem, const SmemLayout& L) {
     using Wn = Win<kW>;
     using WT = typename Wn::T;
+    constexpr uint32_t NT = 32 * kWarps;
     uint32_t* bend = reinterpret_cast<uint32_t*>(smem + L.off_bend);
     uint32_t* order = reinterpret_cast<uint32_t*>(smem + L.off_order);
     uint32_t* fw = reinterpret_cast<uint32_t*>(smem + L.off_fw);
-    uint32_t* scr = reinterpret_cast<uint32_t*>(smem + L.off_scr);
     uint16_t* aux = reinterpret_cast<uint16_t*>(smem + L.off_aux);
+    uint32_t* ctl = reinterpret_cast<uint32_t*>(smem + L.off_ctl);  // kWarps > 1 only
 
-    const uint32_t lane = threadIdx.x;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t lane = tid & 31, warp = kWarps == 1 ? 0u : tid >> 5;
+    uint32_t* scr = reinterpret_cast<uint32_t*>(smem + L.off_scr) + warp * L.scr_words;
+    uint16_t* hb = aux + warp * kSizeHist;  // this warp's h values of the bucket's keys
     const uint64_t s0 = a.start[gid];
     const uint32_t nj = (uint32_t)(a.start[gid + 1] - s0);
     const uint64_t Tj = a.T[gid];
@@ -215,9 +271,9 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
     uint64_t* hk = kKeysInSmem ? reinterpret_cast<uint64_t*>(smem + L.off_hk) : a.bkeys + s0;
 
     // ---- init: counts, doubled free bitmap, scratch, size histogram
-    for (uint32_t b = lane; b <= B; b += 32) bend[b] = 0;
+    for (uint32_t b = tid; b <= B; b += NT) bend[b] = 0;
     const uint32_t fwn = (2 * m + 128) / 32 + 3;
-    for (uint32_t w = lane; w < fwn; w += 32) {
+    for (uint32_t w = tid; w < fwn; w += NT) {
         uint32_t lo = w * 32, v;
         if (lo + 32 <= 2 * m)
             v = kFull;
@@ -227,18 +283,23 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
             v = (1u << (2 * m - lo)) - 1;
         fw[w] = v;
     }
-    for (uint32_t w = lane; w < (m + 31) / 32 + 1; w += 32) scr[w] = 0;
-    for (uint32_t i = lane; i < kSizeHist; i += 32) aux[i] = 0;
-    __syncwarp();
+    {
+        uint32_t* scr0 = reinterpret_cast<uint32_t*>(smem + L.off_scr);
+        const uint32_t sw = (m + 31) / 32 + 1;
+        for (uint32_t w = tid; w < kWarps * L.scr_words; w += NT)
+            if (w % L.scr_words < sw) scr0[w] = 0;
+    }
+    for (uint32_t i = tid; i < kSizeHist; i += NT) aux[i] = 0;
+    cta_sync<kWarps>();
 
     // ---- 1. bucket counts, then counting sort of the keys by bucket
-    for (uint32_t i = lane; i < nj; i += 32) {
+    for (uint32_t i = tid; i < nj; i += NT) {
         uint64_t x = __ldg(a.sorted + s0 + i);
         atomicAdd(&bend[bucket_of(bucket_hash(x), table, B)], 1u);
     }
-    __syncwarp();
+    cta_sync<kWarps>();
     uint32_t local_err = kDevOk;
-    {
+    if (warp == 0) {
         uint32_t carry = 0;
         for (uint32_t b0 = 0; b0 < B; b0 += 32) {
             uint32_t b = b0 + lane;
@@ -253,20 +314,20 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
             if (b < B) bend[b] = carry + x - c;  // start of bucket b (cursor)
             carry += __shfl_sync(kFull, x, 31);
         }
+        local_err = __reduce_max_sync(kFull, local_err);
     }
-    local_err = __reduce_max_sync(kFull, local_err);
-    __syncwarp();
-    for (uint32_t i = lane; i < nj; i += 32) {
+    cta_sync<kWarps>();
+    for (uint32_t i = tid; i < nj; i += NT) {
         uint64_t x = __ldg(a.sorted + s0 + i);
         uint32_t b = bucket_of(bucket_hash(x), table, B);
         hk[atomicAdd(&bend[b], 1u)] = x;
     }
-    __syncwarp();
+    cta_sync<kWarps>();
     // now bend[b] = end of bucket b; start of b = b ? bend[b-1] : 0
 
-    // ---- 2. bucket order: size descending, index descending
+    // ---- 2. bucket order: size descending, index descending (warp 0)
     uint32_t nb = 0;
-    if (local_err == kDevOk) {
+    if (warp == 0 && local_err == kDevOk) {
         for (uint32_t b = lane; b < B; b += 32) {
             uint32_t sz = bend[b] - (b ? bend[b - 1] : 0);
             if (sz) atomicAdd(reinterpret_cast<unsigned int*>(aux + (sz & ~1u)), 1u << ((sz & 1) * 16));
@@ -306,6 +367,16 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
             __syncwarp();
         }
     }
+    if constexpr (kWarps > 1) {
+        if (tid == 0) {
+            ctl[4 * kWarps] = nb;
+            ctl[4 * kWarps + 1] = local_err;
+        }
+        __syncthreads();
+        nb = ctl[4 * kWarps];
+        local_err = ctl[4 * kWarps + 1];
+    }
+    uint32_t bank = 0;  // kWarps > 1: control bank of the next agreement round
 
     // ---- 3. placement
     unsigned long long s_tries = 0, steps = 0;
@@ -333,8 +404,9 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
         uint32_t p = 0;
         if (kMode == 0) {
             // ===== additive displacement =====
-            uint16_t* hb = aux;  // h(x, s) of the bucket's keys
             if (k == 1) {
+                // the remaining buckets are singletons: warp 0 places them alone
+                if (kWarps > 1 && warp != 0) break;
                 // one key: s = 0 always works (free slots remain); d is the
                 // distance from h to the first free slot at or after it
                 // only lane 0 holds the key; every lane scans from its h
@@ -370,9 +442,10 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
                 if (lane == 0) pil[(uint64_t)b * S.np] = p;
                 continue;
             }
-            uint32_t h = 0;
             uint32_t d = 0;
-            uint32_t s = 0;
+            uint32_t sb = 0;           // first s of this round
+            uint32_t winner = 0;       // warp whose s decided
+            uint32_t outcome = kOutNone;
             // lanes per window: chosen once per bucket from the current load
             const uint32_t lg = choose_lanes_log2<kW>(k, m - placed, m);  // lanes per window: 2^lg
             uint64_t bigkey[kBigRegs];
@@ -383,196 +456,252 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
                     bigkey[t] = i < k ? keys[i] : 0;
                 }
             }
-            for (; s < a.s_max; s++) {
-                s_tries++;
-                uint64_t ps;
-                if (s < 32)  // warp-uniform branch: never evaluate both sides
-                    ps = __shfl_sync(kFull, ps_lane, s);
-                else
-                    ps = pilot_seed(s);
-                bool coll = false;
-                if (k <= 32) {
-                    h = lane < k ? position_hash(mykey, ps, m) : (0x80000000u | lane);
-                    if (lane < k) hb[lane] = (uint16_t)h;
-                    if (k > 1) {
+            for (;; sb += kWarps) {
+                const uint32_t s = sb + warp;
+                uint32_t my = kOutNone, myd = 0;
+                if (s >= a.s_max) {
+                    my = kOutLimit;
+                } else {
+                    uint64_t ps;
+                    if (s < 32)  // warp-uniform branch: never evaluate both sides
+                        ps = __shfl_sync(kFull, ps_lane, s);
+                    else
+                        ps = pilot_seed(s);
+                    bool coll = false;
+                    if (k <= 32) {
+                        const uint32_t h = lane < k ? position_hash(mykey, ps, m) : (0x80000000u | lane);
+                        if (lane < k) hb[lane] = (uint16_t)h;
                         uint32_t peers = __match_any_sync(kFull, h);
                         coll = __any_sync(kFull, __popc(peers) > 1);
-                    }
-                } else {
-                    // large bucket: up to kBigRegs keys per lane stay in registers
-                    // across s values; the rest are re-read from the key store
-                    bool c = false;
-                    uint32_t hv[kBigRegs];
+                    } else {
+                        // large bucket: up to kBigRegs keys per lane stay in registers
+                        // across s values; the rest are re-read from the key store
+                        bool c = false;
+                        uint32_t hv[kBigRegs];
 #pragma unroll
-                    for (int t = 0; t < kBigRegs; t++) {
-                        const uint32_t i = lane + 32 * t;
-                        hv[t] = i < k ? position_hash(bigkey[t], ps, m) : 0;
-                    }
-#pragma unroll
-                    for (int t = 0; t < kBigRegs; t++) {
-                        const uint32_t i = lane + 32 * t;
-                        if (i < k) {
-                            hb[i] = (uint16_t)hv[t];
-                            const uint32_t bit = 1u << (hv[t] & 31);
-                            if (atomicOr(&scr[hv[t] >> 5], bit) & bit) c = true;
+                        for (int t = 0; t < kBigRegs; t++) {
+                            const uint32_t i = lane + 32 * t;
+                            hv[t] = i < k ? position_hash(bigkey[t], ps, m) : 0;
                         }
+#pragma unroll
+                        for (int t = 0; t < kBigRegs; t++) {
+                            const uint32_t i = lane + 32 * t;
+                            if (i < k) {
+                                hb[i] = (uint16_t)hv[t];
+                                const uint32_t bit = 1u << (hv[t] & 31);
+                                if (atomicOr(&scr[hv[t] >> 5], bit) & bit) c = true;
+                            }
+                        }
+                        for (uint32_t i = lane + 32 * kBigRegs; i < k; i += 32) {
+                            uint32_t hi = position_hash(keys[i], ps, m);
+                            hb[i] = (uint16_t)hi;
+                            uint32_t bit = 1u << (hi & 31);
+                            if (atomicOr(&scr[hi >> 5], bit) & bit) c = true;
+                        }
+                        coll = __any_sync(kFull, c);
+                        for (uint32_t i = lane; i < k; i += 32) scr[hb[i] >> 5] = 0;
                     }
-                    for (uint32_t i = lane + 32 * kBigRegs; i < k; i += 32) {
-                        uint32_t hi = position_hash(keys[i], ps, m);
-                        hb[i] = (uint16_t)hi;
-                        uint32_t bit = 1u << (hi & 31);
-                        if (atomicOr(&scr[hi >> 5], bit) & bit) c = true;
+                    __syncwarp();
+                    if (coll) {
+                        if (s == 8 && bucket_has_dup(keys, k, lane)) my = kOutDup;
+                    } else {
+                        bool f;
+                        switch (lg) {
+                            case 0: f = scan_windows<kW, 0>(fw, hb, k, m, nw, lane, myd, steps); break;
+                            case 1: f = scan_windows<kW, 1>(fw, hb, k, m, nw, lane, myd, steps); break;
+                            case 2: f = scan_windows<kW, 2>(fw, hb, k, m, nw, lane, myd, steps); break;
+                            case 3: f = scan_windows<kW, 3>(fw, hb, k, m, nw, lane, myd, steps); break;
+                            case 4: f = scan_windows<kW, 4>(fw, hb, k, m, nw, lane, myd, steps); break;
+                            default: f = scan_windows<kW, 5>(fw, hb, k, m, nw, lane, myd, steps); break;
+                        }
+                        if (f) my = kOutFound;
                     }
-                    coll = __any_sync(kFull, c);
-                    for (uint32_t i = lane; i < k; i += 32) scr[hb[i] >> 5] = 0;
                 }
-                __syncwarp();
-                if (coll) {
-                    if (s == 8 && bucket_has_dup(keys, k, lane)) {
-                        local_err = kDevDupHash;
+                if constexpr (kWarps == 1) {
+                    if (my != kOutLimit) s_tries++;
+                    if (my != kOutNone) {
+                        outcome = my;
+                        d = myd;
                         break;
                     }
-                    continue;
+                } else {
+                    uint32_t wo = kOutNone, wv = 0;
+                    const uint32_t w = first_final<kWarps>(ctl, bank, warp, lane, my, myd, wo, wv);
+                    if (w < kWarps) {
+                        outcome = wo;
+                        d = wv;
+                        winner = w;
+                        s_tries += w + (wo == kOutLimit ? 0 : 1);
+                        break;
+                    }
+                    s_tries += kWarps;
                 }
-                switch (lg) {
-                    case 0: found = scan_windows<kW, 0>(fw, hb, k, m, nw, lane, d, steps); break;
-                    case 1: found = scan_windows<kW, 1>(fw, hb, k, m, nw, lane, d, steps); break;
-                    case 2: found = scan_windows<kW, 2>(fw, hb, k, m, nw, lane, d, steps); break;
-                    case 3: found = scan_windows<kW, 3>(fw, hb, k, m, nw, lane, d, steps); break;
-                    case 4: found = scan_windows<kW, 4>(fw, hb, k, m, nw, lane, d, steps); break;
-                    default: found = scan_windows<kW, 5>(fw, hb, k, m, nw, lane, d, steps); break;
-                }
-                if (found) break;
             }
-            if (local_err != kDevOk) break;
-            if (!found) {
-                local_err = kDevSearchLimit;
+            if (outcome != kOutFound) {
+                local_err = outcome == kOutDup ? kDevDupHash : kDevSearchLimit;
                 break;
             }
-            p = s * m + d;
-            for (uint32_t i = lane; i < k; i += 32) {
-                uint32_t pos = (uint32_t)hb[i] + d;
-                if (pos >= m) pos -= m;
-                take_slot(fw, pos, m);
+            p = (sb + winner) * m + d;
+            if (warp == winner) {
+                for (uint32_t i = lane; i < k; i += 32) {
+                    uint32_t pos = (uint32_t)hb[i] + d;
+                    if (pos >= m) pos -= m;
+                    take_slot(fw, pos, m);
+                }
             }
             placed += k;
         } else {
             // ===== PTHash XOR form: p = 0, 1, 2, ... =====
             const uint64_t limit = (uint64_t)a.s_max * m;
-            uint32_t mypos = 0;
+            uint32_t outcome = kOutNone, winner = 0;
             if (k <= 32) {
+                // groups of Lc lanes test G consecutive pilots per warp step
                 const uint32_t lc = k <= 1 ? 0u : 32u - __clz(k - 1);  // log2 pow2ceil(k)
                 const uint32_t Lc = 1u << lc, G = 32u >> lc;
                 const uint32_t g = lane >> lc, rr = lane & (Lc - 1);
                 const uint64_t gkey = rr < k ? keys[rr] : 0;
                 const uint32_t gmask = Lc == 32 ? kFull : ((1u << Lc) - 1);
-                bool dup_checked = false;
-                for (uint64_t p0 = 0; p0 < limit; p0 += G) {
-                    steps++;
-                    if (!dup_checked && p0 >= 8ull * m) {
-                        dup_checked = true;
-                        if (bucket_has_dup(keys, k, lane)) {
-                            local_err = kDevDupHash;
+                uint32_t mypos = 0;
+                for (uint64_t pb = 0;; pb += (uint64_t)kWarps * G) {
+                    const uint64_t p0 = pb + (uint64_t)warp * G;
+                    uint32_t my = kOutNone, myp = 0, pos = 0;
+                    if (p0 >= limit) {
+                        my = kOutLimit;
+                    } else if (p0 >= 8ull * m && p0 < 8ull * m + G && bucket_has_dup(keys, k, lane)) {
+                        my = kOutDup;  // the first step at or past 8 m checks for duplicates
+                    } else {
+                        steps++;
+                        const uint64_t pc = p0 + g;
+                        bool ok = true;
+                        uint32_t key = 0xFFFFFFFFu - lane;  // unique, never a slot
+                        if (rr < k && pc < limit) {
+                            pos = position_hash(gkey, pilot_seed(pc), m);
+                            ok = (fw[pos >> 5] >> (pos & 31)) & 1;
+                            key = (g << 20) | pos;
+                        } else if (pc >= limit) {
+                            ok = false;
+                        }
+                        uint32_t peers = __match_any_sync(kFull, key);
+                        ok = ok && __popc(peers) == 1;
+                        uint32_t bad = __ballot_sync(kFull, !ok);
+                        bool gok = ((bad >> (g * Lc)) & gmask) == 0;
+                        uint32_t win = __ballot_sync(kFull, gok && rr == 0);
+                        if (win) {
+                            uint32_t gi = (__ffs(win) - 1) >> lc;
+                            my = kOutFound;
+                            myp = (uint32_t)(p0 + gi);
+                            mypos = __shfl_sync(kFull, pos, (lane & (Lc - 1)) + gi * Lc);
+                        }
+                    }
+                    if constexpr (kWarps == 1) {
+                        if (my != kOutNone) {
+                            outcome = my;
+                            p = myp;
+                            break;
+                        }
+                    } else {
+                        uint32_t wo = kOutNone, wv = 0;
+                        const uint32_t w = first_final<kWarps>(ctl, bank, warp, lane, my, myp, wo, wv);
+                        if (w < kWarps) {
+                            outcome = wo;
+                            p = wv;
+                            winner = w;
                             break;
                         }
                     }
-                    const uint64_t pc = p0 + g;
-                    uint32_t pos = 0;
-                    bool ok = true;
-                    uint32_t key = 0xFFFFFFFFu - lane;  // unique, never a slot
-                    if (rr < k && pc < limit) {
-                        pos = position_hash(gkey, pilot_seed(pc), m);
-                        ok = (fw[pos >> 5] >> (pos & 31)) & 1;
-                        key = (g << 20) | pos;
-                    } else if (pc >= limit) {
-                        ok = false;
-                    }
-                    uint32_t peers = __match_any_sync(kFull, key);
-                    ok = ok && __popc(peers) == 1;
-                    uint32_t bad = __ballot_sync(kFull, !ok);
-                    bool gok = ((bad >> (g * Lc)) & gmask) == 0;
-                    uint32_t win = __ballot_sync(kFull, gok && rr == 0);
-                    if (win) {
-                        uint32_t gi = (__ffs(win) - 1) >> lc;
-                        p = (uint32_t)(p0 + gi);
-                        mypos = __shfl_sync(kFull, pos, (lane & (Lc - 1)) + gi * Lc);
-                        found = true;
-                        break;
-                    }
                 }
-                if (local_err != kDevOk) break;
-                if (!found) {
-                    local_err = kDevSearchLimit;
+                if (outcome != kOutFound) {
+                    local_err = outcome == kOutDup ? kDevDupHash : kDevSearchLimit;
                     break;
                 }
-                if (lane < k) take_slot(fw, mypos, m);
+                if (warp == winner && lane < k) take_slot(fw, mypos, m);
                 placed += k;
             } else {
-                uint16_t* hb = aux;
-                bool dup_checked = false;
-                for (uint64_t pc = 0; pc < limit; pc++) {
-                    steps++;
-                    if (!dup_checked && pc >= 8ull * m) {
-                        dup_checked = true;
-                        if (bucket_has_dup(keys, k, lane)) {
-                            local_err = kDevDupHash;
+                for (uint64_t pb = 0;; pb += kWarps) {
+                    const uint64_t pc = pb + warp;
+                    uint32_t my = kOutNone;
+                    if (pc >= limit) {
+                        my = kOutLimit;
+                    } else if (pc == 8ull * m && bucket_has_dup(keys, k, lane)) {
+                        my = kOutDup;
+                    } else {
+                        steps++;
+                        const uint64_t ps = pilot_seed(pc);
+                        bool bad = false;
+                        for (uint32_t i = lane; i < k; i += 32) {
+                            uint32_t pos = position_hash(keys[i], ps, m);
+                            hb[i] = (uint16_t)pos;
+                            uint32_t bit = 1u << (pos & 31);
+                            if (!((fw[pos >> 5] >> (pos & 31)) & 1)) bad = true;
+                            if (atomicOr(&scr[pos >> 5], bit) & bit) bad = true;
+                        }
+                        bool anybad = __any_sync(kFull, bad);
+                        for (uint32_t i = lane; i < k; i += 32) scr[hb[i] >> 5] = 0;
+                        __syncwarp();
+                        if (!anybad) my = kOutFound;
+                    }
+                    if constexpr (kWarps == 1) {
+                        if (my != kOutNone) {
+                            outcome = my;
+                            p = (uint32_t)pc;
+                            break;
+                        }
+                    } else {
+                        uint32_t wo = kOutNone, wv = 0;
+                        const uint32_t w = first_final<kWarps>(ctl, bank, warp, lane, my, (uint32_t)pc, wo, wv);
+                        if (w < kWarps) {
+                            outcome = wo;
+                            p = wv;
+                            winner = w;
                             break;
                         }
                     }
-                    const uint64_t ps = pilot_seed(pc);
-                    bool bad = false;
-                    for (uint32_t i = lane; i < k; i += 32) {
-                        uint32_t pos = position_hash(keys[i], ps, m);
-                        hb[i] = (uint16_t)pos;
-                        uint32_t bit = 1u << (pos & 31);
-                        if (!((fw[pos >> 5] >> (pos & 31)) & 1)) bad = true;
-                        if (atomicOr(&scr[pos >> 5], bit) & bit) bad = true;
-                    }
-                    bool anybad = __any_sync(kFull, bad);
-                    for (uint32_t i = lane; i < k; i += 32) scr[hb[i] >> 5] = 0;
-                    __syncwarp();
-                    if (!anybad) {
-                        p = (uint32_t)pc;
-                        found = true;
-                        break;
-                    }
                 }
-                if (local_err != kDevOk) break;
-                if (!found) {
-                    local_err = kDevSearchLimit;
+                if (outcome != kOutFound) {
+                    local_err = outcome == kOutDup ? kDevDupHash : kDevSearchLimit;
                     break;
                 }
-                for (uint32_t i = lane; i < k; i += 32) take_slot(fw, hb[i], m);
+                if (warp == winner)
+                    for (uint32_t i = lane; i < k; i += 32) take_slot(fw, hb[i], m);
                 placed += k;
             }
         }
-        __syncwarp();
-        if (lane == 0) pil[(uint64_t)b * S.np] = p;
+        cta_sync<kWarps>();
+        if (tid == 0) pil[(uint64_t)b * S.np] = p;
     }
 
+    if constexpr (kWarps > 1) {
+        // warp 0 alone may have run on (singletons): its error word decides
+        __syncthreads();
+        if (tid == 0) ctl[4 * kWarps + 1] = local_err;
+        __syncthreads();
+        local_err = ctl[4 * kWarps + 1];
+    }
     if (local_err != kDevOk) {
-        // a duplicate anywhere in the partition takes precedence over other errors
-        if (local_err != kDevDupHash) {
-            for (uint32_t b = 0; b < B; b++) {
-                uint32_t bs = b ? bend[b - 1] : 0, k = bend[b] - bs;
-                if (k > 1 && bucket_has_dup(hk + bs, k, lane)) {
-                    local_err = kDevDupHash;
-                    break;
+        if (warp == 0) {
+            // a duplicate anywhere in the partition takes precedence over other errors
+            if (local_err != kDevDupHash) {
+                for (uint32_t b = 0; b < B; b++) {
+                    uint32_t bs = b ? bend[b - 1] : 0, k = bend[b] - bs;
+                    if (k > 1 && bucket_has_dup(hk + bs, k, lane)) {
+                        local_err = kDevDupHash;
+                        break;
+                    }
                 }
             }
+            if (lane == 0) atomicMax(a.status, local_err);
         }
-        if (lane == 0) atomicMax(a.status, local_err);
         return;
     }
     if (a.work && lane == 0) {
-        atomicAdd(a.work, s_tries);
+        if (warp == 0) atomicAdd(a.work, s_tries);
         atomicAdd(a.work + 1, steps);
     }
 
     // ---- 4. taken slots into the global occupancy bitmap at bit offset T_j
     if (a.taken_bits && m) {
         const uint64_t o0 = Tj >> 5, o1 = (Tj + m - 1) >> 5;
-        for (uint64_t o = o0 + lane; o <= o1; o += 32) {
+        for (uint64_t o = o0 + tid; o <= o1; o += NT) {
             int64_t t0 = (int64_t)(o * 32) - (int64_t)Tj;
             uint32_t v;
             if (t0 >= 0) {
@@ -589,20 +718,27 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
     }
 }
 
-// One warp per CTA.  kQueue = true: persistent kernel, every CTA takes the next
-// partition (a global partition id over every key set of the launch) from a
-// device work queue until none are left.  kQueue = false: CTA g processes
-// partition g.  The order in which partitions are processed does not change any
-// result.
-template <bool kKeysInSmem, int kW, int kMode, bool kQueue>
-__global__ void __launch_bounds__(32, 32) k_search(SearchLaunch a) {
+// kWarps warps per CTA, one partition per CTA at a time.  kQueue = true:
+// persistent kernel, every CTA takes the next partition (a global partition id
+// over every key set of the launch) from a device work queue until none are
+// left.  kQueue = false: CTA g processes partition g.  Neither the order in which
+// partitions are processed nor the number of warps changes any result.
+template <bool kKeysInSmem, int kW, int kMode, bool kQueue, int kWarps>
+__global__ void __launch_bounds__(32 * kWarps, 32 / kWarps) k_search(SearchLaunch a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout L = smem_layout(a.cap_n, a.cap_m, a.cap_B, kKeysInSmem);
+    const SmemLayout L = smem_layout(a.cap_n, a.cap_m, a.cap_B, kKeysInSmem, kWarps);
     unsigned long long gid = blockIdx.x;
     for (;;) {
         if (kQueue) {
-            if (threadIdx.x == 0) gid = atomicAdd(a.queue, 1ull);
-            gid = __shfl_sync(kFull, gid, 0);
+            if constexpr (kWarps == 1) {
+                if (threadIdx.x == 0) gid = atomicAdd(a.queue, 1ull);
+                gid = __shfl_sync(kFull, gid, 0);
+            } else {
+                unsigned long long* slot = reinterpret_cast<unsigned long long*>(smem + L.total);
+                if (threadIdx.x == 0) *slot = atomicAdd(a.queue, 1ull);
+                __syncthreads();
+                gid = *slot;
+            }
             if (gid >= a.total_parts) break;
         }
         uint32_t lo = 0, hi = a.nsets;  // key set: largest s with part_base <= gid
@@ -611,9 +747,9 @@ __global__ void __launch_bounds__(32, 32) k_search(SearchLaunch a) {
             if (a.sets[mid].part_base <= gid) lo = mid; else hi = mid;
         }
         const SearchSet S = a.sets[lo];
-        search_partition<kKeysInSmem, kW, kMode>(a, S, gid, gid - S.part_base, smem, L);
+        search_partition<kKeysInSmem, kW, kMode, kWarps>(a, S, gid, gid - S.part_base, smem, L);
         if (!kQueue) break;
-        __syncwarp();
+        cta_sync<kWarps>();
     }
 }
 
@@ -663,8 +799,9 @@ cudaError_t launch_gather_u64(const uint64_t* src, const uint64_t* idx, uint64_t
     return cudaGetLastError();
 }
 
-size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem) {
-    return smem_layout(cap_n, cap_m, B, keys_in_smem).total;
+size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem, uint32_t warps) {
+    // plus one 8-byte slot for the queue's partition id when several warps share a CTA
+    return smem_layout(cap_n, cap_m, B, keys_in_smem, warps).total + (warps > 1 ? 16 : 0);
 }
 
 size_t search_smem_limit() {
@@ -674,26 +811,37 @@ size_t search_smem_limit() {
     return (size_t)v;
 }
 
+namespace {
+using SearchKernel = void (*)(SearchLaunch);
+
+template <bool SM, int W, int MD, int WP>
+SearchKernel pick_queue(bool q) {
+    return q ? k_search<SM, W, MD, true, WP> : k_search<SM, W, MD, false, WP>;
+}
+
+template <int WP>
+SearchKernel pick_kernel(const SearchLaunch& a) {
+    const bool in_smem = a.keys_in_smem != 0, q = a.use_queue != 0;
+    if (a.mode != 0)  // PTHash XOR pilots: the window width does not apply
+        return in_smem ? pick_queue<true, 32, 1, WP>(q) : pick_queue<false, 32, 1, WP>(q);
+    if (a.window_bits == 64)
+        return in_smem ? pick_queue<true, 64, 0, WP>(q) : pick_queue<false, 64, 0, WP>(q);
+    return in_smem ? pick_queue<true, 32, 0, WP>(q) : pick_queue<false, 32, 0, WP>(q);
+}
+}  // namespace
+
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream) {
-    const bool in_smem = a.keys_in_smem != 0;
-    size_t smem = search_smem_bytes(a.cap_n, a.cap_m, a.cap_B, in_smem);
-    void (*kern)(SearchLaunch);
+    const uint32_t wp = a.warps;
+    if (wp != 1 && wp != 2 && wp != 4) return cudaErrorInvalidValue;
+    const size_t smem = search_smem_bytes(a.cap_n, a.cap_m, a.cap_B, a.keys_in_smem != 0, wp);
+    const SearchKernel kern = wp == 1 ? pick_kernel<1>(a) : wp == 2 ? pick_kernel<2>(a) : pick_kernel<4>(a);
     const bool q = a.use_queue != 0;
-#define PICK(SM, W, MD) kern = q ? k_search<SM, W, MD, true> : k_search<SM, W, MD, false>
-    if (a.mode != 0) {  // PTHash XOR pilots: the window width does not apply
-        if (in_smem) PICK(true, 32, 1); else PICK(false, 32, 1);
-    } else if (a.window_bits == 64) {
-        if (in_smem) PICK(true, 64, 0); else PICK(false, 64, 0);
-    } else {
-        if (in_smem) PICK(true, 32, 0); else PICK(false, 32, 0);
-    }
-#undef PICK
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wp, smem)) != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     uint64_t grid = a.total_parts;
     if (q) {
@@ -703,7 +851,7 @@ cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream) {
     }
     if (grid == 0) return cudaSuccess;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-    kern<<<(unsigned)grid, 32, smem, stream>>>(a);
+    kern<<<(unsigned)grid, 32 * wp, smem, stream>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }

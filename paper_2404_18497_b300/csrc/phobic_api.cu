@@ -168,6 +168,7 @@ struct SharedMem {
     void* ptr = nullptr;
     std::atomic<int> refs{0};
     size_t bytes = 0;
+    bool pooled = false;  // from the stream-ordered pool (builds) rather than cudaMalloc (imports)
 };
 
 struct phobic_handle {
@@ -206,13 +207,37 @@ void handle_destroy(phobic_handle* h) {
     delete h;
 }
 
+}  // namespace
+
+namespace phobic {
+// Frees a handle without synchronising the device: the caller guarantees that
+// no work that reads the handle is in flight.  Pool memory goes back to the
+// pool in stream order on `st`; cudaMalloc'ed memory is freed directly.
+void handle_free_idle(phobic_handle* h, cudaStream_t st) {
+    if (!h) return;
+    SharedMem* m = h->mem;
+    if (m && m->refs.fetch_sub(1) == 1) {
+        if (m->pooled)
+            cudaFreeAsync(m->ptr, st);
+        else
+            cudaFree(m->ptr);
+        delete m;
+    }
+    delete h;
+}
+}  // namespace phobic
+
+namespace {
+
 phobic_status check_params(uint64_t n, const phobic_params& p) {
     if (n == 0) return PHOBIC_ERR_INVALID_ARG;
     if (!(p.lambda > 0.0) || !std::isfinite(p.lambda)) return PHOBIC_ERR_INVALID_ARG;
     if (!(p.alpha > 0.0) || p.alpha > 1.0) return PHOBIC_ERR_INVALID_ARG;
     if (p.partition_size == 0 || p.partition_size > kMaxPartitionSize) return PHOBIC_ERR_INVALID_ARG;
     if (p.encoder > PHOBIC_ENC_IC_D || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
-    if (p.warps_per_partition > 1) return PHOBIC_ERR_INVALID_ARG;  // one warp per partition
+    if (p.warps_per_partition != 0 && p.warps_per_partition != 1 && p.warps_per_partition != 2 &&
+        p.warps_per_partition != 4)
+        return PHOBIC_ERR_INVALID_ARG;
     if (p.candidate_width != 0 && p.candidate_width != 32 && p.candidate_width != 64) return PHOBIC_ERR_INVALID_ARG;
     if (p.search_schedule > 2) return PHOBIC_ERR_INVALID_ARG;
     return PHOBIC_OK;
@@ -357,8 +382,9 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     }
     const char* ks = std::getenv("PHOBIC_KEYS_IN_SMEM");
     const bool keys_in_smem = ks && ks[0] == '1';
+    const uint32_t wpp = prm.warps_per_partition ? prm.warps_per_partition : 1;
     if (max_m >= 65536 || max_n >= (1u << 31) ||
-        search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, cap_B, keys_in_smem) > search_smem_limit())
+        search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, cap_B, keys_in_smem, wpp) > search_smem_limit())
         return PHOBIC_ERR_PARTITION_TOO_LARGE;
     uint32_t s_max = prm.s_max ? prm.s_max : 65536u;
     if (max_m > 0 && (uint64_t)s_max * max_m > 0xFFFFFFFFull) s_max = (uint32_t)(0xFFFFFFFFull / max_m);
@@ -402,6 +428,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     sl.bkeys = bkeys;
     sl.keys_in_smem = keys_in_smem ? 1 : 0;
     sl.window_bits = prm.candidate_width == 32 ? 32 : 64;
+    sl.warps = wpp;
     sl.pilots = pilots;
     sl.taken_bits = taken;
     sl.status = status;
@@ -566,6 +593,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
             return from_cuda(e);
         }
         mem->bytes = aw * 8;
+        mem->pooled = true;
     }
     struct MemGuard {
         SharedMem*& m;
@@ -835,6 +863,35 @@ phobic_status phobic_query(const phobic_handle* h, const uint64_t* d_keys, uint6
     return from_cuda(launch_query(h->view, d_keys, d_out, m, (cudaStream_t)stream));
 }
 
+phobic_status phobic_query_multi(const phobic_handle* const* handles, const uint64_t* const* d_keys,
+                                 uint64_t* const* d_outs, const uint64_t* counts, uint32_t n_req,
+                                 phobic_stream_t stream) {
+    if (n_req == 0) return PHOBIC_OK;
+    if (!handles || !d_keys || !d_outs || !counts) return PHOBIC_ERR_INVALID_ARG;
+    std::vector<MultiQuery> reqs;
+    reqs.reserve(n_req);
+    uint64_t total = 0;
+    for (uint32_t r = 0; r < n_req; r++) {
+        const phobic_handle* h = handles[r];
+        if (!h || h->view.key_kind != 0) return PHOBIC_ERR_INVALID_ARG;
+        if (counts[r] == 0) continue;
+        if (!d_keys[r] || !d_outs[r]) return PHOBIC_ERR_INVALID_ARG;
+        reqs.push_back(MultiQuery{h->view, d_keys[r], d_outs[r], total});
+        total += counts[r];
+    }
+    if (reqs.empty()) return PHOBIC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    MultiQuery* d = nullptr;
+    const size_t bytes = reqs.size() * sizeof(MultiQuery);
+    cudaError_t e = cudaMallocAsync(&d, bytes, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    // from pageable memory: returns once the descriptors are staged
+    e = cudaMemcpyAsync(d, reqs.data(), bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_query_multi(d, (uint32_t)reqs.size(), total, st);
+    cudaError_t e2 = cudaFreeAsync(d, st);
+    return from_cuda(e != cudaSuccess ? e : e2);
+}
+
 phobic_status phobic_query_host(const phobic_handle* h, const uint64_t* h_keys, uint64_t* h_out, uint64_t m,
                                 phobic_stream_t stream) {
     if (!h || h->view.key_kind != 0) return PHOBIC_ERR_INVALID_ARG;
@@ -877,6 +934,38 @@ phobic_status phobic_get_timings(const phobic_handle* h, phobic_timings* t) {
 }
 
 uint64_t phobic_kernel_launches(void) { return phobic::g_launches.load(); }
+
+}  // extern "C"
+
+namespace phobic {
+const QueryView* handle_view(const phobic_handle* h) { return h ? &h->view : nullptr; }
+}  // namespace phobic
+
+extern "C" {
+
+phobic_status phobic_trim(uint64_t keep_bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PHOBIC_ERR_CUDA;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return PHOBIC_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return PHOBIC_ERR_CUDA;
+    return cudaMemPoolTrimTo(pool, (size_t)keep_bytes) == cudaSuccess ? PHOBIC_OK : PHOBIC_ERR_CUDA;
+}
+
+phobic_status phobic_pool_bytes(uint64_t* reserved, uint64_t* used) {
+    if (!reserved || !used) return PHOBIC_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PHOBIC_ERR_CUDA;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return PHOBIC_ERR_CUDA;
+    uint64_t r = 0, u = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u) != cudaSuccess)
+        return PHOBIC_ERR_CUDA;
+    *reserved = r;
+    *used = u;
+    return PHOBIC_OK;
+}
 
 void phobic_free(phobic_handle* h) { handle_destroy(h); }
 

@@ -79,11 +79,12 @@ struct SearchLaunch {
     unsigned long long* work;  // [2]: s tries, window steps (may be null)
     unsigned long long* queue; // work-queue counter (the launcher zeroes it)
     uint32_t use_queue;        // 1: persistent CTAs over a work queue; 0: one CTA per partition
+    uint32_t warps;            // warps sharing one partition: 1, 2 or 4 (speed only)
 };
 // out[i] = src[idx[i]]
 cudaError_t launch_gather_u64(const uint64_t* src, const uint64_t* idx, uint64_t* out, uint64_t count,
                               cudaStream_t stream);
-size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem);
+size_t search_smem_bytes(uint32_t cap_n, uint32_t cap_m, uint32_t B, bool keys_in_smem, uint32_t warps);
 size_t search_smem_limit();
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream);
 
@@ -137,6 +138,23 @@ cudaError_t launch_remap(const uint32_t* bm, const RemapDesc* d_sets, uint32_t n
                          cudaStream_t st);
 
 // ---- k_query.cu ----
+// one request of a coalesced query launch: keys[0 .. count) of one structure,
+// at indexes [begin, begin + count) of the launch; the next request's begin
+// (or the launch total) ends it
+struct MultiQuery {
+    QueryView v;
+    const uint64_t* keys;
+    uint64_t* out;
+    uint64_t begin;
+};
+cudaError_t launch_query_multi(const MultiQuery* d_reqs, uint32_t nreq, uint64_t total, cudaStream_t stream);
+// the query view of a handle (defined with the handle in phobic_api.cu)
+}  // namespace phobic
+struct phobic_handle;
+namespace phobic {
+const QueryView* handle_view(const phobic_handle* h);
+// frees a handle that no in-flight work reads, without a device synchronisation
+void handle_free_idle(phobic_handle* h, cudaStream_t st);
 cudaError_t launch_query(const QueryView& v, const uint64_t* keys, uint64_t* out, uint64_t m, cudaStream_t stream);
 cudaError_t launch_query_strings(const QueryView& v, const uint8_t* bytes, const uint64_t* offsets, uint64_t* out,
                                  uint64_t m, cudaStream_t stream);

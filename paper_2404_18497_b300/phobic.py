@@ -74,6 +74,48 @@ class phobic_info(ctypes.Structure):
 
 _lib = None
 # (name, restype, argtypes): the C ABI, in header order
+REQ_BUILD, REQ_QUERY, REQ_RELEASE = 0, 1, 2
+
+
+class phobic_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("build_slots", ctypes.c_uint32),
+                ("max_batch_requests", ctypes.c_uint32), ("max_batch_keys", ctypes.c_uint64),
+                ("launch_slots", ctypes.c_uint32), ("serial", ctypes.c_uint32)]
+
+
+class phobic_completion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("kind", ctypes.c_uint32), ("status", ctypes.c_int32),
+                ("handle_id", ctypes.c_uint64), ("keys", ctypes.c_uint64), ("t_submit_ns", ctypes.c_int64),
+                ("t_start_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64), ("batch_requests", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("batch_id", ctypes.c_uint64)]
+
+
+COMPLETION_DTYPE = np.dtype([(n, np.dtype(t._type_)) for n, t in phobic_completion._fields_], align=True)
+
+
+class phobic_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "resident_bytes", "reserved_bytes", "peak_accounted_bytes", "resident_handles", "builds_done",
+        "queries_done", "releases_done", "query_launches", "max_batch_requests_seen", "builds_waited_for_memory",
+        "pending")]
+
+
+TUNE_P_CHOICES = (1024, 2500, 4096)
+TUNE_MAX_CLASSES = 20
+
+
+class phobic_tune_class(ctypes.Structure):
+    _fields_ = [("sets", ctypes.c_uint32), ("partition_size", ctypes.c_uint32),
+                ("ns_per_key", ctypes.c_float * 3), ("bits_per_key", ctypes.c_float * 3)]
+
+
+class phobic_tune_info(ctypes.Structure):
+    _fields_ = [("classes", phobic_tune_class * TUNE_MAX_CLASSES),
+                ("warps_per_partition", ctypes.c_uint32), ("candidate_width", ctypes.c_uint32),
+                ("launch_ns_per_key", ctypes.c_float * 6), ("total_partitions", ctypes.c_uint64),
+                ("cached_classes", ctypes.c_uint32), ("cached_launch", ctypes.c_uint32)]
+
+
 _VP, _U64, _U32, _DBL, _INT = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_int
 _PP = ctypes.POINTER(phobic_params)
 _SIGS = [
@@ -100,6 +142,21 @@ _SIGS = [
     ("phobic_partition_sort", _INT, [_VP, _U64, _U64, _VP, _VP, _VP]),
     ("phobic_partition_sort_noalloc", _INT, [_VP, _U64, _U64, _VP, _VP, _VP]),
     ("phobic_bucket_table", _INT, [_DBL, _DBL, _U32, _VP]),
+    ("phobic_tune_batch", _INT, [_VP, _U32, _PP, _VP, _VP, _PP, ctypes.POINTER(phobic_tune_info)]),
+    ("phobic_tune_clear", None, []),
+    ("phobic_trim", _INT, [_U64]),
+    ("phobic_query_multi", _INT, [_VP, _VP, _VP, _VP, _U32, _VP]),
+    ("phobic_server_config_init", None, [ctypes.POINTER(phobic_server_config)]),
+    ("phobic_server_create", _INT, [ctypes.POINTER(phobic_server_config), ctypes.POINTER(_VP)]),
+    ("phobic_server_submit_build", _INT, [_VP, _VP, _U64, _PP, _VP, ctypes.POINTER(_U64)]),
+    ("phobic_server_submit_query", _INT, [_VP, _U64, _VP, _VP, _U64, _VP, ctypes.POINTER(_U64)]),
+    ("phobic_server_submit_release", _INT, [_VP, _U64, ctypes.POINTER(_U64)]),
+    ("phobic_server_poll", _INT, [_VP, _VP, _U32, ctypes.POINTER(_U32)]),
+    ("phobic_server_drain", _INT, [_VP, _DBL]),
+    ("phobic_server_handle", _INT, [_VP, _U64, ctypes.POINTER(_VP)]),
+    ("phobic_server_get_stats", _INT, [_VP, ctypes.POINTER(phobic_server_stats)]),
+    ("phobic_server_destroy", None, [_VP]),
+    ("phobic_pool_bytes", _INT, [ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
 ]
 
 
@@ -165,10 +222,11 @@ def make_params(lam=7.0, alpha=1.0, P=2500, seed=0, encoder="IC-C", mode="additi
 
 
 class Handle:
-    """One built MPHF (owns the C handle)."""
+    """One built MPHF (owns the C handle unless borrowed)."""
 
-    def __init__(self, ptr: int):
+    def __init__(self, ptr: int, borrowed: bool = False):
         self._h = ctypes.c_void_p(ptr)
+        self._borrowed = borrowed
 
     @property
     def ptr(self) -> ctypes.c_void_p:
@@ -177,9 +235,9 @@ class Handle:
         return self._h
 
     def free(self):
-        if self._h.value:
+        if self._h.value and not self._borrowed:
             lib().phobic_free(self._h)
-            self._h = ctypes.c_void_p(0)
+        self._h = ctypes.c_void_p(0)
 
     def __del__(self):
         try:
@@ -236,6 +294,144 @@ def phobic_build_batch(keys: torch.Tensor, set_offsets, params: phobic_params, p
     _check(lib().phobic_build_batch(k.data_ptr(), off.ctypes.data, ns, None if ps is None else ps.ctypes.data,
                                     ctypes.byref(params), _stream(stream), outs), "phobic_build_batch")
     return [Handle(outs[i]) for i in range(ns)]
+
+
+def phobic_tune_batch(set_offsets, params: phobic_params, stream=None):
+    """Autotuned (partition sizes per set, params with the search knobs, info dict)
+    for a batch with these set offsets; see phobic_tune_batch in the header."""
+    off = np.ascontiguousarray(np.asarray(set_offsets, dtype=np.uint64))
+    ns = off.size - 1
+    if ns < 1:
+        raise ValueError("bad set offsets")
+    ps = np.zeros(ns, dtype=np.uint32)
+    pout = phobic_params()
+    info = phobic_tune_info()
+    _check(lib().phobic_tune_batch(off.ctypes.data, ns, ctypes.byref(params), _stream(stream), ps.ctypes.data,
+                                   ctypes.byref(pout), ctypes.byref(info)), "phobic_tune_batch")
+    classes = {}
+    for c in range(TUNE_MAX_CLASSES):
+        tc = info.classes[c]
+        if tc.sets:
+            classes[c] = dict(sets=tc.sets, partition_size=tc.partition_size,
+                              ns_per_key=dict(zip(TUNE_P_CHOICES, map(float, tc.ns_per_key))),
+                              bits_per_key=dict(zip(TUNE_P_CHOICES, map(float, tc.bits_per_key))))
+    combos = [(w, cw) for w in (1, 2, 4) for cw in (32, 64)]
+    d = dict(classes=classes, warps_per_partition=info.warps_per_partition, candidate_width=info.candidate_width,
+             launch_ns_per_key={f"w{w}/c{cw}": float(v) for (w, cw), v in zip(combos, info.launch_ns_per_key)},
+             total_partitions=int(info.total_partitions), cached_classes=info.cached_classes,
+             cached_launch=info.cached_launch)
+    return ps, pout, d
+
+
+def phobic_query_multi(handles, keys, outs, stream=None) -> None:
+    """One coalesced launch: keys[r] against handles[r] into outs[r]."""
+    n = len(handles)
+    if not (len(keys) == len(outs) == n):
+        raise ValueError("one key and one output tensor per handle")
+    hs = (ctypes.c_void_p * n)(*[h.ptr.value for h in handles])
+    ks = (ctypes.c_void_p * n)(*[_dev_u64(k, "keys").data_ptr() for k in keys])
+    os_ = (ctypes.c_void_p * n)()
+    cs = (ctypes.c_uint64 * n)()
+    for i, (k, o) in enumerate(zip(keys, outs)):
+        o = _dev_u64(o, "out")
+        if o.numel() < k.numel():
+            raise ValueError("out shorter than keys")
+        os_[i] = o.data_ptr()
+        cs[i] = k.numel()
+    _check(lib().phobic_query_multi(hs, ks, os_, cs, n, _stream(stream)), "phobic_query_multi")
+
+
+class Server:
+    """Serving loop over resident MPHFs (see phobic_server_* in the header).
+    Keys and outputs are CUDA tensors that the caller keeps alive until the
+    request's completion has been polled."""
+
+    def __init__(self, hbm_budget_bytes=0, build_slots=2, max_batch_requests=1024, max_batch_keys=1 << 24,
+                 launch_slots=4, serial=False):
+        c = phobic_server_config()
+        lib().phobic_server_config_init(ctypes.byref(c))
+        c.hbm_budget_bytes, c.build_slots, c.max_batch_requests = int(hbm_budget_bytes), build_slots, max_batch_requests
+        c.max_batch_keys, c.launch_slots, c.serial = int(max_batch_keys), launch_slots, int(bool(serial))
+        p = ctypes.c_void_p()
+        _check(lib().phobic_server_create(ctypes.byref(c), ctypes.byref(p)), "phobic_server_create")
+        self._s = p
+        self._buf = np.zeros(4096, dtype=COMPLETION_DTYPE)
+
+    @staticmethod
+    def _ev(ready):
+        return None if ready is None else ready.cuda_event if hasattr(ready, "cuda_event") else int(ready)
+
+    def submit_build(self, keys: torch.Tensor, params: phobic_params, ready=None) -> int:
+        k = _dev_u64(keys, "keys")
+        rid = _U64()
+        _check(lib().phobic_server_submit_build(self._s, k.data_ptr(), k.numel(), ctypes.byref(params),
+                                                self._ev(ready), ctypes.byref(rid)), "phobic_server_submit_build")
+        return int(rid.value)
+
+    def submit_query(self, handle_id: int, keys: torch.Tensor, out: torch.Tensor, ready=None) -> int:
+        k, o = _dev_u64(keys, "keys"), _dev_u64(out, "out")
+        if o.numel() < k.numel():
+            raise ValueError("out shorter than keys")
+        rid = _U64()
+        _check(lib().phobic_server_submit_query(self._s, int(handle_id), k.data_ptr(), o.data_ptr(), k.numel(),
+                                                self._ev(ready), ctypes.byref(rid)), "phobic_server_submit_query")
+        return int(rid.value)
+
+    def submit_release(self, handle_id: int) -> int:
+        rid = _U64()
+        _check(lib().phobic_server_submit_release(self._s, int(handle_id), ctypes.byref(rid)),
+               "phobic_server_submit_release")
+        return int(rid.value)
+
+    def poll(self) -> np.ndarray:
+        """Completed requests since the last poll (structured array, oldest first)."""
+        out = []
+        while True:
+            cnt = _U32()
+            _check(lib().phobic_server_poll(self._s, self._buf.ctypes.data, self._buf.size, ctypes.byref(cnt)),
+                   "phobic_server_poll")
+            out.append(self._buf[: cnt.value].copy())
+            if cnt.value < self._buf.size:
+                break
+        return np.concatenate(out)
+
+    def drain(self, timeout_s: float = 600.0) -> None:
+        _check(lib().phobic_server_drain(self._s, float(timeout_s)), "phobic_server_drain")
+
+    def handle(self, handle_id: int) -> Handle:
+        p = ctypes.c_void_p()
+        _check(lib().phobic_server_handle(self._s, int(handle_id), ctypes.byref(p)), "phobic_server_handle")
+        return Handle(p.value, borrowed=True)
+
+    def stats(self) -> dict:
+        st = phobic_server_stats()
+        _check(lib().phobic_server_get_stats(self._s, ctypes.byref(st)), "phobic_server_get_stats")
+        return {f[0]: int(getattr(st, f[0])) for f in phobic_server_stats._fields_}
+
+    def close(self) -> None:
+        if self._s is not None and self._s.value:
+            lib().phobic_server_destroy(self._s)
+        self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def phobic_trim(keep_bytes: int = 0) -> None:
+    _check(lib().phobic_trim(int(keep_bytes)), "phobic_trim")
+
+
+def phobic_pool_bytes() -> tuple:
+    r, u = _U64(), _U64()
+    _check(lib().phobic_pool_bytes(ctypes.byref(r), ctypes.byref(u)), "phobic_pool_bytes")
+    return int(r.value), int(u.value)
+
+
+def phobic_tune_clear() -> None:
+    lib().phobic_tune_clear()
 
 
 def phobic_build_host(keys: np.ndarray, params: phobic_params, stream=None) -> Handle:

@@ -11,7 +11,17 @@ Workload recipes follow the paper's settings and the benchmark configurations:
   continuous 1/r law, r = floor((n + 1)^u) with u uniform in [0, 1), and mapped
   to a key through a seeded permutation;
 - random strings of length uniform in [10, 50] over [A-Za-z0-9] (Section 5's
-  input).
+  input);
+- batches of many key sets with log-uniform sizes, whose keys come from a
+  counter-based stream (below) that the host and the device produce alike, so
+  a test can rebuild any sampled set on the host without copying the batch
+  back.
+
+The counter-based stream: key i = fmix64(seed' + i * W), with W the odd 64-bit
+Weyl increment 0x9E3779B97F4A7C15, seed' = fmix64(seed) and fmix64 the
+MurmurHash3 64-bit finaliser (Appleby).  fmix64 is a bijection on 64-bit words
+and i -> seed' + i W is injective for i < 2^64, so all keys of the stream are
+distinct.
 """
 from __future__ import annotations
 
@@ -68,6 +78,64 @@ def random_strings(n: int, seed: int, lmin: int = 10, lmax: int = 50):
     np.cumsum(lens, out=offsets[1:])
     data = ALNUM[rng.integers(0, ALNUM.size, size=int(offsets[-1]), dtype=np.uint8)]
     return data, offsets
+
+
+_W = 0x9E3779B97F4A7C15
+_F1 = 0xFF51AFD7ED558CCD
+_F2 = 0xC4CEB9FE1A85EC53
+
+
+def _fmix64_np(k: np.ndarray) -> np.ndarray:
+    k = k ^ (k >> np.uint64(33))
+    k = k * np.uint64(_F1)
+    k = k ^ (k >> np.uint64(33))
+    k = k * np.uint64(_F2)
+    return k ^ (k >> np.uint64(33))
+
+
+def _stream_base(seed: int) -> int:
+    with np.errstate(over="ignore"):
+        return int(_fmix64_np(np.array([seed & (2**64 - 1)], dtype=np.uint64))[0])
+
+
+def stream_keys(start: int, n: int, seed: int) -> np.ndarray:
+    """Keys start .. start + n - 1 of the counter-based stream, on the host."""
+    i = np.arange(start, start + n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _fmix64_np(np.uint64(_stream_base(seed)) + i * np.uint64(_W))
+
+
+def _s64(c: int) -> int:
+    return c - 2**64 if c >= 2**63 else c
+
+
+def stream_keys_torch(start: int, n: int, seed: int, device, chunk: int = 1 << 27):
+    """The same keys as stream_keys, generated on `device` as an int64 tensor
+    (the uint64 bit patterns), in chunks to bound temporary memory."""
+    import torch
+
+    out = torch.empty(n, dtype=torch.int64, device=device)
+    base, w, f1, f2 = _s64(_stream_base(seed)), _s64(_W), _s64(_F1), _s64(_F2)
+    m31 = (1 << 31) - 1  # logical shift right by 33 of a 64-bit word
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        k = torch.arange(start + c0, start + c1, dtype=torch.int64, device=device)
+        k.mul_(w).add_(base)
+        k.bitwise_xor_((k >> 33) & m31)
+        k.mul_(f1)
+        k.bitwise_xor_((k >> 33) & m31)
+        k.mul_(f2)
+        k.bitwise_xor_((k >> 33) & m31)
+        out[c0:c1] = k
+    return out
+
+
+def batch_sets(count: int, lo: float, hi: float, seed: int) -> np.ndarray:
+    """Set offsets (uint64[count + 1]) of a batch with log-uniform set sizes."""
+    sizes = np.maximum(1, log_uniform_sizes(count, lo, hi, seed))
+    off = np.zeros(count + 1, dtype=np.uint64)
+    np.cumsum(sizes, out=off[1:])
+    return off
 
 
 def log_uniform_sizes(count: int, lo: float, hi: float, seed: int) -> np.ndarray:

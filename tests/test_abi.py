@@ -58,13 +58,17 @@ def test_status_strings_and_params(libpath):
 
 
 def test_struct_layouts_match_header(libpath):
-    """phobic_params / phobic_info sizes as the C compiler lays them out"""
+    """sizes of the header's structs as the C compiler lays them out"""
     from paper_2404_18497_b300 import phobic
 
     code = r'''
     #include <stdio.h>
     #include "phobic.h"
-    int main(void) { printf("%zu %zu\n", sizeof(phobic_params), sizeof(phobic_info)); return 0; }
+    int main(void) {
+        printf("%zu %zu %zu %zu %zu %zu\n", sizeof(phobic_params), sizeof(phobic_info), sizeof(phobic_tune_info),
+               sizeof(phobic_server_config), sizeof(phobic_completion), sizeof(phobic_server_stats));
+        return 0;
+    }
     '''
     exe = os.path.join(ROOT, "paper_2404_18497_b300", "_build", "layout_probe")
     os.makedirs(os.path.dirname(exe), exist_ok=True)
@@ -72,9 +76,13 @@ def test_struct_layouts_match_header(libpath):
     with open(src, "w") as f:
         f.write(code)
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
-    a, b = map(int, subprocess.check_output([exe], text=True).split())
+    a, b, c, d, e, f = map(int, subprocess.check_output([exe], text=True).split())
+    assert d == ctypes.sizeof(phobic.phobic_server_config)
+    assert e == ctypes.sizeof(phobic.phobic_completion) == phobic.COMPLETION_DTYPE.itemsize
+    assert f == ctypes.sizeof(phobic.phobic_server_stats)
     assert a == ctypes.sizeof(phobic.phobic_params)
     assert b == ctypes.sizeof(phobic.phobic_info)
+    assert c == ctypes.sizeof(phobic.phobic_tune_info)
 
 
 @pytest.mark.parametrize("lam,alpha,P", [(7.0, 1.0, 2500), (7.0, 0.99, 2500), (7.5, 0.99, 2500), (3.0, 1.0, 16),
@@ -99,3 +107,18 @@ def test_invalid_arguments_without_gpu(libpath):
     assert L.phobic_query(None, None, None, 0, None) == 1
     assert L.phobic_import(b"nonsense", 8, None, ctypes.byref(h)) == 8
     L.phobic_free(None)
+    # the tuner validates before it touches a device
+    ps = (ctypes.c_uint32 * 2)()
+    out = phobic.phobic_params()
+    off = (ctypes.c_uint64 * 3)(0, 5, 5)  # an empty set
+    assert L.phobic_tune_batch(off, 2, ctypes.byref(p), None, ps, ctypes.byref(out), None) == 1
+    assert L.phobic_tune_batch(None, 2, ctypes.byref(p), None, ps, ctypes.byref(out), None) == 1
+    # coalesced query and server entry points reject NULL arguments
+    assert L.phobic_query_multi(None, None, None, None, 3, None) == 1
+    assert L.phobic_query_multi(None, None, None, None, 0, None) == 0
+    rid = ctypes.c_uint64()
+    assert L.phobic_server_submit_build(None, None, 0, ctypes.byref(p), None, ctypes.byref(rid)) == 1
+    assert L.phobic_server_submit_query(None, 1, None, None, 0, None, ctypes.byref(rid)) == 1
+    assert L.phobic_server_submit_release(None, 1, ctypes.byref(rid)) == 1
+    assert L.phobic_server_create(None, None) == 1
+    L.phobic_server_destroy(None)

@@ -180,9 +180,21 @@ def test_errors(ph):
     with pytest.raises(ph.PhobicError) as e:
         ph.phobic_build(_dev(dup), 7.0, 1.0, 2500, 0)
     assert e.value.status == "DUP_HASH"
-    with pytest.raises(ph.PhobicError) as e:
-        ph.phobic_build_ex(_dev(keys), ph.make_params(12.0, 1.0, 2500, s_max=1))
-    assert e.value.status == "SEARCH_LIMIT"
+    # every search variant reports the same errors (several warps per partition
+    # keep the first final outcome in enumeration order)
+    for mode in (0, 1):
+        for wpp in (1, 2, 4):
+            with pytest.raises(ph.PhobicError) as e:
+                ph.phobic_build_ex(_dev(dup), ph.make_params(7.0, 1.0, 2500, mode=mode, warps_per_partition=wpp))
+            assert e.value.status == "DUP_HASH", (mode, wpp)
+            with pytest.raises(ph.PhobicError) as e:
+                ph.phobic_build_ex(_dev(keys), ph.make_params(12.0, 1.0, 2500, mode=mode, s_max=1,
+                                                              warps_per_partition=wpp))
+            assert e.value.status == "SEARCH_LIMIT", (mode, wpp)
+    for wpp in (3, 8):
+        with pytest.raises(ph.PhobicError) as e:
+            ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, 1.0, 2500, warps_per_partition=wpp))
+        assert e.value.status == "INVALID_ARG"
     for kw in [dict(lam=0.0), dict(alpha=0.0), dict(alpha=1.5), dict(P=0), dict(P=100_000)]:
         args = dict(lam=7.0, alpha=1.0, P=2500)
         args.update(kw)
@@ -194,23 +206,27 @@ def test_errors(ph):
     assert torch.unique(h.query(_dev(keys))).numel() == keys.size
 
 
-def test_search_limit_matches_oracle(ph, orc):
-    """With a small s_max both sides fail (or succeed) on the same inputs."""
+@pytest.mark.parametrize("mode", [0, 1])
+def test_search_limit_matches_oracle(ph, orc, mode):
+    """With a small s_max both sides fail (or succeed) on the same inputs, for
+    every number of warps per partition."""
     keys = _keys(50_000, 10)
     for s_max in (1, 2, 4, 64):
         try:
-            orc.Oracle(keys, lam=9.0, P=2500, s_max=s_max, threads=0)
+            orc.Oracle(keys, lam=9.0, P=2500, mode=mode, s_max=s_max, threads=0)
             o_ok = True
         except orc.OracleError as e:
             assert e.code == orc.SEARCH_LIMIT
             o_ok = False
-        try:
-            ph.phobic_build_ex(_dev(keys), ph.make_params(9.0, 1.0, 2500, s_max=s_max)).free()
-            g_ok = True
-        except ph.PhobicError as e:
-            assert e.status == "SEARCH_LIMIT"
-            g_ok = False
-        assert o_ok == g_ok, s_max
+        for wpp in (1, 2, 4):
+            try:
+                ph.phobic_build_ex(_dev(keys), ph.make_params(9.0, 1.0, 2500, mode=mode, s_max=s_max,
+                                                              warps_per_partition=wpp)).free()
+                g_ok = True
+            except ph.PhobicError as e:
+                assert e.status == "SEARCH_LIMIT"
+                g_ok = False
+            assert o_ok == g_ok, (s_max, wpp)
 
 
 def test_host_entry_points(ph, orc):
@@ -223,20 +239,24 @@ def test_host_entry_points(ph, orc):
     assert np.array_equal(out, _host(h2.query(_dev(keys))))
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_search_variants_agree(ph, orc, mode, monkeypatch):
-    """Window width (32 or 64 displacements per lane) and key placement (shared
-    memory or global scratch) change speed only: pilots equal the oracle's."""
+@pytest.mark.parametrize("mode,lam,P", [(0, 7.0, 2500), (1, 7.0, 2500), (0, 9.0, 1024), (1, 8.0, 4096)])
+def test_search_variants_agree(ph, orc, mode, lam, P, monkeypatch):
+    """Window width (32 or 64 displacements per lane), key placement (shared
+    memory or global scratch), schedule (one CTA per partition or a work queue)
+    and warps per partition change speed only: pilots equal the oracle's."""
     keys = _keys(200_000, 31)
-    o = orc.Oracle(keys, lam=7.0, alpha=0.99, P=2500, mode=mode, threads=0)
+    o = orc.Oracle(keys, lam=lam, alpha=0.99, P=P, mode=mode, threads=0)
     for in_smem in ("0", "1"):
         monkeypatch.setenv("PHOBIC_KEYS_IN_SMEM", in_smem)
         for width in (32, 64):
             for sched in (1, 2):
-                h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, 0.99, 2500, mode=mode, keep_pilots=True,
-                                                                  candidate_width=width, search_schedule=sched))
-                assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots), (in_smem, width, sched)
-                h.free()
+                for wpp in (1, 2, 4):
+                    h = ph.phobic_build_ex(_dev(keys), ph.make_params(lam, 0.99, P, mode=mode, keep_pilots=True,
+                                                                      candidate_width=width, search_schedule=sched,
+                                                                      warps_per_partition=wpp))
+                    assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots), \
+                        (in_smem, width, sched, wpp)
+                    h.free()
 
 
 @pytest.mark.parametrize("n,lam,alpha,enc", [(1, 7.5, 0.99, 0), (50_000, 7.5, 0.99, 1), (1_000_000, 7.5, 0.99, 1),
@@ -293,7 +313,8 @@ def test_batch_build_matches_single_builds(ph, orc, alpha, enc):
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     keys = _keys(int(off[-1]), 51)
     Ps = rng.choice([1024, 2500, 4096], size=sizes.size).astype(np.uint32)
-    prm = ph.make_params(7.0, alpha, 2500, seed=3, encoder=enc, keep_pilots=True)
+    prm = ph.make_params(7.0, alpha, 2500, seed=3, encoder=enc, keep_pilots=True,
+                         warps_per_partition=2 if enc else 1)
     hs = ph.phobic_build_batch(_dev(keys), off, prm, partition_sizes=Ps)
     assert len(hs) == sizes.size
     for s, h in enumerate(hs):
