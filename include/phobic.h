@@ -300,6 +300,24 @@ phobic_status phobic_hash_strings(const uint8_t* d_bytes, const uint64_t* d_offs
 phobic_status phobic_partition_sort(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions,
                                     uint64_t* d_sorted, uint64_t* d_start, phobic_stream_t stream);
 
+/*
+ * Self-test of failure detection in the partition sort (the paper has no
+ * counterpart).  Every wait of the sort's decoupled look-back is bounded: after
+ * a number of polls of a predecessor tile that has not published its state,
+ * the kernel records a timeout in a device status word, stops waiting and
+ * finishes; the call then returns PHOBIC_ERR_TIMEOUT and the context stays
+ * usable.  This entry point runs phobic_partition_sort with tile mute_tile
+ * (of 4096 keys each) withholding its state, so that the wait of the tile after
+ * it runs out after spin_limit polls (a flag that nothing sets).  Nothing faults
+ * or hangs.  Returns TIMEOUT when a wait ran out, OK when none did (mute_tile
+ * past the last tile, or a single pass-free sort); d_sorted / d_start are then
+ * unspecified.  Errors: INVALID_ARG (as phobic_partition_sort, or spin_limit 0),
+ * OOM, CUDA.
+ */
+phobic_status phobic_selftest_sort_wait_timeout(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions,
+                                                uint64_t mute_tile, uint32_t spin_limit, uint64_t* d_sorted,
+                                                uint64_t* d_start, phobic_stream_t stream);
+
 /* Largest n accepted by phobic_partition_sort_noalloc. */
 #define PHOBIC_NOALLOC_MAX_KEYS 1048576u
 

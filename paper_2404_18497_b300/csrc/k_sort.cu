@@ -129,6 +129,8 @@ struct PassArgs {
     unsigned long long* status;            // [tiles x R]: flag | value
     uint32_t* tile_counter;
     uint32_t* error;
+    uint32_t spin_limit;  // polls of an unpublished predecessor before the wait gives up
+    uint64_t mute_tile;   // self-test: this tile never publishes its state (~0: none)
 };
 
 // One digit pass.  Tile = kTile consecutive keys.  Warp w ranks its 32 x kItems
@@ -200,10 +202,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(PassArgs a) {
         const uint64_t cnt = tile_start[d];
         volatile unsigned long long* st = a.status;
         uint64_t excl = 0;
+        const bool publish = tile != a.mute_tile;
         if (tile == first) {
-            st[tile * R + d] = kFlagPre | cnt;
+            if (publish) st[tile * R + d] = kFlagPre | cnt;
         } else {
-            st[tile * R + d] = kFlagAgg | cnt;
+            if (publish) st[tile * R + d] = kFlagAgg | cnt;
             int64_t t = (int64_t)tile - 1;  // next predecessor to account for
             uint32_t spins = 0;
             bool done = false;
@@ -225,14 +228,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(PassArgs a) {
                 if (done) break;
                 t -= u;
                 if (u == 0) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > a.spin_limit) {
                         atomicMax(a.error, kDevTimeout);
                         break;
                     }
                     if (spins > 32) __nanosleep(64);
                 }
             }
-            st[tile * R + d] = kFlagPre | (excl + cnt);
+            if (publish) st[tile * R + d] = kFlagPre | (excl + cnt);
         }
         gbase[d] = a.digit_base[((uint64_t)sg * a.passes + a.pass) * R + d] + excl;
     }
@@ -353,7 +356,7 @@ size_t sort_scratch_bytes(uint64_t n, uint64_t np) {
 cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint64_t kseed, const SortSeg* d_segs,
                                        uint32_t nseg, uint64_t n_total, uint64_t tiles, uint64_t max_np,
                                        uint64_t total_parts, uint64_t* sorted, uint64_t* start, void* scratch,
-                                       uint32_t* d_error, cudaStream_t stream) {
+                                       uint32_t* d_error, cudaStream_t stream, const SortWaitTest* wait_test) {
     uint32_t passes, bits;
     sort_plan(max_np, &passes, &bits);
     const uint32_t R = 1u << bits;
@@ -414,6 +417,8 @@ cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint6
             a.status = status;
             a.tile_counter = counters + ps;
             a.error = d_error;
+            a.spin_limit = wait_test ? wait_test->spin_limit : kSpinLimit;
+            a.mute_tile = wait_test ? wait_test->mute_tile : ~0ull;
             k_sort_pass<<<(unsigned)tiles, kThreads, smem, stream>>>(a);
             note_launches(1);
             src = dst;
@@ -429,7 +434,7 @@ cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint6
 
 cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t kseed, uint64_t n, uint64_t np,
                                   uint64_t* sorted, uint64_t* start, void* scratch, uint32_t* d_error,
-                                  cudaStream_t stream) {
+                                  cudaStream_t stream, const SortWaitTest* wait_test) {
     // one segment; its record sits at the end of the scratch region
     const uint64_t tiles = sort_tiles(n);
     SortSeg* d_seg = reinterpret_cast<SortSeg*>(static_cast<unsigned char*>(scratch) +
@@ -443,7 +448,7 @@ cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t k
     cudaError_t e = cudaMemcpyAsync(d_seg, &hs, sizeof(SortSeg), cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return e;
     return launch_partition_sort_segs(in, hash_input, kseed, d_seg, 1, n, tiles, np, np, sorted, start, scratch,
-                                      d_error, stream);
+                                      d_error, stream, wait_test);
 }
 
 cudaError_t launch_hash_u64(const uint64_t* keys, uint64_t n, uint64_t kseed, uint64_t* out, cudaStream_t stream) {

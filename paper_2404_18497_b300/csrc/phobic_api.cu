@@ -1177,8 +1177,9 @@ phobic_status phobic_hash_u64(const uint64_t* d_keys, uint64_t n, uint64_t seed,
     return from_cuda(launch_hash_u64(d_keys, n, key_seed(seed), d_hk, (cudaStream_t)stream));
 }
 
-phobic_status phobic_partition_sort(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions, uint64_t* d_sorted,
-                                    uint64_t* d_start, phobic_stream_t stream) {
+namespace {
+phobic_status partition_sort_impl(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions, uint64_t* d_sorted,
+                                  uint64_t* d_start, phobic_stream_t stream, const SortWaitTest* wait_test) {
     if (n == 0 || num_partitions == 0 || !d_hk || !d_sorted || !d_start) return PHOBIC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     ensure_pool();
@@ -1188,11 +1189,25 @@ phobic_status phobic_partition_sort(const uint64_t* d_hk, uint64_t n, uint64_t n
     CK(tmp.alloc(&scratch, sort_scratch_bytes(n, num_partitions)));
     CK(tmp.alloc(&err, 16));
     CK(cudaMemsetAsync(err, 0, 16, st));
-    CK(launch_partition_sort(d_hk, 0, 0, n, num_partitions, d_sorted, d_start, scratch, err, st));
+    CK(launch_partition_sort(d_hk, 0, 0, n, num_partitions, d_sorted, d_start, scratch, err, st, wait_test));
     uint32_t herr = 0;
     CK(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return herr ? PHOBIC_ERR_TIMEOUT : PHOBIC_OK;
+}
+}  // namespace
+
+phobic_status phobic_partition_sort(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions, uint64_t* d_sorted,
+                                    uint64_t* d_start, phobic_stream_t stream) {
+    return partition_sort_impl(d_hk, n, num_partitions, d_sorted, d_start, stream, nullptr);
+}
+
+phobic_status phobic_selftest_sort_wait_timeout(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions,
+                                                uint64_t mute_tile, uint32_t spin_limit, uint64_t* d_sorted,
+                                                uint64_t* d_start, phobic_stream_t stream) {
+    if (spin_limit == 0) return PHOBIC_ERR_INVALID_ARG;
+    const SortWaitTest t{mute_tile, spin_limit};
+    return partition_sort_impl(d_hk, n, num_partitions, d_sorted, d_start, stream, &t);
 }
 
 phobic_status phobic_bucket_table(double lambda, double alpha, uint32_t partition_size, uint64_t* h_table) {

@@ -20,6 +20,12 @@ constexpr uint32_t kSortTileKeys = 4096;  // keys per onesweep tile
 struct SortSeg {
     uint64_t key_base, n, np, part_base, first_tile;
 };
+// Self-test of the look-back wait: tile mute_tile never publishes its state,
+// so the wait of its successor runs out after spin_limit polls.
+struct SortWaitTest {
+    uint64_t mute_tile;
+    uint32_t spin_limit;
+};
 void sort_plan(uint64_t np, uint32_t* passes, uint32_t* bits);
 uint64_t sort_tiles(uint64_t n);
 size_t sort_seg_scratch_bytes(uint64_t n_total, uint64_t tiles, uint32_t nseg, uint64_t max_np);
@@ -27,10 +33,11 @@ size_t sort_scratch_bytes(uint64_t n, uint64_t np);
 cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint64_t kseed, const SortSeg* d_segs,
                                        uint32_t nseg, uint64_t n_total, uint64_t tiles, uint64_t max_np,
                                        uint64_t total_parts, uint64_t* sorted, uint64_t* start, void* scratch,
-                                       uint32_t* d_error, cudaStream_t stream);
+                                       uint32_t* d_error, cudaStream_t stream,
+                                       const SortWaitTest* wait_test = nullptr);
 cudaError_t launch_partition_sort(const uint64_t* in, int hash_input, uint64_t kseed, uint64_t n, uint64_t np,
                                   uint64_t* sorted, uint64_t* start, void* scratch, uint32_t* d_error,
-                                  cudaStream_t stream);
+                                  cudaStream_t stream, const SortWaitTest* wait_test = nullptr);
 cudaError_t launch_hash_u64(const uint64_t* keys, uint64_t n, uint64_t kseed, uint64_t* out, cudaStream_t stream);
 cudaError_t launch_hash_strings(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint64_t seed,
                                 uint64_t* out, cudaStream_t stream);

@@ -141,6 +141,7 @@ _SIGS = [
     ("phobic_hash_strings", _INT, [_VP, _VP, _U64, _U64, _VP, _VP]),
     ("phobic_partition_sort", _INT, [_VP, _U64, _U64, _VP, _VP, _VP]),
     ("phobic_partition_sort_noalloc", _INT, [_VP, _U64, _U64, _VP, _VP, _VP]),
+    ("phobic_selftest_sort_wait_timeout", _INT, [_VP, _U64, _U64, _U64, _U32, _VP, _VP, _VP]),
     ("phobic_bucket_table", _INT, [_DBL, _DBL, _U32, _VP]),
     ("phobic_tune_batch", _INT, [_VP, _U32, _PP, _VP, _VP, _PP, ctypes.POINTER(phobic_tune_info)]),
     ("phobic_tune_clear", None, []),
@@ -558,6 +559,18 @@ def phobic_partition_sort(hk: torch.Tensor, num_partitions: int, stream=None):
     _check(lib().phobic_partition_sort(h.data_ptr(), h.numel(), int(num_partitions), sorted_.data_ptr(),
                                        start.data_ptr(), _stream(stream)), "phobic_partition_sort")
     return sorted_, start
+
+
+def phobic_selftest_sort_wait_timeout(hk: torch.Tensor, num_partitions: int, mute_tile: int, spin_limit: int,
+                                      stream=None) -> int:
+    """Runs the partition sort with one tile withholding its look-back state;
+    returns the status code (TIMEOUT when a bounded wait ran out)."""
+    h = _dev_u64(hk, "hk")
+    sorted_ = torch.empty_like(h, dtype=torch.int64)
+    start = torch.empty(num_partitions + 1, dtype=torch.int64, device=h.device)
+    return int(lib().phobic_selftest_sort_wait_timeout(h.data_ptr(), h.numel(), int(num_partitions), int(mute_tile),
+                                                       int(spin_limit), sorted_.data_ptr(), start.data_ptr(),
+                                                       _stream(stream)))
 
 
 NOALLOC_MAX_KEYS = 1048576
