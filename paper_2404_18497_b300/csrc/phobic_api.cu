@@ -382,7 +382,21 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     }
     const char* ks = std::getenv("PHOBIC_KEYS_IN_SMEM");
     const bool keys_in_smem = ks && ks[0] == '1';
-    const uint32_t wpp = prm.warps_per_partition ? prm.warps_per_partition : 1;
+    // warps per partition: as asked, or (0) chosen from the partition count.  One
+    // warp per partition fills the GPU once there are several partitions per
+    // resident one-warp CTA slot (32 per SM); with fewer partitions, 2 or 4
+    // warps test consecutive candidate ranges of each bucket at once.
+    uint32_t wpp = prm.warps_per_partition;
+    if (wpp == 0) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const uint64_t slots = (uint64_t)sms * 32;
+        wpp = NPT * 4 <= slots ? 4 : NPT * 2 <= slots ? 2 : 1;
+        while (wpp > 1 && search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, cap_B, keys_in_smem, wpp) >
+                              search_smem_limit())
+            wpp /= 2;
+    }
     if (max_m >= 65536 || max_n >= (1u << 31) ||
         search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, cap_B, keys_in_smem, wpp) > search_smem_limit())
         return PHOBIC_ERR_PARTITION_TOO_LARGE;
