@@ -18,7 +18,7 @@ _SRC = os.path.join(_HERE, "phobic_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 
 OK, INVALID_ARG, OOM, DUP_HASH, SEARCH_LIMIT = 0, 1, 2, 3, 4
-ENC_IC_C, ENC_IC_D = 0, 1
+ENC_IC_C, ENC_IC_D, ENC_IC_R = 0, 1, 2
 PILOT_ADDITIVE, PILOT_XOR = 0, 1
 
 
@@ -71,6 +71,7 @@ def lib():
         L.or_mix64.restype = u64; L.or_mix64.argtypes = [u64]
         L.or_mulhi64.restype = u64; L.or_mulhi64.argtypes = [u64, u64]
         L.or_bitlen.restype = u32; L.or_bitlen.argtypes = [u64]
+        L.or_rice_param.restype = u32; L.or_rice_param.argtypes = [u64, u64]
         L.or_beta_star.restype = dbl; L.or_beta_star.argtypes = [dbl]
         L.or_gamma.restype = dbl; L.or_gamma.argtypes = [dbl, dbl, dbl]
         L.or_epsilon.restype = dbl; L.or_epsilon.argtypes = [dbl, u32]

@@ -19,7 +19,8 @@
  *     Section 5 ("Further Remarks") adds a secondary order: increasing expected
  *     size.
  *   - Section 4.1 (Interleaved Coding): encoder i holds the pilot of bucket i of
- *     every partition (Compact; Dictionary as named in Figure 3b).
+ *     every partition (Compact; Dictionary as named in Figure 3b; Golomb-Rice
+ *     with Kiely's parameter and a select sample every 64 values).
  *   - Section 5 ("Further Remarks"): the PTHash non-minimal trick of building on
  *     M > n slots and remapping slots >= n onto free slots < n, with Elias-Fano.
  *
@@ -295,6 +296,15 @@ struct or_mphf {
     uint64_t rank_nbits, dict_nbits;
     uint64_t* rank_words;
     uint64_t* dict_words;
+    /* IC-R */
+    uint32_t* col_l;      /* Rice parameter: low bits per value */
+    uint64_t* col_lbase;  /* bit offset of the column's low parts */
+    uint64_t* col_hbase;  /* bit offset of the column's unary parts */
+    uint64_t* col_H;      /* bits of the column's unary parts */
+    uint64_t rlow_nbits, rhigh_nbits, rsamp_count;
+    uint64_t* rice_low;
+    uint64_t* rice_high;
+    uint32_t* rice_samples;
     /* remap of slots >= n (alpha < 1) */
     uint64_t ef_N, ef_U;
     uint32_t ef_l;
@@ -314,7 +324,7 @@ static int check_params(uint64_t n, const or_params* p) {
     if (!(p->lambda > 0.0) || !isfinite(p->lambda)) return OR_ERR_INVALID_ARG;
     if (!(p->alpha > 0.0) || p->alpha > 1.0) return OR_ERR_INVALID_ARG;
     if (p->partition_size == 0) return OR_ERR_INVALID_ARG;
-    if (p->encoder > OR_ENC_IC_D || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
+    if (p->encoder > OR_ENC_IC_R || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
     if (p->s_max == 0) return OR_ERR_INVALID_ARG;
     return OR_OK;
 }
@@ -626,9 +636,89 @@ static void encode_dictionary(or_mphf* h) {
     free(tmp);
 }
 
+/* Golomb-Rice (Section 4.1 names it with Kiely's parameter choice).  For a
+ * geometric source with parameter theta, the Rice parameter with the smallest
+ * expected code length is max(0, 1 + floor(log2(log(phi - 1) / log(theta)))),
+ * phi the golden ratio (Kiely 2004).  The column's values are modelled as
+ * geometric with the column's mean mu: theta = mu / (mu + 1). */
+uint32_t or_rice_param(uint64_t sum, uint64_t count) {
+    if (sum == 0 || count == 0) return 0;
+    double mu = (double)sum / (double)count;
+    double theta = mu / (mu + 1.0);
+    double ratio = log((sqrt(5.0) - 1.0) / 2.0) / log(theta);
+    double k = 1.0 + floor(log2(ratio));
+    if (!(k > 0.0)) return 0;
+    if (k > 31.0) return 31;
+    return (uint32_t)k;
+}
+
+/* Column b: the low l bits of each value packed at width l; the rest in unary,
+ * value j setting bit j + sum_{i <= j} (v_i >> l) of the column's unary bits;
+ * the position of that bit for every 64th value kept as a select sample. */
+static void encode_rice(or_mphf* h) {
+    uint32_t B = h->B;
+    uint64_t NP = h->NP, ns = (NP + 63) / 64;
+    h->col_l = (uint32_t*)calloc(B, sizeof(uint32_t));
+    h->col_lbase = (uint64_t*)calloc(B, sizeof(uint64_t));
+    h->col_hbase = (uint64_t*)calloc(B, sizeof(uint64_t));
+    h->col_H = (uint64_t*)calloc(B, sizeof(uint64_t));
+    uint64_t lbase = 0, hbase = 0;
+    for (uint32_t b = 0; b < B; b++) {
+        uint64_t sum = 0;
+        for (uint64_t j = 0; j < NP; j++) sum += h->pilots[(uint64_t)b * NP + j];
+        uint32_t l = or_rice_param(sum, NP);
+        uint64_t H = NP;
+        for (uint64_t j = 0; j < NP; j++) H += h->pilots[(uint64_t)b * NP + j] >> l;
+        h->col_l[b] = l;
+        h->col_lbase[b] = lbase;
+        h->col_hbase[b] = hbase;
+        h->col_H[b] = H;
+        lbase += NP * (uint64_t)l;
+        hbase += H;
+    }
+    h->rlow_nbits = lbase;
+    h->rhigh_nbits = hbase;
+    h->rsamp_count = (uint64_t)B * ns;
+    h->rice_low = (uint64_t*)calloc(packed_words(lbase), sizeof(uint64_t));
+    h->rice_high = (uint64_t*)calloc(packed_words(hbase), sizeof(uint64_t));
+    h->rice_samples = (uint32_t*)calloc(h->rsamp_count ? h->rsamp_count : 1, sizeof(uint32_t));
+    for (uint32_t b = 0; b < B; b++) {
+        uint32_t l = h->col_l[b];
+        uint64_t acc = 0;
+        for (uint64_t j = 0; j < NP; j++) {
+            uint32_t v = h->pilots[(uint64_t)b * NP + j];
+            put_bits(h->rice_low, h->col_lbase[b] + j * l, l ? (v & ((1ULL << l) - 1)) : 0, l);
+            acc += v >> l;
+            uint64_t pos = j + acc; /* the j-th one of the column */
+            put_bits(h->rice_high, h->col_hbase[b] + pos, 1, 1);
+            if (j % 64 == 0) h->rice_samples[(uint64_t)b * ns + j / 64] = (uint32_t)pos;
+        }
+    }
+}
+
+/* position (relative to the column) of the t-th one of column b's unary bits */
+static uint64_t rice_select(const or_mphf* h, uint32_t b, uint64_t t) {
+    uint64_t ns = (h->NP + 63) / 64;
+    uint64_t pos = h->rice_samples[(uint64_t)b * ns + t / 64];
+    uint64_t left = t % 64; /* ones still to pass */
+    while (left) {
+        pos++;
+        if (get_bits(h->rice_high, h->col_hbase[b] + pos, 1)) left--;
+    }
+    return pos;
+}
+
+static uint32_t decode_rice(const or_mphf* h, uint32_t b, uint64_t j) {
+    uint64_t c = rice_select(h, b, j);
+    uint64_t q = (j == 0) ? c : c - rice_select(h, b, j - 1) - 1;
+    uint32_t l = h->col_l[b];
+    return (uint32_t)((q << l) | get_bits(h->rice_low, h->col_lbase[b] + j * l, l));
+}
+
 static uint32_t decode_pilot(const or_mphf* h, uint32_t b, uint64_t j) {
     if (h->prm.encoder == OR_ENC_IC_C)
         return (uint32_t)get_bits(h->pil_words, h->col_base[b] + j * h->col_w[b], h->col_w[b]);
+    if (h->prm.encoder == OR_ENC_IC_R) return decode_rice(h, b, j);
     uint64_t r = get_bits(h->rank_words, h->col_rbase[b] + j * h->col_rw[b], h->col_rw[b]);
     return (uint32_t)get_bits(h->dict_words, h->col_dbase[b] + r * h->col_dw[b], h->col_dw[b]);
 }
@@ -700,6 +790,8 @@ static void account_bits(or_mphf* h) {
     for (uint32_t b = 0; b < h->B; b++) {
         if (h->prm.encoder == OR_ENC_IC_C)
             bp += NP * (uint64_t)h->col_w[b] + 64 + 8;
+        else if (h->prm.encoder == OR_ENC_IC_R)
+            bp += NP * (uint64_t)h->col_l[b] + h->col_H[b] + 32 * ((NP + 63) / 64) + 64 + 64 + 8;
         else
             bp += NP * (uint64_t)h->col_rw[b] + h->col_K[b] * (uint64_t)h->col_dw[b] + 64 + 64 + 8 + 8;
     }
@@ -717,6 +809,8 @@ void or_free(or_mphf* h) {
     free(h->col_w); free(h->col_base); free(h->pil_words);
     free(h->col_rw); free(h->col_rbase); free(h->col_dw); free(h->col_dbase); free(h->col_K);
     free(h->rank_words); free(h->dict_words);
+    free(h->col_l); free(h->col_lbase); free(h->col_hbase); free(h->col_H);
+    free(h->rice_low); free(h->rice_high); free(h->rice_samples);
     free(h->fs); free(h->ef_low); free(h->ef_high); free(h->ef_samples);
     free(h);
 }
@@ -820,6 +914,8 @@ int or_build_hashed(const uint64_t* hk, uint64_t n, const or_params* prm, int th
     encode_offsets(h);
     if (prm->encoder == OR_ENC_IC_C)
         encode_compact(h);
+    else if (prm->encoder == OR_ENC_IC_R)
+        encode_rice(h);
     else
         encode_dictionary(h);
     build_remap(h, taken_global);
@@ -876,7 +972,7 @@ double or_bits_per_key(const or_mphf* h) { return (double)h->bits_total / (doubl
 uint64_t or_get_u64(const or_mphf* h, const char* name) {
 #define G(x) if (!strcmp(name, #x)) return (uint64_t)h->x
     G(n); G(M); G(NP); G(B); G(off_Q); G(off_w); G(off_nbits); G(pil_nbits); G(rank_nbits);
-    G(dict_nbits); G(ef_N); G(ef_U); G(ef_l); G(ef_low_nbits); G(ef_high_nbits); G(ef_nsamples);
+    G(dict_nbits); G(rlow_nbits); G(rhigh_nbits); G(rsamp_count); G(ef_N); G(ef_U); G(ef_l); G(ef_low_nbits); G(ef_high_nbits); G(ef_nsamples);
     G(bits_header); G(bits_offsets); G(bits_pilots); G(bits_remap); G(bits_total);
     G(stat_candidates); G(stat_key_tests); G(stat_s_tries);
 #undef G
@@ -896,6 +992,14 @@ const void* or_get_array(const or_mphf* h, const char* name, uint64_t* count, ui
         A(col_w, h->B, 4);
         A(col_base, h->B, 8);
         A(pil_words, packed_words(h->pil_nbits), 8);
+    } else if (h->prm.encoder == OR_ENC_IC_R) {
+        A(col_l, h->B, 4);
+        A(col_lbase, h->B, 8);
+        A(col_hbase, h->B, 8);
+        A(col_H, h->B, 8);
+        A(rice_low, packed_words(h->rlow_nbits), 8);
+        A(rice_high, packed_words(h->rhigh_nbits), 8);
+        A(rice_samples, h->rsamp_count, 4);
     } else {
         A(col_rw, h->B, 4);
         A(col_rbase, h->B, 8);

@@ -29,6 +29,7 @@ extern "C" {
 
 #define OR_ENC_IC_C 0
 #define OR_ENC_IC_D 1
+#define OR_ENC_IC_R 2
 
 #define OR_PILOT_ADDITIVE 0
 #define OR_PILOT_XOR 1
@@ -52,6 +53,9 @@ typedef struct or_mphf or_mphf;
 uint64_t or_mix64(uint64_t z);
 uint64_t or_mulhi64(uint64_t a, uint64_t b);
 uint32_t or_bitlen(uint64_t v);
+/* Golomb-Rice parameter of a column with `count` values summing to `sum`
+ * (Kiely's choice for a geometric source with the column's mean). */
+uint32_t or_rice_param(uint64_t sum, uint64_t count);
 double   or_beta_star(double x);
 double   or_gamma(double x, double eps, double alpha);
 double   or_epsilon(double lambda, uint32_t P);

@@ -245,7 +245,7 @@ def test_every_pilot_is_the_first_valid(orc, mode, lam, alpha, P, n):
     assert h.verify_first_valid(hk)
 
 
-@pytest.mark.parametrize("enc", [0, 1])
+@pytest.mark.parametrize("enc", [0, 1, 2])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("alpha", [1.0, 0.99, 0.9])
 def test_query_is_bijection(orc, enc, mode, alpha):
@@ -330,6 +330,66 @@ def test_interleaved_dictionary_layout(orc):
             assert d[r] == pil[b, j]
 
 
+def _expected_rice_length(theta, k):
+    """Expected Rice code length with parameter k for a geometric source
+    P(V = v) = (1 - theta) theta^v: k low bits plus a unary part of
+    1 + floor(V / 2^k) bits, whose mean is 1 + sum_t P(V >= t 2^k)."""
+    q = theta ** (2 ** k)
+    return k + 1 + q / (1 - q)
+
+
+def test_rice_parameter_is_the_expected_length_minimiser(orc):
+    """Section 4.1 takes the Golomb-Rice parameter from Kiely's formula.  For a
+    geometric source it must agree with brute-force minimisation of the expected
+    code length over k (a closed form for the mean unary length; no formula in
+    common with the oracle's)."""
+    L = orc.lib()
+    rng = np.random.default_rng(31)
+    count = 1_000_000
+    checked = 0
+    for mu in np.exp(rng.uniform(np.log(0.05), np.log(5e6), size=400)):
+        s = int(round(mu * count))
+        theta = (s / count) / (s / count + 1)
+        lens = [_expected_rice_length(theta, k) for k in range(45)]
+        best = int(np.argmin(lens))
+        srt = sorted(lens)
+        if srt[1] - srt[0] < 1e-9 * srt[0]:
+            continue  # on a boundary between two parameters: either is optimal
+        assert L.or_rice_param(s, count) == best, (mu, best)
+        checked += 1
+    assert checked > 390
+    assert L.or_rice_param(0, 10) == 0
+
+
+def test_interleaved_rice_layout(orc):
+    """IC-R, decoded by an independent numpy reader: low parts at width l_b,
+    unary high parts with one set bit per value at j + sum_{i<=j} (v_i >> l_b),
+    and the position of every 64th one as a select sample."""
+    rng = np.random.default_rng(23)
+    keys = rng.integers(0, 2**64, size=60_000, dtype=np.uint64)
+    h = orc.Oracle(keys, lam=7.0, alpha=0.99, P=800, encoder=orc.ENC_IC_R, threads=4)
+    pil = h.pilots
+    B, NP = pil.shape
+    l, lb, hb, H = h.array("col_l"), h.array("col_lbase"), h.array("col_hbase"), h.array("col_H")
+    low, high, samp = h.array("rice_low"), h.array("rice_high"), h.array("rice_samples")
+    ns = (NP + 63) // 64
+    high_bits = np.unpackbits(high.view(np.uint8), bitorder="little")
+    total = 0
+    for b in range(B):
+        assert l[b] == orc.lib().or_rice_param(int(pil[b].astype(np.int64).sum()), NP)
+        assert H[b] == NP + int((pil[b].astype(np.int64) >> int(l[b])).sum())
+        ones = np.flatnonzero(high_bits[int(hb[b]):int(hb[b]) + int(H[b])])
+        assert ones.size == NP
+        q = np.diff(np.concatenate([[-1], ones])) - 1
+        lo = np.array([_bits(low, int(lb[b]) + j * int(l[b]), int(l[b])) for j in range(NP)], dtype=np.int64)
+        assert np.array_equal((q << int(l[b])) | lo, pil[b].astype(np.int64)), b
+        assert np.array_equal(samp[b * ns:(b + 1) * ns], ones[::64])
+        total += NP * int(l[b]) + int(H[b]) + 32 * ns + 136
+    assert h.u64("bits_pilots") == total
+    q = h.query(keys)
+    assert np.unique(q).size == keys.size and q.max() < keys.size
+
+
 def test_offsets_are_differences_to_expectation(orc):
     """Section 4: sizes are differences of consecutive offsets; offsets are
     stored as the difference to their expectation."""
@@ -382,3 +442,8 @@ def test_space_bands_from_the_paper(orc):
     assert bpk > math.log2(math.e)
     ref = bands["fig3b_lambda8"]["IC-C"]["bits_per_key"]
     assert abs(bpk - ref) < bands["band"], (bpk, ref)
+    # IC-R (Golomb-Rice columns) on the same keys: the paper's most compact encoder
+    hr = orc.Oracle(keys, lam=8.0, P=2500, encoder=orc.ENC_IC_R, threads=8)
+    ref_r = bands["fig3b_lambda8"]["IC-R"]["bits_per_key"]
+    assert math.log2(math.e) < hr.bits_per_key() < bpk
+    assert abs(hr.bits_per_key() - ref_r) < bands["band"], (hr.bits_per_key(), ref_r)
