@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-target-s", type=float, default=12.0)
     ap.add_argument("--candidate-width", type=int, default=0, help="search window width (32/64; 0 = default)")
+    ap.add_argument("--encoder", choices=["ic-c", "ic-d", "ic-r"], default=None,
+                    help="pilot encoder instead of the workload's own")
+    ap.add_argument("--lam", type=float, default=None, help="average bucket size instead of the workload's own")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-build section")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
@@ -82,7 +85,14 @@ def workload(a):
         n = int(a.n or 1e6)
         return dict(name=SMALL, n=n, lam=7.0, alpha=1.0, P=2500, encoder=0, q_uniform=10 * n, q_zipf=0)
     n = int(a.n or 1e8)
-    return dict(name=WORKLOAD, n=n, lam=7.0, alpha=0.99, P=2500, encoder=1, q_uniform=n, q_zipf=n)
+    w = dict(name=WORKLOAD, n=n, lam=7.0, alpha=0.99, P=2500, encoder=1, q_uniform=n, q_zipf=n)
+    if a.encoder or a.lam:
+        enc = {"ic-c": 0, "ic-d": 1, "ic-r": 2}[a.encoder] if a.encoder else w["encoder"]
+        w.update(encoder=enc, lam=a.lam or w["lam"])
+        w["name"] = (f"{n:.0e} distinct uniform uint64 keys, lambda={w['lam']:g}, alpha=0.99 with Elias-Fano remap, "
+                     f"partition size 2500, {['IC-C', 'IC-D', 'IC-R'][enc]} pilot encoding; {n:.0e} uniform + "
+                     f"{n:.0e} Zipf(s=1) positive queries (variant of the default workload)")
+    return w
 
 
 # Per-key counters from the ncu captures summarised in profiles/ (3e7-key case of
@@ -456,7 +466,7 @@ def run_ours(a):
         "dtype": "u64",
         "data": "synthetic",
         "config": {"workload": w["name"], "n": n, "lambda": w["lam"], "alpha": w["alpha"], "P": w["P"],
-                   "encoder": "IC-D" if w["encoder"] else "IC-C", "queries_uniform": w["q_uniform"],
+                   "encoder": ["IC-C", "IC-D", "IC-R"][w["encoder"]], "queries_uniform": w["q_uniform"],
                    "queries_zipf": w["q_zipf"], "parallelism": f"independent key set per GPU x{world}",
                    "l2": "inputs larger than L2 (8e8-byte key and query arrays vs 126 MB L2)", "gpu": gpu_name},
         "build_ms": b_ms,

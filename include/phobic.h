@@ -50,7 +50,12 @@ typedef enum {
 /* pilot encoders (Section 4.1, interleaved coding) */
 typedef enum {
     PHOBIC_ENC_IC_C = 0, /* interleaved Compact: column width = bit length of its largest pilot */
-    PHOBIC_ENC_IC_D = 1  /* interleaved Dictionary: sorted distinct pilots + compact ranks */
+    PHOBIC_ENC_IC_D = 1, /* interleaved Dictionary: sorted distinct pilots + compact ranks */
+    PHOBIC_ENC_IC_R = 2  /* interleaved Golomb-Rice: per column, the low l bits packed at width l and the
+                            rest in unary, l by Kiely's rule from the column mean; a select sample every
+                            64 partitions.  Export layout: col_meta[2b] = low base | l << 56,
+                            col_meta[2b+1] = unary base; the dictionary array holds the u32 select samples
+                            (B x ceil(N_P/64), padded to whole words) followed by the unary bits */
 } phobic_encoder;
 
 /* pilot hash (Section 4, "Hash Function") */

@@ -16,6 +16,11 @@
 //   bit-packed at the bit length of (#distinct - 1).  The distinct values are
 //   found by marking a presence bitmap over [0, max]; a rank is a prefix
 //   popcount over that bitmap.
+//   IC-R (Golomb-Rice, parameter l by Kiely's rule from the column mean): the
+//   low l bits of each pilot packed at width l (the IC-C packer with width l);
+//   the rest in unary, the pilot of partition j setting bit
+//   j + sum_{i <= j} (v_i >> l) of the column's unary bits; and that position
+//   for every 64th partition as a select sample.
 // Columns of all sets are described by ColDesc records; packing is a gather in
 // which each thread assembles one 64-bit output word from the values that
 // overlap it (atomicOr where two columns share a word).
@@ -127,20 +132,106 @@ __global__ void k_offset_pack(const uint64_t* __restrict__ T, const OffDesc* __r
 // ---------------------------------------------------------------- columns ---
 __global__ void __launch_bounds__(256) k_column_max(const uint32_t* __restrict__ pilots,
                                                     const ColDesc* __restrict__ cols, uint32_t ncols,
-                                                    uint32_t* __restrict__ colmax) {
+                                                    uint32_t* __restrict__ colmax, uint64_t* __restrict__ colsum) {
     __shared__ uint32_t sm[8];
+    __shared__ unsigned long long ss[8];
     for (uint32_t c = blockIdx.x; c < ncols; c += gridDim.x) {
         const ColDesc d = cols[c];
         uint32_t mx = 0;
-        for (uint64_t j = threadIdx.x; j < d.count; j += blockDim.x) mx = max(mx, __ldg(pilots + d.src + j));
+        unsigned long long sum = 0;
+        for (uint64_t j = threadIdx.x; j < d.count; j += blockDim.x) {
+            const uint32_t v = __ldg(pilots + d.src + j);
+            mx = max(mx, v);
+            sum += v;
+        }
         mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int i = 1; i < 8; i++) mx = max(mx, sm[i]);
-            colmax[c] = mx;
+        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        if ((threadIdx.x & 31) == 0) {
+            sm[threadIdx.x >> 5] = mx;
+            ss[threadIdx.x >> 5] = sum;
         }
         __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 1; i < 8; i++) {
+                mx = max(mx, sm[i]);
+                sum += ss[i];
+            }
+            colmax[c] = mx;
+            if (colsum) colsum[c] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// IC-R: per column, the sum of (pilot >> l)
+__global__ void __launch_bounds__(256) k_rice_unary_len(const uint32_t* __restrict__ pilots,
+                                                        const ColDesc* __restrict__ cols, uint32_t ncols,
+                                                        uint64_t* __restrict__ hlen) {
+    __shared__ unsigned long long ss[8];
+    for (uint32_t c = blockIdx.x; c < ncols; c += gridDim.x) {
+        const ColDesc d = cols[c];
+        unsigned long long sum = 0;
+        for (uint64_t j = threadIdx.x; j < d.count; j += blockDim.x) sum += __ldg(pilots + d.src + j) >> d.width;
+        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        if ((threadIdx.x & 31) == 0) ss[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 1; i < 8; i++) sum += ss[i];
+            hlen[c] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// IC-R: one block per column.  An inclusive block scan of (pilot >> l) over
+// the column's partitions, chunk by chunk with a carry, gives each value's set
+// bit j + sum_{i <= j}; bits go in with atomicOr (neighbours share words), and
+// every 64th position becomes a select sample.
+__global__ void __launch_bounds__(1024) k_rice_unary(const uint32_t* __restrict__ pilots,
+                                                     const ColDesc* __restrict__ cols, uint32_t ncols,
+                                                     uint64_t* __restrict__ arena) {
+    __shared__ unsigned long long warp_sums[32];
+    __shared__ unsigned long long carry_s;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t c = blockIdx.x; c < ncols; c += gridDim.x) {
+        const ColDesc d = cols[c];
+        uint64_t* high = arena + d.hi_dst_word;
+        uint32_t* samples = reinterpret_cast<uint32_t*>(arena + d.samp_dst_word) + d.samp_base;
+        if (tid == 0) carry_s = 0;
+        __syncthreads();
+        for (uint64_t j0 = 0; j0 < d.count; j0 += 1024) {
+            const uint64_t j = j0 + tid;
+            const unsigned long long q = j < d.count ? (__ldg(pilots + d.src + j) >> d.width) : 0;
+            unsigned long long x = q;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            if (lane == 31) warp_sums[warp] = x;
+            __syncthreads();
+            if (warp == 0) {
+                const unsigned long long s = warp_sums[lane];
+                unsigned long long z = s;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+                    if (lane >= (uint32_t)o) z += y;
+                }
+                warp_sums[lane] = z - s;  // exclusive prefix of the warp totals
+            }
+            __syncthreads();
+            const unsigned long long carry = carry_s;
+            if (j < d.count) {
+                const uint64_t pos = j + carry + warp_sums[warp] + x;  // inclusive sum
+                const uint64_t bit = d.hi_base + pos;
+                atomicOr((unsigned long long*)(high + (bit >> 6)), 1ull << (bit & 63));
+                if ((j & 63) == 0) samples[j >> 6] = (uint32_t)pos;
+            }
+            __syncthreads();
+            if (tid == 1023) carry_s = carry + warp_sums[31] + x;
+            __syncthreads();
+        }
     }
 }
 
@@ -286,8 +377,22 @@ cudaError_t launch_offset_pack(const uint64_t* T, const OffDesc* sets, uint32_t 
 }
 
 cudaError_t launch_column_max(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint32_t* colmax,
+                              uint64_t* colsum, cudaStream_t stream) {
+    k_column_max<<<grid_items(ncols), 256, 0, stream>>>(pilots, cols, ncols, colmax, colsum);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rice_unary_len(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* hlen,
+                                  cudaStream_t stream) {
+    k_rice_unary_len<<<grid_items(ncols), 256, 0, stream>>>(pilots, cols, ncols, hlen);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rice_unary(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* arena,
                               cudaStream_t stream) {
-    k_column_max<<<grid_items(ncols), 256, 0, stream>>>(pilots, cols, ncols, colmax);
+    k_rice_unary<<<grid_items(ncols), 1024, 0, stream>>>(pilots, cols, ncols, arena);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -81,6 +81,57 @@ __device__ __forceinline__ uint64_t ef_access(const QueryView& v, uint64_t i) {
     return ((one - i) << v.ef_l) | low;
 }
 
+// first one at or after bit g of `words` (one exists)
+__device__ __forceinline__ uint64_t next_one(const uint64_t* __restrict__ words, uint64_t g) {
+    uint64_t wi = g >> 6;
+    uint64_t w = __ldg(words + wi) & (~0ull << (g & 63));
+    while (!w) w = __ldg(words + ++wi);
+    return wi * 64 + (uint64_t)(__ffsll((long long)w) - 1);
+}
+
+// last one strictly before bit g of `words` (one exists)
+__device__ __forceinline__ uint64_t prev_one(const uint64_t* __restrict__ words, uint64_t g) {
+    uint64_t wi = g >> 6;
+    uint64_t w = (g & 63) ? (__ldg(words + wi) & ((1ull << (g & 63)) - 1)) : 0;
+    while (!w) w = __ldg(words + --wi);
+    return wi * 64 + 63 - (uint64_t)__clzll((long long)w);
+}
+
+// IC-R pilot of partition j in column b: the low part at width l, plus the
+// unary part (the distance between the ones of partitions j-1 and j, minus
+// one).  The one of partition j-1 is found from the column's select sample
+// for partition 64 floor(j / 64) by skipping ones with popcounts.
+__device__ __forceinline__ uint32_t rice_pilot(const QueryView& v, uint32_t b, uint64_t j) {
+    const uint64_t m0 = __ldg(v.col_meta + 2 * b), hb = __ldg(v.col_meta + 2 * b + 1);
+    const uint32_t l = (uint32_t)(m0 >> 56);
+    const uint32_t* samples = reinterpret_cast<const uint32_t*>(v.dict_words) + (uint64_t)b * v.rice_ns;
+    const uint64_t* high = v.rice_high;
+    const uint64_t s = hb + __ldg(samples + (j >> 6));  // bit of the one of partition 64 floor(j / 64)
+    uint64_t a, c;  // bits of the ones of partitions j - 1 and j (a = hb - 1 for j = 0)
+    if ((j & 63) == 0) {
+        c = s;
+        a = j ? prev_one(high, c) : hb - 1;
+    } else {
+        uint32_t need = (uint32_t)(j & 63) - 1;  // further ones after the sample's, up to partition j - 1
+        a = s;
+        if (need) {
+            uint64_t wi = (s + 1) >> 6;
+            uint64_t w = __ldg(high + wi) & (~0ull << ((s + 1) & 63));
+            for (;;) {
+                const uint32_t cnt = (uint32_t)__popcll(w);
+                if (need <= cnt) break;
+                need -= cnt;
+                w = __ldg(high + ++wi);
+            }
+            for (uint32_t t = 1; t < need; t++) w &= w - 1;
+            a = wi * 64 + (uint64_t)(__ffsll((long long)w) - 1);
+        }
+        c = next_one(high, a + 1);
+    }
+    const uint64_t q = c - a - 1;
+    return (uint32_t)((q << l) | read_bits(v.pil_words, (m0 & kMeta) + j * l, l));
+}
+
 constexpr int kSeedTable = 64;  // pilot seeds mix64(s ^ C) for s < 64, per block
 
 __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds);
@@ -102,7 +153,9 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
     if (m == 0) return 0;  // only a key outside the set can land in an empty partition
     const uint32_t b = bucket_of(bucket_hash(hk), v.table, v.B);
     uint32_t p;
-    if (v.small_bits) {
+    if (v.encoder == 2) {
+        p = rice_pilot(v, b, j);
+    } else if (v.small_bits) {
         const uint32_t jj = (uint32_t)j;
         if (v.encoder == 0) {
             const uint64_t meta = __ldg(v.col_meta + b);

@@ -62,6 +62,21 @@ uint32_t num_buckets(double lambda, uint32_t P) {
     return b < 1.0 ? 1u : (uint32_t)b;
 }
 
+// Golomb-Rice parameter of an IC-R column with `count` pilots summing to `sum`:
+// Kiely's choice for a geometric source with the column's mean mu,
+// max(0, 1 + floor(log2(log(phi - 1) / log(theta)))), theta = mu / (mu + 1),
+// phi the golden ratio; at most 31.  Computed on the host in double.
+uint32_t rice_param(uint64_t sum, uint64_t count) {
+    if (sum == 0 || count == 0) return 0;
+    const double mu = (double)sum / (double)count;
+    const double theta = mu / (mu + 1.0);
+    const double ratio = std::log((std::sqrt(5.0) - 1.0) / 2.0) / std::log(theta);
+    const double k = 1.0 + std::floor(std::log2(ratio));
+    if (!(k > 0.0)) return 0;
+    if (k > 31.0) return 31;
+    return (uint32_t)k;
+}
+
 uint64_t num_partitions(uint64_t n, uint32_t P) {
     uint64_t np = (n + P - 1) / P;
     return np ? np : 1;
@@ -234,7 +249,7 @@ phobic_status check_params(uint64_t n, const phobic_params& p) {
     if (!(p.lambda > 0.0) || !std::isfinite(p.lambda)) return PHOBIC_ERR_INVALID_ARG;
     if (!(p.alpha > 0.0) || p.alpha > 1.0) return PHOBIC_ERR_INVALID_ARG;
     if (p.partition_size == 0 || p.partition_size > kMaxPartitionSize) return PHOBIC_ERR_INVALID_ARG;
-    if (p.encoder > PHOBIC_ENC_IC_D || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
+    if (p.encoder > PHOBIC_ENC_IC_R || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
     if (p.warps_per_partition != 0 && p.warps_per_partition != 1 && p.warps_per_partition != 2 &&
         p.warps_per_partition != 4)
         return PHOBIC_ERR_INVALID_ARG;
@@ -274,7 +289,7 @@ struct SetPlan {
     uint32_t off_w;
     // arena word offsets and sizes
     uint64_t a_off, n_off, a_meta, n_meta, a_pil, n_pil, a_dict, n_dict, a_low, n_low, a_high, n_high, a_samp,
-        n_samp, a_pilots;
+        n_samp, a_pilots, samp_words;
     uint32_t ef_l;
     uint64_t bits_header, bits_offsets, bits_pilots, bits_remap, bits_total;
 };
@@ -483,9 +498,13 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     CK(h2d(d_cd, cd.data(), cols_total, st));
     CK(ev.mark(5, st));
     CK(launch_offset_minmax(T, d_od, S, mm, st));
-    CK(launch_column_max(pilots, d_cd, (uint32_t)cols_total, colmax, st));
+    const bool icr = prm.encoder == PHOBIC_ENC_IC_R;
+    uint64_t* colsum = nullptr;
+    if (icr) CK(tmp.alloc(&colsum, (size_t)cols_total * 8));
+    CK(launch_column_max(pilots, d_cd, (uint32_t)cols_total, colmax, colsum, st));
     CK(d2h(hmm, mm, 2 * (size_t)S, st));
     CK(d2h(hcolmax, colmax, cols_total, st));
+    if (icr) CK(d2h(hK, colsum, cols_total, st));
     CK(d2h(hstatus, status, 1, st));
     if (work) CK(d2h(hst + 12, reinterpret_cast<uint64_t*>(work), 2, st));
     CK(cudaStreamSynchronize(st));
@@ -517,6 +536,17 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         CK(cudaStreamSynchronize(st));
     }
 
+    // ---- IC-R: Rice parameters from the column sums, then the unary lengths
+    if (icr) {
+        for (uint64_t c = 0; c < cols_total; c++) cd[c].width = rice_param(hK[c], cd[c].count);
+        uint64_t* dH;
+        CK(tmp.alloc(&dH, cols_total * 8));
+        CK(h2d(d_cd, cd.data(), cols_total, st));
+        CK(launch_rice_unary_len(pilots, d_cd, (uint32_t)cols_total, dH, st));
+        CK(d2h(hK, dH, cols_total, st));
+        CK(cudaStreamSynchronize(st));
+    }
+
     // ---- layouts and the arena
     uint64_t aw = (uint64_t)ntab * (kTablePoints + 1);  // tables first
     std::vector<uint64_t> off_begin(S + 1, 0), col_begin(cols_total + 1, 0), remap_sets;
@@ -530,15 +560,27 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         aw += p.n_off;
         off_begin[s + 1] = off_begin[s] + p.n_off;
         const bool icd = prm.encoder == PHOBIC_ENC_IC_D;
-        p.n_meta = icd ? 2 * (uint64_t)p.B : p.B;
+        p.n_meta = (icd || icr) ? 2 * (uint64_t)p.B : p.B;
         p.a_meta = aw;
         aw += p.n_meta;
         metas[s].resize(p.n_meta);
         uint64_t rbase = 0, dbase = 0, bp = 0;
+        const uint64_t ns = (p.NP + 63) / 64;  // IC-R select samples per column
         for (uint32_t b = 0; b < p.B; b++) {
             ColDesc& c = cd[p.col_base + b];
             const uint64_t c_id = p.col_base + b;
-            if (!icd) {
+            if (icr) {
+                // c.width = Rice parameter (set above); dbase counts unary bits
+                const uint64_t H = p.NP + hK[c_id];
+                c.base = rbase;
+                c.hi_base = dbase;
+                c.samp_base = (uint64_t)b * ns;
+                metas[s][2 * b] = rbase | ((uint64_t)c.width << 56);
+                metas[s][2 * b + 1] = dbase;
+                rbase += p.NP * (uint64_t)c.width;
+                dbase += H;
+                bp += p.NP * (uint64_t)c.width + H + 32 * ns + 64 + 64 + 8;
+            } else if (!icd) {
                 c.width = bitlen64(hcolmax[c_id]);
                 c.base = rbase;
                 metas[s][b] = rbase | ((uint64_t)c.width << 56);
@@ -562,12 +604,15 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         p.n_pil = packed_words(rbase);
         p.a_pil = aw;
         aw += p.n_pil;
-        p.n_dict = icd ? packed_words(dbase) : 0;
+        p.samp_words = icr ? ((uint64_t)p.B * ns + 1) / 2 : 0;
+        p.n_dict = icd ? packed_words(dbase) : icr ? p.samp_words + packed_words(dbase) : 0;
         p.a_dict = aw;
         aw += p.n_dict;
         for (uint32_t b = 0; b < p.B; b++) {
             cd[p.col_base + b].dst_word = p.a_pil;
             cd[p.col_base + b].dict_dst_word = p.a_dict;
+            cd[p.col_base + b].samp_dst_word = p.a_dict;
+            cd[p.col_base + b].hi_dst_word = p.a_dict + p.samp_words;
         }
         // Elias-Fano remap of slots >= n
         const uint64_t N = p.M - p.n;
@@ -636,6 +681,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     const bool icd = prm.encoder == PHOBIC_ENC_IC_D;
     CK(launch_pack_columns(pilots, d_cd, (uint32_t)cols_total, d_cbeg, col_begin[cols_total], icd, bitmaps, brank,
                            arena, st));
+    if (icr) CK(launch_rice_unary(pilots, d_cd, (uint32_t)cols_total, arena, st));
     if (icd) {
         uint64_t* d_bmbeg;
         CK(tmp.alloc(&d_bmbeg, (cols_total + 1) * 8));
@@ -757,6 +803,8 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         v.ef_low = h->ef_low;
         v.ef_high = h->ef_high;
         v.ef_samples = h->ef_samples;
+        v.rice_high = icr ? arena + p.a_dict + p.samp_words : nullptr;
+        v.rice_ns = icr ? (uint32_t)((p.NP + 63) / 64) : 0;
         v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
         v.key_kind = key_kind;
         v.string_seed = prm.seed;
@@ -1095,6 +1143,31 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
             }
         }
     }
+    // IC-R: every column's unary region lies inside the array, holds exactly N_P
+    // ones, and each select sample is the position of its 64k-th one, so the
+    // query's scans never leave the column
+    uint64_t rice_sw = 0;
+    if (p.encoder == PHOBIC_ENC_IC_R) {
+        const uint64_t ns = (NP + 63) / 64;
+        rice_sw = (B * ns + 1) / 2;
+        if (counts[3] < rice_sw + 1) return PHOBIC_ERR_FORMAT;
+        const uint64_t* meta = w + kHeaderWords + counts[0];
+        const uint32_t* samp = reinterpret_cast<const uint32_t*>(w + kHeaderWords + counts[0] + counts[1] + counts[2]);
+        const uint64_t* high = w + kHeaderWords + counts[0] + counts[1] + counts[2] + rice_sw;
+        const uint64_t hbits = (counts[3] - rice_sw - 1) * 64;  // the last word is padding
+        for (uint64_t b = 0; b < B; b++) {
+            const uint64_t hb = meta[2 * b + 1], he = b + 1 < B ? meta[2 * b + 3] : hbits;
+            if ((meta[2 * b] >> 56) > 31 || hb > he || he > hbits) return PHOBIC_ERR_FORMAT;
+            uint64_t ones = 0;
+            for (uint64_t bit = hb; bit < he; bit++) {
+                if (!((high[bit >> 6] >> (bit & 63)) & 1)) continue;
+                if (ones >= NP) return PHOBIC_ERR_FORMAT;
+                if (ones % 64 == 0 && samp[b * ns + ones / 64] != bit - hb) return PHOBIC_ERR_FORMAT;
+                ones++;
+            }
+            if (ones != NP) return PHOBIC_ERR_FORMAT;
+        }
+    }
     (void)stream;  // the copies below are synchronous
     phobic_handle* h = new (std::nothrow) phobic_handle();
     if (!h) return PHOBIC_ERR_OOM;
@@ -1175,6 +1248,8 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     v.ef_low = h->ef_low;
     v.ef_high = h->ef_high;
     v.ef_samples = h->ef_samples;
+    v.rice_high = p.encoder == PHOBIC_ENC_IC_R ? h->dict_words + rice_sw : nullptr;
+    v.rice_ns = p.encoder == PHOBIC_ENC_IC_R ? (uint32_t)((NP + 63) / 64) : 0;
     v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
     v.key_kind = key_kind;
     v.string_seed = p.seed;

@@ -107,18 +107,29 @@ struct OffDesc {
 struct ColDesc {
     uint64_t src;       // first pilot of the column in the pilot buffer
     uint64_t count;     // N_P of the set
-    uint64_t dst_word;  // arena word where the set's packed pilots (IC-C) / ranks (IC-D) start
+    uint64_t dst_word;  // arena word where the set's packed pilots (IC-C) / ranks (IC-D) / low parts (IC-R) start
     uint64_t base;      // bit offset of this column inside that array
-    uint32_t width;     // bits per value
+    uint32_t width;     // bits per value (IC-R: the Rice parameter)
     uint32_t dict_width;  // IC-D: bits per dictionary value
     uint64_t bm_base, bm_words;  // IC-D: the column's presence bitmap (words)
     uint64_t dict_dst_word, dict_base;  // IC-D: the set's dictionary array, this column's bit offset
+    // IC-R: the set's select samples (u32) start at arena word samp_dst_word, this
+    // column's at index samp_base; its unary bits at bit hi_base of the array at
+    // arena word hi_dst_word
+    uint64_t samp_dst_word, samp_base, hi_dst_word, hi_base;
 };
 cudaError_t launch_offset_minmax(const uint64_t* T, const OffDesc* sets, uint32_t nsets, long long* mm,
                                  cudaStream_t stream);
 cudaError_t launch_offset_pack(const uint64_t* T, const OffDesc* sets, uint32_t nsets, const uint64_t* word_begin,
                                uint64_t total_words, uint64_t* arena, cudaStream_t stream);
+// colsum (may be null): sum of each column's pilots
 cudaError_t launch_column_max(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint32_t* colmax,
+                              uint64_t* colsum, cudaStream_t stream);
+// IC-R: hlen[c] = sum over the column of (pilot >> width), i.e. its unary bits minus N_P
+cudaError_t launch_rice_unary_len(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* hlen,
+                                  cudaStream_t stream);
+// IC-R: unary bits and select samples of every column
+cudaError_t launch_rice_unary(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* arena,
                               cudaStream_t stream);
 cudaError_t launch_pack_columns(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, const uint64_t* word_begin,
                                 uint64_t total_words, bool ranks, const uint64_t* bitmaps,

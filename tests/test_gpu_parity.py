@@ -48,6 +48,13 @@ def compare_structure(ph, orc_h, h, encoder):
         assert ((meta >> np.uint64(56)).astype(np.uint32) == o.array("col_w")).all()
         assert ((meta & mask) == o.array("col_base")).all()
         assert (ex["pil_words"] == o.array("pil_words")).all()
+    elif encoder == 2:
+        assert ((meta[0::2] >> np.uint64(56)).astype(np.uint32) == o.array("col_l")).all()
+        assert ((meta[0::2] & mask) == o.array("col_lbase")).all()
+        assert (meta[1::2] == o.array("col_hbase")).all()
+        assert (ex["pil_words"] == o.array("rice_low")).all()
+        assert (ex["rice_high"] == o.array("rice_high")).all()
+        assert (ex["rice_samples"] == o.array("rice_samples")).all()
     else:
         assert ((meta[0::2] >> np.uint64(56)).astype(np.uint32) == o.array("col_rw")).all()
         assert ((meta[0::2] & mask) == o.array("col_rbase")).all()
@@ -114,6 +121,14 @@ CASES = [
     (300_000, 7.0, 0.99, 1024, 0, 0),
     (1_000_000, 7.0, 1.0, 2500, 0, 0),   # the 1M-key configuration (IC-C, alpha = 1)
     (1_000_000, 7.0, 0.99, 2500, 1, 0),  # the 1e8-key configuration's parameters at 1M keys
+    # IC-R (interleaved Golomb-Rice)
+    (1, 7.0, 1.0, 2500, 2, 0),
+    (100, 3.0, 1.0, 8, 2, 0),
+    (2501, 7.0, 0.99, 2500, 2, 0),
+    (70_001, 6.0, 0.9, 300, 2, 1),
+    (300_000, 9.0, 0.99, 1024, 2, 0),
+    (1_000_000, 8.0, 1.0, 2500, 2, 0),
+    (1_000_000, 7.0, 0.99, 2500, 2, 0),
 ]
 
 
@@ -158,7 +173,7 @@ def test_query_unaligned_and_odd_lengths(ph, orc):
 
 def test_export_import_roundtrip(ph, orc):
     keys = _keys(123_457, 8)
-    for enc, alpha in [(0, 1.0), (1, 0.95)]:
+    for enc, alpha in [(0, 1.0), (1, 0.95), (2, 0.99)]:
         h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, alpha, 2500, encoder=enc))
         data = ph.phobic_export(h)
         h2 = ph.phobic_import(data)
@@ -172,6 +187,22 @@ def test_export_import_roundtrip(ph, orc):
         assert e.value.status == "FORMAT"
         with pytest.raises(ph.PhobicError):
             ph.phobic_import(data[:-8])
+        if enc == 2:
+            # a unary region with a missing one, or a wrong select sample, is refused
+            ex = ph.parse_export(data)
+            w = np.frombuffer(data, dtype=np.uint64).copy()
+            hi0 = len(ph.HEADER_FIELDS) + sum(ex["n_" + a] for a in ph.ARRAYS[:3]) + (
+                ex["n_dict_words"] - ex["rice_high"].size)
+            nz = hi0 + int(np.flatnonzero(ex["rice_high"])[3])
+            for flip_word, bit in [(nz, None), (hi0 - (ex["n_dict_words"] - ex["rice_high"].size), 40)]:
+                bad = w.copy()
+                if bit is None:
+                    bad[flip_word] &= bad[flip_word] - np.uint64(1)  # clear the lowest set bit
+                else:
+                    bad[flip_word] ^= np.uint64(1) << np.uint64(bit)  # corrupt the second sample
+                with pytest.raises(ph.PhobicError) as e:
+                    ph.phobic_import(bad.tobytes())
+                assert e.value.status == "FORMAT"
 
 
 def test_errors(ph):
@@ -300,7 +331,7 @@ def test_string_hash_unaligned_and_tails(ph, orc):
         assert np.array_equal(got, orc.string_hashes(data, off, 123))
 
 
-@pytest.mark.parametrize("alpha,enc", [(0.99, 1), (1.0, 0)])
+@pytest.mark.parametrize("alpha,enc", [(0.99, 1), (1.0, 0), (0.99, 2)])
 def test_batch_build_matches_single_builds(ph, orc, alpha, enc):
     """Batched construction: every set's structure equals the oracle's build of
     that set alone (and so the single-set path), for uneven set sizes and mixed
