@@ -270,7 +270,7 @@ def run_reference(a):
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "u64", "data": "synthetic",
            "config": {"workload": w["name"], "n": w["n"], "lambda": w["lam"], "alpha": w["alpha"], "P": w["P"],
-                      "encoder": "IC-D" if w["encoder"] else "IC-C"},
+                      "encoder": ["IC-C", "IC-D", "IC-R"][w["encoder"]]},
            "cpu_baseline": {"value": v, "unit": "Mkeys/s", "cores": cores, "kind": "oracle",
                             "sample": f"each step: oracle build of the first {n_s} keys of the workload on {cores} "
                                       f"threads"},
