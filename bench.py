@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
-    ap.add_argument("--only", choices=["batch", "serve"], default=None, help="run one extra section alone")
+    ap.add_argument("--only", choices=["batch", "serve", "lambda"], default=None,
+                    help="run one extra section alone (lambda: the large-lambda sweep)")
     return ap.parse_args()
 
 
@@ -566,6 +567,55 @@ def run_batch(a, phobic, workloads, torch):
     }
 
 
+# ------------------------------------------------------ large-lambda sweep ---
+# the paper's PHOBIC-GPU rows (RTX 3090 through Vulkan, 1e8 strings, IC-R, alpha 1), context only
+PAPER_GPU_NS_PER_KEY = {9: 27.0, 13: 560.0, 14: 1470.0}
+
+
+def run_lambda_sweep(a, phobic, workloads, torch):
+    """Build and query across lambda = 7 .. 14 (IC-R, alpha 1, P 2500): the
+    regime where the pilot search dominates (about e^lambda slot tests per
+    key, Section 3).  1e8 keys up to lambda 10, 1e7 above (bounded time)."""
+    stream = torch.cuda.current_stream()
+    out = []
+    for lam in (7.0, 8.0, 9.0, 10.0, 11.0, 12.0, 13.0, 14.0):
+        n = 100_000_000 if lam <= 10 else 10_000_000
+        keys = workloads.stream_keys_torch(0, n, 29, "cuda")
+        res = torch.empty_like(keys)
+        prm = phobic.make_params(lam, 1.0, 2500, encoder=2, record_timings=True)
+        steps = 3 if lam <= 12 else 2
+        bms, qms, tm = [], [], None
+        h = phobic.phobic_build_ex(keys, prm, stream)  # warm-up
+        h.free()
+        for _ in range(steps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            h = phobic.phobic_build_ex(keys, prm, stream)
+            e[1].record(stream)
+            phobic.phobic_query(h, keys, res, stream)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            bms.append(e[0].elapsed_time(e[1]))
+            qms.append(e[1].elapsed_time(e[2]))
+            tm = phobic.phobic_get_timings(h)
+            bpk = h.bits_per_key()
+            h.free()
+        ok = bool(torch.equal(torch.sort(res).values, torch.arange(n, device="cuda")))
+        b = statistics.mean(bms)
+        out.append({"lambda": lam, "n": n, "build_ms": b, "ns_per_key": b * 1e6 / n, "build_mkeys_s": n / b / 1e3,
+                    "search_ms": tm["search_ms"], "s_tries_per_key": tm["search_s_tries"] / n,
+                    "bits_per_key": bpk, "query_mkeys_s": n / statistics.mean(qms) / 1e3, "permutation": ok,
+                    "paper_gpu_ns_per_key": PAPER_GPU_NS_PER_KEY.get(int(lam))})
+        del keys, res
+    torch.cuda.empty_cache()
+    phobic.phobic_trim(0)
+    return {"workload": "large-lambda sweep: distinct uniform uint64 keys (counter-based stream), alpha=1, "
+                        "partition size 2500, IC-R; 1e8 keys for lambda <= 10, 1e7 above; every key queried",
+            "rows": out,
+            "paper_context": "PHOBIC-GPU ns/key from the paper's Table 1 (RTX 3090, Vulkan, 1e8 strings, incl. "
+                             "its CPU share); not the same machine or input"}
+
+
 # ------------------------------------------------------------ serving (C5) ---
 def _percentiles(x):
     if len(x) == 0:
@@ -824,6 +874,8 @@ def run_only(a):
 
     if a.only == "batch":
         print(json.dumps({"batch": run_batch(a, phobic, workloads, torch)}))
+    elif a.only == "lambda":
+        print(json.dumps({"lambda_sweep": run_lambda_sweep(a, phobic, workloads, torch)}))
     else:
         print(json.dumps({"serve": run_serve(a, phobic, workloads, torch)}))
 

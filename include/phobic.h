@@ -71,7 +71,9 @@ typedef struct {
     uint32_t partition_size;      /* expected partition size P, 1..16384 (Section 4) */
     uint32_t encoder;             /* phobic_encoder */
     uint32_t pilot_mode;          /* phobic_pilot_mode */
-    uint32_t s_max;               /* search limit: s < s_max (ADDITIVE), p < s_max*m (XOR); 0 = default */
+    uint32_t s_max;               /* search limit: s < s_max (ADDITIVE), p < s_max*m (XOR); 0 = none beyond the
+                                     32-bit pilot: in every partition s < floor((2^32-1)/m_j), which also
+                                     caps any other value */
     uint64_t seed;                /* master-hash seed */
     uint32_t warps_per_partition; /* search tuning: warps sharing one partition, 1, 2 or 4; 0 = chosen from
                                      the partition count (4 while partitions x 4 fit the GPU's one-warp CTA
@@ -115,7 +117,7 @@ typedef struct {
 } phobic_info;
 
 /* Fills *p with the defaults: lambda 7, alpha 1, P 2500, IC-C, ADDITIVE,
- * s_max 65536 (capped so that pilots fit 32 bits), seed 0. */
+ * s_max 0 (only the 32-bit pilot bound), seed 0. */
 void phobic_params_init(phobic_params* p);
 
 /*

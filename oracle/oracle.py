@@ -55,7 +55,7 @@ class _Params(ctypes.Structure):
     ]
 
 
-def params(lam=7.0, alpha=1.0, P=2500, encoder=ENC_IC_C, mode=PILOT_ADDITIVE, s_max=65536, seed=0):
+def params(lam=7.0, alpha=1.0, P=2500, encoder=ENC_IC_C, mode=PILOT_ADDITIVE, s_max=0, seed=0):
     return _Params(float(lam), float(alpha), int(P), int(encoder), int(mode), int(s_max), int(seed))
 
 
@@ -116,7 +116,7 @@ class Oracle:
     """One MPHF built by the oracle."""
 
     def __init__(self, keys=None, *, hashed=None, lam=7.0, alpha=1.0, P=2500, encoder=ENC_IC_C,
-                 mode=PILOT_ADDITIVE, s_max=65536, seed=0, threads=0):
+                 mode=PILOT_ADDITIVE, s_max=0, seed=0, threads=0):
         L = lib()
         self.prm = params(lam, alpha, P, encoder, mode, s_max, seed)
         h = ctypes.c_void_p()
@@ -205,7 +205,7 @@ def partition_sizes(hk, lam, alpha, P, seed=0) -> np.ndarray:
     return out
 
 
-def search_partitions(hk, sel, lam=7.0, alpha=1.0, P=2500, mode=PILOT_ADDITIVE, s_max=65536,
+def search_partitions(hk, sel, lam=7.0, alpha=1.0, P=2500, mode=PILOT_ADDITIVE, s_max=0,
                       threads=0) -> np.ndarray:
     L = lib()
     hk = _u64(hk)

@@ -325,7 +325,6 @@ static int check_params(uint64_t n, const or_params* p) {
     if (!(p->alpha > 0.0) || p->alpha > 1.0) return OR_ERR_INVALID_ARG;
     if (p->partition_size == 0) return OR_ERR_INVALID_ARG;
     if (p->encoder > OR_ENC_IC_R || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
-    if (p->s_max == 0) return OR_ERR_INVALID_ARG;
     return OR_OK;
 }
 
@@ -361,6 +360,10 @@ static int search_partition(const uint64_t* hk, uint64_t nj, uint64_t m, const u
     for (uint32_t b = 0; b < B; b++) pilot[b] = 0;
     for (uint64_t t = 0; t < m; t++) taken[t] = 0;
     if (nj == 0) return OR_OK;
+    /* seeds s < s_lim: the requested limit (0: none), and never past the
+     * largest s whose pilots s m + d all fit 32 bits in this partition */
+    const uint64_t s_cap = 0xFFFFFFFFULL / m;
+    const uint64_t s_lim = (prm->s_max && prm->s_max < s_cap) ? prm->s_max : s_cap;
 
     /* Section 3.1: bucket of every key */
     uint32_t* bk = (uint32_t*)malloc(nj * sizeof(uint32_t));
@@ -408,7 +411,7 @@ static int search_partition(const uint64_t* hk, uint64_t nj, uint64_t m, const u
             /* Section 4 "Hash Function": p = s m + d, d in [0, m); for each s
              * compute h(x, s) for all keys of the bucket, then try d = 0, 1, ...
              * until all (h + d) mod m are free; if none, increment s. */
-            for (uint64_t s = 0; s < prm->s_max && !found; s++) {
+            for (uint64_t s = 0; s < s_lim && !found; s++) {
                 st->s_tries++;
                 for (uint32_t i = 0; i < k; i++) hpos[i] = or_position_hash(keys[i], s, m);
                 /* If two keys share h(x, s), every displacement d moves them
@@ -445,7 +448,7 @@ static int search_partition(const uint64_t* hk, uint64_t nj, uint64_t m, const u
         } else {
             /* PTHash's XOR form (Section 4 "Hash Function"): position
              * h(x xor h(p)) reduced onto [0, m), pilots p = 0, 1, 2, ... */
-            uint64_t limit = (uint64_t)prm->s_max * m;
+            uint64_t limit = s_lim * m;
             for (uint64_t q = 0; q < limit; q++) {
                 int ok = 1;
                 stamp++;

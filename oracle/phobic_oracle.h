@@ -43,7 +43,8 @@ typedef struct {
     uint32_t partition_size;/* expected partition size P */
     uint32_t encoder;       /* OR_ENC_* */
     uint32_t pilot_mode;    /* OR_PILOT_* */
-    uint32_t s_max;         /* search limit on s (ADDITIVE) or p/m (XOR) */
+    uint32_t s_max;         /* search limit on s (ADDITIVE) or p/m (XOR); 0: only the 32-bit pilot bound,
+                               s < floor((2^32 - 1) / m_j), which also caps any other value */
     uint64_t seed;
 } or_params;
 

@@ -27,7 +27,8 @@
 //   4. Write the pilots (column-major, i.e. interleaved order) and, when a
 //      global occupancy bitmap is requested (alpha < 1), the partition's taken
 //      slots at bit offset T_j.
-// Bounded work: a bucket that needs s >= s_max, or holds more than 1023 keys,
+// Bounded work: a bucket that needs s >= min(s_max, floor((2^32 - 1) / m)) (the
+// largest s whose pilots fit 32 bits), or holds more than 1023 keys,
 // stops its partition with SEARCH_LIMIT.  Equal master hashes inside a bucket
 // (duplicate keys) are detected and reported as DUP_HASH.
 #include "phobic_dev.cuh"
@@ -268,6 +269,9 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
     const uint64_t* const table = S.table;
     uint32_t* const pil = a.pilots + S.pilot_base + j;  // pilot of bucket b at pil[b * S.np]
     if (nj == 0) return;
+    // seeds s < s_lim: the requested limit, and never past the largest s whose
+    // pilots s m + d all fit 32 bits in this partition
+    const uint32_t s_lim = min(a.s_max, 0xFFFFFFFFu / m);
     uint64_t* hk = kKeysInSmem ? reinterpret_cast<uint64_t*>(smem + L.off_hk) : a.bkeys + s0;
 
     // ---- init: counts, doubled free bitmap, scratch, size histogram
@@ -459,7 +463,7 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
             for (;; sb += kWarps) {
                 const uint32_t s = sb + warp;
                 uint32_t my = kOutNone, myd = 0;
-                if (s >= a.s_max) {
+                if (s >= s_lim) {
                     my = kOutLimit;
                 } else {
                     uint64_t ps;
@@ -552,7 +556,7 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
             placed += k;
         } else {
             // ===== PTHash XOR form: p = 0, 1, 2, ... =====
-            const uint64_t limit = (uint64_t)a.s_max * m;
+            const uint64_t limit = (uint64_t)s_lim * m;
             uint32_t outcome = kOutNone, winner = 0;
             if (k <= 32) {
                 // groups of Lc lanes test G consecutive pilots per warp step

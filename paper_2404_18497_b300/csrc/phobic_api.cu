@@ -415,8 +415,8 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     if (max_m >= 65536 || max_n >= (1u << 31) ||
         search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, cap_B, keys_in_smem, wpp) > search_smem_limit())
         return PHOBIC_ERR_PARTITION_TOO_LARGE;
-    uint32_t s_max = prm.s_max ? prm.s_max : 65536u;
-    if (max_m > 0 && (uint64_t)s_max * max_m > 0xFFFFFFFFull) s_max = (uint32_t)(0xFFFFFFFFull / max_m);
+    // 0: no limit beyond the 32-bit pilot, which the search applies per partition
+    const uint32_t s_max = prm.s_max ? prm.s_max : 0xFFFFFFFFu;
 
     // ---- K3 + K4: bucketing and pilot search, one persistent launch over all sets
     std::vector<SearchSet> ss(S);
@@ -845,7 +845,7 @@ void phobic_params_init(phobic_params* p) {
     p->partition_size = 2500;
     p->encoder = PHOBIC_ENC_IC_C;
     p->pilot_mode = PHOBIC_PILOT_ADDITIVE;
-    p->s_max = 65536;
+    p->s_max = 0;
     p->seed = 0;
 }
 

@@ -54,7 +54,7 @@ def test_status_strings_and_params(libpath):
     for code in range(9):
         assert phobic.phobic_status_str(code)
     p = phobic.make_params()
-    assert p.lambda_ == 7.0 and p.alpha == 1.0 and p.partition_size == 2500 and p.s_max == 65536
+    assert p.lambda_ == 7.0 and p.alpha == 1.0 and p.partition_size == 2500 and p.s_max == 0
 
 
 def test_struct_layouts_match_header(libpath):

@@ -129,6 +129,10 @@ CASES = [
     (300_000, 9.0, 0.99, 1024, 2, 0),
     (1_000_000, 8.0, 1.0, 2500, 2, 0),
     (1_000_000, 7.0, 0.99, 2500, 2, 0),
+    # the large-lambda regime (search cost ~ e^lambda per key, Section 3)
+    (400_000, 10.0, 1.0, 2500, 2, 0),
+    (150_000, 12.0, 1.0, 2500, 2, 0),
+    (150_000, 11.0, 0.99, 2500, 0, 1),
 ]
 
 

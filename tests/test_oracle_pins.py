@@ -264,10 +264,13 @@ def test_errors(orc):
     with pytest.raises(orc.OracleError) as e:
         orc.Oracle(np.concatenate([keys, keys[:1]]), lam=5.0)
     assert e.value.code == orc.DUP_HASH
-    for kw in [dict(lam=0.0), dict(alpha=0.0), dict(alpha=1.5), dict(P=0), dict(s_max=0)]:
+    for kw in [dict(lam=0.0), dict(alpha=0.0), dict(alpha=1.5), dict(P=0)]:
         with pytest.raises(orc.OracleError) as e:
             orc.Oracle(keys, **kw)
         assert e.value.code == orc.INVALID_ARG
+    # s_max = 0: no limit beyond the 32-bit pilot; the same result as a limit never reached
+    a, b = orc.Oracle(keys, lam=5.0, s_max=0), orc.Oracle(keys, lam=5.0, s_max=1 << 20)
+    assert np.array_equal(a.pilots, b.pilots)
     with pytest.raises(orc.OracleError) as e:
         orc.Oracle(keys, lam=12.0, P=2500, s_max=1)
     assert e.value.code == orc.SEARCH_LIMIT
