@@ -397,17 +397,22 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     }
     const char* ks = std::getenv("PHOBIC_KEYS_IN_SMEM");
     const bool keys_in_smem = ks && ks[0] == '1';
-    // warps per partition: as asked, or (0) chosen from the partition count.  One
-    // warp per partition fills the GPU once there are several partitions per
-    // resident one-warp CTA slot (32 per SM); with fewer partitions, 2 or 4
-    // warps test consecutive candidate ranges of each bucket at once.
+    // warps per partition: as asked, or (0) chosen from the partition count and
+    // lambda.  The build ends with its slowest partitions, and the spread of
+    // per-partition search work grows like e^lambda, so 2 or 4 warps (testing
+    // consecutive candidate ranges of a bucket at once) pay off while there are
+    // few waves of partitions per resident one-warp CTA slot (32 per SM), the
+    // more so at large lambda; with many waves one warp per partition wastes
+    // the fewest issue slots.  Measured crossovers: lambda 7: 4 warps at 0.08
+    // waves, 1 at 0.84; lambda 9-14: 4 warps at 0.84 waves; lambda 10: 1 at 8.4.
     uint32_t wpp = prm.warps_per_partition;
     if (wpp == 0) {
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const uint64_t slots = (uint64_t)sms * 32;
-        wpp = NPT * 4 <= slots ? 4 : NPT * 2 <= slots ? 2 : 1;
+        const double waves = (double)NPT / ((double)sms * 32.0);
+        const double t = 0.3 * std::exp((prm.lambda - 7.0) / 1.5);
+        wpp = waves <= t ? 4 : waves <= 2.0 * t ? 2 : 1;
         while (wpp > 1 && search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, cap_B, keys_in_smem, wpp) >
                               search_smem_limit())
             wpp /= 2;
