@@ -52,11 +52,17 @@ class _Params(ctypes.Structure):
         ("pilot_mode", ctypes.c_uint32),
         ("s_max", ctypes.c_uint32),
         ("seed", ctypes.c_uint64),
+        ("bucket_fn", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
     ]
 
 
-def params(lam=7.0, alpha=1.0, P=2500, encoder=ENC_IC_C, mode=PILOT_ADDITIVE, s_max=0, seed=0):
-    return _Params(float(lam), float(alpha), int(P), int(encoder), int(mode), int(s_max), int(seed))
+BUCKET_OPTIMIZED, BUCKET_BETA_STAR, BUCKET_SKEWED, BUCKET_UNIFORM = 0, 1, 2, 3
+
+
+def params(lam=7.0, alpha=1.0, P=2500, encoder=ENC_IC_C, mode=PILOT_ADDITIVE, s_max=0, seed=0, bucket_fn=0):
+    return _Params(float(lam), float(alpha), int(P), int(encoder), int(mode), int(s_max), int(seed),
+                   int(bucket_fn), 0)
 
 
 _lib = None
@@ -76,6 +82,8 @@ def lib():
         L.or_gamma.restype = dbl; L.or_gamma.argtypes = [dbl, dbl, dbl]
         L.or_epsilon.restype = dbl; L.or_epsilon.argtypes = [dbl, u32]
         L.or_bucket_table.restype = None; L.or_bucket_table.argtypes = [dbl, dbl, u32, vp]
+        L.or_gamma_fn.restype = dbl; L.or_gamma_fn.argtypes = [dbl, dbl, dbl, u32]
+        L.or_bucket_table_fn.restype = None; L.or_bucket_table_fn.argtypes = [dbl, dbl, u32, u32, vp]
         L.or_num_buckets.restype = u32; L.or_num_buckets.argtypes = [dbl, u32]
         L.or_num_partitions.restype = u64; L.or_num_partitions.argtypes = [u64, u32]
         L.or_bucket.restype = u32; L.or_bucket.argtypes = [u64, vp, u32]
@@ -116,9 +124,9 @@ class Oracle:
     """One MPHF built by the oracle."""
 
     def __init__(self, keys=None, *, hashed=None, lam=7.0, alpha=1.0, P=2500, encoder=ENC_IC_C,
-                 mode=PILOT_ADDITIVE, s_max=0, seed=0, threads=0):
+                 mode=PILOT_ADDITIVE, s_max=0, seed=0, threads=0, bucket_fn=0):
         L = lib()
-        self.prm = params(lam, alpha, P, encoder, mode, s_max, seed)
+        self.prm = params(lam, alpha, P, encoder, mode, s_max, seed, bucket_fn)
         h = ctypes.c_void_p()
         if hashed is not None:
             hk = _u64(hashed)
@@ -219,9 +227,9 @@ def search_partitions(hk, sel, lam=7.0, alpha=1.0, P=2500, mode=PILOT_ADDITIVE, 
     return out
 
 
-def bucket_table(lam, alpha, P) -> np.ndarray:
+def bucket_table(lam, alpha, P, bucket_fn=0) -> np.ndarray:
     t = np.zeros(2049, dtype=np.uint64)
-    lib().or_bucket_table(lam, alpha, P, _ptr(t))
+    lib().or_bucket_table_fn(lam, alpha, P, bucket_fn, _ptr(t))
     return t
 
 

@@ -105,19 +105,44 @@ double or_gamma(double x, double eps, double alpha) {
     return num / den;
 }
 
+/* The other bucket assignment functions of Figure 3a, for the ablations:
+ * beta_* itself (eps = 0); PTHash's skewed split, which sends the keys with
+ * normalised hash below 0.6 (60 %) to the first 30 % of the buckets and the
+ * rest to the other 70 %; and the uniform gamma(x) = x of CHD.  For alpha < 1
+ * every one is rescaled as gamma(alpha x) / gamma(alpha) (Appendix B). */
+static double gamma_base(double x, double eps, uint32_t fn) {
+    if (x >= 1.0) return 1.0;
+    switch (fn) {
+        case OR_BUCKET_BETA_STAR: return or_beta_star(x);
+        case OR_BUCKET_SKEWED: return x < 0.6 ? 0.5 * x : 0.3 + 1.75 * (x - 0.6);
+        case OR_BUCKET_UNIFORM: return x;
+        default: return eps * x + (1.0 - eps) * or_beta_star(x);
+    }
+}
+
+double or_gamma_fn(double x, double eps, double alpha, uint32_t fn) {
+    if (fn == OR_BUCKET_OPTIMIZED) return or_gamma(x, eps, alpha);
+    if (alpha == 1.0) return gamma_base(x, eps, fn);
+    return gamma_base(alpha * x, eps, fn) / gamma_base(alpha, eps, fn);
+}
+
 /* Appendix C: gamma tabulated at 2048 points, here as 32-bit fixed point:
  * table[k] = round(gamma(k / 2048) * 2^32), k = 0..2048. */
-void or_bucket_table(double lambda, double alpha, uint32_t P, uint64_t* table) {
+void or_bucket_table_fn(double lambda, double alpha, uint32_t P, uint32_t fn, uint64_t* table) {
     double eps = or_epsilon(lambda, P);
     for (int k = 0; k <= OR_TABLE_POINTS; k++) {
         double x = (double)k / (double)OR_TABLE_POINTS;
-        double g = or_gamma(x, eps, alpha);
+        double g = or_gamma_fn(x, eps, alpha, fn);
         double v = g * 4294967296.0;
         long long r = llround(v);
         if (r < 0) r = 0;
         if (r > 4294967296LL) r = 4294967296LL;
         table[k] = (uint64_t)r;
     }
+}
+
+void or_bucket_table(double lambda, double alpha, uint32_t P, uint64_t* table) {
+    or_bucket_table_fn(lambda, alpha, P, OR_BUCKET_OPTIMIZED, table);
 }
 
 /* Section 4.1: B = P / lambda buckets per partition (rounded up, at least 1) */
@@ -325,6 +350,7 @@ static int check_params(uint64_t n, const or_params* p) {
     if (!(p->alpha > 0.0) || p->alpha > 1.0) return OR_ERR_INVALID_ARG;
     if (p->partition_size == 0) return OR_ERR_INVALID_ARG;
     if (p->encoder > OR_ENC_IC_R || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
+    if (p->bucket_fn > OR_BUCKET_UNIFORM) return OR_ERR_INVALID_ARG;
     return OR_OK;
 }
 
@@ -833,7 +859,7 @@ int or_build_hashed(const uint64_t* hk, uint64_t n, const or_params* prm, int th
     h->NP = or_num_partitions(n, prm->partition_size);
     h->B = or_num_buckets(prm->lambda, prm->partition_size);
     h->eps = or_epsilon(prm->lambda, prm->partition_size);
-    or_bucket_table(prm->lambda, prm->alpha, prm->partition_size, h->table);
+    or_bucket_table_fn(prm->lambda, prm->alpha, prm->partition_size, prm->bucket_fn, h->table);
     uint64_t NP = h->NP;
     uint32_t B = h->B;
 
@@ -1041,7 +1067,7 @@ int or_search_partitions(const uint64_t* hk, uint64_t n, const or_params* prm, c
     uint64_t NP = or_num_partitions(n, prm->partition_size);
     uint32_t B = or_num_buckets(prm->lambda, prm->partition_size);
     uint64_t table[OR_TABLE_POINTS + 1];
-    or_bucket_table(prm->lambda, prm->alpha, prm->partition_size, table);
+    or_bucket_table_fn(prm->lambda, prm->alpha, prm->partition_size, prm->bucket_fn, table);
     int status = OR_OK;
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);

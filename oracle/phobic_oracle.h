@@ -31,6 +31,14 @@ extern "C" {
 #define OR_ENC_IC_D 1
 #define OR_ENC_IC_R 2
 
+/* bucket assignment functions (Figure 3a): the optimised beta_eps (Theorem 2),
+ * beta_* (eps = 0), PTHash's skewed split (60 % of the keys into 30 % of the
+ * buckets) and the uniform one (CHD) */
+#define OR_BUCKET_OPTIMIZED 0
+#define OR_BUCKET_BETA_STAR 1
+#define OR_BUCKET_SKEWED 2
+#define OR_BUCKET_UNIFORM 3
+
 #define OR_PILOT_ADDITIVE 0
 #define OR_PILOT_XOR 1
 
@@ -46,6 +54,8 @@ typedef struct {
     uint32_t s_max;         /* search limit on s (ADDITIVE) or p/m (XOR); 0: only the 32-bit pilot bound,
                                s < floor((2^32 - 1) / m_j), which also caps any other value */
     uint64_t seed;
+    uint32_t bucket_fn;     /* OR_BUCKET_*: the bucket assignment function gamma */
+    uint32_t pad;
 } or_params;
 
 typedef struct or_mphf or_mphf;
@@ -61,6 +71,9 @@ double   or_beta_star(double x);
 double   or_gamma(double x, double eps, double alpha);
 double   or_epsilon(double lambda, uint32_t P);
 void     or_bucket_table(double lambda, double alpha, uint32_t P, uint64_t* table /* 2049 */);
+/* gamma of one of the OR_BUCKET_* functions, with the alpha rescaling, and its table */
+double   or_gamma_fn(double x, double eps, double alpha, uint32_t fn);
+void     or_bucket_table_fn(double lambda, double alpha, uint32_t P, uint32_t fn, uint64_t* table);
 uint32_t or_num_buckets(double lambda, uint32_t P);
 uint64_t or_num_partitions(uint64_t n, uint32_t P);
 uint32_t or_bucket(uint64_t x, const uint64_t* table, uint32_t B);

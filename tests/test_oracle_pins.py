@@ -106,6 +106,51 @@ def test_bucket_table_matches_exact_closed_form(orc, lam, alpha, P):
         assert abs(Decimal(int(t[k])) - exact) <= Decimal("0.5000001"), (k, t[k], exact)
 
 
+@pytest.mark.parametrize("alpha", [1.0, 0.99])
+def test_ablation_bucket_functions(orc, alpha):
+    """Figure 3a's other bucket assignment functions (the ablations), each
+    pinned to its own definition: the uniform gamma(x) = x of CHD; PTHash's skewed
+    split (keys with hash below 0.6, i.e. 60 %, go to the first 30 % of buckets);
+    and beta_* (eps = 0) against a 40-digit evaluation.  For alpha < 1 every
+    table is gamma(alpha x) / gamma(alpha) (Appendix B)."""
+    getcontext().prec = 40
+    L = orc.lib()
+    a = Decimal(alpha)
+
+    def resc(g, x):
+        return g(a * x) / g(a) if alpha != 1.0 else g(x)
+
+    def skew(x):
+        return x / 2 if x < Decimal("0.6") else Decimal("0.3") + Decimal("1.75") * (x - Decimal("0.6"))
+
+    def bstar(x):
+        return Decimal(1) if x >= 1 else x + (1 - x) * (1 - x).ln()
+
+    for fn, g in [(orc.BUCKET_UNIFORM, lambda x: x), (orc.BUCKET_SKEWED, skew), (orc.BUCKET_BETA_STAR, bstar)]:
+        t = orc.bucket_table(7.0, alpha, 2500, fn)
+        assert t[0] == 0 and t[2048] == 1 << 32 and (np.diff(t.astype(np.int64)) >= 0).all()
+        for k in list(range(0, 2049, 29)) + [1, 1228, 1229, 2047]:
+            exact = resc(g, Decimal(k) / 2048) * (1 << 32)
+            assert abs(Decimal(int(t[k])) - exact) <= Decimal("0.5000001"), (fn, k)
+    # the skewed split: 60 % of uniform hashes land in the first 30 % of the buckets
+    if alpha == 1.0:
+        t = orc.bucket_table(7.0, 1.0, 2500, orc.BUCKET_SKEWED)
+        B = 358
+        xs = np.random.default_rng(5).integers(0, 2**64, size=200_000, dtype=np.uint64)
+        b = np.array([L.or_bucket(int(x), t.ctypes.data, B) for x in xs[:40_000]])
+        share = np.mean(b < int(0.3 * B))
+        assert abs(share - 0.6) < 0.01, share
+    # every variant gives a bijection, and less work per key than uniform buckets (Section 3)
+    keys = np.random.default_rng(6).integers(0, 2**64, size=60_000, dtype=np.uint64)
+    work = {}
+    for fn in range(4):
+        h = orc.Oracle(keys, lam=6.0, alpha=alpha, P=2500, encoder=orc.ENC_IC_R, bucket_fn=fn, threads=4)
+        q = h.query(keys)
+        assert np.unique(q).size == keys.size and q.max() < keys.size
+        work[fn] = h.u64("stat_key_tests") / keys.size
+    assert work[orc.BUCKET_OPTIMIZED] < work[orc.BUCKET_UNIFORM] / 3
+
+
 def test_bucket_function_follows_gamma(orc):
     """Section 3.1: a key with normalised hash x goes to bucket ceil(gamma(x) B);
     0-based that is floor(gamma(x) B).  The tabulated version may differ from
