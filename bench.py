@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
-    ap.add_argument("--only", choices=["batch", "serve", "lambda"], default=None,
-                    help="run one extra section alone (lambda: the large-lambda sweep)")
+    ap.add_argument("--only", choices=["batch", "serve", "lambda", "ablation"], default=None,
+                    help="run one extra section alone (lambda: the large-lambda sweep; ablation: the bucket "
+                         "functions of Fig. 3a)")
     return ap.parse_args()
 
 
@@ -616,6 +617,47 @@ def run_lambda_sweep(a, phobic, workloads, torch):
                              "its CPU share); not the same machine or input"}
 
 
+# ------------------------------------------------------- bucket functions ---
+def run_ablation(a, phobic, workloads, torch):
+    """Figure 3a's comparison on this GPU: construction time and space of each
+    bucket assignment function (the optimised beta_eps, beta_* without eps,
+    PTHash's skewed split, CHD's uniform one) across lambda.  1e7 keys, IC-R,
+    alpha 1, P 2500; device-resident keys, CUDA events."""
+    stream = torch.cuda.current_stream()
+    n = 10_000_000
+    keys = workloads.stream_keys_torch(0, n, 31, "cuda")
+    names = {0: "optimized (beta_eps)", 1: "beta_* (eps = 0)", 2: "skewed (PTHash)", 3: "uniform (CHD)"}
+    rows = []
+    for fn in (0, 1, 2, 3):
+        for lam in (4.0, 5.0, 6.0, 7.0, 8.0):
+            prm = phobic.make_params(lam, 1.0, 2500, encoder=2, bucket_function=fn, record_timings=True)
+            try:
+                phobic.phobic_build_ex(keys, prm, stream).free()
+                ms, sms = [], []
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    h = phobic.phobic_build_ex(keys, prm, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                    t = phobic.phobic_get_timings(h)
+                    sms.append(t["search_ms"])
+                    bpk = h.bits_per_key()
+                    tries = t["search_s_tries"]
+                    h.free()
+                rows.append({"bucket_function": names[fn], "lambda": lam, "build_ms": statistics.mean(ms),
+                             "ns_per_key": statistics.mean(ms) * 1e6 / n, "search_ms": statistics.mean(sms),
+                             "s_tries_per_key": tries / n, "bits_per_key": bpk})
+            except phobic.PhobicError as e:
+                rows.append({"bucket_function": names[fn], "lambda": lam, "error": e.status})
+    del keys
+    torch.cuda.empty_cache()
+    phobic.phobic_trim(0)
+    return {"workload": "bucket assignment functions (Fig. 3a): 1e7 distinct uniform uint64 keys (counter-based "
+                        "stream), IC-R, alpha=1, partition size 2500, lambda 4..8", "rows": rows}
+
+
 # ------------------------------------------------------------ serving (C5) ---
 def _percentiles(x):
     if len(x) == 0:
@@ -876,6 +918,8 @@ def run_only(a):
         print(json.dumps({"batch": run_batch(a, phobic, workloads, torch)}))
     elif a.only == "lambda":
         print(json.dumps({"lambda_sweep": run_lambda_sweep(a, phobic, workloads, torch)}))
+    elif a.only == "ablation":
+        print(json.dumps({"ablation": run_ablation(a, phobic, workloads, torch)}))
     else:
         print(json.dumps({"serve": run_serve(a, phobic, workloads, torch)}))
 

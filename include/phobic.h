@@ -58,6 +58,18 @@ typedef enum {
                             (B x ceil(N_P/64), padded to whole words) followed by the unary bits */
 } phobic_encoder;
 
+/* bucket assignment functions (Section 3, Figure 3a): the optimised beta_eps of
+ * Theorem 2 (the default), and for ablations beta_* (eps = 0), PTHash's skewed
+ * split (keys with normalised hash below 0.6 go to the first 30 % of the
+ * buckets) and the uniform function of CHD.  For alpha < 1 each is rescaled as
+ * gamma(alpha x) / gamma(alpha) (Appendix B). */
+typedef enum {
+    PHOBIC_BUCKET_OPTIMIZED = 0,
+    PHOBIC_BUCKET_BETA_STAR = 1,
+    PHOBIC_BUCKET_SKEWED = 2,
+    PHOBIC_BUCKET_UNIFORM = 3
+} phobic_bucket_function;
+
 /* pilot hash (Section 4, "Hash Function") */
 typedef enum {
     PHOBIC_PILOT_ADDITIVE = 0, /* p = s m + d; position (h(x, s) + d) mod m  (the paper's PHOBIC) */
@@ -87,6 +99,7 @@ typedef struct {
                                      results do not depend on it */
     uint32_t search_schedule;     /* search tuning: 0 auto, 1 one CTA per partition, 2 persistent CTAs taking
                                      partitions from a device work queue; results do not depend on it */
+    uint32_t bucket_function;     /* phobic_bucket_function: gamma of the bucket assignment (default 0) */
 } phobic_params;
 
 /* Device time of each build phase (CUDA events recorded on the build stream
@@ -115,6 +128,8 @@ typedef struct {
     uint64_t max_partition; /* largest n_j */
     uint64_t bits_header, bits_offsets, bits_pilots, bits_remap, bits_total;
     uint64_t device_bytes;  /* device memory owned by the handle */
+    uint32_t bucket_function;
+    uint32_t pad;
 } phobic_info;
 
 /* Fills *p with the defaults: lambda 7, alpha 1, P 2500, IC-C, ADDITIVE,
@@ -355,6 +370,9 @@ phobic_status phobic_partition_sort_noalloc(const uint64_t* d_hk, uint64_t n, ui
 
 /* Writes the 2049-entry fixed-point bucket table (Appendix C) to h_table. */
 phobic_status phobic_bucket_table(double lambda, double alpha, uint32_t partition_size, uint64_t* h_table);
+/* The same for any phobic_bucket_function. */
+phobic_status phobic_bucket_table_ex(double lambda, double alpha, uint32_t partition_size, uint32_t bucket_function,
+                                     uint64_t* h_table);
 
 /*
  * Serving (the paper has no counterpart; a deployment layer that leaves the

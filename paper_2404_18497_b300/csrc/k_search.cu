@@ -840,7 +840,7 @@ cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream) {
     const size_t smem = search_smem_bytes(a.cap_n, a.cap_m, a.cap_B, a.keys_in_smem != 0, wp);
     const SearchKernel kern = wp == 1 ? pick_kernel<1>(a) : wp == 2 ? pick_kernel<2>(a) : pick_kernel<4>(a);
     const bool q = a.use_queue != 0;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);

@@ -384,18 +384,14 @@ cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint6
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         uint64_t hblocks = tiles < (uint64_t)sms * 8 ? tiles : (uint64_t)sms * 8;
         if (hblocks == 0) hblocks = 1;
-        if ((e = cudaFuncSetAttribute(k_sort_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(8 * passes * R * 4))) != cudaSuccess)
-            return e;
+        if ((e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_sort_hist))) != cudaSuccess) return e;
         k_sort_hist<<<(unsigned)hblocks, 256, 8 * passes * R * 4, stream>>>(in, d_segs, nseg, tiles, kseed,
                                                                             hash_input, passes, bits, hist);
         note_launches(1);
         k_sort_hist_scan<<<nseg * passes, 512, 0, stream>>>(hist, d_segs, passes, bits);
         note_launches(1);
         size_t smem = sort_pass_smem(bits);
-        if ((e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
-            return e;
+        if ((e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_sort_pass))) != cudaSuccess) return e;
         const uint64_t* src = in;
         int hash_now = hash_input;
         // ping-pong so that the last pass lands in `sorted`

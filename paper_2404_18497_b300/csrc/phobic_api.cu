@@ -39,16 +39,30 @@ double eps_of(double lambda, uint32_t P) {
 
 double beta_star(double x) { return x >= 1.0 ? 1.0 : x + (1.0 - x) * std::log1p(-x); }
 
-void make_table(double lambda, double alpha, uint32_t P, uint64_t* t) {
+// gamma before the alpha rescaling: beta_eps (Theorem 2), beta_* (eps = 0),
+// PTHash's skewed split (hash < 0.6 -> first 30 % of the buckets) or uniform
+double gamma_base(double x, double eps, uint32_t fn) {
+    if (x >= 1.0) return 1.0;
+    switch (fn) {
+        case PHOBIC_BUCKET_BETA_STAR: return beta_star(x);
+        case PHOBIC_BUCKET_SKEWED: return x < 0.6 ? 0.5 * x : 0.3 + 1.75 * (x - 0.6);
+        case PHOBIC_BUCKET_UNIFORM: return x;
+        default: return eps * x + (1.0 - eps) * beta_star(x);
+    }
+}
+
+void make_table(double lambda, double alpha, uint32_t P, uint64_t* t, uint32_t fn = PHOBIC_BUCKET_OPTIMIZED) {
     const double eps = eps_of(lambda, P);
     for (int k = 0; k <= kTablePoints; k++) {
         const double x = (double)k / (double)kTablePoints;
         double g;
         if (alpha == 1.0) {
-            g = x >= 1.0 ? 1.0 : eps * x + (1.0 - eps) * beta_star(x);
-        } else {
+            g = gamma_base(x, eps, fn);
+        } else if (fn == PHOBIC_BUCKET_OPTIMIZED) {
             const double ax = alpha * x;
             g = (eps * ax + (1.0 - eps) * beta_star(ax)) / (eps * alpha + (1.0 - eps) * beta_star(alpha));
+        } else {
+            g = gamma_base(alpha * x, eps, fn) / gamma_base(alpha, eps, fn);  // Appendix B
         }
         long long r = std::llround(g * 4294967296.0);
         if (r < 0) r = 0;
@@ -255,6 +269,7 @@ phobic_status check_params(uint64_t n, const phobic_params& p) {
         return PHOBIC_ERR_INVALID_ARG;
     if (p.candidate_width != 0 && p.candidate_width != 32 && p.candidate_width != 64) return PHOBIC_ERR_INVALID_ARG;
     if (p.search_schedule > 2) return PHOBIC_ERR_INVALID_ARG;
+    if (p.bucket_function > PHOBIC_BUCKET_UNIFORM) return PHOBIC_ERR_INVALID_ARG;
     return PHOBIC_OK;
 }
 
@@ -338,7 +353,9 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     }
     const uint32_t ntab = (uint32_t)table_P.size();
     std::vector<uint64_t> tables((size_t)ntab * (kTablePoints + 1));
-    for (uint32_t t = 0; t < ntab; t++) make_table(prm.lambda, prm.alpha, table_P[t], tables.data() + (size_t)t * (kTablePoints + 1));
+    for (uint32_t t = 0; t < ntab; t++)
+        make_table(prm.lambda, prm.alpha, table_P[t], tables.data() + (size_t)t * (kTablePoints + 1),
+                   prm.bucket_function);
 
     PinnedBuf pin;
     CK(pin.alloc(4096 + (size_t)S * 48 + (size_t)cols_total * 12));
@@ -779,6 +796,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         I.encoder = prm.encoder;
         I.pilot_mode = prm.pilot_mode;
         I.seed = prm.seed;
+        I.bucket_function = prm.bucket_function;
         I.max_partition = max_n;
         I.bits_header = p.bits_header;
         I.bits_offsets = p.bits_offsets;
@@ -1078,7 +1096,9 @@ phobic_status phobic_export(const phobic_handle* h, void* h_buf, size_t* len) {
     std::memcpy(&lam, &I.lambda, 8);
     std::memcpy(&alp, &I.alpha, 8);
     uint64_t hdr[kHeaderWords] = {kMagic, kFormatVersion, I.n, I.M, I.num_partitions, I.num_buckets,
-                                  I.partition_size, lam, alp, I.seed, I.encoder, (uint64_t)I.pilot_mode | ((uint64_t)h->view.key_kind << 32), h->view.off_w,
+                                  I.partition_size, lam, alp, I.seed,
+                                  (uint64_t)I.encoder | ((uint64_t)I.bucket_function << 32),
+                                  (uint64_t)I.pilot_mode | ((uint64_t)h->view.key_kind << 32), h->view.off_w,
                                   h->view.off_Q, (uint64_t)h->view.off_dmin, h->view.ef_l};
     for (int i = 0; i < 7; i++) hdr[16 + i] = counts[i];
     hdr[23] = I.bits_header;
@@ -1113,6 +1133,7 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     p.partition_size = (uint32_t)P;
     p.seed = w[9];
     p.encoder = (uint32_t)w[10];
+    p.bucket_function = (uint32_t)(w[10] >> 32);
     p.pilot_mode = (uint32_t)w[11];
     const uint32_t key_kind = (uint32_t)(w[11] >> 32);
     if (key_kind > 1) return PHOBIC_ERR_FORMAT;
@@ -1190,6 +1211,7 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     I.encoder = p.encoder;
     I.pilot_mode = p.pilot_mode;
     I.seed = p.seed;
+    I.bucket_function = p.bucket_function;
     I.bits_header = w[23];
     I.bits_offsets = w[24];
     I.bits_pilots = w[25];
@@ -1200,7 +1222,7 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     uint64_t* cnts[7] = {&h->n_off_words, &h->n_col_meta, &h->n_pil_words, &h->n_dict_words,
                          &h->n_ef_low,    &h->n_ef_high,  &h->n_ef_samples};
     std::vector<uint64_t> table(kTablePoints + 1);
-    make_table(p.lambda, p.alpha, p.partition_size, table.data());
+    make_table(p.lambda, p.alpha, p.partition_size, table.data(), p.bucket_function);
     // one allocation: the table, then the seven arrays in file order
     SharedMem* mem = new (std::nothrow) SharedMem();
     if (!mem) {
@@ -1302,6 +1324,15 @@ phobic_status phobic_selftest_sort_wait_timeout(const uint64_t* d_hk, uint64_t n
     if (spin_limit == 0) return PHOBIC_ERR_INVALID_ARG;
     const SortWaitTest t{mute_tile, spin_limit};
     return partition_sort_impl(d_hk, n, num_partitions, d_sorted, d_start, stream, &t);
+}
+
+phobic_status phobic_bucket_table_ex(double lambda, double alpha, uint32_t partition_size, uint32_t bucket_function,
+                                     uint64_t* h_table) {
+    if (!h_table || !(lambda > 0.0) || !(alpha > 0.0) || alpha > 1.0 || partition_size == 0 ||
+        bucket_function > PHOBIC_BUCKET_UNIFORM)
+        return PHOBIC_ERR_INVALID_ARG;
+    make_table(lambda, alpha, partition_size, h_table, bucket_function);
+    return PHOBIC_OK;
 }
 
 phobic_status phobic_bucket_table(double lambda, double alpha, uint32_t partition_size, uint64_t* h_table) {

@@ -8,6 +8,20 @@
 #include "phobic_dev.cuh"
 
 namespace phobic {
+// Lets `kern` launch with up to the device's opt-in maximum of dynamic shared
+// memory.  Every caller sets the same value, so builds running in several host
+// threads never lower the limit under one another's launch; the occupancy
+// still follows each launch's own size.
+inline cudaError_t allow_max_dynamic_smem(const void* kern) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 
 // process-wide count of kernel launches (diagnostic)
 void note_launches(uint64_t k);

@@ -57,10 +57,10 @@ __global__ void k_trial_keys(uint64_t* __restrict__ out, uint64_t n, uint64_t sa
 struct ParamKey {
     int dev;
     double lambda, alpha;
-    uint32_t encoder, mode, s_max;
+    uint32_t encoder, mode, s_max, bucket_fn;
     bool operator<(const ParamKey& o) const {
-        return std::tie(dev, lambda, alpha, encoder, mode, s_max) <
-               std::tie(o.dev, o.lambda, o.alpha, o.encoder, o.mode, o.s_max);
+        return std::tie(dev, lambda, alpha, encoder, mode, s_max, bucket_fn) <
+               std::tie(o.dev, o.lambda, o.alpha, o.encoder, o.mode, o.s_max, o.bucket_fn);
     }
 };
 
@@ -168,7 +168,8 @@ extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PHOBIC_ERR_CUDA;
-    const ParamKey pk{dev, params->lambda, params->alpha, params->encoder, params->pilot_mode, params->s_max};
+    const ParamKey pk{dev,           params->lambda,     params->alpha,          params->encoder,
+                      params->pilot_mode, params->s_max, params->bucket_function};
     phobic_params base = *params;
     base.keep_pilots = 0;
     base.record_timings = 0;

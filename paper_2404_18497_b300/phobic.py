@@ -52,6 +52,7 @@ class phobic_params(ctypes.Structure):
         ("record_timings", ctypes.c_uint32),
         ("candidate_width", ctypes.c_uint32),
         ("search_schedule", ctypes.c_uint32),
+        ("bucket_function", ctypes.c_uint32),
     ]
 
 
@@ -70,6 +71,7 @@ class phobic_info(ctypes.Structure):
         ("max_partition", ctypes.c_uint64),
         ("bits_header", ctypes.c_uint64), ("bits_offsets", ctypes.c_uint64), ("bits_pilots", ctypes.c_uint64),
         ("bits_remap", ctypes.c_uint64), ("bits_total", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+        ("bucket_function", ctypes.c_uint32), ("pad", ctypes.c_uint32),
     ]
 
 
@@ -144,6 +146,7 @@ _SIGS = [
     ("phobic_partition_sort_noalloc", _INT, [_VP, _U64, _U64, _VP, _VP, _VP]),
     ("phobic_selftest_sort_wait_timeout", _INT, [_VP, _U64, _U64, _U64, _U32, _VP, _VP, _VP]),
     ("phobic_bucket_table", _INT, [_DBL, _DBL, _U32, _VP]),
+    ("phobic_bucket_table_ex", _INT, [_DBL, _DBL, _U32, _U32, _VP]),
     ("phobic_tune_batch", _INT, [_VP, _U32, _PP, _VP, _VP, _PP, ctypes.POINTER(phobic_tune_info)]),
     ("phobic_tune_clear", None, []),
     ("phobic_trim", _INT, [_U64]),
@@ -204,7 +207,7 @@ def _dev_u64(t: torch.Tensor, what: str) -> torch.Tensor:
 
 def make_params(lam=7.0, alpha=1.0, P=2500, seed=0, encoder="IC-C", mode="additive", s_max=0,
                 keep_pilots=False, warps_per_partition=0, record_timings=False,
-                candidate_width=0, search_schedule=0) -> phobic_params:
+                candidate_width=0, search_schedule=0, bucket_function=0) -> phobic_params:
     p = phobic_params()
     lib().phobic_params_init(ctypes.byref(p))
     p.lambda_ = float(lam)
@@ -220,6 +223,7 @@ def make_params(lam=7.0, alpha=1.0, P=2500, seed=0, encoder="IC-C", mode="additi
     p.record_timings = 1 if record_timings else 0
     p.candidate_width = int(candidate_width)
     p.search_schedule = int(search_schedule)
+    p.bucket_function = int(bucket_function)
     return p
 
 
@@ -591,9 +595,13 @@ def phobic_partition_sort_noalloc(hk: torch.Tensor, num_partitions: int, sorted_
     return sorted_out, start_out
 
 
-def phobic_bucket_table(lam: float, alpha: float, P: int) -> np.ndarray:
+BUCKET_OPTIMIZED, BUCKET_BETA_STAR, BUCKET_SKEWED, BUCKET_UNIFORM = 0, 1, 2, 3
+
+
+def phobic_bucket_table(lam: float, alpha: float, P: int, bucket_function: int = 0) -> np.ndarray:
     t = np.zeros(2049, dtype=np.uint64)
-    _check(lib().phobic_bucket_table(float(lam), float(alpha), int(P), t.ctypes.data), "phobic_bucket_table")
+    _check(lib().phobic_bucket_table_ex(float(lam), float(alpha), int(P), int(bucket_function), t.ctypes.data),
+           "phobic_bucket_table_ex")
     return t
 
 
@@ -614,6 +622,8 @@ def parse_export(data: bytes) -> dict:
     hdr = {k: int(w[i]) for i, k in enumerate(HEADER_FIELDS)}
     hdr["key_kind"] = hdr["pilot_mode"] >> 32
     hdr["pilot_mode"] &= 0xFFFFFFFF
+    hdr["bucket_function"] = hdr["encoder"] >> 32
+    hdr["encoder"] &= 0xFFFFFFFF
     hdr["off_dmin"] = int(np.uint64(hdr["off_dmin"]).astype(np.int64))
     at = len(HEADER_FIELDS)
     for name in ARRAYS:

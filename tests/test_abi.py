@@ -93,6 +93,8 @@ def test_bucket_table_equals_oracle(libpath, orc, lam, alpha, P):
     from paper_2404_18497_b300 import phobic
 
     assert (phobic.phobic_bucket_table(lam, alpha, P) == orc.bucket_table(lam, alpha, P)).all()
+    for fn in (1, 2, 3):  # the ablation bucket functions
+        assert (phobic.phobic_bucket_table(lam, alpha, P, fn) == orc.bucket_table(lam, alpha, P, fn)).all(), fn
 
 
 def test_invalid_arguments_without_gpu(libpath):

@@ -162,6 +162,25 @@ def test_build_and_query_parity(ph, orc, n, lam, alpha, P, enc, mode):
     h.free()
 
 
+@pytest.mark.parametrize("fn", [1, 2, 3])
+@pytest.mark.parametrize("alpha,enc", [(1.0, 0), (0.99, 2)])
+def test_ablation_bucket_functions_parity(ph, orc, fn, alpha, enc):
+    """Figure 3a's other bucket assignment functions (beta_*, PTHash's skewed
+    split, uniform): the same bit-exact structure and queries as the oracle, and
+    the function survives export and import."""
+    keys = _keys(150_000, 70 + fn)
+    o = orc.Oracle(keys, lam=5.0, alpha=alpha, P=2500, encoder=enc, bucket_fn=fn, threads=0)
+    h = ph.phobic_build_ex(_dev(keys), ph.make_params(5.0, alpha, 2500, encoder=enc, keep_pilots=True,
+                                                      bucket_function=fn))
+    assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots)
+    compare_structure(ph, o, h, enc)
+    assert h.info()["bucket_function"] == fn
+    assert np.array_equal(_host(h.query(_dev(keys))), o.query(keys))
+    h2 = ph.phobic_import(ph.phobic_export(h))
+    assert h2.info()["bucket_function"] == fn
+    assert torch.equal(h2.query(_dev(keys)), h.query(_dev(keys)))
+
+
 def test_query_unaligned_and_odd_lengths(ph, orc):
     keys = _keys(30_001, 4)
     o = orc.Oracle(keys, lam=6.0, P=500, threads=0)
