@@ -212,8 +212,9 @@ phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32_t n_sets, 
 /* Forget every tuning decision and free the trial keys. */
 void phobic_tune_clear(void);
 
-/* Same, from host memory: the keys are copied in chunks through pinned staging
- * buffers and hashed on the device as they arrive. */
+/* Same, from host memory: the keys are copied to a temporary device buffer on
+ * `stream` (one copy; page-locked host memory gives the full link bandwidth),
+ * then built as phobic_build_ex builds them. */
 phobic_status phobic_build_host(const uint64_t* h_keys, uint64_t n, const phobic_params* params,
                                 phobic_stream_t stream, phobic_handle** out);
 
@@ -243,8 +244,12 @@ phobic_status phobic_query_multi(const phobic_handle* const* handles, const uint
                                  uint64_t* const* d_outs, const uint64_t* counts, uint32_t n_req,
                                  phobic_stream_t stream);
 
-/* Query from host memory: copies keys in, results out, on `stream`; returns
- * after the results are in h_out. */
+/* Query from host memory; returns after the results are in h_out.  Up to 2^22
+ * keys go in one piece.  Larger batches are pipelined in chunks of 2^22 keys over
+ * three device slots: chunk c+1 is copied in and chunk c queried on `stream`
+ * while chunk c-1's results are copied out on a second stream of the calling
+ * thread, so both copy directions overlap.  Page-locked host memory is needed
+ * for the copies to overlap. */
 phobic_status phobic_query_host(const phobic_handle* h, const uint64_t* h_keys, uint64_t* h_out,
                                 uint64_t m, phobic_stream_t stream);
 

@@ -1,10 +1,31 @@
 // Exclusive scan of u32 counts into u64 offsets, three phases: per-tile
 // sums, one block scanning the tile sums, then per-tile scans plus the tile's
 // offset.  The grand total lands in tiles[ntiles] (see scan_total).
+#include <mutex>
+#include <set>
+
 #include "phobic_dev.cuh"
 #include "phobic_kernels.cuh"
 
 namespace phobic {
+
+cudaError_t allow_max_dynamic_smem(const void* kern) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({dev, kern})) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done.insert({dev, kern});
+    return e;
+}
 
 namespace {
 

@@ -269,9 +269,6 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
     const uint64_t* const table = S.table;
     uint32_t* const pil = a.pilots + S.pilot_base + j;  // pilot of bucket b at pil[b * S.np]
     if (nj == 0) return;
-    // seeds s < s_lim: the requested limit, and never past the largest s whose
-    // pilots s m + d all fit 32 bits in this partition
-    const uint32_t s_lim = min(a.s_max, 0xFFFFFFFFu / m);
     uint64_t* hk = kKeysInSmem ? reinterpret_cast<uint64_t*>(smem + L.off_hk) : a.bkeys + s0;
 
     // ---- init: counts, doubled free bitmap, scratch, size histogram
@@ -463,7 +460,13 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
             for (;; sb += kWarps) {
                 const uint32_t s = sb + warp;
                 uint32_t my = kOutNone, myd = 0;
-                if (s >= s_lim) {
+                // seeds s < min(s_max, floor((2^32 - 1) / m)): the requested limit, and
+                // never past the largest s whose pilots s m + d all fit 32 bits
+                // (s >= floor(X / m) exactly when (s + 1) m > X).  Below s_fast, the
+                // same bound for the launch's largest m, neither can hold.
+                bool at_limit = false;
+                if (__builtin_expect(s >= a.s_fast, 0)) at_limit = s >= a.s_max || (uint64_t)(s + 1) * m > 0xFFFFFFFFull;
+                if (at_limit) {
                     my = kOutLimit;
                 } else {
                     uint64_t ps;
@@ -556,7 +559,7 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
             placed += k;
         } else {
             // ===== PTHash XOR form: p = 0, 1, 2, ... =====
-            const uint64_t limit = (uint64_t)s_lim * m;
+            const uint64_t limit = (uint64_t)min(a.s_max, 0xFFFFFFFFu / m) * m;  // pilots < 2^32
             uint32_t outcome = kOutNone, winner = 0;
             if (k <= 32) {
                 // groups of Lc lanes test G consecutive pilots per warp step
@@ -842,13 +845,14 @@ cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream) {
     const bool q = a.use_queue != 0;
     cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 148, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wp, smem)) != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
     uint64_t grid = a.total_parts;
     if (q) {
+        int dev = 0, sms = 148, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wp, smem)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) per_sm = 1;
         grid = (uint64_t)sms * per_sm;  // persistent: every CTA resident, work from the queue
         if (grid > a.total_parts) grid = a.total_parts;
         if ((e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream)) != cudaSuccess) return e;

@@ -474,6 +474,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     sl.cap_B = cap_B;
     sl.mode = prm.pilot_mode;
     sl.s_max = s_max;
+    sl.s_fast = max_m > 0 ? (uint32_t)std::min<uint64_t>(s_max, 0xFFFFFFFFull / max_m) : s_max;
     sl.cap_n = (uint32_t)max_n;
     sl.cap_m = (uint32_t)max_m;
     sl.bkeys = bkeys;
@@ -977,6 +978,29 @@ phobic_status phobic_query_multi(const phobic_handle* const* handles, const uint
     return from_cuda(e != cudaSuccess ? e : e2);
 }
 
+}  // extern "C"
+
+namespace {
+// Per host thread: the second stream and the events of the chunked host query.
+struct QueryPipe {
+    cudaStream_t out = nullptr;
+    cudaEvent_t queried[3] = {}, copied[3] = {};
+    bool ok = false;
+    QueryPipe() {
+        ok = cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 3 && ok; i++)
+            ok = cudaEventCreateWithFlags(&queried[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+};
+}  // namespace
+
+extern "C" {
+
+// Chunks of keys go in on `stream`, are queried there, and their results go
+// out on a second stream, through three device slots: the copy of chunk c+1 in,
+// the query of chunk c and the copy of chunk c-1 out overlap (the two
+// directions use separate copy engines).
 phobic_status phobic_query_host(const phobic_handle* h, const uint64_t* h_keys, uint64_t* h_out, uint64_t m,
                                 phobic_stream_t stream) {
     if (!h || h->view.key_kind != 0) return PHOBIC_ERR_INVALID_ARG;
@@ -984,13 +1008,41 @@ phobic_status phobic_query_host(const phobic_handle* h, const uint64_t* h_keys, 
     if (!h_keys || !h_out) return PHOBIC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     ensure_pool();
+    constexpr uint64_t kChunk = 1ull << 22;
+    thread_local QueryPipe pipe;
+    const uint64_t slots = m <= kChunk ? 1 : 3;
+    const uint64_t cap = m <= kChunk ? m : kChunk;
+    if (slots > 1 && !pipe.ok) return PHOBIC_ERR_CUDA;
     uint64_t* d = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&d, m * 16, st);
+    cudaError_t e = cudaMallocAsync((void**)&d, slots * cap * 16, st);
     if (e != cudaSuccess) return from_cuda(e);
-    e = cudaMemcpyAsync(d, h_keys, m * 8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_query(h->view, d, d + m, m, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d + m, m * 8, cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(d, st);
+    if (slots == 1) {
+        e = cudaMemcpyAsync(d, h_keys, m * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_query(h->view, d, d + m, m, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d + m, m * 8, cudaMemcpyDeviceToHost, st);
+    } else {
+        // the out stream must not run ahead of the allocation on `stream`
+        e = cudaEventRecord(pipe.queried[0], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(pipe.out, pipe.queried[0], 0);
+        for (uint64_t c = 0, at = 0; at < m && e == cudaSuccess; c++, at += kChunk) {
+            const uint64_t len = m - at < kChunk ? m - at : kChunk;
+            const uint64_t slot = c % 3;
+            uint64_t* din = d + slot * cap * 2;
+            uint64_t* dout = din + cap;
+            if (c >= 3) e = cudaStreamWaitEvent(st, pipe.copied[slot], 0);  // the slot's last results are out
+            if (e == cudaSuccess) e = cudaMemcpyAsync(din, h_keys + at, len * 8, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = launch_query(h->view, din, dout, len, st);
+            if (e == cudaSuccess) e = cudaEventRecord(pipe.queried[slot], st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(pipe.out, pipe.queried[slot], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_out + at, dout, len * 8, cudaMemcpyDeviceToHost, pipe.out);
+            if (e == cudaSuccess) e = cudaEventRecord(pipe.copied[slot], pipe.out);
+        }
+        // the buffer is freed on `stream` after the last copy out
+        for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaStreamWaitEvent(st, pipe.copied[i], 0);
+    }
+    const cudaError_t e2 = cudaFreeAsync(d, st);
+    if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return from_cuda(e);
 }

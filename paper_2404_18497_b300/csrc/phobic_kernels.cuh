@@ -11,16 +11,8 @@ namespace phobic {
 // Lets `kern` launch with up to the device's opt-in maximum of dynamic shared
 // memory.  Every caller sets the same value, so builds running in several host
 // threads never lower the limit under one another's launch; the occupancy
-// still follows each launch's own size.
-inline cudaError_t allow_max_dynamic_smem(const void* kern) {
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-}
+// still follows each launch's own size.  Done once per kernel and device.
+cudaError_t allow_max_dynamic_smem(const void* kern);
 
 
 // process-wide count of kernel launches (diagnostic)
@@ -88,7 +80,8 @@ struct SearchLaunch {
     uint64_t total_parts;
     uint32_t cap_B;        // largest B over the sets
     uint32_t mode;
-    uint32_t s_max;
+    uint32_t s_max;        // requested seed limit (0xFFFFFFFF: none)
+    uint32_t s_fast;       // min(s_max, floor((2^32 - 1) / cap_m)): no partition stops below it
     uint32_t cap_n; // largest n_j
     uint32_t cap_m; // largest m_j
     uint64_t* bkeys;       // [n] scratch for the bucket-sorted keys (used unless keys_in_smem)

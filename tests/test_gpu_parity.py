@@ -291,6 +291,11 @@ def test_host_entry_points(ph, orc):
     assert ph.phobic_export(h1) == ph.phobic_export(h2)
     out = ph.phobic_query_host(h1, keys)
     assert np.array_equal(out, _host(h2.query(_dev(keys))))
+    # more than one 4M-key chunk: the pipelined path (slots reused, a ragged last chunk)
+    big = np.random.default_rng(5).integers(0, 2**64, size=10_500_001, dtype=np.uint64)
+    big[::3] = keys[np.arange(0, big.size, 3) % keys.size]
+    out = ph.phobic_query_host(h1, big)
+    assert np.array_equal(out, _host(h2.query(_dev(big))))
 
 
 @pytest.mark.parametrize("mode,lam,P", [(0, 7.0, 2500), (1, 7.0, 2500), (0, 9.0, 1024), (1, 8.0, 4096)])
