@@ -18,7 +18,7 @@ _SRC = os.path.join(_HERE, "phobic_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 
 OK, INVALID_ARG, OOM, DUP_HASH, SEARCH_LIMIT = 0, 1, 2, 3, 4
-ENC_IC_C, ENC_IC_D, ENC_IC_R = 0, 1, 2
+ENC_IC_C, ENC_IC_D, ENC_IC_R, ENC_IC_EF = 0, 1, 2, 3
 PILOT_ADDITIVE, PILOT_XOR = 0, 1
 
 

@@ -20,7 +20,8 @@
  *     size.
  *   - Section 4.1 (Interleaved Coding): encoder i holds the pilot of bucket i of
  *     every partition (Compact; Dictionary as named in Figure 3b; Golomb-Rice
- *     with Kiely's parameter and a select sample every 64 values).
+ *     with Kiely's parameter and a select sample every 64 values; Elias-Fano
+ *     over the column's prefix sums, named in Figure 3b as IC-EF).
  *   - Section 5 ("Further Remarks"): the PTHash non-minimal trick of building on
  *     M > n slots and remapping slots >= n onto free slots < n, with Elias-Fano.
  *
@@ -349,7 +350,7 @@ static int check_params(uint64_t n, const or_params* p) {
     if (!(p->lambda > 0.0) || !isfinite(p->lambda)) return OR_ERR_INVALID_ARG;
     if (!(p->alpha > 0.0) || p->alpha > 1.0) return OR_ERR_INVALID_ARG;
     if (p->partition_size == 0) return OR_ERR_INVALID_ARG;
-    if (p->encoder > OR_ENC_IC_R || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
+    if (p->encoder > OR_ENC_IC_EF || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
     if (p->bucket_fn > OR_BUCKET_UNIFORM) return OR_ERR_INVALID_ARG;
     return OR_OK;
 }
@@ -725,6 +726,56 @@ static void encode_rice(or_mphf* h) {
     }
 }
 
+/* IC-EF: column b stores the inclusive prefix sums E_j = v_0 + ... + v_j of its
+ * values with Elias-Fano over the universe [0, E_last]: with N = N_P values and
+ * U = E_last + 1, l = floor(log2(U / N)) (0 when U < N) low bits of E_j packed
+ * at width l, and in the high part bit j + (E_j >> l) set (N + (E_last >> l) + 1
+ * bits); the position of every 64th one is a select sample.  A value is
+ * E_j - E_{j-1}.  The arrays and samples reuse the IC-R slots. */
+static uint32_t ef_low_bits(uint64_t last, uint64_t count) {
+    uint64_t U = last + 1;
+    if (U < count || count == 0) return 0;
+    return or_bitlen(U / count) - 1;
+}
+
+static void encode_ef_columns(or_mphf* h) {
+    uint32_t B = h->B;
+    uint64_t NP = h->NP, ns = (NP + 63) / 64;
+    h->col_l = (uint32_t*)calloc(B, sizeof(uint32_t));
+    h->col_lbase = (uint64_t*)calloc(B, sizeof(uint64_t));
+    h->col_hbase = (uint64_t*)calloc(B, sizeof(uint64_t));
+    h->col_H = (uint64_t*)calloc(B, sizeof(uint64_t));
+    uint64_t lbase = 0, hbase = 0;
+    for (uint32_t b = 0; b < B; b++) {
+        uint64_t last = 0;
+        for (uint64_t j = 0; j < NP; j++) last += h->pilots[(uint64_t)b * NP + j];
+        uint32_t l = ef_low_bits(last, NP);
+        h->col_l[b] = l;
+        h->col_lbase[b] = lbase;
+        h->col_hbase[b] = hbase;
+        h->col_H[b] = NP + (last >> l) + 1;
+        lbase += NP * (uint64_t)l;
+        hbase += h->col_H[b];
+    }
+    h->rlow_nbits = lbase;
+    h->rhigh_nbits = hbase;
+    h->rsamp_count = (uint64_t)B * ns;
+    h->rice_low = (uint64_t*)calloc(packed_words(lbase), sizeof(uint64_t));
+    h->rice_high = (uint64_t*)calloc(packed_words(hbase), sizeof(uint64_t));
+    h->rice_samples = (uint32_t*)calloc(h->rsamp_count ? h->rsamp_count : 1, sizeof(uint32_t));
+    for (uint32_t b = 0; b < B; b++) {
+        uint32_t l = h->col_l[b];
+        uint64_t E = 0;
+        for (uint64_t j = 0; j < NP; j++) {
+            E += h->pilots[(uint64_t)b * NP + j];
+            put_bits(h->rice_low, h->col_lbase[b] + j * l, l ? (E & ((1ULL << l) - 1)) : 0, l);
+            uint64_t pos = j + (E >> l);
+            put_bits(h->rice_high, h->col_hbase[b] + pos, 1, 1);
+            if (j % 64 == 0) h->rice_samples[(uint64_t)b * ns + j / 64] = (uint32_t)pos;
+        }
+    }
+}
+
 /* position (relative to the column) of the t-th one of column b's unary bits */
 static uint64_t rice_select(const or_mphf* h, uint32_t b, uint64_t t) {
     uint64_t ns = (h->NP + 63) / 64;
@@ -744,10 +795,23 @@ static uint32_t decode_rice(const or_mphf* h, uint32_t b, uint64_t j) {
     return (uint32_t)((q << l) | get_bits(h->rice_low, h->col_lbase[b] + j * l, l));
 }
 
+/* IC-EF: E_j from its high part (select) and its low bits */
+static uint64_t ef_prefix(const or_mphf* h, uint32_t b, uint64_t j) {
+    uint32_t l = h->col_l[b];
+    uint64_t pos = rice_select(h, b, j);
+    return ((pos - j) << l) | get_bits(h->rice_low, h->col_lbase[b] + j * l, l);
+}
+
+static uint32_t decode_ef_column(const or_mphf* h, uint32_t b, uint64_t j) {
+    uint64_t e = ef_prefix(h, b, j);
+    return (uint32_t)(j == 0 ? e : e - ef_prefix(h, b, j - 1));
+}
+
 static uint32_t decode_pilot(const or_mphf* h, uint32_t b, uint64_t j) {
     if (h->prm.encoder == OR_ENC_IC_C)
         return (uint32_t)get_bits(h->pil_words, h->col_base[b] + j * h->col_w[b], h->col_w[b]);
     if (h->prm.encoder == OR_ENC_IC_R) return decode_rice(h, b, j);
+    if (h->prm.encoder == OR_ENC_IC_EF) return decode_ef_column(h, b, j);
     uint64_t r = get_bits(h->rank_words, h->col_rbase[b] + j * h->col_rw[b], h->col_rw[b]);
     return (uint32_t)get_bits(h->dict_words, h->col_dbase[b] + r * h->col_dw[b], h->col_dw[b]);
 }
@@ -819,7 +883,7 @@ static void account_bits(or_mphf* h) {
     for (uint32_t b = 0; b < h->B; b++) {
         if (h->prm.encoder == OR_ENC_IC_C)
             bp += NP * (uint64_t)h->col_w[b] + 64 + 8;
-        else if (h->prm.encoder == OR_ENC_IC_R)
+        else if (h->prm.encoder == OR_ENC_IC_R || h->prm.encoder == OR_ENC_IC_EF)
             bp += NP * (uint64_t)h->col_l[b] + h->col_H[b] + 32 * ((NP + 63) / 64) + 64 + 64 + 8;
         else
             bp += NP * (uint64_t)h->col_rw[b] + h->col_K[b] * (uint64_t)h->col_dw[b] + 64 + 64 + 8 + 8;
@@ -945,6 +1009,8 @@ int or_build_hashed(const uint64_t* hk, uint64_t n, const or_params* prm, int th
         encode_compact(h);
     else if (prm->encoder == OR_ENC_IC_R)
         encode_rice(h);
+    else if (prm->encoder == OR_ENC_IC_EF)
+        encode_ef_columns(h);
     else
         encode_dictionary(h);
     build_remap(h, taken_global);
@@ -1021,7 +1087,7 @@ const void* or_get_array(const or_mphf* h, const char* name, uint64_t* count, ui
         A(col_w, h->B, 4);
         A(col_base, h->B, 8);
         A(pil_words, packed_words(h->pil_nbits), 8);
-    } else if (h->prm.encoder == OR_ENC_IC_R) {
+    } else if (h->prm.encoder == OR_ENC_IC_R || h->prm.encoder == OR_ENC_IC_EF) {
         A(col_l, h->B, 4);
         A(col_lbase, h->B, 8);
         A(col_hbase, h->B, 8);

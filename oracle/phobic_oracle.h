@@ -30,6 +30,7 @@ extern "C" {
 #define OR_ENC_IC_C 0
 #define OR_ENC_IC_D 1
 #define OR_ENC_IC_R 2
+#define OR_ENC_IC_EF 3
 
 /* bucket assignment functions (Figure 3a): the optimised beta_eps (Theorem 2),
  * beta_* (eps = 0), PTHash's skewed split (60 % of the keys into 30 % of the

@@ -290,7 +290,7 @@ def test_every_pilot_is_the_first_valid(orc, mode, lam, alpha, P, n):
     assert h.verify_first_valid(hk)
 
 
-@pytest.mark.parametrize("enc", [0, 1, 2])
+@pytest.mark.parametrize("enc", [0, 1, 2, 3])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("alpha", [1.0, 0.99, 0.9])
 def test_query_is_bijection(orc, enc, mode, alpha):
@@ -438,6 +438,37 @@ def test_interleaved_rice_layout(orc):
     assert np.unique(q).size == keys.size and q.max() < keys.size
 
 
+def test_interleaved_elias_fano_layout(orc):
+    """IC-EF, decoded by an independent numpy reader: column b holds the prefix
+    sums E_j of its pilots in Elias-Fano form, with l = floor(log2(U / N)) low bits
+    (U = E_last + 1, N = N_P; 0 when U < N), bit j + (E_j >> l) set in the high part
+    of N + (E_last >> l) + 1 bits, and every 64th one as a select sample."""
+    rng = np.random.default_rng(24)
+    keys = rng.integers(0, 2**64, size=60_000, dtype=np.uint64)
+    h = orc.Oracle(keys, lam=7.0, alpha=0.99, P=800, encoder=orc.ENC_IC_EF, threads=4)
+    pil = h.pilots
+    B, NP = pil.shape
+    l, lb, hb, H = h.array("col_l"), h.array("col_lbase"), h.array("col_hbase"), h.array("col_H")
+    low, high, samp = h.array("rice_low"), h.array("rice_high"), h.array("rice_samples")
+    ns = (NP + 63) // 64
+    high_bits = np.unpackbits(high.view(np.uint8), bitorder="little")
+    total = 0
+    for b in range(B):
+        E = np.cumsum(pil[b].astype(np.int64))
+        U = int(E[-1]) + 1
+        lw = (U // NP).bit_length() - 1 if U >= NP else 0
+        assert l[b] == lw and H[b] == NP + (int(E[-1]) >> lw) + 1
+        ones = np.flatnonzero(high_bits[int(hb[b]):int(hb[b]) + int(H[b])])
+        assert ones.size == NP
+        lo = np.array([_bits(low, int(lb[b]) + j * lw, lw) for j in range(NP)], dtype=np.int64)
+        got = ((ones - np.arange(NP)) << lw) | lo
+        assert np.array_equal(got, E), b
+        assert np.array_equal(np.diff(np.concatenate([[0], got])), pil[b].astype(np.int64))
+        assert np.array_equal(samp[b * ns:(b + 1) * ns], ones[::64])
+        total += NP * lw + int(H[b]) + 32 * ns + 136
+    assert h.u64("bits_pilots") == total
+
+
 def test_offsets_are_differences_to_expectation(orc):
     """Section 4: sizes are differences of consecutive offsets; offsets are
     stored as the difference to their expectation."""
@@ -495,3 +526,8 @@ def test_space_bands_from_the_paper(orc):
     ref_r = bands["fig3b_lambda8"]["IC-R"]["bits_per_key"]
     assert math.log2(math.e) < hr.bits_per_key() < bpk
     assert abs(hr.bits_per_key() - ref_r) < bands["band"], (hr.bits_per_key(), ref_r)
+    # IC-EF (Elias-Fano over each column's prefix sums): between IC-R and IC-C, as in Fig. 3b
+    he = orc.Oracle(keys, lam=8.0, P=2500, encoder=orc.ENC_IC_EF, threads=8)
+    ref_e = bands["fig3b_lambda8"]["IC-EF"]["bits_per_key"]
+    assert hr.bits_per_key() < he.bits_per_key() < bpk
+    assert abs(he.bits_per_key() - ref_e) < bands["band"], (he.bits_per_key(), ref_e)
