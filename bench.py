@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-target-s", type=float, default=12.0)
     ap.add_argument("--candidate-width", type=int, default=0, help="search window width (32/64; 0 = default)")
-    ap.add_argument("--encoder", choices=["ic-c", "ic-d", "ic-r"], default=None,
+    ap.add_argument("--encoder", choices=["ic-c", "ic-d", "ic-r", "ic-ef"], default=None,
                     help="pilot encoder instead of the workload's own")
     ap.add_argument("--lam", type=float, default=None, help="average bucket size instead of the workload's own")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-build section")
@@ -89,10 +89,10 @@ def workload(a):
     n = int(a.n or 1e8)
     w = dict(name=WORKLOAD, n=n, lam=7.0, alpha=0.99, P=2500, encoder=1, q_uniform=n, q_zipf=n)
     if a.encoder or a.lam:
-        enc = {"ic-c": 0, "ic-d": 1, "ic-r": 2}[a.encoder] if a.encoder else w["encoder"]
+        enc = {"ic-c": 0, "ic-d": 1, "ic-r": 2, "ic-ef": 3}[a.encoder] if a.encoder else w["encoder"]
         w.update(encoder=enc, lam=a.lam or w["lam"])
         w["name"] = (f"{n:.0e} distinct uniform uint64 keys, lambda={w['lam']:g}, alpha=0.99 with Elias-Fano remap, "
-                     f"partition size 2500, {['IC-C', 'IC-D', 'IC-R'][enc]} pilot encoding; {n:.0e} uniform + "
+                     f"partition size 2500, {['IC-C', 'IC-D', 'IC-R', 'IC-EF'][enc]} pilot encoding; {n:.0e} uniform + "
                      f"{n:.0e} Zipf(s=1) positive queries (variant of the default workload)")
     return w
 
@@ -272,7 +272,7 @@ def run_reference(a):
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "u64", "data": "synthetic",
            "config": {"workload": w["name"], "n": w["n"], "lambda": w["lam"], "alpha": w["alpha"], "P": w["P"],
-                      "encoder": ["IC-C", "IC-D", "IC-R"][w["encoder"]]},
+                      "encoder": ["IC-C", "IC-D", "IC-R", "IC-EF"][w["encoder"]]},
            "cpu_baseline": {"value": v, "unit": "Mkeys/s", "cores": cores, "kind": "oracle",
                             "sample": f"each step: oracle build of the first {n_s} keys of the workload on {cores} "
                                       f"threads"},
@@ -468,7 +468,7 @@ def run_ours(a):
         "dtype": "u64",
         "data": "synthetic",
         "config": {"workload": w["name"], "n": n, "lambda": w["lam"], "alpha": w["alpha"], "P": w["P"],
-                   "encoder": ["IC-C", "IC-D", "IC-R"][w["encoder"]], "queries_uniform": w["q_uniform"],
+                   "encoder": ["IC-C", "IC-D", "IC-R", "IC-EF"][w["encoder"]], "queries_uniform": w["q_uniform"],
                    "queries_zipf": w["q_zipf"], "parallelism": f"independent key set per GPU x{world}",
                    "l2": "inputs larger than L2 (8e8-byte key and query arrays vs 126 MB L2)", "gpu": gpu_name},
         "build_ms": b_ms,

@@ -51,11 +51,14 @@ typedef enum {
 typedef enum {
     PHOBIC_ENC_IC_C = 0, /* interleaved Compact: column width = bit length of its largest pilot */
     PHOBIC_ENC_IC_D = 1, /* interleaved Dictionary: sorted distinct pilots + compact ranks */
-    PHOBIC_ENC_IC_R = 2  /* interleaved Golomb-Rice: per column, the low l bits packed at width l and the
+    PHOBIC_ENC_IC_R = 2, /* interleaved Golomb-Rice: per column, the low l bits packed at width l and the
                             rest in unary, l by Kiely's rule from the column mean; a select sample every
                             64 partitions.  Export layout: col_meta[2b] = low base | l << 56,
                             col_meta[2b+1] = unary base; the dictionary array holds the u32 select samples
                             (B x ceil(N_P/64), padded to whole words) followed by the unary bits */
+    PHOBIC_ENC_IC_EF = 3 /* interleaved Elias-Fano: per column, the prefix sums E_j of its pilots with
+                            l = floor(log2((E_last + 1) / N_P)) low bits packed, bit j + (E_j >> l) set in the
+                            high part, a select sample every 64 partitions; the same export layout as IC-R */
 } phobic_encoder;
 
 /* bucket assignment functions (Section 3, Figure 3a): the optimised beta_eps of

@@ -21,6 +21,9 @@
 //   the rest in unary, the pilot of partition j setting bit
 //   j + sum_{i <= j} (v_i >> l) of the column's unary bits; and that position
 //   for every 64th partition as a select sample.
+//   IC-EF (Elias-Fano over each column's prefix sums E_j, l = floor(log2((E_last
+//   + 1) / N_P)) low bits): the low bits of E_j packed at width l, bit
+//   j + (E_j >> l) set in the high part, and the same select samples.
 // Columns of all sets are described by ColDesc records; packing is a gather in
 // which each thread assembles one 64-bit output word from the values that
 // overlap it (atomicOr where two columns share a word).
@@ -183,25 +186,33 @@ __global__ void __launch_bounds__(256) k_rice_unary_len(const uint32_t* __restri
     }
 }
 
-// IC-R: one block per column.  An inclusive block scan of (pilot >> l) over
-// the column's partitions, chunk by chunk with a carry, gives each value's set
-// bit j + sum_{i <= j}; bits go in with atomicOr (neighbours share words), and
-// every 64th position becomes a select sample.
-__global__ void __launch_bounds__(1024) k_rice_unary(const uint32_t* __restrict__ pilots,
-                                                     const ColDesc* __restrict__ cols, uint32_t ncols,
-                                                     uint64_t* __restrict__ arena) {
+// IC-R and IC-EF: one block per column, an inclusive block scan over the
+// column's partitions, chunk by chunk with a carry.
+//   IC-R (kEF = false): scan of q_j = pilot >> l; value j sets bit
+//   j + sum_{i <= j} q_i of the unary bits (its low part is packed separately).
+//   IC-EF (kEF = true): scan of the pilots themselves, E_j = sum_{i <= j} v_i;
+//   value j writes the low l bits of E_j at bit base + j l of the low array and
+//   sets bit j + (E_j >> l) of the high bits.
+// Bits go in with atomicOr (neighbours share words); every 64th set bit's
+// position becomes a select sample.
+template <bool kEF>
+__global__ void __launch_bounds__(1024) k_column_unary(const uint32_t* __restrict__ pilots,
+                                                       const ColDesc* __restrict__ cols, uint32_t ncols,
+                                                       uint64_t* __restrict__ arena) {
     __shared__ unsigned long long warp_sums[32];
     __shared__ unsigned long long carry_s;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t c = blockIdx.x; c < ncols; c += gridDim.x) {
         const ColDesc d = cols[c];
         uint64_t* high = arena + d.hi_dst_word;
+        uint64_t* low = arena + d.dst_word;
         uint32_t* samples = reinterpret_cast<uint32_t*>(arena + d.samp_dst_word) + d.samp_base;
         if (tid == 0) carry_s = 0;
         __syncthreads();
         for (uint64_t j0 = 0; j0 < d.count; j0 += 1024) {
             const uint64_t j = j0 + tid;
-            const unsigned long long q = j < d.count ? (__ldg(pilots + d.src + j) >> d.width) : 0;
+            const uint32_t v = j < d.count ? __ldg(pilots + d.src + j) : 0u;
+            const unsigned long long q = kEF ? (unsigned long long)v : (unsigned long long)(v >> d.width);
             unsigned long long x = q;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -223,7 +234,21 @@ __global__ void __launch_bounds__(1024) k_rice_unary(const uint32_t* __restrict_
             __syncthreads();
             const unsigned long long carry = carry_s;
             if (j < d.count) {
-                const uint64_t pos = j + carry + warp_sums[warp] + x;  // inclusive sum
+                const uint64_t incl = carry + warp_sums[warp] + x;  // inclusive sum
+                uint64_t pos;
+                if (kEF) {
+                    pos = j + (incl >> d.width);
+                    if (d.width) {
+                        const uint64_t lv = incl & ((1ull << d.width) - 1);
+                        const uint64_t o = d.base + j * d.width;
+                        const uint32_t sh = (uint32_t)(o & 63);
+                        atomicOr((unsigned long long*)(low + (o >> 6)), (unsigned long long)(lv << sh));
+                        if (sh + d.width > 64)
+                            atomicOr((unsigned long long*)(low + (o >> 6) + 1), (unsigned long long)(lv >> (64 - sh)));
+                    }
+                } else {
+                    pos = j + incl;
+                }
                 const uint64_t bit = d.hi_base + pos;
                 atomicOr((unsigned long long*)(high + (bit >> 6)), 1ull << (bit & 63));
                 if ((j & 63) == 0) samples[j >> 6] = (uint32_t)pos;
@@ -392,7 +417,14 @@ cudaError_t launch_rice_unary_len(const uint32_t* pilots, const ColDesc* cols, u
 
 cudaError_t launch_rice_unary(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* arena,
                               cudaStream_t stream) {
-    k_rice_unary<<<grid_items(ncols), 1024, 0, stream>>>(pilots, cols, ncols, arena);
+    k_column_unary<false><<<grid_items(ncols), 1024, 0, stream>>>(pilots, cols, ncols, arena);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ef_columns(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* arena,
+                              cudaStream_t stream) {
+    k_column_unary<true><<<grid_items(ncols), 1024, 0, stream>>>(pilots, cols, ncols, arena);
     note_launches(1);
     return cudaGetLastError();
 }

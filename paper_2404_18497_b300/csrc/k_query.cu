@@ -97,17 +97,15 @@ __device__ __forceinline__ uint64_t prev_one(const uint64_t* __restrict__ words,
     return wi * 64 + 63 - (uint64_t)__clzll((long long)w);
 }
 
-// IC-R pilot of partition j in column b: the low part at width l, plus the
-// unary part (the distance between the ones of partitions j-1 and j, minus
-// one).  The one of partition j-1 is found from the column's select sample
-// for partition 64 floor(j / 64) by skipping ones with popcounts.
-__device__ __forceinline__ uint32_t rice_pilot(const QueryView& v, uint32_t b, uint64_t j) {
-    const uint64_t m0 = __ldg(v.col_meta + 2 * b), hb = __ldg(v.col_meta + 2 * b + 1);
-    const uint32_t l = (uint32_t)(m0 >> 56);
+// Bits of the ones of partitions j - 1 and j in column b's select-sampled
+// unary part (a = hb - 1 for j = 0): from the column's sample for partition
+// 64 floor(j / 64), skipping ones with popcounts.  hb: the column's first bit.
+__device__ __forceinline__ void unary_pair(const QueryView& v, uint32_t b, uint64_t j, uint64_t hb, uint64_t* a_out,
+                                           uint64_t* c_out) {
     const uint32_t* samples = reinterpret_cast<const uint32_t*>(v.dict_words) + (uint64_t)b * v.rice_ns;
     const uint64_t* high = v.rice_high;
     const uint64_t s = hb + __ldg(samples + (j >> 6));  // bit of the one of partition 64 floor(j / 64)
-    uint64_t a, c;  // bits of the ones of partitions j - 1 and j (a = hb - 1 for j = 0)
+    uint64_t a, c;
     if ((j & 63) == 0) {
         c = s;
         a = j ? prev_one(high, c) : hb - 1;
@@ -128,8 +126,32 @@ __device__ __forceinline__ uint32_t rice_pilot(const QueryView& v, uint32_t b, u
         }
         c = next_one(high, a + 1);
     }
+    *a_out = a;
+    *c_out = c;
+}
+
+// IC-R pilot of partition j in column b: the low part at width l, plus the
+// unary part (the distance between the ones of partitions j-1 and j, minus one)
+__device__ __forceinline__ uint32_t rice_pilot(const QueryView& v, uint32_t b, uint64_t j) {
+    const uint64_t m0 = __ldg(v.col_meta + 2 * b), hb = __ldg(v.col_meta + 2 * b + 1);
+    const uint32_t l = (uint32_t)(m0 >> 56);
+    uint64_t a, c;
+    unary_pair(v, b, j, hb, &a, &c);
     const uint64_t q = c - a - 1;
     return (uint32_t)((q << l) | read_bits(v.pil_words, (m0 & kMeta) + j * l, l));
+}
+
+// IC-EF pilot of partition j in column b: E_j - E_{j-1}, each prefix sum from
+// the position of its one (high part: position - index) and its low l bits
+__device__ __forceinline__ uint32_t ef_column_pilot(const QueryView& v, uint32_t b, uint64_t j) {
+    const uint64_t m0 = __ldg(v.col_meta + 2 * b), hb = __ldg(v.col_meta + 2 * b + 1);
+    const uint32_t l = (uint32_t)(m0 >> 56);
+    const uint64_t lb = m0 & kMeta;
+    uint64_t a, c;
+    unary_pair(v, b, j, hb, &a, &c);
+    const uint64_t ej = ((c - hb - j) << l) | read_bits(v.pil_words, lb + j * l, l);
+    const uint64_t ep = j ? (((a - hb - (j - 1)) << l) | read_bits(v.pil_words, lb + (j - 1) * l, l)) : 0;
+    return (uint32_t)(ej - ep);
 }
 
 constexpr int kSeedTable = 64;  // pilot seeds mix64(s ^ C) for s < 64, per block
@@ -155,6 +177,8 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
     uint32_t p;
     if (v.encoder == 2) {
         p = rice_pilot(v, b, j);
+    } else if (v.encoder == 3) {
+        p = ef_column_pilot(v, b, j);
     } else if (v.small_bits) {
         const uint32_t jj = (uint32_t)j;
         if (v.encoder == 0) {

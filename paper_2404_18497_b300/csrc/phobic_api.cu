@@ -263,7 +263,7 @@ phobic_status check_params(uint64_t n, const phobic_params& p) {
     if (!(p.lambda > 0.0) || !std::isfinite(p.lambda)) return PHOBIC_ERR_INVALID_ARG;
     if (!(p.alpha > 0.0) || p.alpha > 1.0) return PHOBIC_ERR_INVALID_ARG;
     if (p.partition_size == 0 || p.partition_size > kMaxPartitionSize) return PHOBIC_ERR_INVALID_ARG;
-    if (p.encoder > PHOBIC_ENC_IC_R || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
+    if (p.encoder > PHOBIC_ENC_IC_EF || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
     if (p.warps_per_partition != 0 && p.warps_per_partition != 1 && p.warps_per_partition != 2 &&
         p.warps_per_partition != 4)
         return PHOBIC_ERR_INVALID_ARG;
@@ -522,12 +522,14 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     CK(ev.mark(5, st));
     CK(launch_offset_minmax(T, d_od, S, mm, st));
     const bool icr = prm.encoder == PHOBIC_ENC_IC_R;
+    const bool icef = prm.encoder == PHOBIC_ENC_IC_EF;
+    const bool unary = icr || icef;  // column layouts with a select-sampled unary part
     uint64_t* colsum = nullptr;
-    if (icr) CK(tmp.alloc(&colsum, (size_t)cols_total * 8));
+    if (unary) CK(tmp.alloc(&colsum, (size_t)cols_total * 8));
     CK(launch_column_max(pilots, d_cd, (uint32_t)cols_total, colmax, colsum, st));
     CK(d2h(hmm, mm, 2 * (size_t)S, st));
     CK(d2h(hcolmax, colmax, cols_total, st));
-    if (icr) CK(d2h(hK, colsum, cols_total, st));
+    if (unary) CK(d2h(hK, colsum, cols_total, st));
     CK(d2h(hstatus, status, 1, st));
     if (work) CK(d2h(hst + 12, reinterpret_cast<uint64_t*>(work), 2, st));
     CK(cudaStreamSynchronize(st));
@@ -559,6 +561,12 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         CK(cudaStreamSynchronize(st));
     }
 
+    // ---- IC-EF: low bits from the column sums (the unary lengths follow from them)
+    if (icef)
+        for (uint64_t c = 0; c < cols_total; c++) {
+            const uint64_t U = hK[c] + 1, N = cd[c].count;
+            cd[c].width = U >= N ? bitlen64(U / N) - 1 : 0;
+        }
     // ---- IC-R: Rice parameters from the column sums, then the unary lengths
     if (icr) {
         for (uint64_t c = 0; c < cols_total; c++) cd[c].width = rice_param(hK[c], cd[c].count);
@@ -583,7 +591,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         aw += p.n_off;
         off_begin[s + 1] = off_begin[s] + p.n_off;
         const bool icd = prm.encoder == PHOBIC_ENC_IC_D;
-        p.n_meta = (icd || icr) ? 2 * (uint64_t)p.B : p.B;
+        p.n_meta = (icd || unary) ? 2 * (uint64_t)p.B : p.B;
         p.a_meta = aw;
         aw += p.n_meta;
         metas[s].resize(p.n_meta);
@@ -592,9 +600,10 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         for (uint32_t b = 0; b < p.B; b++) {
             ColDesc& c = cd[p.col_base + b];
             const uint64_t c_id = p.col_base + b;
-            if (icr) {
-                // c.width = Rice parameter (set above); dbase counts unary bits
-                const uint64_t H = p.NP + hK[c_id];
+            if (unary) {
+                // c.width = Rice parameter / Elias-Fano low bits (set above); dbase counts
+                // unary bits: IC-R N_P + sum (v >> l); IC-EF N_P + (E_last >> l) + 1
+                const uint64_t H = icr ? p.NP + hK[c_id] : p.NP + (hK[c_id] >> c.width) + 1;
                 c.base = rbase;
                 c.hi_base = dbase;
                 c.samp_base = (uint64_t)b * ns;
@@ -627,8 +636,8 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         p.n_pil = packed_words(rbase);
         p.a_pil = aw;
         aw += p.n_pil;
-        p.samp_words = icr ? ((uint64_t)p.B * ns + 1) / 2 : 0;
-        p.n_dict = icd ? packed_words(dbase) : icr ? p.samp_words + packed_words(dbase) : 0;
+        p.samp_words = unary ? ((uint64_t)p.B * ns + 1) / 2 : 0;
+        p.n_dict = icd ? packed_words(dbase) : unary ? p.samp_words + packed_words(dbase) : 0;
         p.a_dict = aw;
         aw += p.n_dict;
         for (uint32_t b = 0; b < p.B; b++) {
@@ -702,9 +711,11 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     CK(h2d(d_cbeg, col_begin.data(), cols_total + 1, st));
     CK(launch_offset_pack(T, d_od, S, d_obeg, off_begin[S], arena, st));
     const bool icd = prm.encoder == PHOBIC_ENC_IC_D;
-    CK(launch_pack_columns(pilots, d_cd, (uint32_t)cols_total, d_cbeg, col_begin[cols_total], icd, bitmaps, brank,
-                           arena, st));
+    if (!icef)  // IC-C values, IC-D ranks, IC-R low parts
+        CK(launch_pack_columns(pilots, d_cd, (uint32_t)cols_total, d_cbeg, col_begin[cols_total], icd, bitmaps,
+                               brank, arena, st));
     if (icr) CK(launch_rice_unary(pilots, d_cd, (uint32_t)cols_total, arena, st));
+    if (icef) CK(launch_ef_columns(pilots, d_cd, (uint32_t)cols_total, arena, st));
     if (icd) {
         uint64_t* d_bmbeg;
         CK(tmp.alloc(&d_bmbeg, (cols_total + 1) * 8));
@@ -827,8 +838,8 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         v.ef_low = h->ef_low;
         v.ef_high = h->ef_high;
         v.ef_samples = h->ef_samples;
-        v.rice_high = icr ? arena + p.a_dict + p.samp_words : nullptr;
-        v.rice_ns = icr ? (uint32_t)((p.NP + 63) / 64) : 0;
+        v.rice_high = unary ? arena + p.a_dict + p.samp_words : nullptr;
+        v.rice_ns = unary ? (uint32_t)((p.NP + 63) / 64) : 0;
         v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
         v.key_kind = key_kind;
         v.string_seed = prm.seed;
@@ -1225,7 +1236,8 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     // ones, and each select sample is the position of its 64k-th one, so the
     // query's scans never leave the column
     uint64_t rice_sw = 0;
-    if (p.encoder == PHOBIC_ENC_IC_R) {
+    const bool unary_enc = p.encoder == PHOBIC_ENC_IC_R || p.encoder == PHOBIC_ENC_IC_EF;
+    if (unary_enc) {
         const uint64_t ns = (NP + 63) / 64;
         rice_sw = (B * ns + 1) / 2;
         if (counts[3] < rice_sw + 1) return PHOBIC_ERR_FORMAT;
@@ -1327,8 +1339,8 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     v.ef_low = h->ef_low;
     v.ef_high = h->ef_high;
     v.ef_samples = h->ef_samples;
-    v.rice_high = p.encoder == PHOBIC_ENC_IC_R ? h->dict_words + rice_sw : nullptr;
-    v.rice_ns = p.encoder == PHOBIC_ENC_IC_R ? (uint32_t)((NP + 63) / 64) : 0;
+    v.rice_high = unary_enc ? h->dict_words + rice_sw : nullptr;
+    v.rice_ns = unary_enc ? (uint32_t)((NP + 63) / 64) : 0;
     v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
     v.key_kind = key_kind;
     v.string_seed = p.seed;

@@ -138,6 +138,9 @@ cudaError_t launch_rice_unary_len(const uint32_t* pilots, const ColDesc* cols, u
 // IC-R: unary bits and select samples of every column
 cudaError_t launch_rice_unary(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* arena,
                               cudaStream_t stream);
+// IC-EF: low bits, high bits and select samples of every column (prefix sums)
+cudaError_t launch_ef_columns(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* arena,
+                              cudaStream_t stream);
 cudaError_t launch_pack_columns(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, const uint64_t* word_begin,
                                 uint64_t total_words, bool ranks, const uint64_t* bitmaps,
                                 const uint64_t* bitmaps_rank, uint64_t* arena, cudaStream_t stream);

@@ -24,10 +24,10 @@ STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "DUP_HASH", 4: "SEARCH_LIMIT",
     5: "PARTITION_TOO_LARGE", 6: "CUDA", 7: "TIMEOUT", 8: "FORMAT",
 }
-ENC_IC_C, ENC_IC_D, ENC_IC_R = 0, 1, 2
+ENC_IC_C, ENC_IC_D, ENC_IC_R, ENC_IC_EF = 0, 1, 2, 3
 PILOT_ADDITIVE, PILOT_XOR = 0, 1
-_ENC = {"IC-C": ENC_IC_C, "IC-D": ENC_IC_D, "IC-R": ENC_IC_R, ENC_IC_C: ENC_IC_C, ENC_IC_D: ENC_IC_D,
-        ENC_IC_R: ENC_IC_R}
+_ENC = {"IC-C": ENC_IC_C, "IC-D": ENC_IC_D, "IC-R": ENC_IC_R, "IC-EF": ENC_IC_EF, ENC_IC_C: ENC_IC_C,
+        ENC_IC_D: ENC_IC_D, ENC_IC_R: ENC_IC_R, ENC_IC_EF: ENC_IC_EF}
 _MODE = {"additive": PILOT_ADDITIVE, "xor": PILOT_XOR, PILOT_ADDITIVE: PILOT_ADDITIVE, PILOT_XOR: PILOT_XOR}
 
 
@@ -630,7 +630,7 @@ def parse_export(data: bytes) -> dict:
         c = hdr["n_" + name]
         hdr[name] = w[at: at + c].copy()
         at += c
-    if hdr["encoder"] == ENC_IC_R:
+    if hdr["encoder"] in (ENC_IC_R, ENC_IC_EF):
         # the dictionary array holds the u32 select samples, then the unary bits
         ns = (hdr["NP"] + 63) // 64
         sw = (hdr["B"] * ns + 1) // 2

@@ -48,7 +48,7 @@ def compare_structure(ph, orc_h, h, encoder):
         assert ((meta >> np.uint64(56)).astype(np.uint32) == o.array("col_w")).all()
         assert ((meta & mask) == o.array("col_base")).all()
         assert (ex["pil_words"] == o.array("pil_words")).all()
-    elif encoder == 2:
+    elif encoder in (2, 3):
         assert ((meta[0::2] >> np.uint64(56)).astype(np.uint32) == o.array("col_l")).all()
         assert ((meta[0::2] & mask) == o.array("col_lbase")).all()
         assert (meta[1::2] == o.array("col_hbase")).all()
@@ -129,6 +129,11 @@ CASES = [
     (300_000, 9.0, 0.99, 1024, 2, 0),
     (1_000_000, 8.0, 1.0, 2500, 2, 0),
     (1_000_000, 7.0, 0.99, 2500, 2, 0),
+    # IC-EF (interleaved Elias-Fano over each column's prefix sums)
+    (1, 7.0, 1.0, 2500, 3, 0),
+    (2501, 7.0, 0.99, 2500, 3, 0),
+    (70_001, 6.0, 0.9, 300, 3, 1),
+    (1_000_000, 8.0, 1.0, 2500, 3, 0),
     # the large-lambda regime (search cost ~ e^lambda per key, Section 3)
     (400_000, 10.0, 1.0, 2500, 2, 0),
     (150_000, 12.0, 1.0, 2500, 2, 0),
@@ -196,7 +201,7 @@ def test_query_unaligned_and_odd_lengths(ph, orc):
 
 def test_export_import_roundtrip(ph, orc):
     keys = _keys(123_457, 8)
-    for enc, alpha in [(0, 1.0), (1, 0.95), (2, 0.99)]:
+    for enc, alpha in [(0, 1.0), (1, 0.95), (2, 0.99), (3, 0.99)]:
         h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, alpha, 2500, encoder=enc))
         data = ph.phobic_export(h)
         h2 = ph.phobic_import(data)
@@ -210,7 +215,7 @@ def test_export_import_roundtrip(ph, orc):
         assert e.value.status == "FORMAT"
         with pytest.raises(ph.PhobicError):
             ph.phobic_import(data[:-8])
-        if enc == 2:
+        if enc in (2, 3):
             # a unary region with a missing one, or a wrong select sample, is refused
             ex = ph.parse_export(data)
             w = np.frombuffer(data, dtype=np.uint64).copy()
@@ -359,7 +364,7 @@ def test_string_hash_unaligned_and_tails(ph, orc):
         assert np.array_equal(got, orc.string_hashes(data, off, 123))
 
 
-@pytest.mark.parametrize("alpha,enc", [(0.99, 1), (1.0, 0), (0.99, 2)])
+@pytest.mark.parametrize("alpha,enc", [(0.99, 1), (1.0, 0), (0.99, 2), (1.0, 3)])
 def test_batch_build_matches_single_builds(ph, orc, alpha, enc):
     """Batched construction: every set's structure equals the oracle's build of
     that set alone (and so the single-set path), for uneven set sizes and mixed
