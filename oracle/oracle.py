@@ -18,7 +18,7 @@ _SRC = os.path.join(_HERE, "phobic_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 
 OK, INVALID_ARG, OOM, DUP_HASH, SEARCH_LIMIT = 0, 1, 2, 3, 4
-ENC_IC_C, ENC_IC_D, ENC_IC_R, ENC_IC_EF = 0, 1, 2, 3
+ENC_IC_C, ENC_IC_D, ENC_IC_R, ENC_IC_EF, ENC_IC_CR = 0, 1, 2, 3, 4
 PILOT_ADDITIVE, PILOT_XOR = 0, 1
 
 
@@ -53,16 +53,17 @@ class _Params(ctypes.Structure):
         ("s_max", ctypes.c_uint32),
         ("seed", ctypes.c_uint64),
         ("bucket_fn", ctypes.c_uint32),
-        ("pad", ctypes.c_uint32),
+        ("compact_columns", ctypes.c_uint32),
     ]
 
 
 BUCKET_OPTIMIZED, BUCKET_BETA_STAR, BUCKET_SKEWED, BUCKET_UNIFORM = 0, 1, 2, 3
 
 
-def params(lam=7.0, alpha=1.0, P=2500, encoder=ENC_IC_C, mode=PILOT_ADDITIVE, s_max=0, seed=0, bucket_fn=0):
+def params(lam=7.0, alpha=1.0, P=2500, encoder=ENC_IC_C, mode=PILOT_ADDITIVE, s_max=0, seed=0, bucket_fn=0,
+           compact_columns=0):
     return _Params(float(lam), float(alpha), int(P), int(encoder), int(mode), int(s_max), int(seed),
-                   int(bucket_fn), 0)
+                   int(bucket_fn), int(compact_columns))
 
 
 _lib = None
@@ -124,9 +125,9 @@ class Oracle:
     """One MPHF built by the oracle."""
 
     def __init__(self, keys=None, *, hashed=None, lam=7.0, alpha=1.0, P=2500, encoder=ENC_IC_C,
-                 mode=PILOT_ADDITIVE, s_max=0, seed=0, threads=0, bucket_fn=0):
+                 mode=PILOT_ADDITIVE, s_max=0, seed=0, threads=0, bucket_fn=0, compact_columns=0):
         L = lib()
-        self.prm = params(lam, alpha, P, encoder, mode, s_max, seed, bucket_fn)
+        self.prm = params(lam, alpha, P, encoder, mode, s_max, seed, bucket_fn, compact_columns)
         h = ctypes.c_void_p()
         if hashed is not None:
             hk = _u64(hashed)

@@ -21,7 +21,9 @@
  *   - Section 4.1 (Interleaved Coding): encoder i holds the pilot of bucket i of
  *     every partition (Compact; Dictionary as named in Figure 3b; Golomb-Rice
  *     with Kiely's parameter and a select sample every 64 values; Elias-Fano
- *     over the column's prefix sums, named in Figure 3b as IC-EF).
+ *     over the column's prefix sums, named in Figure 3b as IC-EF; and the
+ *     mixture of Section 4.1 with Compact for the first columns, the large
+ *     buckets, and Golomb-Rice for the rest).
  *   - Section 5 ("Further Remarks"): the PTHash non-minimal trick of building on
  *     M > n slots and remapping slots >= n onto free slots < n, with Elias-Fano.
  *
@@ -350,7 +352,7 @@ static int check_params(uint64_t n, const or_params* p) {
     if (!(p->lambda > 0.0) || !isfinite(p->lambda)) return OR_ERR_INVALID_ARG;
     if (!(p->alpha > 0.0) || p->alpha > 1.0) return OR_ERR_INVALID_ARG;
     if (p->partition_size == 0) return OR_ERR_INVALID_ARG;
-    if (p->encoder > OR_ENC_IC_EF || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
+    if (p->encoder > OR_ENC_IC_CR || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
     if (p->bucket_fn > OR_BUCKET_UNIFORM) return OR_ERR_INVALID_ARG;
     return OR_OK;
 }
@@ -776,10 +778,77 @@ static void encode_ef_columns(or_mphf* h) {
     }
 }
 
+/* Section 4.1: interleaving lets each column use its own encoder.  IC-CR puts
+ * the first c = min(compact_columns, B) columns (the largest buckets, read most
+ * often) in Compact form, width = bit length of the column's largest pilot, and
+ * the others in Golomb-Rice form as IC-R.  The Compact values and the Rice low
+ * parts share one array in column order; unary bits and select samples exist
+ * for the Rice columns only (column b >= c has sample column b - c). */
+static void encode_mixture(or_mphf* h) {
+    uint32_t B = h->B;
+    uint64_t NP = h->NP, ns = (NP + 63) / 64;
+    uint32_t c = h->prm.compact_columns < B ? h->prm.compact_columns : B;
+    h->col_l = (uint32_t*)calloc(B, sizeof(uint32_t));
+    h->col_lbase = (uint64_t*)calloc(B, sizeof(uint64_t));
+    h->col_hbase = (uint64_t*)calloc(B, sizeof(uint64_t));
+    h->col_H = (uint64_t*)calloc(B, sizeof(uint64_t));
+    uint64_t lbase = 0, hbase = 0;
+    for (uint32_t b = 0; b < B; b++) {
+        const uint32_t* col = h->pilots + (uint64_t)b * NP;
+        uint32_t l;
+        uint64_t H = 0;
+        if (b < c) {
+            uint32_t mx = 0;
+            for (uint64_t j = 0; j < NP; j++)
+                if (col[j] > mx) mx = col[j];
+            l = or_bitlen(mx);
+        } else {
+            uint64_t sum = 0;
+            for (uint64_t j = 0; j < NP; j++) sum += col[j];
+            l = or_rice_param(sum, NP);
+            H = NP;
+            for (uint64_t j = 0; j < NP; j++) H += col[j] >> l;
+        }
+        h->col_l[b] = l;
+        h->col_lbase[b] = lbase;
+        h->col_hbase[b] = hbase;
+        h->col_H[b] = H;
+        lbase += NP * (uint64_t)l;
+        hbase += H;
+    }
+    h->rlow_nbits = lbase;
+    h->rhigh_nbits = hbase;
+    h->rsamp_count = (uint64_t)(B - c) * ns;
+    h->rice_low = (uint64_t*)calloc(packed_words(lbase), sizeof(uint64_t));
+    h->rice_high = (uint64_t*)calloc(packed_words(hbase), sizeof(uint64_t));
+    h->rice_samples = (uint32_t*)calloc(h->rsamp_count ? h->rsamp_count : 1, sizeof(uint32_t));
+    for (uint32_t b = 0; b < B; b++) {
+        const uint32_t* col = h->pilots + (uint64_t)b * NP;
+        uint32_t l = h->col_l[b];
+        uint64_t acc = 0;
+        for (uint64_t j = 0; j < NP; j++) {
+            uint32_t v = col[j];
+            put_bits(h->rice_low, h->col_lbase[b] + j * l, l ? (v & ((1ULL << l) - 1)) : 0, l);
+            if (b < c) continue;
+            acc += v >> l;
+            uint64_t pos = j + acc;
+            put_bits(h->rice_high, h->col_hbase[b] + pos, 1, 1);
+            if (j % 64 == 0) h->rice_samples[(uint64_t)(b - c) * ns + j / 64] = (uint32_t)pos;
+        }
+    }
+}
+
+/* the select-sample column of column b (IC-CR: Rice columns only) */
+static uint64_t sample_column(const or_mphf* h, uint32_t b) {
+    if (h->prm.encoder != OR_ENC_IC_CR) return b;
+    uint32_t c = h->prm.compact_columns < h->B ? h->prm.compact_columns : h->B;
+    return b - c;
+}
+
 /* position (relative to the column) of the t-th one of column b's unary bits */
 static uint64_t rice_select(const or_mphf* h, uint32_t b, uint64_t t) {
     uint64_t ns = (h->NP + 63) / 64;
-    uint64_t pos = h->rice_samples[(uint64_t)b * ns + t / 64];
+    uint64_t pos = h->rice_samples[sample_column(h, b) * ns + t / 64];
     uint64_t left = t % 64; /* ones still to pass */
     while (left) {
         pos++;
@@ -812,6 +881,11 @@ static uint32_t decode_pilot(const or_mphf* h, uint32_t b, uint64_t j) {
         return (uint32_t)get_bits(h->pil_words, h->col_base[b] + j * h->col_w[b], h->col_w[b]);
     if (h->prm.encoder == OR_ENC_IC_R) return decode_rice(h, b, j);
     if (h->prm.encoder == OR_ENC_IC_EF) return decode_ef_column(h, b, j);
+    if (h->prm.encoder == OR_ENC_IC_CR) {
+        uint32_t c = h->prm.compact_columns < h->B ? h->prm.compact_columns : h->B;
+        if (b < c) return (uint32_t)get_bits(h->rice_low, h->col_lbase[b] + j * h->col_l[b], h->col_l[b]);
+        return decode_rice(h, b, j);
+    }
     uint64_t r = get_bits(h->rank_words, h->col_rbase[b] + j * h->col_rw[b], h->col_rw[b]);
     return (uint32_t)get_bits(h->dict_words, h->col_dbase[b] + r * h->col_dw[b], h->col_dw[b]);
 }
@@ -883,11 +957,15 @@ static void account_bits(or_mphf* h) {
     for (uint32_t b = 0; b < h->B; b++) {
         if (h->prm.encoder == OR_ENC_IC_C)
             bp += NP * (uint64_t)h->col_w[b] + 64 + 8;
-        else if (h->prm.encoder == OR_ENC_IC_R || h->prm.encoder == OR_ENC_IC_EF)
+        else if (h->prm.encoder == OR_ENC_IC_R || h->prm.encoder == OR_ENC_IC_EF ||
+                 (h->prm.encoder == OR_ENC_IC_CR && b >= h->prm.compact_columns))
             bp += NP * (uint64_t)h->col_l[b] + h->col_H[b] + 32 * ((NP + 63) / 64) + 64 + 64 + 8;
+        else if (h->prm.encoder == OR_ENC_IC_CR)
+            bp += NP * (uint64_t)h->col_l[b] + 64 + 8; /* a Compact column of the mixture */
         else
             bp += NP * (uint64_t)h->col_rw[b] + h->col_K[b] * (uint64_t)h->col_dw[b] + 64 + 64 + 8 + 8;
     }
+    if (h->prm.encoder == OR_ENC_IC_CR) bp += 32; /* the number of Compact columns */
     h->bits_pilots = bp;
     h->bits_remap = 0;
     if (h->ef_N)
@@ -1011,6 +1089,8 @@ int or_build_hashed(const uint64_t* hk, uint64_t n, const or_params* prm, int th
         encode_rice(h);
     else if (prm->encoder == OR_ENC_IC_EF)
         encode_ef_columns(h);
+    else if (prm->encoder == OR_ENC_IC_CR)
+        encode_mixture(h);
     else
         encode_dictionary(h);
     build_remap(h, taken_global);
@@ -1087,7 +1167,7 @@ const void* or_get_array(const or_mphf* h, const char* name, uint64_t* count, ui
         A(col_w, h->B, 4);
         A(col_base, h->B, 8);
         A(pil_words, packed_words(h->pil_nbits), 8);
-    } else if (h->prm.encoder == OR_ENC_IC_R || h->prm.encoder == OR_ENC_IC_EF) {
+    } else if (h->prm.encoder >= OR_ENC_IC_R) {
         A(col_l, h->B, 4);
         A(col_lbase, h->B, 8);
         A(col_hbase, h->B, 8);

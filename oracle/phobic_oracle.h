@@ -31,6 +31,7 @@ extern "C" {
 #define OR_ENC_IC_D 1
 #define OR_ENC_IC_R 2
 #define OR_ENC_IC_EF 3
+#define OR_ENC_IC_CR 4 /* mixture: the first compact_columns columns Compact, the rest Golomb-Rice */
 
 /* bucket assignment functions (Figure 3a): the optimised beta_eps (Theorem 2),
  * beta_* (eps = 0), PTHash's skewed split (60 % of the keys into 30 % of the
@@ -56,7 +57,7 @@ typedef struct {
                                s < floor((2^32 - 1) / m_j), which also caps any other value */
     uint64_t seed;
     uint32_t bucket_fn;     /* OR_BUCKET_*: the bucket assignment function gamma */
-    uint32_t pad;
+    uint32_t compact_columns; /* OR_ENC_IC_CR: columns 0 .. c-1 Compact, the rest Golomb-Rice */
 } or_params;
 
 typedef struct or_mphf or_mphf;

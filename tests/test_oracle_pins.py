@@ -469,6 +469,50 @@ def test_interleaved_elias_fano_layout(orc):
     assert h.u64("bits_pilots") == total
 
 
+def test_compact_rice_mixture(orc):
+    """Section 4.1: interleaving lets the first c columns (the large buckets) use
+    Compact and the rest Golomb-Rice.  c = 0 is IC-R and c = B is IC-C, word for
+    word, plus the 32 bits that record c; an independent reader decodes every
+    column of a mixture; the space grows with c between the two."""
+    rng = np.random.default_rng(26)
+    keys = rng.integers(0, 2**64, size=60_000, dtype=np.uint64)
+    kw = dict(lam=7.0, alpha=0.99, P=800, threads=4)
+    r = orc.Oracle(keys, encoder=orc.ENC_IC_R, **kw)
+    c0 = orc.Oracle(keys, encoder=orc.ENC_IC_CR, compact_columns=0, **kw)
+    for name in ("col_l", "col_lbase", "col_hbase", "col_H", "rice_low", "rice_high", "rice_samples"):
+        assert np.array_equal(c0.array(name), r.array(name)), name
+    assert c0.u64("bits_pilots") == r.u64("bits_pilots") + 32
+    cc = orc.Oracle(keys, encoder=orc.ENC_IC_C, **kw)
+    B = cc.pilots.shape[0]
+    cB = orc.Oracle(keys, encoder=orc.ENC_IC_CR, compact_columns=B + 5, **kw)
+    assert np.array_equal(cB.array("col_l"), cc.array("col_w"))
+    assert np.array_equal(cB.array("col_lbase"), cc.array("col_base"))
+    assert np.array_equal(cB.array("rice_low"), cc.array("pil_words"))
+    assert cB.u64("bits_pilots") == cc.u64("bits_pilots") + 32
+    c = 7
+    h = orc.Oracle(keys, encoder=orc.ENC_IC_CR, compact_columns=c, **kw)
+    pil = h.pilots
+    NP = pil.shape[1]
+    l, lb, hb, H = h.array("col_l"), h.array("col_lbase"), h.array("col_hbase"), h.array("col_H")
+    low, high, samp = h.array("rice_low"), h.array("rice_high"), h.array("rice_samples")
+    ns = (NP + 63) // 64
+    assert samp.size == (B - c) * ns
+    high_bits = np.unpackbits(high.view(np.uint8), bitorder="little")
+    for b in range(B):
+        lo = np.array([_bits(low, int(lb[b]) + j * int(l[b]), int(l[b])) for j in range(NP)], dtype=np.int64)
+        if b < c:
+            assert l[b] == int(pil[b].max()).bit_length() and H[b] == 0
+            assert np.array_equal(lo, pil[b].astype(np.int64))
+        else:
+            ones = np.flatnonzero(high_bits[int(hb[b]):int(hb[b]) + int(H[b])])
+            q = np.diff(np.concatenate([[-1], ones])) - 1
+            assert np.array_equal((q << int(l[b])) | lo, pil[b].astype(np.int64)), b
+            assert np.array_equal(samp[(b - c) * ns:(b - c + 1) * ns], ones[::64])
+    q = h.query(keys)
+    assert np.unique(q).size == keys.size and q.max() < keys.size
+    assert c0.bits_per_key() <= h.bits_per_key() <= cB.bits_per_key()
+
+
 def test_offsets_are_differences_to_expectation(orc):
     """Section 4: sizes are differences of consecutive offsets; offsets are
     stored as the difference to their expectation."""
