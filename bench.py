@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
-    ap.add_argument("--only", choices=["batch", "serve", "lambda", "ablation"], default=None,
+    ap.add_argument("--only", choices=["batch", "serve", "lambda", "ablation", "encoders"], default=None,
                     help="run one extra section alone (lambda: the large-lambda sweep; ablation: the bucket "
                          "functions of Fig. 3a)")
     return ap.parse_args()
@@ -617,6 +617,45 @@ def run_lambda_sweep(a, phobic, workloads, torch):
                              "its CPU share); not the same machine or input"}
 
 
+# ---------------------------------------------------------------- encoders ---
+def run_encoders(a, phobic, workloads, torch):
+    """Figure 3b's comparison on this GPU: space and query rate of every pilot
+    encoder, and of Compact/Rice mixtures with c leading Compact columns (lambda 8,
+    alpha 1, P 2500, 1e8 keys, every key queried in random order)."""
+    stream = torch.cuda.current_stream()
+    n = 100_000_000
+    keys = workloads.stream_keys_torch(0, n, 37, "cuda")
+    perm = torch.randperm(n, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    qkeys = keys[perm]
+    del perm
+    out = torch.empty_like(qkeys)
+    rows = []
+    configs = [("IC-C", 0, 0), ("IC-D", 1, 0), ("IC-EF", 3, 0), ("IC-R", 2, 0)] + [
+        (f"IC-CR c={c}", 4, c) for c in (8, 32, 80, 160)]
+    for name, enc, c in configs:
+        prm = phobic.make_params(8.0, 1.0, 2500, encoder=enc, compact_columns=c, record_timings=True)
+        h = phobic.phobic_build_ex(keys, prm, stream)
+        for _ in range(3):
+            phobic.phobic_query(h, qkeys, out, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            phobic.phobic_query(h, qkeys, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        q_ms = e0.elapsed_time(e1) / 5
+        rows.append({"encoder": name, "bits_per_key": h.bits_per_key(), "query_ns_per_key": q_ms * 1e6 / n,
+                     "query_mkeys_s": n / q_ms / 1e3, "encode_ms": phobic.phobic_get_timings(h)["encode_ms"]})
+        h.free()
+    del keys, qkeys, out
+    torch.cuda.empty_cache()
+    phobic.phobic_trim(0)
+    return {"workload": "pilot encoders (Fig. 3b): 1e8 distinct uniform uint64 keys (counter-based stream), lambda=8, "
+                        "alpha=1, partition size 2500; every key queried once in a random order",
+            "rows": rows,
+            "paper_context": "Fig. 3b (CPU queries, 1e8 strings): IC-C 2.208 b/k, IC-D 2.599, IC-EF 1.824, IC-R 1.775"}
+
+
 # ------------------------------------------------------- bucket functions ---
 def run_ablation(a, phobic, workloads, torch):
     """Figure 3a's comparison on this GPU: construction time and space of each
@@ -920,6 +959,8 @@ def run_only(a):
         print(json.dumps({"lambda_sweep": run_lambda_sweep(a, phobic, workloads, torch)}))
     elif a.only == "ablation":
         print(json.dumps({"ablation": run_ablation(a, phobic, workloads, torch)}))
+    elif a.only == "encoders":
+        print(json.dumps({"encoders": run_encoders(a, phobic, workloads, torch)}))
     else:
         print(json.dumps({"serve": run_serve(a, phobic, workloads, torch)}))
 

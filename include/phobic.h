@@ -56,9 +56,14 @@ typedef enum {
                             64 partitions.  Export layout: col_meta[2b] = low base | l << 56,
                             col_meta[2b+1] = unary base; the dictionary array holds the u32 select samples
                             (B x ceil(N_P/64), padded to whole words) followed by the unary bits */
-    PHOBIC_ENC_IC_EF = 3 /* interleaved Elias-Fano: per column, the prefix sums E_j of its pilots with
+    PHOBIC_ENC_IC_EF = 3, /* interleaved Elias-Fano: per column, the prefix sums E_j of its pilots with
                             l = floor(log2((E_last + 1) / N_P)) low bits packed, bit j + (E_j >> l) set in the
                             high part, a select sample every 64 partitions; the same export layout as IC-R */
+    PHOBIC_ENC_IC_CR = 4  /* Section 4.1's mixture: the first c = min(compact_columns, B) columns (the largest
+                             buckets) Compact, the others Golomb-Rice as IC-R.  The Compact values and Rice low
+                             parts share the low array; col_meta[2b] = base | width << 56 for every column,
+                             col_meta[2b+1] = unary base; select samples for columns b >= c only (sample
+                             column b - c).  c is exported in bits 40..63 of the encoder header word */
 } phobic_encoder;
 
 /* bucket assignment functions (Section 3, Figure 3a): the optimised beta_eps of
@@ -103,6 +108,7 @@ typedef struct {
     uint32_t search_schedule;     /* search tuning: 0 auto, 1 one CTA per partition, 2 persistent CTAs taking
                                      partitions from a device work queue; results do not depend on it */
     uint32_t bucket_function;     /* phobic_bucket_function: gamma of the bucket assignment (default 0) */
+    uint32_t compact_columns;     /* PHOBIC_ENC_IC_CR: number of leading Compact columns (clamped to B) */
 } phobic_params;
 
 /* Device time of each build phase (CUDA events recorded on the build stream
@@ -132,7 +138,7 @@ typedef struct {
     uint64_t bits_header, bits_offsets, bits_pilots, bits_remap, bits_total;
     uint64_t device_bytes;  /* device memory owned by the handle */
     uint32_t bucket_function;
-    uint32_t pad;
+    uint32_t compact_columns; /* PHOBIC_ENC_IC_CR: leading Compact columns (min(c, B)) */
 } phobic_info;
 
 /* Fills *p with the defaults: lambda 7, alpha 1, P 2500, IC-C, ADDITIVE,

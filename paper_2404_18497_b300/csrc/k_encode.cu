@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(1024) k_column_unary(const uint32_t* __restric
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t c = blockIdx.x; c < ncols; c += gridDim.x) {
         const ColDesc d = cols[c];
+        if (d.samp_dst_word == ~0ull) continue;  // a Compact column of a mixture
         uint64_t* high = arena + d.hi_dst_word;
         uint64_t* low = arena + d.dst_word;
         uint32_t* samples = reinterpret_cast<uint32_t*>(arena + d.samp_dst_word) + d.samp_base;

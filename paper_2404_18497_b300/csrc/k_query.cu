@@ -100,9 +100,10 @@ __device__ __forceinline__ uint64_t prev_one(const uint64_t* __restrict__ words,
 // Bits of the ones of partitions j - 1 and j in column b's select-sampled
 // unary part (a = hb - 1 for j = 0): from the column's sample for partition
 // 64 floor(j / 64), skipping ones with popcounts.  hb: the column's first bit.
-__device__ __forceinline__ void unary_pair(const QueryView& v, uint32_t b, uint64_t j, uint64_t hb, uint64_t* a_out,
+__device__ __forceinline__ void unary_pair(const QueryView& v, uint32_t sc, uint64_t j, uint64_t hb, uint64_t* a_out,
                                            uint64_t* c_out) {
-    const uint32_t* samples = reinterpret_cast<const uint32_t*>(v.dict_words) + (uint64_t)b * v.rice_ns;
+    // sc: the column's select-sample column (IC-CR: b - mix_c)
+    const uint32_t* samples = reinterpret_cast<const uint32_t*>(v.dict_words) + (uint64_t)sc * v.rice_ns;
     const uint64_t* high = v.rice_high;
     const uint64_t s = hb + __ldg(samples + (j >> 6));  // bit of the one of partition 64 floor(j / 64)
     uint64_t a, c;
@@ -136,7 +137,7 @@ __device__ __forceinline__ uint32_t rice_pilot(const QueryView& v, uint32_t b, u
     const uint64_t m0 = __ldg(v.col_meta + 2 * b), hb = __ldg(v.col_meta + 2 * b + 1);
     const uint32_t l = (uint32_t)(m0 >> 56);
     uint64_t a, c;
-    unary_pair(v, b, j, hb, &a, &c);
+    unary_pair(v, b - v.mix_c, j, hb, &a, &c);
     const uint64_t q = c - a - 1;
     return (uint32_t)((q << l) | read_bits(v.pil_words, (m0 & kMeta) + j * l, l));
 }
@@ -179,6 +180,14 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
         p = rice_pilot(v, b, j);
     } else if (v.encoder == 3) {
         p = ef_column_pilot(v, b, j);
+    } else if (v.encoder == 4) {  // IC-CR: Compact below mix_c, Rice from there on
+        if (b < v.mix_c) {
+            const uint64_t meta = __ldg(v.col_meta + 2 * b);
+            const uint32_t w = (uint32_t)(meta >> 56);
+            p = (uint32_t)read_bits(v.pil_words, (meta & kMeta) + j * w, w);
+        } else {
+            p = rice_pilot(v, b, j);
+        }
     } else if (v.small_bits) {
         const uint32_t jj = (uint32_t)j;
         if (v.encoder == 0) {

@@ -263,7 +263,8 @@ phobic_status check_params(uint64_t n, const phobic_params& p) {
     if (!(p.lambda > 0.0) || !std::isfinite(p.lambda)) return PHOBIC_ERR_INVALID_ARG;
     if (!(p.alpha > 0.0) || p.alpha > 1.0) return PHOBIC_ERR_INVALID_ARG;
     if (p.partition_size == 0 || p.partition_size > kMaxPartitionSize) return PHOBIC_ERR_INVALID_ARG;
-    if (p.encoder > PHOBIC_ENC_IC_EF || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
+    if (p.encoder > PHOBIC_ENC_IC_CR || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
+    if (p.compact_columns >= (1u << 24)) return PHOBIC_ERR_INVALID_ARG;
     if (p.warps_per_partition != 0 && p.warps_per_partition != 1 && p.warps_per_partition != 2 &&
         p.warps_per_partition != 4)
         return PHOBIC_ERR_INVALID_ARG;
@@ -305,6 +306,7 @@ struct SetPlan {
     // arena word offsets and sizes
     uint64_t a_off, n_off, a_meta, n_meta, a_pil, n_pil, a_dict, n_dict, a_low, n_low, a_high, n_high, a_samp,
         n_samp, a_pilots, samp_words;
+    uint32_t mix_c;
     uint32_t ef_l;
     uint64_t bits_header, bits_offsets, bits_pilots, bits_remap, bits_total;
 };
@@ -523,7 +525,8 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     CK(launch_offset_minmax(T, d_od, S, mm, st));
     const bool icr = prm.encoder == PHOBIC_ENC_IC_R;
     const bool icef = prm.encoder == PHOBIC_ENC_IC_EF;
-    const bool unary = icr || icef;  // column layouts with a select-sampled unary part
+    const bool icmix = prm.encoder == PHOBIC_ENC_IC_CR;
+    const bool unary = icr || icef || icmix;  // column layouts with a select-sampled unary part
     uint64_t* colsum = nullptr;
     if (unary) CK(tmp.alloc(&colsum, (size_t)cols_total * 8));
     CK(launch_column_max(pilots, d_cd, (uint32_t)cols_total, colmax, colsum, st));
@@ -567,9 +570,16 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
             const uint64_t U = hK[c] + 1, N = cd[c].count;
             cd[c].width = U >= N ? bitlen64(U / N) - 1 : 0;
         }
-    // ---- IC-R: Rice parameters from the column sums, then the unary lengths
-    if (icr) {
-        for (uint64_t c = 0; c < cols_total; c++) cd[c].width = rice_param(hK[c], cd[c].count);
+    // ---- IC-R (and the Rice columns of IC-CR): Rice parameters from the column
+    // sums, then the unary lengths; IC-CR's Compact columns take the bit length
+    // of their largest pilot
+    if (icr || icmix) {
+        for (uint32_t s = 0; s < S; s++)
+            for (uint32_t b = 0; b < pl[s].B; b++) {
+                const uint64_t c = pl[s].col_base + b;
+                const bool compact = icmix && b < std::min<uint32_t>(prm.compact_columns, pl[s].B);
+                cd[c].width = compact ? bitlen64(hcolmax[c]) : rice_param(hK[c], cd[c].count);
+            }
         uint64_t* dH;
         CK(tmp.alloc(&dH, cols_total * 8));
         CK(h2d(d_cd, cd.data(), cols_total, st));
@@ -595,18 +605,28 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         p.a_meta = aw;
         aw += p.n_meta;
         metas[s].resize(p.n_meta);
-        uint64_t rbase = 0, dbase = 0, bp = 0;
+        uint64_t rbase = 0, dbase = 0, bp = icmix ? 32 : 0;  // IC-CR records its c
         const uint64_t ns = (p.NP + 63) / 64;  // IC-R select samples per column
+        const uint32_t cmix = icmix ? std::min<uint32_t>(prm.compact_columns, p.B) : 0;
         for (uint32_t b = 0; b < p.B; b++) {
             ColDesc& c = cd[p.col_base + b];
             const uint64_t c_id = p.col_base + b;
-            if (unary) {
-                // c.width = Rice parameter / Elias-Fano low bits (set above); dbase counts
-                // unary bits: IC-R N_P + sum (v >> l); IC-EF N_P + (E_last >> l) + 1
-                const uint64_t H = icr ? p.NP + hK[c_id] : p.NP + (hK[c_id] >> c.width) + 1;
+            if (icmix && b < cmix) {
+                // a Compact column of the mixture: values in the shared low array
                 c.base = rbase;
                 c.hi_base = dbase;
-                c.samp_base = (uint64_t)b * ns;
+                c.samp_base = 0;
+                metas[s][2 * b] = rbase | ((uint64_t)c.width << 56);
+                metas[s][2 * b + 1] = dbase;
+                rbase += p.NP * (uint64_t)c.width;
+                bp += p.NP * (uint64_t)c.width + 64 + 8;
+            } else if (unary) {
+                // c.width = Rice parameter / Elias-Fano low bits (set above); dbase counts
+                // unary bits: IC-R N_P + sum (v >> l); IC-EF N_P + (E_last >> l) + 1
+                const uint64_t H = icef ? p.NP + (hK[c_id] >> c.width) + 1 : p.NP + hK[c_id];
+                c.base = rbase;
+                c.hi_base = dbase;
+                c.samp_base = (uint64_t)(b - cmix) * ns;
                 metas[s][2 * b] = rbase | ((uint64_t)c.width << 56);
                 metas[s][2 * b + 1] = dbase;
                 rbase += p.NP * (uint64_t)c.width;
@@ -636,14 +656,15 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         p.n_pil = packed_words(rbase);
         p.a_pil = aw;
         aw += p.n_pil;
-        p.samp_words = unary ? ((uint64_t)p.B * ns + 1) / 2 : 0;
+        p.samp_words = unary ? ((uint64_t)(p.B - cmix) * ns + 1) / 2 : 0;
+        p.mix_c = cmix;
         p.n_dict = icd ? packed_words(dbase) : unary ? p.samp_words + packed_words(dbase) : 0;
         p.a_dict = aw;
         aw += p.n_dict;
         for (uint32_t b = 0; b < p.B; b++) {
             cd[p.col_base + b].dst_word = p.a_pil;
             cd[p.col_base + b].dict_dst_word = p.a_dict;
-            cd[p.col_base + b].samp_dst_word = p.a_dict;
+            cd[p.col_base + b].samp_dst_word = (icmix && b < cmix) ? ~0ull : p.a_dict;
             cd[p.col_base + b].hi_dst_word = p.a_dict + p.samp_words;
         }
         // Elias-Fano remap of slots >= n
@@ -714,7 +735,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     if (!icef)  // IC-C values, IC-D ranks, IC-R low parts
         CK(launch_pack_columns(pilots, d_cd, (uint32_t)cols_total, d_cbeg, col_begin[cols_total], icd, bitmaps,
                                brank, arena, st));
-    if (icr) CK(launch_rice_unary(pilots, d_cd, (uint32_t)cols_total, arena, st));
+    if (icr || icmix) CK(launch_rice_unary(pilots, d_cd, (uint32_t)cols_total, arena, st));
     if (icef) CK(launch_ef_columns(pilots, d_cd, (uint32_t)cols_total, arena, st));
     if (icd) {
         uint64_t* d_bmbeg;
@@ -809,6 +830,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         I.pilot_mode = prm.pilot_mode;
         I.seed = prm.seed;
         I.bucket_function = prm.bucket_function;
+        I.compact_columns = p.mix_c;
         I.max_partition = max_n;
         I.bits_header = p.bits_header;
         I.bits_offsets = p.bits_offsets;
@@ -840,6 +862,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         v.ef_samples = h->ef_samples;
         v.rice_high = unary ? arena + p.a_dict + p.samp_words : nullptr;
         v.rice_ns = unary ? (uint32_t)((p.NP + 63) / 64) : 0;
+        v.mix_c = p.mix_c;
         v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
         v.key_kind = key_kind;
         v.string_seed = prm.seed;
@@ -1160,7 +1183,8 @@ phobic_status phobic_export(const phobic_handle* h, void* h_buf, size_t* len) {
     std::memcpy(&alp, &I.alpha, 8);
     uint64_t hdr[kHeaderWords] = {kMagic, kFormatVersion, I.n, I.M, I.num_partitions, I.num_buckets,
                                   I.partition_size, lam, alp, I.seed,
-                                  (uint64_t)I.encoder | ((uint64_t)I.bucket_function << 32),
+                                  (uint64_t)I.encoder | ((uint64_t)I.bucket_function << 32) |
+                                      ((uint64_t)I.compact_columns << 40),
                                   (uint64_t)I.pilot_mode | ((uint64_t)h->view.key_kind << 32), h->view.off_w,
                                   h->view.off_Q, (uint64_t)h->view.off_dmin, h->view.ef_l};
     for (int i = 0; i < 7; i++) hdr[16 + i] = counts[i];
@@ -1196,7 +1220,8 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     p.partition_size = (uint32_t)P;
     p.seed = w[9];
     p.encoder = (uint32_t)w[10];
-    p.bucket_function = (uint32_t)(w[10] >> 32);
+    p.bucket_function = (uint32_t)((w[10] >> 32) & 0xFF);
+    p.compact_columns = (uint32_t)(w[10] >> 40);
     p.pilot_mode = (uint32_t)w[11];
     const uint32_t key_kind = (uint32_t)(w[11] >> 32);
     if (key_kind > 1) return PHOBIC_ERR_FORMAT;
@@ -1236,10 +1261,13 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     // ones, and each select sample is the position of its 64k-th one, so the
     // query's scans never leave the column
     uint64_t rice_sw = 0;
-    const bool unary_enc = p.encoder == PHOBIC_ENC_IC_R || p.encoder == PHOBIC_ENC_IC_EF;
+    const bool unary_enc =
+        p.encoder == PHOBIC_ENC_IC_R || p.encoder == PHOBIC_ENC_IC_EF || p.encoder == PHOBIC_ENC_IC_CR;
+    const uint64_t cmix = p.encoder == PHOBIC_ENC_IC_CR ? std::min<uint64_t>(p.compact_columns, B) : 0;
+    if (p.encoder == PHOBIC_ENC_IC_CR && p.compact_columns > B) return PHOBIC_ERR_FORMAT;  // exported clamped
     if (unary_enc) {
         const uint64_t ns = (NP + 63) / 64;
-        rice_sw = (B * ns + 1) / 2;
+        rice_sw = ((B - cmix) * ns + 1) / 2;
         if (counts[3] < rice_sw + 1) return PHOBIC_ERR_FORMAT;
         const uint64_t* meta = w + kHeaderWords + counts[0];
         const uint32_t* samp = reinterpret_cast<const uint32_t*>(w + kHeaderWords + counts[0] + counts[1] + counts[2]);
@@ -1247,12 +1275,16 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
         const uint64_t hbits = (counts[3] - rice_sw - 1) * 64;  // the last word is padding
         for (uint64_t b = 0; b < B; b++) {
             const uint64_t hb = meta[2 * b + 1], he = b + 1 < B ? meta[2 * b + 3] : hbits;
+            if (b < cmix) {  // a Compact column of a mixture: no unary bits
+                if ((meta[2 * b] >> 56) > 32 || hb != he) return PHOBIC_ERR_FORMAT;
+                continue;
+            }
             if ((meta[2 * b] >> 56) > 31 || hb > he || he > hbits) return PHOBIC_ERR_FORMAT;
             uint64_t ones = 0;
             for (uint64_t bit = hb; bit < he; bit++) {
                 if (!((high[bit >> 6] >> (bit & 63)) & 1)) continue;
                 if (ones >= NP) return PHOBIC_ERR_FORMAT;
-                if (ones % 64 == 0 && samp[b * ns + ones / 64] != bit - hb) return PHOBIC_ERR_FORMAT;
+                if (ones % 64 == 0 && samp[(b - cmix) * ns + ones / 64] != bit - hb) return PHOBIC_ERR_FORMAT;
                 ones++;
             }
             if (ones != NP) return PHOBIC_ERR_FORMAT;
@@ -1276,6 +1308,7 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     I.pilot_mode = p.pilot_mode;
     I.seed = p.seed;
     I.bucket_function = p.bucket_function;
+    I.compact_columns = (uint32_t)cmix;
     I.bits_header = w[23];
     I.bits_offsets = w[24];
     I.bits_pilots = w[25];
@@ -1341,6 +1374,7 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     v.ef_samples = h->ef_samples;
     v.rice_high = unary_enc ? h->dict_words + rice_sw : nullptr;
     v.rice_ns = unary_enc ? (uint32_t)((NP + 63) / 64) : 0;
+    v.mix_c = (uint32_t)cmix;
     v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
     v.key_kind = key_kind;
     v.string_seed = p.seed;

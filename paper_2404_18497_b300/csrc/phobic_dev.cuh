@@ -106,7 +106,7 @@ __host__ __device__ __forceinline__ uint64_t packed_words(uint64_t nbits) { retu
 struct QueryView {
     uint64_t n, M, NP;
     uint32_t B;
-    uint32_t encoder;    // 0 IC-C, 1 IC-D, 2 IC-R
+    uint32_t encoder;    // 0 IC-C, 1 IC-D, 2 IC-R, 3 IC-EF, 4 IC-CR
     uint32_t pilot_mode; // 0 additive, 1 xor
     uint32_t off_w;
     uint64_t kseed;      // mix64(seed ^ kSeedMix)
@@ -130,6 +130,7 @@ struct QueryView {
     // samples (u32, rice_ns per column), followed by the unary bits at rice_high
     const uint64_t* rice_high;
     uint32_t rice_ns;
+    uint32_t mix_c;       // IC-CR: columns below mix_c are Compact (sample column of b >= mix_c: b - mix_c)
     uint32_t small_bits;  // 1: every packed array has < 2^32 bits (32-bit offsets)
     uint32_t key_kind;    // 0: 64-bit keys, 1: byte strings (XXH64 with string_seed)
     uint64_t string_seed;

@@ -24,10 +24,10 @@ STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "DUP_HASH", 4: "SEARCH_LIMIT",
     5: "PARTITION_TOO_LARGE", 6: "CUDA", 7: "TIMEOUT", 8: "FORMAT",
 }
-ENC_IC_C, ENC_IC_D, ENC_IC_R, ENC_IC_EF = 0, 1, 2, 3
+ENC_IC_C, ENC_IC_D, ENC_IC_R, ENC_IC_EF, ENC_IC_CR = 0, 1, 2, 3, 4
 PILOT_ADDITIVE, PILOT_XOR = 0, 1
-_ENC = {"IC-C": ENC_IC_C, "IC-D": ENC_IC_D, "IC-R": ENC_IC_R, "IC-EF": ENC_IC_EF, ENC_IC_C: ENC_IC_C,
-        ENC_IC_D: ENC_IC_D, ENC_IC_R: ENC_IC_R, ENC_IC_EF: ENC_IC_EF}
+_ENC = {"IC-C": ENC_IC_C, "IC-D": ENC_IC_D, "IC-R": ENC_IC_R, "IC-EF": ENC_IC_EF, "IC-CR": ENC_IC_CR,
+        ENC_IC_C: ENC_IC_C, ENC_IC_D: ENC_IC_D, ENC_IC_R: ENC_IC_R, ENC_IC_EF: ENC_IC_EF, ENC_IC_CR: ENC_IC_CR}
 _MODE = {"additive": PILOT_ADDITIVE, "xor": PILOT_XOR, PILOT_ADDITIVE: PILOT_ADDITIVE, PILOT_XOR: PILOT_XOR}
 
 
@@ -53,6 +53,7 @@ class phobic_params(ctypes.Structure):
         ("candidate_width", ctypes.c_uint32),
         ("search_schedule", ctypes.c_uint32),
         ("bucket_function", ctypes.c_uint32),
+        ("compact_columns", ctypes.c_uint32),
     ]
 
 
@@ -71,7 +72,7 @@ class phobic_info(ctypes.Structure):
         ("max_partition", ctypes.c_uint64),
         ("bits_header", ctypes.c_uint64), ("bits_offsets", ctypes.c_uint64), ("bits_pilots", ctypes.c_uint64),
         ("bits_remap", ctypes.c_uint64), ("bits_total", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-        ("bucket_function", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+        ("bucket_function", ctypes.c_uint32), ("compact_columns", ctypes.c_uint32),
     ]
 
 
@@ -207,7 +208,7 @@ def _dev_u64(t: torch.Tensor, what: str) -> torch.Tensor:
 
 def make_params(lam=7.0, alpha=1.0, P=2500, seed=0, encoder="IC-C", mode="additive", s_max=0,
                 keep_pilots=False, warps_per_partition=0, record_timings=False,
-                candidate_width=0, search_schedule=0, bucket_function=0) -> phobic_params:
+                candidate_width=0, search_schedule=0, bucket_function=0, compact_columns=0) -> phobic_params:
     p = phobic_params()
     lib().phobic_params_init(ctypes.byref(p))
     p.lambda_ = float(lam)
@@ -224,6 +225,7 @@ def make_params(lam=7.0, alpha=1.0, P=2500, seed=0, encoder="IC-C", mode="additi
     p.candidate_width = int(candidate_width)
     p.search_schedule = int(search_schedule)
     p.bucket_function = int(bucket_function)
+    p.compact_columns = int(compact_columns)
     return p
 
 
@@ -622,7 +624,8 @@ def parse_export(data: bytes) -> dict:
     hdr = {k: int(w[i]) for i, k in enumerate(HEADER_FIELDS)}
     hdr["key_kind"] = hdr["pilot_mode"] >> 32
     hdr["pilot_mode"] &= 0xFFFFFFFF
-    hdr["bucket_function"] = hdr["encoder"] >> 32
+    hdr["bucket_function"] = (hdr["encoder"] >> 32) & 0xFF
+    hdr["compact_columns"] = hdr["encoder"] >> 40
     hdr["encoder"] &= 0xFFFFFFFF
     hdr["off_dmin"] = int(np.uint64(hdr["off_dmin"]).astype(np.int64))
     at = len(HEADER_FIELDS)
@@ -630,11 +633,13 @@ def parse_export(data: bytes) -> dict:
         c = hdr["n_" + name]
         hdr[name] = w[at: at + c].copy()
         at += c
-    if hdr["encoder"] in (ENC_IC_R, ENC_IC_EF):
-        # the dictionary array holds the u32 select samples, then the unary bits
+    if hdr["encoder"] in (ENC_IC_R, ENC_IC_EF, ENC_IC_CR):
+        # the dictionary array holds the u32 select samples (of the Rice columns),
+        # then the unary bits
         ns = (hdr["NP"] + 63) // 64
-        sw = (hdr["B"] * ns + 1) // 2
+        cols = hdr["B"] - (hdr["compact_columns"] if hdr["encoder"] == ENC_IC_CR else 0)
+        sw = (cols * ns + 1) // 2
         d = hdr["dict_words"]
-        hdr["rice_samples"] = d[:sw].view(np.uint32)[: hdr["B"] * ns].copy()
+        hdr["rice_samples"] = d[:sw].view(np.uint32)[: cols * ns].copy()
         hdr["rice_high"] = d[sw:].copy()
     return hdr

@@ -48,7 +48,7 @@ def compare_structure(ph, orc_h, h, encoder):
         assert ((meta >> np.uint64(56)).astype(np.uint32) == o.array("col_w")).all()
         assert ((meta & mask) == o.array("col_base")).all()
         assert (ex["pil_words"] == o.array("pil_words")).all()
-    elif encoder in (2, 3):
+    elif encoder in (2, 3, 4):
         assert ((meta[0::2] >> np.uint64(56)).astype(np.uint32) == o.array("col_l")).all()
         assert ((meta[0::2] & mask) == o.array("col_lbase")).all()
         assert (meta[1::2] == o.array("col_hbase")).all()
@@ -184,6 +184,26 @@ def test_ablation_bucket_functions_parity(ph, orc, fn, alpha, enc):
     h2 = ph.phobic_import(ph.phobic_export(h))
     assert h2.info()["bucket_function"] == fn
     assert torch.equal(h2.query(_dev(keys)), h.query(_dev(keys)))
+
+
+@pytest.mark.parametrize("c", [0, 6, 40, 358, 400])
+def test_compact_rice_mixture_parity(ph, orc, c):
+    """Section 4.1's mixture (the first c columns Compact, the rest Golomb-Rice):
+    bit-exact structure and queries for c from 0 (IC-R) to past B (IC-C), with
+    alpha < 1 and both pilot modes, through export and import."""
+    keys = _keys(400_000, 90 + c)
+    for mode, alpha in [(0, 0.99), (1, 1.0)]:
+        o = orc.Oracle(keys, lam=7.0, alpha=alpha, P=2500, encoder=4, mode=mode, compact_columns=c, threads=0)
+        h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, alpha, 2500, encoder=4, mode=mode,
+                                                          compact_columns=c, keep_pilots=True))
+        assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots)
+        compare_structure(ph, o, h, 4)
+        assert h.bits_per_key() == o.bits_per_key()
+        assert h.info()["compact_columns"] == min(c, 358)
+        assert np.array_equal(_host(h.query(_dev(keys))), o.query(keys))
+        h2 = ph.phobic_import(ph.phobic_export(h))
+        assert torch.equal(h2.query(_dev(keys)), h.query(_dev(keys)))
+        h.free()
 
 
 def test_query_unaligned_and_odd_lengths(ph, orc):
