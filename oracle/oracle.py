@@ -19,6 +19,8 @@ _SO = os.path.join(_HERE, "liboracle.so")
 
 OK, INVALID_ARG, OOM, DUP_HASH, SEARCH_LIMIT = 0, 1, 2, 3, 4
 ENC_IC_C, ENC_IC_D, ENC_IC_R, ENC_IC_EF, ENC_IC_CR = 0, 1, 2, 3, 4
+# mono-X: encoder X over one column holding all pilots in column order
+ENC_MONO_C, ENC_MONO_D, ENC_MONO_R, ENC_MONO_EF = 5, 6, 7, 8
 PILOT_ADDITIVE, PILOT_XOR = 0, 1
 
 

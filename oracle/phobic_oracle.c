@@ -352,7 +352,7 @@ static int check_params(uint64_t n, const or_params* p) {
     if (!(p->lambda > 0.0) || !isfinite(p->lambda)) return OR_ERR_INVALID_ARG;
     if (!(p->alpha > 0.0) || p->alpha > 1.0) return OR_ERR_INVALID_ARG;
     if (p->partition_size == 0) return OR_ERR_INVALID_ARG;
-    if (p->encoder > OR_ENC_IC_CR || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
+    if (p->encoder > OR_ENC_MONO_EF || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
     if (p->bucket_fn > OR_BUCKET_UNIFORM) return OR_ERR_INVALID_ARG;
     return OR_OK;
 }
@@ -876,18 +876,27 @@ static uint32_t decode_ef_column(const or_mphf* h, uint32_t b, uint64_t j) {
     return (uint32_t)(j == 0 ? e : e - ef_prefix(h, b, j - 1));
 }
 
-static uint32_t decode_pilot(const or_mphf* h, uint32_t b, uint64_t j) {
-    if (h->prm.encoder == OR_ENC_IC_C)
+static uint32_t decode_column(const or_mphf* h, uint32_t enc, uint32_t b, uint64_t j) {
+    if (enc == OR_ENC_IC_C)
         return (uint32_t)get_bits(h->pil_words, h->col_base[b] + j * h->col_w[b], h->col_w[b]);
-    if (h->prm.encoder == OR_ENC_IC_R) return decode_rice(h, b, j);
-    if (h->prm.encoder == OR_ENC_IC_EF) return decode_ef_column(h, b, j);
-    if (h->prm.encoder == OR_ENC_IC_CR) {
+    if (enc == OR_ENC_IC_R) return decode_rice(h, b, j);
+    if (enc == OR_ENC_IC_EF) return decode_ef_column(h, b, j);
+    if (enc == OR_ENC_IC_CR) {
         uint32_t c = h->prm.compact_columns < h->B ? h->prm.compact_columns : h->B;
         if (b < c) return (uint32_t)get_bits(h->rice_low, h->col_lbase[b] + j * h->col_l[b], h->col_l[b]);
         return decode_rice(h, b, j);
     }
     uint64_t r = get_bits(h->rank_words, h->col_rbase[b] + j * h->col_rw[b], h->col_rw[b]);
     return (uint32_t)get_bits(h->dict_words, h->col_dbase[b] + r * h->col_dw[b], h->col_dw[b]);
+}
+
+/* a mono encoder is its column encoder over the single column of all pilots:
+ * pilot (b, j) is value b N_P + j of column 0 (column 0 decodes the same whatever
+ * N_P is, as only the column index scales by it) */
+static uint32_t decode_pilot(const or_mphf* h, uint32_t b, uint64_t j) {
+    if (h->prm.encoder >= OR_ENC_MONO_C)
+        return decode_column(h, h->prm.encoder - OR_ENC_MONO_C, 0, (uint64_t)b * h->NP + j);
+    return decode_column(h, h->prm.encoder, b, j);
 }
 
 /* ---- Section 5 (PTHash non-minimal trick): slots q in [n, M) are remapped
@@ -953,19 +962,24 @@ static void account_bits(or_mphf* h) {
     uint64_t NP = h->NP;
     h->bits_header = 9 * 64;
     h->bits_offsets = (NP + 1) * (uint64_t)h->off_w + 64 + 64 + 8;
+    /* a mono encoder: one column of B N_P values */
+    int mono = h->prm.encoder >= OR_ENC_MONO_C;
+    uint32_t enc = mono ? h->prm.encoder - OR_ENC_MONO_C : h->prm.encoder;
+    uint32_t ncol = mono ? 1 : h->B;
+    uint64_t nv = mono ? (uint64_t)h->B * NP : NP;
     uint64_t bp = 0;
-    for (uint32_t b = 0; b < h->B; b++) {
-        if (h->prm.encoder == OR_ENC_IC_C)
-            bp += NP * (uint64_t)h->col_w[b] + 64 + 8;
-        else if (h->prm.encoder == OR_ENC_IC_R || h->prm.encoder == OR_ENC_IC_EF ||
-                 (h->prm.encoder == OR_ENC_IC_CR && b >= h->prm.compact_columns))
-            bp += NP * (uint64_t)h->col_l[b] + h->col_H[b] + 32 * ((NP + 63) / 64) + 64 + 64 + 8;
-        else if (h->prm.encoder == OR_ENC_IC_CR)
-            bp += NP * (uint64_t)h->col_l[b] + 64 + 8; /* a Compact column of the mixture */
+    for (uint32_t b = 0; b < ncol; b++) {
+        if (enc == OR_ENC_IC_C)
+            bp += nv * (uint64_t)h->col_w[b] + 64 + 8;
+        else if (enc == OR_ENC_IC_R || enc == OR_ENC_IC_EF ||
+                 (enc == OR_ENC_IC_CR && b >= h->prm.compact_columns))
+            bp += nv * (uint64_t)h->col_l[b] + h->col_H[b] + 32 * ((nv + 63) / 64) + 64 + 64 + 8;
+        else if (enc == OR_ENC_IC_CR)
+            bp += nv * (uint64_t)h->col_l[b] + 64 + 8; /* a Compact column of the mixture */
         else
-            bp += NP * (uint64_t)h->col_rw[b] + h->col_K[b] * (uint64_t)h->col_dw[b] + 64 + 64 + 8 + 8;
+            bp += nv * (uint64_t)h->col_rw[b] + h->col_K[b] * (uint64_t)h->col_dw[b] + 64 + 64 + 8 + 8;
     }
-    if (h->prm.encoder == OR_ENC_IC_CR) bp += 32; /* the number of Compact columns */
+    if (enc == OR_ENC_IC_CR) bp += 32; /* the number of Compact columns */
     h->bits_pilots = bp;
     h->bits_remap = 0;
     if (h->ef_N)
@@ -1083,16 +1097,28 @@ int or_build_hashed(const uint64_t* hk, uint64_t n, const or_params* prm, int th
         return status;
     }
     encode_offsets(h);
-    if (prm->encoder == OR_ENC_IC_C)
+    /* a mono encoder runs its column encoder over one column of B N_P values: the
+     * column-major pilot array is that column, so B and N_P are swapped meanwhile */
+    int mono = prm->encoder >= OR_ENC_MONO_C;
+    uint32_t enc = mono ? prm->encoder - OR_ENC_MONO_C : prm->encoder;
+    uint32_t B_saved = h->B;
+    uint64_t NP_saved = h->NP;
+    if (mono) {
+        h->NP = (uint64_t)h->B * h->NP;
+        h->B = 1;
+    }
+    if (enc == OR_ENC_IC_C)
         encode_compact(h);
-    else if (prm->encoder == OR_ENC_IC_R)
+    else if (enc == OR_ENC_IC_R)
         encode_rice(h);
-    else if (prm->encoder == OR_ENC_IC_EF)
+    else if (enc == OR_ENC_IC_EF)
         encode_ef_columns(h);
-    else if (prm->encoder == OR_ENC_IC_CR)
+    else if (enc == OR_ENC_IC_CR)
         encode_mixture(h);
     else
         encode_dictionary(h);
+    h->B = B_saved;
+    h->NP = NP_saved;
     build_remap(h, taken_global);
     free(taken_global);
     account_bits(h);
@@ -1163,24 +1189,26 @@ const void* or_get_array(const or_mphf* h, const char* name, uint64_t* count, ui
     A(T, h->NP + 1, 8);
     A(pilots, (uint64_t)h->B * h->NP, 4);
     A(off_words, packed_words(h->off_nbits), 8);
-    if (h->prm.encoder == OR_ENC_IC_C) {
-        A(col_w, h->B, 4);
-        A(col_base, h->B, 8);
+    uint32_t enc = h->prm.encoder >= OR_ENC_MONO_C ? h->prm.encoder - OR_ENC_MONO_C : h->prm.encoder;
+    uint64_t nc = h->prm.encoder >= OR_ENC_MONO_C ? 1 : h->B; /* a mono encoder has one column */
+    if (enc == OR_ENC_IC_C) {
+        A(col_w, nc, 4);
+        A(col_base, nc, 8);
         A(pil_words, packed_words(h->pil_nbits), 8);
-    } else if (h->prm.encoder >= OR_ENC_IC_R) {
-        A(col_l, h->B, 4);
-        A(col_lbase, h->B, 8);
-        A(col_hbase, h->B, 8);
-        A(col_H, h->B, 8);
+    } else if (enc >= OR_ENC_IC_R) {
+        A(col_l, nc, 4);
+        A(col_lbase, nc, 8);
+        A(col_hbase, nc, 8);
+        A(col_H, nc, 8);
         A(rice_low, packed_words(h->rlow_nbits), 8);
         A(rice_high, packed_words(h->rhigh_nbits), 8);
         A(rice_samples, h->rsamp_count, 4);
     } else {
-        A(col_rw, h->B, 4);
-        A(col_rbase, h->B, 8);
-        A(col_dw, h->B, 4);
-        A(col_dbase, h->B, 8);
-        A(col_K, h->B, 8);
+        A(col_rw, nc, 4);
+        A(col_rbase, nc, 8);
+        A(col_dw, nc, 4);
+        A(col_dbase, nc, 8);
+        A(col_K, nc, 8);
         A(rank_words, packed_words(h->rank_nbits), 8);
         A(dict_words, packed_words(h->dict_nbits), 8);
     }

@@ -32,6 +32,12 @@ extern "C" {
 #define OR_ENC_IC_R 2
 #define OR_ENC_IC_EF 3
 #define OR_ENC_IC_CR 4 /* mixture: the first compact_columns columns Compact, the rest Golomb-Rice */
+/* mono-X: encoder X (C, D, R, EF) applied to ONE column holding all B N_P pilots
+ * in column order (value i = b N_P + j); the comparison of Section 5, Figure 3b */
+#define OR_ENC_MONO_C 5
+#define OR_ENC_MONO_D 6
+#define OR_ENC_MONO_R 7
+#define OR_ENC_MONO_EF 8
 
 /* bucket assignment functions (Figure 3a): the optimised beta_eps (Theorem 2),
  * beta_* (eps = 0), PTHash's skewed split (60 % of the keys into 30 % of the

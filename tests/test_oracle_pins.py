@@ -290,7 +290,7 @@ def test_every_pilot_is_the_first_valid(orc, mode, lam, alpha, P, n):
     assert h.verify_first_valid(hk)
 
 
-@pytest.mark.parametrize("enc", [0, 1, 2, 3])
+@pytest.mark.parametrize("enc", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("alpha", [1.0, 0.99, 0.9])
 def test_query_is_bijection(orc, enc, mode, alpha):
@@ -511,6 +511,87 @@ def test_compact_rice_mixture(orc):
     q = h.query(keys)
     assert np.unique(q).size == keys.size and q.max() < keys.size
     assert c0.bits_per_key() <= h.bits_per_key() <= cB.bits_per_key()
+
+
+def _unary_ones(words, H):
+    return np.flatnonzero(np.unpackbits(words.view(np.uint8), bitorder="little")[:H])
+
+
+def test_mono_encoders(orc):
+    """Section 5, Figure 3b: a mono encoder places all seeds in ONE encoder, here
+    the column encoder over the B N_P pilots in column order (value i = b N_P + j).
+    An independent numpy reader decodes each of mono-C/D/R/EF from its arrays,
+    with the parameters the encoder definitions fix (width of the global maximum,
+    one dictionary of the distinct values, one Rice parameter from the total, one
+    Elias-Fano universe from the total), and recounts the space."""
+    rng = np.random.default_rng(27)
+    keys = rng.integers(0, 2**64, size=60_000, dtype=np.uint64)
+    kw = dict(lam=7.0, alpha=0.99, P=800, threads=4)
+    for enc in (orc.ENC_MONO_C, orc.ENC_MONO_D, orc.ENC_MONO_R, orc.ENC_MONO_EF):
+        h = orc.Oracle(keys, encoder=enc, **kw)
+        v = h.pilots.astype(np.int64).ravel()  # (B, N_P) row-major = column order
+        N = v.size
+        if enc == orc.ENC_MONO_C:
+            w = int(v.max()).bit_length()
+            assert h.array("col_w").tolist() == [w] and h.array("col_base").tolist() == [0]
+            got = np.array([_bits(h.array("pil_words"), i * w, w) for i in range(N)])
+            bits = N * w + 72
+        elif enc == orc.ENC_MONO_D:
+            d = np.unique(v)
+            rw, dw = int(d.size - 1).bit_length(), int(d[-1]).bit_length()
+            assert h.array("col_K").tolist() == [d.size]
+            assert h.array("col_rw").tolist() == [rw] and h.array("col_dw").tolist() == [dw]
+            dv = np.array([_bits(h.array("dict_words"), r * dw, dw) for r in range(d.size)])
+            assert np.array_equal(dv, d)
+            got = dv[[_bits(h.array("rank_words"), i * rw, rw) for i in range(N)]]
+            bits = N * rw + d.size * dw + 144  # two 64-bit bases, two 8-bit widths
+        else:
+            l = int(h.array("col_l")[0])
+            H = int(h.array("col_H")[0])
+            ones = _unary_ones(h.array("rice_high"), H)
+            assert ones.size == N and h.array("col_hbase").tolist() == [0]
+            lo = np.array([_bits(h.array("rice_low"), i * l, l) for i in range(N)], dtype=np.int64)
+            if enc == orc.ENC_MONO_R:
+                assert l == orc.lib().or_rice_param(int(v.sum()), N)
+                assert H == N + int((v >> l).sum())
+                q = np.diff(np.concatenate([[-1], ones])) - 1
+                got = (q << l) | lo
+            else:
+                E = np.cumsum(v)
+                U = int(E[-1]) + 1
+                assert l == ((U // N).bit_length() - 1 if U >= N else 0)
+                assert H == N + (int(E[-1]) >> l) + 1
+                got = np.diff(np.concatenate([[0], ((ones - np.arange(N)) << l) | lo]))
+            assert np.array_equal(h.array("rice_samples"), ones[::64])
+            bits = N * l + H + 32 * ((N + 63) // 64) + 136
+        assert np.array_equal(got, v), enc
+        assert h.u64("bits_pilots") == bits, enc
+        q = h.query(keys)
+        assert np.unique(q).size == keys.size and q.max() < keys.size
+
+
+def test_mono_against_interleaved(orc):
+    """Section 5: interleaving helps every encoder but the dictionary, whose
+    single table beats one table per column (Figure 3b: mono-D below IC-D); for
+    Rice and Elias-Fano the gain is per-column parameters, for Compact per-column
+    widths.  The mono encoders' space lies in the band of Figure 3b where it does
+    not depend on n (Rice and Elias-Fano: one parameter from the mean)."""
+    with open(os.path.join(GOLDEN, "paper_bands.json")) as f:
+        bands = json.load(f)
+    rng = np.random.default_rng(25)
+    keys = rng.integers(0, 2**64, size=1_000_000, dtype=np.uint64)
+    bpk = {}
+    for name, enc in (("IC-C", orc.ENC_IC_C), ("IC-D", orc.ENC_IC_D), ("IC-R", orc.ENC_IC_R),
+                      ("IC-EF", orc.ENC_IC_EF), ("mono-C", orc.ENC_MONO_C), ("mono-D", orc.ENC_MONO_D),
+                      ("mono-R", orc.ENC_MONO_R), ("mono-EF", orc.ENC_MONO_EF)):
+        bpk[name] = orc.Oracle(keys, lam=8.0, P=2500, encoder=enc, threads=8).bits_per_key()
+    assert bpk["IC-C"] < bpk["mono-C"]
+    assert bpk["mono-D"] < bpk["IC-D"]
+    assert bpk["IC-R"] < bpk["mono-R"]
+    assert bpk["IC-R"] < bpk["IC-EF"] and bpk["mono-R"] < bpk["mono-EF"]
+    for name in ("mono-R", "mono-EF"):
+        ref = bands["fig3b_lambda8"][name]["bits_per_key"]
+        assert abs(bpk[name] - ref) < bands["band"], (name, bpk[name], ref)
 
 
 def test_offsets_are_differences_to_expectation(orc):
