@@ -620,8 +620,9 @@ def run_lambda_sweep(a, phobic, workloads, torch):
 # ---------------------------------------------------------------- encoders ---
 def run_encoders(a, phobic, workloads, torch):
     """Figure 3b's comparison on this GPU: space and query rate of every pilot
-    encoder, and of Compact/Rice mixtures with c leading Compact columns (lambda 8,
-    alpha 1, P 2500, 1e8 keys, every key queried in random order)."""
+    encoder, interleaved and mono (all pilots in one encoder), and of Compact/Rice
+    mixtures with c leading Compact columns (lambda 8, alpha 1, P 2500, 1e8 keys,
+    every key queried in random order)."""
     stream = torch.cuda.current_stream()
     n = 100_000_000
     keys = workloads.stream_keys_torch(0, n, 37, "cuda")
@@ -631,7 +632,8 @@ def run_encoders(a, phobic, workloads, torch):
     out = torch.empty_like(qkeys)
     rows = []
     configs = [("IC-C", 0, 0), ("IC-D", 1, 0), ("IC-EF", 3, 0), ("IC-R", 2, 0)] + [
-        (f"IC-CR c={c}", 4, c) for c in (8, 32, 80, 160)]
+        (f"IC-CR c={c}", 4, c) for c in (8, 32, 80, 160)] + [
+        ("mono-C", 5, 0), ("mono-D", 6, 0), ("mono-EF", 8, 0), ("mono-R", 7, 0)]
     for name, enc, c in configs:
         prm = phobic.make_params(8.0, 1.0, 2500, encoder=enc, compact_columns=c, record_timings=True)
         h = phobic.phobic_build_ex(keys, prm, stream)
@@ -653,7 +655,8 @@ def run_encoders(a, phobic, workloads, torch):
     return {"workload": "pilot encoders (Fig. 3b): 1e8 distinct uniform uint64 keys (counter-based stream), lambda=8, "
                         "alpha=1, partition size 2500; every key queried once in a random order",
             "rows": rows,
-            "paper_context": "Fig. 3b (CPU queries, 1e8 strings): IC-C 2.208 b/k, IC-D 2.599, IC-EF 1.824, IC-R 1.775"}
+            "paper_context": "Fig. 3b (CPU queries, 1e8 strings): IC-C 2.208 b/k, IC-D 2.599, IC-EF 1.824, IC-R 1.775; "
+                             "mono-C 3.012, mono-D 2.163, mono-EF 1.909, mono-R 1.862"}
 
 
 # ------------------------------------------------------- bucket functions ---

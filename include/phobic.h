@@ -59,11 +59,23 @@ typedef enum {
     PHOBIC_ENC_IC_EF = 3, /* interleaved Elias-Fano: per column, the prefix sums E_j of its pilots with
                             l = floor(log2((E_last + 1) / N_P)) low bits packed, bit j + (E_j >> l) set in the
                             high part, a select sample every 64 partitions; the same export layout as IC-R */
-    PHOBIC_ENC_IC_CR = 4  /* Section 4.1's mixture: the first c = min(compact_columns, B) columns (the largest
+    PHOBIC_ENC_IC_CR = 4, /* Section 4.1's mixture: the first c = min(compact_columns, B) columns (the largest
                              buckets) Compact, the others Golomb-Rice as IC-R.  The Compact values and Rice low
                              parts share the low array; col_meta[2b] = base | width << 56 for every column,
                              col_meta[2b+1] = unary base; select samples for columns b >= c only (sample
                              column b - c).  c is exported in bits 40..63 of the encoder header word */
+    /* The "mono" encoders of the comparison in Section 5 (Figure 3b): ALL pilots in
+     * one encoder, namely the column encoder above applied to a single column that
+     * holds the B N_P pilots in column order (pilot of bucket b, partition j is value
+     * b N_P + j).  One Compact width, one dictionary, one Rice parameter or one
+     * Elias-Fano universe for the whole structure; the export layout is that of the
+     * column encoder with one column (1 or 2 metadata words).  mono-R and mono-EF keep
+     * 32-bit select samples, so their unary part must stay below 2^32 bits (about
+     * 2 n / lambda bits): a larger build returns PHOBIC_ERR_INVALID_ARG. */
+    PHOBIC_ENC_MONO_C = 5,
+    PHOBIC_ENC_MONO_D = 6,
+    PHOBIC_ENC_MONO_R = 7,
+    PHOBIC_ENC_MONO_EF = 8
 } phobic_encoder;
 
 /* bucket assignment functions (Section 3, Figure 3a): the optimised beta_eps of

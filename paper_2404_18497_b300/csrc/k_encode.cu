@@ -194,7 +194,10 @@ __global__ void __launch_bounds__(256) k_rice_unary_len(const uint32_t* __restri
 //   value j writes the low l bits of E_j at bit base + j l of the low array and
 //   sets bit j + (E_j >> l) of the high bits.
 // Bits go in with atomicOr (neighbours share words); every 64th set bit's
-// position becomes a select sample.
+// position becomes a select sample.  A mono encoder's column continues its
+// set's single sequence from value index idx0 with the scan carried in at sum0,
+// so value i = idx0 + j sets bit i + (sum0 + incl) (Rice) or i + ((sum0 + incl)
+// >> l) (Elias-Fano), and samples go by the global index i.
 template <bool kEF>
 __global__ void __launch_bounds__(1024) k_column_unary(const uint32_t* __restrict__ pilots,
                                                        const ColDesc* __restrict__ cols, uint32_t ncols,
@@ -235,10 +238,11 @@ __global__ void __launch_bounds__(1024) k_column_unary(const uint32_t* __restric
             __syncthreads();
             const unsigned long long carry = carry_s;
             if (j < d.count) {
-                const uint64_t incl = carry + warp_sums[warp] + x;  // inclusive sum
+                const uint64_t incl = d.sum0 + carry + warp_sums[warp] + x;  // inclusive sum
+                const uint64_t i = d.idx0 + j;
                 uint64_t pos;
                 if (kEF) {
-                    pos = j + (incl >> d.width);
+                    pos = i + (incl >> d.width);
                     if (d.width) {
                         const uint64_t lv = incl & ((1ull << d.width) - 1);
                         const uint64_t o = d.base + j * d.width;
@@ -248,11 +252,11 @@ __global__ void __launch_bounds__(1024) k_column_unary(const uint32_t* __restric
                             atomicOr((unsigned long long*)(low + (o >> 6) + 1), (unsigned long long)(lv >> (64 - sh)));
                     }
                 } else {
-                    pos = j + incl;
+                    pos = i + incl;
                 }
                 const uint64_t bit = d.hi_base + pos;
                 atomicOr((unsigned long long*)(high + (bit >> 6)), 1ull << (bit & 63));
-                if ((j & 63) == 0) samples[j >> 6] = (uint32_t)pos;
+                if ((i & 63) == 0) samples[i >> 6] = (uint32_t)pos;
             }
             __syncthreads();
             if (tid == 1023) carry_s = carry + warp_sums[31] + x;

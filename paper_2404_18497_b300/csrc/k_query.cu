@@ -164,23 +164,30 @@ __device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key, 
 }
 
 __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds) {
-    const uint64_t j = partition_of(hk, v.NP);
+    const uint64_t jp = partition_of(hk, v.NP);
     uint64_t Tj, Tj1;
     if (v.off_w <= 31) {
-        offsets_of(v, j, &Tj, &Tj1);
+        offsets_of(v, jp, &Tj, &Tj1);
     } else {
-        Tj = offset_of(v, j);
-        Tj1 = offset_of(v, j + 1);
+        Tj = offset_of(v, jp);
+        Tj1 = offset_of(v, jp + 1);
     }
     const uint32_t m = (uint32_t)(Tj1 - Tj);
     if (m == 0) return 0;  // only a key outside the set can land in an empty partition
-    const uint32_t b = bucket_of(bucket_hash(hk), v.table, v.B);
+    uint32_t b = bucket_of(bucket_hash(hk), v.table, v.B);
+    uint32_t enc = v.encoder;
+    uint64_t j = jp;
+    if (enc >= 5) {  // a mono encoder: value b N_P + j of its single column
+        enc -= 5;
+        j += (uint64_t)b * v.NP;
+        b = 0;
+    }
     uint32_t p;
-    if (v.encoder == 2) {
+    if (enc == 2) {
         p = rice_pilot(v, b, j);
-    } else if (v.encoder == 3) {
+    } else if (enc == 3) {
         p = ef_column_pilot(v, b, j);
-    } else if (v.encoder == 4) {  // IC-CR: Compact below mix_c, Rice from there on
+    } else if (enc == 4) {  // IC-CR: Compact below mix_c, Rice from there on
         if (b < v.mix_c) {
             const uint64_t meta = __ldg(v.col_meta + 2 * b);
             const uint32_t w = (uint32_t)(meta >> 56);
@@ -190,7 +197,7 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
         }
     } else if (v.small_bits) {
         const uint32_t jj = (uint32_t)j;
-        if (v.encoder == 0) {
+        if (enc == 0) {
             const uint64_t meta = __ldg(v.col_meta + b);
             const uint32_t w = (uint32_t)(meta >> 56);
             p = read_bits32(v.pil_words, (uint32_t)meta + jj * w, w);
@@ -200,7 +207,7 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
             const uint32_t r = read_bits32(v.pil_words, (uint32_t)rm + jj * rw, rw);
             p = read_bits32(v.dict_words, (uint32_t)dm + r * dw, dw);
         }
-    } else if (v.encoder == 0) {
+    } else if (enc == 0) {
         uint64_t meta = __ldg(v.col_meta + b);
         uint32_t w = (uint32_t)(meta >> 56);
         p = (uint32_t)read_bits(v.pil_words, (meta & kMeta) + j * w, w);

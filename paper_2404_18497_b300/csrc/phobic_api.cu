@@ -263,7 +263,7 @@ phobic_status check_params(uint64_t n, const phobic_params& p) {
     if (!(p.lambda > 0.0) || !std::isfinite(p.lambda)) return PHOBIC_ERR_INVALID_ARG;
     if (!(p.alpha > 0.0) || p.alpha > 1.0) return PHOBIC_ERR_INVALID_ARG;
     if (p.partition_size == 0 || p.partition_size > kMaxPartitionSize) return PHOBIC_ERR_INVALID_ARG;
-    if (p.encoder > PHOBIC_ENC_IC_CR || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
+    if (p.encoder > PHOBIC_ENC_MONO_EF || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
     if (p.compact_columns >= (1u << 24)) return PHOBIC_ERR_INVALID_ARG;
     if (p.warps_per_partition != 0 && p.warps_per_partition != 1 && p.warps_per_partition != 2 &&
         p.warps_per_partition != 4)
@@ -523,9 +523,14 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     CK(h2d(d_cd, cd.data(), cols_total, st));
     CK(ev.mark(5, st));
     CK(launch_offset_minmax(T, d_od, S, mm, st));
-    const bool icr = prm.encoder == PHOBIC_ENC_IC_R;
-    const bool icef = prm.encoder == PHOBIC_ENC_IC_EF;
-    const bool icmix = prm.encoder == PHOBIC_ENC_IC_CR;
+    // a mono encoder runs its column encoder over one column per set: the set's
+    // physical columns keep their work items and continue one sequence
+    const bool mono = prm.encoder >= PHOBIC_ENC_MONO_C;
+    const uint32_t enc = mono ? prm.encoder - PHOBIC_ENC_MONO_C : prm.encoder;
+    const bool icr = enc == PHOBIC_ENC_IC_R;
+    const bool icef = enc == PHOBIC_ENC_IC_EF;
+    const bool icmix = enc == PHOBIC_ENC_IC_CR;
+    const bool icd = enc == PHOBIC_ENC_IC_D;
     const bool unary = icr || icef || icmix;  // column layouts with a select-sampled unary part
     uint64_t* colsum = nullptr;
     if (unary) CK(tmp.alloc(&colsum, (size_t)cols_total * 8));
@@ -543,42 +548,84 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         default: return PHOBIC_ERR_TIMEOUT;
     }
 
-    // ---- IC-D: presence bitmaps, ranks, dictionary sizes
+    // largest pilot and (Rice, Elias-Fano) pilot sum of each set, for the mono encoders
+    std::vector<uint32_t> set_max(S, 0);
+    std::vector<uint64_t> set_sum(S, 0);
+    if (mono)
+        for (uint32_t s = 0; s < S; s++)
+            for (uint32_t b = 0; b < pl[s].B; b++) {
+                set_max[s] = std::max(set_max[s], hcolmax[pl[s].col_base + b]);
+                if (unary) set_sum[s] += hK[pl[s].col_base + b];
+            }
+
+    // ---- IC-D: presence bitmaps, ranks, dictionary sizes; one dictionary per
+    // column, or (mono-D) one per set whose bitmap all the set's columns mark
     uint64_t *bitmaps = nullptr, *brank = nullptr;
-    std::vector<uint64_t> bm_begin(cols_total + 1, 0);
-    if (prm.encoder == PHOBIC_ENC_IC_D) {
-        for (uint64_t c = 0; c < cols_total; c++) {
-            cd[c].bm_base = bm_begin[c];
-            cd[c].bm_words = ((uint64_t)hcolmax[c] + 64) / 64;
-            bm_begin[c + 1] = bm_begin[c] + cd[c].bm_words;
+    const uint64_t ndict = icd ? (mono ? S : cols_total) : 0;
+    std::vector<uint64_t> bm_begin(ndict + 1, 0);
+    std::vector<ColDesc> dd(mono && icd ? S : 0);
+    ColDesc* d_dd = nullptr;
+    if (icd) {
+        if (mono) {
+            for (uint32_t s = 0; s < S; s++) {
+                std::memset(&dd[s], 0, sizeof(ColDesc));
+                dd[s].bm_base = bm_begin[s];
+                dd[s].bm_words = ((uint64_t)set_max[s] + 64) / 64;
+                bm_begin[s + 1] = bm_begin[s] + dd[s].bm_words;
+                for (uint32_t b = 0; b < pl[s].B; b++) {
+                    cd[pl[s].col_base + b].bm_base = dd[s].bm_base;
+                    cd[pl[s].col_base + b].bm_words = dd[s].bm_words;
+                }
+            }
+            CK(tmp.alloc(&d_dd, (size_t)S * sizeof(ColDesc)));
+            CK(h2d(d_dd, dd.data(), S, st));
+        } else {
+            for (uint64_t c = 0; c < cols_total; c++) {
+                cd[c].bm_base = bm_begin[c];
+                cd[c].bm_words = ((uint64_t)hcolmax[c] + 64) / 64;
+                bm_begin[c + 1] = bm_begin[c] + cd[c].bm_words;
+            }
         }
         uint64_t* dK;
-        CK(tmp.alloc(&bitmaps, bm_begin[cols_total] * 8));
-        CK(tmp.alloc(&brank, bm_begin[cols_total] * 8));
-        CK(tmp.alloc(&dK, cols_total * 8));
+        CK(tmp.alloc(&bitmaps, bm_begin[ndict] * 8));
+        CK(tmp.alloc(&brank, bm_begin[ndict] * 8));
+        CK(tmp.alloc(&dK, ndict * 8));
         CK(h2d(d_cd, cd.data(), cols_total, st));
-        CK(cudaMemsetAsync(bitmaps, 0, bm_begin[cols_total] * 8, st));
+        CK(cudaMemsetAsync(bitmaps, 0, bm_begin[ndict] * 8, st));
         CK(launch_dict_mark(pilots, d_cd, (uint32_t)cols_total, bitmaps, st));
-        CK(launch_dict_rank(d_cd, (uint32_t)cols_total, brank, bitmaps, dK, st));
-        CK(d2h(hK, dK, cols_total, st));
+        CK(launch_dict_rank(mono ? d_dd : d_cd, (uint32_t)ndict, brank, bitmaps, dK, st));
+        CK(d2h(hK, dK, ndict, st));
         CK(cudaStreamSynchronize(st));
     }
 
-    // ---- IC-EF: low bits from the column sums (the unary lengths follow from them)
+    // ---- IC-EF: low bits from the column sums (the unary lengths follow from
+    // them); mono-EF: one universe per set, the column sums carried as sum0
     if (icef)
-        for (uint64_t c = 0; c < cols_total; c++) {
-            const uint64_t U = hK[c] + 1, N = cd[c].count;
-            cd[c].width = U >= N ? bitlen64(U / N) - 1 : 0;
+        for (uint32_t s = 0; s < S; s++) {
+            uint64_t carry = 0;
+            for (uint32_t b = 0; b < pl[s].B; b++) {
+                ColDesc& c = cd[pl[s].col_base + b];
+                const uint64_t N = mono ? (uint64_t)pl[s].B * pl[s].NP : c.count;
+                const uint64_t U = (mono ? set_sum[s] : hK[pl[s].col_base + b]) + 1;
+                c.width = U >= N ? bitlen64(U / N) - 1 : 0;
+                if (mono) {
+                    c.idx0 = (uint64_t)b * pl[s].NP;
+                    c.sum0 = carry;
+                    carry += hK[pl[s].col_base + b];
+                }
+            }
         }
     // ---- IC-R (and the Rice columns of IC-CR): Rice parameters from the column
-    // sums, then the unary lengths; IC-CR's Compact columns take the bit length
-    // of their largest pilot
+    // sums (mono-R: from the set's sum), then the unary lengths; IC-CR's Compact
+    // columns take the bit length of their largest pilot
     if (icr || icmix) {
         for (uint32_t s = 0; s < S; s++)
             for (uint32_t b = 0; b < pl[s].B; b++) {
                 const uint64_t c = pl[s].col_base + b;
                 const bool compact = icmix && b < std::min<uint32_t>(prm.compact_columns, pl[s].B);
-                cd[c].width = compact ? bitlen64(hcolmax[c]) : rice_param(hK[c], cd[c].count);
+                cd[c].width = compact ? bitlen64(hcolmax[c])
+                              : mono  ? rice_param(set_sum[s], (uint64_t)pl[s].B * pl[s].NP)
+                                      : rice_param(hK[c], cd[c].count);
             }
         uint64_t* dH;
         CK(tmp.alloc(&dH, cols_total * 8));
@@ -600,15 +647,64 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         p.a_off = aw;
         aw += p.n_off;
         off_begin[s + 1] = off_begin[s] + p.n_off;
-        const bool icd = prm.encoder == PHOBIC_ENC_IC_D;
-        p.n_meta = (icd || unary) ? 2 * (uint64_t)p.B : p.B;
+        p.n_meta = ((icd || unary) ? 2 : 1) * (mono ? 1 : (uint64_t)p.B);
         p.a_meta = aw;
         aw += p.n_meta;
         metas[s].resize(p.n_meta);
         uint64_t rbase = 0, dbase = 0, bp = icmix ? 32 : 0;  // IC-CR records its c
         const uint64_t ns = (p.NP + 63) / 64;  // IC-R select samples per column
         const uint32_t cmix = icmix ? std::min<uint32_t>(prm.compact_columns, p.B) : 0;
-        for (uint32_t b = 0; b < p.B; b++) {
+        const uint64_t Nm = (uint64_t)p.B * p.NP;  // a mono encoder's values
+        if (mono) {
+            // one encoder: column b's values continue at index b N_P, every column
+            // with the set's width (Compact), rank width (Dictionary) or parameter
+            uint32_t w = 0, dw = 0;
+            uint64_t K = 0, Hc = 0;
+            if (unary) {
+                w = cd[p.col_base].width;
+            } else if (icd) {
+                K = hK[s];
+                w = bitlen64(K - 1);
+                dw = bitlen64(set_max[s]);
+            } else {
+                w = bitlen64(set_max[s]);
+            }
+            for (uint32_t b = 0; b < p.B; b++) {
+                ColDesc& c = cd[p.col_base + b];
+                c.width = w;
+                c.base = (uint64_t)b * p.NP * w;
+                if (unary) {
+                    c.hi_base = 0;
+                    c.samp_base = 0;
+                    c.idx0 = (uint64_t)b * p.NP;
+                    if (icr) {  // Rice: sum of pilot >> l over the columns before
+                        c.sum0 = Hc;
+                        Hc += hK[p.col_base + b];
+                    }
+                }
+                const uint64_t bits = p.NP * (uint64_t)w;
+                col_begin[p.col_base + b + 1] =
+                    col_begin[p.col_base + b] + (bits ? ((c.base + bits - 1) >> 6) - (c.base >> 6) + 1 : 0);
+            }
+            rbase = Nm * w;
+            metas[s][0] = (uint64_t)w << 56;
+            if (unary) {
+                dbase = icef ? Nm + (set_sum[s] >> w) + 1 : Nm + Hc;
+                // select samples are 32-bit positions in the unary part
+                if (dbase > (1ull << 32)) return PHOBIC_ERR_INVALID_ARG;
+                metas[s][1] = 0;
+                bp = Nm * w + dbase + 32 * ((Nm + 63) / 64) + 64 + 64 + 8;
+            } else if (icd) {
+                dd[s].dict_width = dw;
+                dd[s].dict_base = 0;
+                dbase = K * dw;
+                metas[s][1] = (uint64_t)dw << 56;
+                bp = Nm * w + K * dw + 64 + 64 + 8 + 8;
+            } else {
+                bp = Nm * w + 64 + 8;
+            }
+        }
+        for (uint32_t b = 0; b < p.B && !mono; b++) {
             ColDesc& c = cd[p.col_base + b];
             const uint64_t c_id = p.col_base + b;
             if (icmix && b < cmix) {
@@ -656,7 +752,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         p.n_pil = packed_words(rbase);
         p.a_pil = aw;
         aw += p.n_pil;
-        p.samp_words = unary ? ((uint64_t)(p.B - cmix) * ns + 1) / 2 : 0;
+        p.samp_words = !unary ? 0 : mono ? ((Nm + 63) / 64 + 1) / 2 : ((uint64_t)(p.B - cmix) * ns + 1) / 2;
         p.mix_c = cmix;
         p.n_dict = icd ? packed_words(dbase) : unary ? p.samp_words + packed_words(dbase) : 0;
         p.a_dict = aw;
@@ -667,6 +763,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
             cd[p.col_base + b].samp_dst_word = (icmix && b < cmix) ? ~0ull : p.a_dict;
             cd[p.col_base + b].hi_dst_word = p.a_dict + p.samp_words;
         }
+        if (mono && icd) dd[s].dict_dst_word = p.a_dict;
         // Elias-Fano remap of slots >= n
         const uint64_t N = p.M - p.n;
         if (N) {
@@ -731,7 +828,6 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     CK(h2d(d_obeg, off_begin.data(), S + 1, st));
     CK(h2d(d_cbeg, col_begin.data(), cols_total + 1, st));
     CK(launch_offset_pack(T, d_od, S, d_obeg, off_begin[S], arena, st));
-    const bool icd = prm.encoder == PHOBIC_ENC_IC_D;
     if (!icef)  // IC-C values, IC-D ranks, IC-R low parts
         CK(launch_pack_columns(pilots, d_cd, (uint32_t)cols_total, d_cbeg, col_begin[cols_total], icd, bitmaps,
                                brank, arena, st));
@@ -739,10 +835,11 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     if (icef) CK(launch_ef_columns(pilots, d_cd, (uint32_t)cols_total, arena, st));
     if (icd) {
         uint64_t* d_bmbeg;
-        CK(tmp.alloc(&d_bmbeg, (cols_total + 1) * 8));
-        CK(h2d(d_bmbeg, bm_begin.data(), cols_total + 1, st));
-        CK(launch_dict_pack_values(d_cd, (uint32_t)cols_total, d_bmbeg, bm_begin[cols_total], bitmaps, brank, arena,
-                                   st));
+        CK(tmp.alloc(&d_bmbeg, (ndict + 1) * 8));
+        CK(h2d(d_bmbeg, bm_begin.data(), ndict + 1, st));
+        if (mono) CK(h2d(d_dd, dd.data(), S, st));
+        CK(launch_dict_pack_values(mono ? d_dd : d_cd, (uint32_t)ndict, d_bmbeg, bm_begin[ndict], bitmaps, brank,
+                                   arena, st));
     }
     CK(ev.mark(6, st));
 
@@ -1239,17 +1336,21 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     const uint64_t off_w = w[12];
     if (off_w > 64 || w[15] > 63) return PHOBIC_ERR_FORMAT;
     if (counts[0] < packed_words((NP + 1) * off_w)) return PHOBIC_ERR_FORMAT;
-    if (counts[1] != (p.encoder == PHOBIC_ENC_IC_C ? B : 2 * B)) return PHOBIC_ERR_FORMAT;
-    if (counts[2] == 0 || (p.encoder == PHOBIC_ENC_IC_D && counts[3] == 0)) return PHOBIC_ERR_FORMAT;
+    // a mono encoder has the layout of its column encoder with one column of B N_P values
+    const bool mono = p.encoder >= PHOBIC_ENC_MONO_C;
+    const uint32_t enc = mono ? p.encoder - PHOBIC_ENC_MONO_C : p.encoder;
+    const uint64_t ncol = mono ? 1 : B, nv = mono ? B * NP : NP;
+    if (counts[1] != (enc == PHOBIC_ENC_IC_C ? ncol : 2 * ncol)) return PHOBIC_ERR_FORMAT;
+    if (counts[2] == 0 || (enc == PHOBIC_ENC_IC_D && counts[3] == 0)) return PHOBIC_ERR_FORMAT;
     if ((M > n) != (counts[4] != 0 && counts[5] != 0 && counts[6] != 0)) return PHOBIC_ERR_FORMAT;
     // every metadata entry must address inside its array
     {
         const uint64_t* meta = w + kHeaderWords + counts[0];
-        for (uint64_t b = 0; b < B; b++) {
-            for (int t = 0; t < (p.encoder == PHOBIC_ENC_IC_C ? 1 : 2); t++) {
-                uint64_t mv = meta[p.encoder == PHOBIC_ENC_IC_C ? b : 2 * b + t];
+        for (uint64_t b = 0; b < ncol; b++) {
+            for (int t = 0; t < (enc == PHOBIC_ENC_IC_C ? 1 : 2); t++) {
+                uint64_t mv = meta[enc == PHOBIC_ENC_IC_C ? b : 2 * b + t];
                 uint64_t base = mv & ((1ull << 56) - 1), wd = mv >> 56;
-                uint64_t cnt = (t == 0) ? NP : 0;
+                uint64_t cnt = (t == 0) ? nv : 0;
                 if (wd > 32) return PHOBIC_ERR_FORMAT;
                 uint64_t arr = (t == 0) ? counts[2] : counts[3];
                 if (t == 0 && base + cnt * wd > (arr - 1) * 64) return PHOBIC_ERR_FORMAT;
@@ -1261,20 +1362,20 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     // ones, and each select sample is the position of its 64k-th one, so the
     // query's scans never leave the column
     uint64_t rice_sw = 0;
-    const bool unary_enc =
-        p.encoder == PHOBIC_ENC_IC_R || p.encoder == PHOBIC_ENC_IC_EF || p.encoder == PHOBIC_ENC_IC_CR;
-    const uint64_t cmix = p.encoder == PHOBIC_ENC_IC_CR ? std::min<uint64_t>(p.compact_columns, B) : 0;
-    if (p.encoder == PHOBIC_ENC_IC_CR && p.compact_columns > B) return PHOBIC_ERR_FORMAT;  // exported clamped
+    const bool unary_enc = enc == PHOBIC_ENC_IC_R || enc == PHOBIC_ENC_IC_EF || enc == PHOBIC_ENC_IC_CR;
+    const uint64_t cmix = enc == PHOBIC_ENC_IC_CR ? std::min<uint64_t>(p.compact_columns, B) : 0;
+    if (enc == PHOBIC_ENC_IC_CR && p.compact_columns > B) return PHOBIC_ERR_FORMAT;  // exported clamped
+    if (mono && p.compact_columns) return PHOBIC_ERR_FORMAT;
     if (unary_enc) {
-        const uint64_t ns = (NP + 63) / 64;
-        rice_sw = ((B - cmix) * ns + 1) / 2;
+        const uint64_t ns = (nv + 63) / 64;
+        rice_sw = ((ncol - cmix) * ns + 1) / 2;
         if (counts[3] < rice_sw + 1) return PHOBIC_ERR_FORMAT;
         const uint64_t* meta = w + kHeaderWords + counts[0];
         const uint32_t* samp = reinterpret_cast<const uint32_t*>(w + kHeaderWords + counts[0] + counts[1] + counts[2]);
         const uint64_t* high = w + kHeaderWords + counts[0] + counts[1] + counts[2] + rice_sw;
         const uint64_t hbits = (counts[3] - rice_sw - 1) * 64;  // the last word is padding
-        for (uint64_t b = 0; b < B; b++) {
-            const uint64_t hb = meta[2 * b + 1], he = b + 1 < B ? meta[2 * b + 3] : hbits;
+        for (uint64_t b = 0; b < ncol; b++) {
+            const uint64_t hb = meta[2 * b + 1], he = b + 1 < ncol ? meta[2 * b + 3] : hbits;
             if (b < cmix) {  // a Compact column of a mixture: no unary bits
                 if ((meta[2 * b] >> 56) > 32 || hb != he) return PHOBIC_ERR_FORMAT;
                 continue;
@@ -1283,11 +1384,11 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
             uint64_t ones = 0;
             for (uint64_t bit = hb; bit < he; bit++) {
                 if (!((high[bit >> 6] >> (bit & 63)) & 1)) continue;
-                if (ones >= NP) return PHOBIC_ERR_FORMAT;
+                if (ones >= nv) return PHOBIC_ERR_FORMAT;
                 if (ones % 64 == 0 && samp[(b - cmix) * ns + ones / 64] != bit - hb) return PHOBIC_ERR_FORMAT;
                 ones++;
             }
-            if (ones != NP) return PHOBIC_ERR_FORMAT;
+            if (ones != nv) return PHOBIC_ERR_FORMAT;
         }
     }
     (void)stream;  // the copies below are synchronous

@@ -106,7 +106,7 @@ __host__ __device__ __forceinline__ uint64_t packed_words(uint64_t nbits) { retu
 struct QueryView {
     uint64_t n, M, NP;
     uint32_t B;
-    uint32_t encoder;    // 0 IC-C, 1 IC-D, 2 IC-R, 3 IC-EF, 4 IC-CR
+    uint32_t encoder;    // 0 IC-C, 1 IC-D, 2 IC-R, 3 IC-EF, 4 IC-CR; 5..8 mono-C/D/R/EF (one column)
     uint32_t pilot_mode; // 0 additive, 1 xor
     uint32_t off_w;
     uint64_t kseed;      // mix64(seed ^ kSeedMix)

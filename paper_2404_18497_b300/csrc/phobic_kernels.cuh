@@ -124,6 +124,11 @@ struct ColDesc {
     // column's at index samp_base; its unary bits at bit hi_base of the array at
     // arena word hi_dst_word
     uint64_t samp_dst_word, samp_base, hi_dst_word, hi_base;
+    // a mono encoder's physical column b continues the set's single sequence:
+    // idx0 = its first value's index b N_P, sum0 = the scanned quantity (Rice:
+    // sum of pilot >> l; Elias-Fano: sum of pilots) of the columns before it.
+    // Both 0 for an interleaved column.
+    uint64_t idx0, sum0;
 };
 cudaError_t launch_offset_minmax(const uint64_t* T, const OffDesc* sets, uint32_t nsets, long long* mm,
                                  cudaStream_t stream);

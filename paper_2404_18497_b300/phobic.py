@@ -25,9 +25,12 @@ STATUS_NAMES = {
     5: "PARTITION_TOO_LARGE", 6: "CUDA", 7: "TIMEOUT", 8: "FORMAT",
 }
 ENC_IC_C, ENC_IC_D, ENC_IC_R, ENC_IC_EF, ENC_IC_CR = 0, 1, 2, 3, 4
+# mono-X: the column encoder X over one column holding all pilots (Section 5, Fig. 3b)
+ENC_MONO_C, ENC_MONO_D, ENC_MONO_R, ENC_MONO_EF = 5, 6, 7, 8
 PILOT_ADDITIVE, PILOT_XOR = 0, 1
 _ENC = {"IC-C": ENC_IC_C, "IC-D": ENC_IC_D, "IC-R": ENC_IC_R, "IC-EF": ENC_IC_EF, "IC-CR": ENC_IC_CR,
-        ENC_IC_C: ENC_IC_C, ENC_IC_D: ENC_IC_D, ENC_IC_R: ENC_IC_R, ENC_IC_EF: ENC_IC_EF, ENC_IC_CR: ENC_IC_CR}
+        "mono-C": ENC_MONO_C, "mono-D": ENC_MONO_D, "mono-R": ENC_MONO_R, "mono-EF": ENC_MONO_EF}
+_ENC.update({v: v for v in list(_ENC.values())})
 _MODE = {"additive": PILOT_ADDITIVE, "xor": PILOT_XOR, PILOT_ADDITIVE: PILOT_ADDITIVE, PILOT_XOR: PILOT_XOR}
 
 
@@ -633,11 +636,12 @@ def parse_export(data: bytes) -> dict:
         c = hdr["n_" + name]
         hdr[name] = w[at: at + c].copy()
         at += c
-    if hdr["encoder"] in (ENC_IC_R, ENC_IC_EF, ENC_IC_CR):
+    if hdr["encoder"] in (ENC_IC_R, ENC_IC_EF, ENC_IC_CR, ENC_MONO_R, ENC_MONO_EF):
         # the dictionary array holds the u32 select samples (of the Rice columns),
-        # then the unary bits
-        ns = (hdr["NP"] + 63) // 64
-        cols = hdr["B"] - (hdr["compact_columns"] if hdr["encoder"] == ENC_IC_CR else 0)
+        # then the unary bits; a mono encoder has one column of B N_P values
+        mono = hdr["encoder"] >= ENC_MONO_C
+        ns = ((hdr["B"] * hdr["NP"] if mono else hdr["NP"]) + 63) // 64
+        cols = 1 if mono else hdr["B"] - (hdr["compact_columns"] if hdr["encoder"] == ENC_IC_CR else 0)
         sw = (cols * ns + 1) // 2
         d = hdr["dict_words"]
         hdr["rice_samples"] = d[:sw].view(np.uint32)[: cols * ns].copy()

@@ -36,8 +36,11 @@ def _keys(n, seed):
 
 
 def compare_structure(ph, orc_h, h, encoder):
-    """Every array of the exported structure equals the oracle's."""
+    """Every array of the exported structure equals the oracle's.  A mono encoder
+    (5..8) has its column encoder's arrays for a single column."""
     ex = ph.parse_export(ph.phobic_export(h))
+    assert ex["encoder"] == encoder
+    encoder = encoder - 5 if encoder >= 5 else encoder
     o = orc_h
     assert ex["n"] == o.u64("n") and ex["M"] == o.u64("M") and ex["NP"] == o.u64("NP") and ex["B"] == o.u64("B")
     assert ex["off_w"] == o.u64("off_w") and ex["off_Q"] == o.u64("off_Q") and ex["off_dmin"] == o.u64("off_dmin")
@@ -206,6 +209,26 @@ def test_compact_rice_mixture_parity(ph, orc, c):
         h.free()
 
 
+@pytest.mark.parametrize("enc", [5, 6, 7, 8])
+def test_mono_encoder_parity(ph, orc, enc):
+    """Section 5, Figure 3b: mono-C/D/R/EF place all pilots in one encoder.  The
+    GPU keeps one work item per physical column and carries the set-wide width,
+    dictionary, Rice parameter or Elias-Fano prefix across them; the structure is
+    bit-exact with the oracle's one-column encoding, for alpha < 1 and both pilot
+    modes, ragged partition counts, and through export and import."""
+    keys = _keys(400_000 + 3 * enc, 110 + enc)
+    for mode, alpha, P in [(0, 0.99, 2500), (1, 1.0, 1000), (0, 0.97, 4096)]:
+        o = orc.Oracle(keys, lam=7.0, alpha=alpha, P=P, encoder=enc, mode=mode, threads=0)
+        h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, alpha, P, encoder=enc, mode=mode, keep_pilots=True))
+        assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots)
+        compare_structure(ph, o, h, enc)
+        assert h.bits_per_key() == o.bits_per_key()
+        assert np.array_equal(_host(h.query(_dev(keys))), o.query(keys))
+        h2 = ph.phobic_import(ph.phobic_export(h))
+        assert torch.equal(h2.query(_dev(keys)), h.query(_dev(keys)))
+        h.free()
+
+
 def test_query_unaligned_and_odd_lengths(ph, orc):
     keys = _keys(30_001, 4)
     o = orc.Oracle(keys, lam=6.0, P=500, threads=0)
@@ -221,7 +244,7 @@ def test_query_unaligned_and_odd_lengths(ph, orc):
 
 def test_export_import_roundtrip(ph, orc):
     keys = _keys(123_457, 8)
-    for enc, alpha in [(0, 1.0), (1, 0.95), (2, 0.99), (3, 0.99)]:
+    for enc, alpha in [(0, 1.0), (1, 0.95), (2, 0.99), (3, 0.99), (5, 1.0), (6, 0.99), (7, 0.99), (8, 1.0)]:
         h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, alpha, 2500, encoder=enc))
         data = ph.phobic_export(h)
         h2 = ph.phobic_import(data)
@@ -235,7 +258,7 @@ def test_export_import_roundtrip(ph, orc):
         assert e.value.status == "FORMAT"
         with pytest.raises(ph.PhobicError):
             ph.phobic_import(data[:-8])
-        if enc in (2, 3):
+        if enc in (2, 3, 7, 8):
             # a unary region with a missing one, or a wrong select sample, is refused
             ex = ph.parse_export(data)
             w = np.frombuffer(data, dtype=np.uint64).copy()
@@ -384,7 +407,8 @@ def test_string_hash_unaligned_and_tails(ph, orc):
         assert np.array_equal(got, orc.string_hashes(data, off, 123))
 
 
-@pytest.mark.parametrize("alpha,enc", [(0.99, 1), (1.0, 0), (0.99, 2), (1.0, 3)])
+@pytest.mark.parametrize("alpha,enc", [(0.99, 1), (1.0, 0), (0.99, 2), (1.0, 3), (1.0, 5), (0.99, 6), (0.99, 7),
+                                       (1.0, 8)])
 def test_batch_build_matches_single_builds(ph, orc, alpha, enc):
     """Batched construction: every set's structure equals the oracle's build of
     that set alone (and so the single-set path), for uneven set sizes and mixed

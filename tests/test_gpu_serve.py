@@ -39,7 +39,8 @@ def _negatives(n, seed):
 
 def test_query_multi_equals_separate_queries(ph):
     hs, keysets = [], []
-    cfgs = [(7.0, 1.0, 2500, 0, 0), (7.0, 0.99, 2500, 1, 0), (6.0, 0.97, 1024, 1, 1), (8.0, 0.99, 4096, 0, 0)]
+    cfgs = [(7.0, 1.0, 2500, 0, 0), (7.0, 0.99, 2500, 1, 0), (6.0, 0.97, 1024, 1, 1), (8.0, 0.99, 4096, 0, 0),
+            (7.0, 0.99, 2500, 2, 0), (7.0, 0.99, 2500, 7, 1), (7.0, 1.0, 2500, 6, 0)]
     for i, (lam, alpha, P, enc, mode) in enumerate(cfgs):
         k = _stream_keys(i * 10_000_000, 200_000 + 37_771 * i, 3)
         hs.append(ph.phobic_build_ex(k, ph.make_params(lam, alpha, P, encoder=enc, mode=mode)))
