@@ -358,7 +358,7 @@ phobic_status phobic_partition_sort(const uint64_t* d_hk, uint64_t n, uint64_t n
  * the kernel records a timeout in a device status word, stops waiting and
  * finishes; the call then returns PHOBIC_ERR_TIMEOUT and the context stays
  * usable.  This entry point runs phobic_partition_sort with tile mute_tile
- * (of 4096 keys each) withholding its state, so that the wait of the tile after
+ * (of 6144 keys each) withholding its state, so that the wait of the tile after
  * it runs out after spin_limit polls (a flag that nothing sets).  Nothing faults
  * or hangs.  Returns TIMEOUT when a wait ran out, OK when none did (mute_tile
  * past the last tile, or a single pass-free sort); d_sorted / d_start are then

@@ -476,10 +476,17 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
                         ps = pilot_seed(s);
                     bool coll = false;
                     if (k <= 32) {
-                        const uint32_t h = lane < k ? position_hash(mykey, ps, m) : (0x80000000u | lane);
+                        const uint32_t h = lane < k ? position_hash(mykey, ps, m) : 0u;
                         if (lane < k) hb[lane] = (uint16_t)h;
-                        uint32_t peers = __match_any_sync(kFull, h);
-                        coll = __any_sync(kFull, __popc(peers) > 1);
+                        // two keys on one slot: mark each slot in the warp's
+                        // scratch bitmap and look at the bit's old value
+                        bool c = false;
+                        if (lane < k) {
+                            const uint32_t bit = 1u << (h & 31);
+                            c = (atomicOr(&scr[h >> 5], bit) & bit) != 0;
+                        }
+                        coll = __any_sync(kFull, c);
+                        if (lane < k) scr[h >> 5] = 0;
                     } else {
                         // large bucket: up to kBigRegs keys per lane stay in registers
                         // across s values; the rest are re-read from the key store

@@ -22,7 +22,7 @@ namespace phobic {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 384;
 constexpr int kItems = 16;
 constexpr int kTile = kThreads * kItems;  // keys per tile
 static_assert(kTile == (int)kSortTileKeys, "tile size");
@@ -74,7 +74,19 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ 
         const uint64_t k0 = S.key_base + (ta - S.first_tile) * kTile;
         uint64_t k1 = S.key_base + (tb - S.first_tile) * kTile;
         if (k1 > S.key_base + S.n) k1 = S.key_base + S.n;
-        for (uint64_t i = k0 + threadIdx.x; i < k1; i += blockDim.x) {
+        // four keys per thread per step, so that four loads are in flight
+        uint64_t i = k0 + threadIdx.x;
+        for (; i + 3ull * blockDim.x < k1; i += 4ull * blockDim.x) {
+            uint64_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = __ldg(in + i + (uint64_t)u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint64_t j = partition_of(hash_input ? key_hash(v[u], kseed) : v[u], S.np);
+                for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
+            }
+        }
+        for (; i < k1; i += blockDim.x) {
             const uint64_t v = __ldg(in + i);
             const uint64_t j = partition_of(hash_input ? key_hash(v, kseed) : v, S.np);
             for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
@@ -134,13 +146,14 @@ struct PassArgs {
 };
 
 // One digit pass.  Tile = kTile consecutive keys.  Warp w ranks its 32 x kItems
-// keys (order: item, lane) with __match_any_sync: the leader of each group of
-// equal digits adds the group size to the warp's counter with one shared
-// atomicAdd and hands the old value to its peers, so ranks are stable.  Then
+// keys (order: item, lane): the lanes with equal digits are found as the AND,
+// over the digit's bits, of the ballots of the lanes that agree on that bit;
+// the leader of each group adds the group size to the warp's counter with one
+// shared atomicAdd and hands the old value to its peers, so ranks are stable.  Then
 // per digit: prefix over warps, decoupled look-back for the tile's global
 // offset, a block scan for the tile-local digit starts, a shared-memory
 // reorder and a coalesced write-out.
-__global__ void __launch_bounds__(kThreads, 3) k_sort_pass(PassArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t R = 1u << a.bits, mask = R - 1;
     uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);                      // kTile
@@ -175,7 +188,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(PassArgs a) {
     for (int i = 0; i < kItems; i++) {
         const bool valid = wbase + (uint64_t)i * 32 + lane < seg_end;
         const uint32_t dg = valid ? (uint32_t)((partition_of(k[i], S.np) >> a.shift) & mask) : R;
-        const uint32_t peers = __match_any_sync(kFull, dg);
+        uint32_t peers = __ballot_sync(kFull, valid);
+        for (uint32_t bb = 0; bb < a.bits; bb++) {
+            const uint32_t bit = (dg >> bb) & 1u;
+            const uint32_t bal = __ballot_sync(kFull, bit);
+            peers &= bit ? bal : ~bal;
+        }
         const uint32_t leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (lane == leader && dg < R) old = atomicAdd(&myh[dg], (uint32_t)__popc(peers));

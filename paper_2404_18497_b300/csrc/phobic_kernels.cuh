@@ -19,7 +19,7 @@ cudaError_t allow_max_dynamic_smem(const void* kern);
 void note_launches(uint64_t k);
 
 // ---- k_sort.cu: master hash + onesweep sort by partition id ----
-constexpr uint32_t kSortTileKeys = 4096;  // keys per onesweep tile
+constexpr uint32_t kSortTileKeys = 6144;  // keys per onesweep tile (384 threads x 16)
 // one independent key set of a (batched) sort: keys [key_base, key_base + n)
 // grouped by partition j = floor(hk np / 2^64) into [key_base, key_base + n);
 // partition starts go to start[part_base + j]; tiles [first_tile, ...)

@@ -28,7 +28,7 @@ def ph():
 def test_lookback_wait_runs_out_and_context_survives(ph, orc):
     from paper_2404_18497_b300 import workloads
 
-    n, P = 1_000_000, 2500
+    n, P = 2_000_000, 2500  # 326 sort tiles of 6144 keys: every muted tile below exists
     np_ = (n + P - 1) // P
     keys = workloads.distinct_u64(n, 61)
     dk = torch.from_numpy(keys.view(np.int64)).cuda()
