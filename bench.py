@@ -55,6 +55,7 @@ def parse():
                     help="pilot encoder instead of the workload's own")
     ap.add_argument("--lam", type=float, default=None, help="average bucket size instead of the workload's own")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-build section")
+    ap.add_argument("--no-xor", action="store_true", help="skip the XOR-pilot section")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -438,6 +439,10 @@ def run_ours(a):
                "note": "phobic_build_host (pinned keys, H2D inside) + phobic_query_host (H2D keys, D2H results)",
                "check": ok}
 
+    xor = None
+    if not a.no_xor and a.impl == "ours":
+        xor = run_xor(a, phobic, torch, dk, dqu, out, w, n, world)
+
     batch = serve = None
     if world == 1 and not (a.no_batch and a.no_serve):
         dk = dqu = dqz = out = None
@@ -486,10 +491,47 @@ def run_ours(a):
         "gpu_launches_per_step": launches / a.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "xor_mode": xor,
         "batch": batch,
         "serve": serve,
     }
     print(json.dumps(res_line))
+
+# ------------------------------------------------------------- XOR pilots ---
+def run_xor(a, phobic, torch, dk, dqu, out, w, n, world):
+    """The same workload with PTHash's pilot form, position h(x XOR h(p)) mod m
+    and p = 0, 1, 2, ... (the form without displacement): one warm-up build, two
+    timed builds and one timed uniform query batch, CUDA events on the stream."""
+    stream = torch.cuda.current_stream()
+    prm = phobic.make_params(w["lam"], w["alpha"], w["P"], seed=0, encoder=w["encoder"], mode="xor",
+                             record_timings=True)
+    h = phobic.phobic_build_ex(dk, prm, stream)
+    h.free()
+    bms, sms = [], []
+    for _ in range(2):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        h = phobic.phobic_build_ex(dk, prm, stream)
+        e1.record(stream)
+        phobic.phobic_query(h, dqu, out[: dqu.numel()], stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        bms.append(e0.elapsed_time(e1))
+        sms.append(phobic.phobic_get_timings(h)["search_ms"])
+        qms = e1.elapsed_time(e2)
+        if _ == 0:
+            h.free()
+    res = h.query(dk)
+    perm_ok = bool(torch.equal(torch.sort(res).values, torch.arange(n, device="cuda")))
+    bpk = h.bits_per_key()
+    del res
+    h.free()
+    b_ms = reduce_max(statistics.mean(bms), world)
+    return {"pilot_form": "h(x XOR h(p)) mod m, p = 0, 1, 2, ... (same keys, lambda, alpha, P and encoder)",
+            "build_ms": b_ms, "build_mkeys_s": world * n / (b_ms / 1e3) / 1e6,
+            "search_ms": statistics.mean(sms), "query_mkeys_s": world * w["q_uniform"] / (qms / 1e3) / 1e6,
+            "bits_per_key": bpk, "result_is_permutation": perm_ok}
+
 
 # ------------------------------------------------------- batched build (C4) ---
 def run_batch(a, phobic, workloads, torch):

@@ -294,16 +294,33 @@ __global__ void k_pack_columns(const uint32_t* __restrict__ pilots, const ColDes
     }
 }
 
-// IC-D presence bitmaps: bit v of column c's bitmap is set when v occurs
+// IC-D presence bitmaps: bit v of column c's bitmap is set when v occurs.  The
+// low kMarkWords words of the column's bitmap are gathered in shared memory
+// first (small pilots are by far the most frequent, and a mono dictionary's
+// columns all mark one bitmap) and OR-ed into it once per non-zero word.
+constexpr uint32_t kMarkWords = 2048;  // 64-bit words: pilots < 131072
 __global__ void __launch_bounds__(256) k_dict_mark(const uint32_t* __restrict__ pilots,
                                                    const ColDesc* __restrict__ cols, uint32_t ncols,
                                                    uint64_t* __restrict__ bitmaps) {
+    __shared__ uint32_t sbm[2 * kMarkWords];
     for (uint32_t c = blockIdx.x; c < ncols; c += gridDim.x) {
         const ColDesc d = cols[c];
+        const uint32_t sw = d.bm_words < kMarkWords ? (uint32_t)d.bm_words : kMarkWords;  // staged words
+        for (uint32_t i = threadIdx.x; i < 2 * sw; i += blockDim.x) sbm[i] = 0;
+        __syncthreads();
         for (uint64_t j = threadIdx.x; j < d.count; j += blockDim.x) {
             const uint32_t v = __ldg(pilots + d.src + j);
-            atomicOr((unsigned long long*)(bitmaps + d.bm_base + (v >> 6)), 1ull << (v & 63));
+            if ((v >> 6) < sw)
+                atomicOr(&sbm[v >> 5], 1u << (v & 31));
+            else
+                atomicOr((unsigned long long*)(bitmaps + d.bm_base + (v >> 6)), 1ull << (v & 63));
         }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < sw; i += blockDim.x) {
+            const uint64_t w = (uint64_t)sbm[2 * i] | ((uint64_t)sbm[2 * i + 1] << 32);
+            if (w) atomicOr((unsigned long long*)(bitmaps + d.bm_base + i), (unsigned long long)w);
+        }
+        __syncthreads();
     }
 }
 

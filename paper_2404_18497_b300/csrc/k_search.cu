@@ -569,13 +569,20 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
             const uint64_t limit = (uint64_t)min(a.s_max, 0xFFFFFFFFu / m) * m;  // pilots < 2^32
             uint32_t outcome = kOutNone, winner = 0;
             if (k <= 32) {
-                // groups of Lc lanes test G consecutive pilots per warp step
-                const uint32_t lc = k <= 1 ? 0u : 32u - __clz(k - 1);  // log2 pow2ceil(k)
-                const uint32_t Lc = 1u << lc, G = 32u >> lc;
-                const uint32_t g = lane >> lc, rr = lane & (Lc - 1);
-                const uint64_t gkey = rr < k ? keys[rr] : 0;
-                const uint32_t gmask = Lc == 32 ? kFull : ((1u << Lc) - 1);
+                // groups of k lanes test G = floor(32 / k) consecutive pilots per warp
+                // step (lanes g >= G idle): lane rr of group g hashes key rr with pilot
+                // p0 + g.  A group wins when its k slots are free and pairwise
+                // distinct; distinctness is looked at only in steps where some group
+                // has all its slots free
+                const uint32_t G = 32u / k;
+                const uint32_t g = lane / k, rr = lane - g * k;
+                const bool act = g < G;
+                const uint64_t gkey = act ? keys[rr] : 0;
+                const uint32_t gmask = k == 32 ? kFull : ((1u << k) - 1);
                 uint32_t mypos = 0;
+                // pilot seeds of 32 consecutive pilots from cb on, one per lane (one
+                // warp per partition, G < 32)
+                uint64_t cb = 0, ps_cache = pilot_seed(lane);
                 for (uint64_t pb = 0;; pb += (uint64_t)kWarps * G) {
                     const uint64_t p0 = pb + (uint64_t)warp * G;
                     uint32_t my = kOutNone, myp = 0, pos = 0;
@@ -586,25 +593,37 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
                     } else {
                         steps++;
                         const uint64_t pc = p0 + g;
-                        bool ok = true;
-                        uint32_t key = 0xFFFFFFFFu - lane;  // unique, never a slot
-                        if (rr < k && pc < limit) {
-                            pos = position_hash(gkey, pilot_seed(pc), m);
-                            ok = (fw[pos >> 5] >> (pos & 31)) & 1;
-                            key = (g << 20) | pos;
-                        } else if (pc >= limit) {
-                            ok = false;
+                        bool free_slot = false;  // idle lanes and pilots past the limit count as taken
+                        uint64_t ps;
+                        if (G == 32 || kWarps > 1) {
+                            // singletons need a new seed in every lane at every step, and
+                            // several warps per partition jump past the cache every round
+                            ps = pilot_seed(pc);
+                        } else {
+                            if (p0 + G > cb + 32) {  // warp-uniform: refill the seed cache from p0
+                                cb = p0;
+                                ps_cache = pilot_seed(cb + lane);
+                            }
+                            ps = __shfl_sync(kFull, ps_cache, (uint32_t)(p0 - cb) + (act ? g : 0u));
                         }
-                        uint32_t peers = __match_any_sync(kFull, key);
-                        ok = ok && __popc(peers) == 1;
-                        uint32_t bad = __ballot_sync(kFull, !ok);
-                        bool gok = ((bad >> (g * Lc)) & gmask) == 0;
-                        uint32_t win = __ballot_sync(kFull, gok && rr == 0);
-                        if (win) {
-                            uint32_t gi = (__ffs(win) - 1) >> lc;
-                            my = kOutFound;
-                            myp = (uint32_t)(p0 + gi);
-                            mypos = __shfl_sync(kFull, pos, (lane & (Lc - 1)) + gi * Lc);
+                        if (act && pc < limit) {
+                            pos = position_hash(gkey, ps, m);
+                            free_slot = (fw[pos >> 5] >> (pos & 31)) & 1;
+                        }
+                        const uint32_t taken = __ballot_sync(kFull, !free_slot);
+                        const bool gfree = act && ((taken >> (g * k)) & gmask) == 0;
+                        if (__ballot_sync(kFull, gfree && rr == 0)) {
+                            const uint32_t key = gfree ? ((g << 20) | pos) : (0xFFFFFFFFu - lane);  // filler never a slot
+                            const uint32_t peers = __match_any_sync(kFull, key);
+                            const uint32_t dup = __ballot_sync(kFull, gfree && __popc(peers) > 1);
+                            const bool gok = gfree && ((dup >> (g * k)) & gmask) == 0;
+                            const uint32_t win = __ballot_sync(kFull, gok && rr == 0);
+                            if (win) {
+                                const uint32_t fl = __ffs(win) - 1;  // first lane of the winning group
+                                my = kOutFound;
+                                myp = (uint32_t)(p0 + fl / k);
+                                mypos = __shfl_sync(kFull, pos, fl + (lane < k ? lane : 0u));
+                            }
                         }
                     }
                     if constexpr (kWarps == 1) {
