@@ -155,39 +155,60 @@ __device__ __forceinline__ uint32_t ef_column_pilot(const QueryView& v, uint32_t
     return (uint32_t)(ej - ep);
 }
 
-constexpr int kSeedTable = 64;  // pilot seeds mix64(s ^ C) for s < 64, per block
-
-__device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds);
-
-__device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key, const uint64_t* seeds) {
-    return query_hashed(v, key_hash(key, v.kseed), seeds);
+// A mono encoder (5..8: Compact, Dictionary, Rice, Elias-Fano over one column of
+// all pilots): value i = b N_P + j of column 0
+__device__ __forceinline__ uint32_t mono_pilot(const QueryView& v, uint64_t i) {
+    const uint64_t m0 = __ldg(v.col_meta);
+    const uint32_t w = (uint32_t)(m0 >> 56);
+    switch (v.encoder) {
+        case 5:
+            return (uint32_t)read_bits(v.pil_words, (m0 & kMeta) + i * w, w);
+        case 6: {
+            const uint64_t dm = __ldg(v.col_meta + 1);
+            const uint32_t dw = (uint32_t)(dm >> 56);
+            const uint64_t r = read_bits(v.pil_words, (m0 & kMeta) + i * w, w);
+            return (uint32_t)read_bits(v.dict_words, (dm & kMeta) + r * dw, dw);
+        }
+        case 7:
+            return rice_pilot(v, 0, i);
+        default:
+            return ef_column_pilot(v, 0, i);
+    }
 }
 
+constexpr int kSeedTable = 64;  // pilot seeds mix64(s ^ C) for s < 64, per block
+
+// kMono: the handle uses a mono encoder (5..8).  The kernels are instantiated
+// for both, so that the interleaved encoders' code is not shaped by the other.
+template <bool kMono>
+__device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds);
+
+template <bool kMono>
+__device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key, const uint64_t* seeds) {
+    return query_hashed<kMono>(v, key_hash(key, v.kseed), seeds);
+}
+
+template <bool kMono>
 __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds) {
-    const uint64_t jp = partition_of(hk, v.NP);
+    const uint64_t j = partition_of(hk, v.NP);
     uint64_t Tj, Tj1;
     if (v.off_w <= 31) {
-        offsets_of(v, jp, &Tj, &Tj1);
+        offsets_of(v, j, &Tj, &Tj1);
     } else {
-        Tj = offset_of(v, jp);
-        Tj1 = offset_of(v, jp + 1);
+        Tj = offset_of(v, j);
+        Tj1 = offset_of(v, j + 1);
     }
     const uint32_t m = (uint32_t)(Tj1 - Tj);
     if (m == 0) return 0;  // only a key outside the set can land in an empty partition
-    uint32_t b = bucket_of(bucket_hash(hk), v.table, v.B);
-    uint32_t enc = v.encoder;
-    uint64_t j = jp;
-    if (enc >= 5) {  // a mono encoder: value b N_P + j of its single column
-        enc -= 5;
-        j += (uint64_t)b * v.NP;
-        b = 0;
-    }
+    const uint32_t b = bucket_of(bucket_hash(hk), v.table, v.B);
     uint32_t p;
-    if (enc == 2) {
+    if (kMono) {
+        p = mono_pilot(v, (uint64_t)b * v.NP + j);
+    } else if (v.encoder == 2) {
         p = rice_pilot(v, b, j);
-    } else if (enc == 3) {
+    } else if (v.encoder == 3) {
         p = ef_column_pilot(v, b, j);
-    } else if (enc == 4) {  // IC-CR: Compact below mix_c, Rice from there on
+    } else if (v.encoder == 4) {  // IC-CR: Compact below mix_c, Rice from there on
         if (b < v.mix_c) {
             const uint64_t meta = __ldg(v.col_meta + 2 * b);
             const uint32_t w = (uint32_t)(meta >> 56);
@@ -197,7 +218,7 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
         }
     } else if (v.small_bits) {
         const uint32_t jj = (uint32_t)j;
-        if (enc == 0) {
+        if (v.encoder == 0) {
             const uint64_t meta = __ldg(v.col_meta + b);
             const uint32_t w = (uint32_t)(meta >> 56);
             p = read_bits32(v.pil_words, (uint32_t)meta + jj * w, w);
@@ -207,7 +228,7 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
             const uint32_t r = read_bits32(v.pil_words, (uint32_t)rm + jj * rw, rw);
             p = read_bits32(v.dict_words, (uint32_t)dm + r * dw, dw);
         }
-    } else if (enc == 0) {
+    } else if (v.encoder == 0) {
         uint64_t meta = __ldg(v.col_meta + b);
         uint32_t w = (uint32_t)(meta >> 56);
         p = (uint32_t)read_bits(v.pil_words, (meta & kMeta) + j * w, w);
@@ -233,6 +254,7 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
     return g;
 }
 
+template <bool kMono>
 __global__ void __launch_bounds__(256) k_query(const QueryView v, const uint64_t* __restrict__ keys,
                                                uint64_t* __restrict__ out, uint64_t m) {
     __shared__ uint64_t seeds[kSeedTable];
@@ -247,18 +269,19 @@ __global__ void __launch_bounds__(256) k_query(const QueryView v, const uint64_t
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < pairs; i += stride) {
             ulonglong2 k = __ldcs(k2 + i);
             ulonglong2 r;
-            r.x = query_one(v, k.x, seeds);
-            r.y = query_one(v, k.y, seeds);
+            r.x = query_one<kMono>(v, k.x, seeds);
+            r.y = query_one<kMono>(v, k.y, seeds);
             __stcs(o2 + i, r);
         }
-        if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[m - 1] = query_one(v, keys[m - 1], seeds);
+        if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[m - 1] = query_one<kMono>(v, keys[m - 1], seeds);
     } else {
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += stride)
-            out[i] = query_one(v, keys[i], seeds);
+            out[i] = query_one<kMono>(v, keys[i], seeds);
     }
 }
 
 // string keys: XXH64 master hash of each string (Section 5), then the same query
+template <bool kMono>
 __global__ void __launch_bounds__(256) k_query_strings(const QueryView v, const uint8_t* __restrict__ bytes,
                                                        const uint64_t* __restrict__ offsets, uint64_t* __restrict__ out,
                                                        uint64_t m) {
@@ -267,7 +290,7 @@ __global__ void __launch_bounds__(256) k_query_strings(const QueryView v, const 
     __syncthreads();
     const uint64_t total = __ldg(offsets + m);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = query_hashed(v, string_master_hash(bytes, offsets, total, i, v.string_seed), seeds);
+        out[i] = query_hashed<kMono>(v, string_master_hash(bytes, offsets, total, i, v.string_seed), seeds);
 }
 
 // Several query batches against different structures in one launch.  The
@@ -302,7 +325,9 @@ __global__ void __launch_bounds__(256) k_query_multi(const MultiQuery* __restric
             while (r + 1 < nreq && reqs[r + 1].begin <= i) r++;
             const MultiQuery* q = reqs + r;
             const uint64_t x = __ldcs(q->keys + (i - q->begin));
-            __stcs(q->out + (i - q->begin), query_one(q->v, x, seeds));
+            // a handle's encoder is uniform over its request
+            const uint64_t y = q->v.encoder >= 5 ? query_one<true>(q->v, x, seeds) : query_one<false>(q->v, x, seeds);
+            __stcs(q->out + (i - q->begin), y);
         }
     }
 }
@@ -331,7 +356,10 @@ cudaError_t launch_query_strings(const QueryView& v, const uint8_t* bytes, const
     uint64_t want = (m + 255) / 256;
     uint64_t cap = (uint64_t)sms * 8;
     unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
-    k_query_strings<<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m);
+    if (v.encoder >= 5)
+        k_query_strings<true><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m);
+    else
+        k_query_strings<false><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -344,7 +372,10 @@ cudaError_t launch_query(const QueryView& v, const uint64_t* keys, uint64_t* out
     uint64_t want = (m / 2 + 255) / 256;
     uint64_t cap = (uint64_t)sms * 8;  // 8 resident blocks of 256 threads per SM
     unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
-    k_query<<<grid, 256, 0, stream>>>(v, keys, out, m);
+    if (v.encoder >= 5)
+        k_query<true><<<grid, 256, 0, stream>>>(v, keys, out, m);
+    else
+        k_query<false><<<grid, 256, 0, stream>>>(v, keys, out, m);
     note_launches(1);
     return cudaGetLastError();
 }
