@@ -298,13 +298,45 @@ phobic_status phobic_get_info(const phobic_handle* h, phobic_info* info);
 /*
  * Serialization (exact words).  With h_buf NULL, *len receives the byte size.
  * Otherwise *len is the buffer capacity on input and the bytes written on
- * output.  Format: a versioned header followed by the packed arrays, all
- * little-endian u64 words.  Synchronises the device.
+ * output.  Synchronises the device.
+ *
+ * Format version 1, little-endian u64 words throughout.  A 28-word header:
+ *   0 magic "PHOBIC01" (0x31304349424F4850)   1 version (1)
+ *   2 n   3 M (table slots, >= n)   4 N_P (partitions)   5 B (buckets per partition)
+ *   6 partition size P   7 lambda (IEEE double bits)   8 alpha (double bits)   9 seed
+ *  10 encoder | bucket_function << 32 | compact_columns << 40
+ *  11 pilot_mode | key_kind << 32 (0: u64 keys, 1: byte strings)
+ *  12 offset width   13 offset slope Q   14 offset minimum (two's complement)
+ *  15 Elias-Fano low bits of the remap
+ *  16..22 word counts of the seven arrays below, in order
+ *  23..27 space in bits: header, offsets, pilots, remap, total
+ * followed by the seven arrays: packed offsets; column metadata (base | width
+ * << 56, one or two words per column as the encoder's documentation above
+ * says); packed values / ranks / low parts; dictionary, or u32 select samples
+ * padded to whole words followed by unary bits; Elias-Fano remap low bits,
+ * high bits and u64 select samples (empty when M = n).  Every packed array ends
+ * with one padding word.  The bucket table is not stored: it follows from
+ * lambda, alpha, P and the bucket function.
  */
 phobic_status phobic_export(const phobic_handle* h, void* h_buf, size_t* len);
 
-/* Rebuilds a handle from phobic_export bytes (FORMAT on malformed input). */
+/* Rebuilds a handle from phobic_export bytes (FORMAT on malformed input, after
+ * the checks of phobic_inspect). */
 phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t stream, phobic_handle** out);
+
+/* Validates phobic_export bytes on the host, without a device, and fills info
+ * as phobic_get_info would for the imported handle (device_bytes: what
+ * phobic_import would allocate).  The checks are those phobic_import makes
+ * before any copy:
+ *   - magic and version;
+ *   - parameters that phobic_build would accept, with N_P and B as they imply;
+ *   - array sizes that add up to len;
+ *   - every metadata entry inside its array;
+ *   - for the unary encoders, each column's unary region holds exactly its
+ *     number of ones, and every select sample is the position of its one.
+ * Errors: FORMAT, INVALID_ARG (info NULL).  Safe on untrusted input: reads
+ * stay within len. */
+phobic_status phobic_inspect(const void* h_buf, size_t len, phobic_info* info);
 
 /* Copies the raw pilot matrix [B x N_P] (pilot of bucket b of partition j at
  * b * N_P + j) to d_out; needs params.keep_pilots at build time (else INVALID_ARG). */

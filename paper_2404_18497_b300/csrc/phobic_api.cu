@@ -1303,13 +1303,35 @@ phobic_status phobic_export(const phobic_handle* h, void* h_buf, size_t* len) {
     return PHOBIC_OK;
 }
 
-phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t stream, phobic_handle** out) {
-    if (!out) return PHOBIC_ERR_INVALID_ARG;
-    *out = nullptr;
+// Host-side validation of phobic_export bytes: every check that the device
+// copies and the query kernels rely on (sizes, metadata inside their arrays,
+// unary regions and select samples).  Fills the parsed parameters and counts.
+struct ParsedExport {
+    phobic_params p;
+    uint64_t n, M, NP, B;
+    uint32_t key_kind;
+    uint64_t counts[7];
+    uint64_t words;
+    uint64_t cmix, rice_sw;
+    bool unary_enc;
+};
+
+// width <= 64 bits at bit o of a packed array; the caller keeps o + width within
+// the array's bits and the array ends with a padding word
+static uint64_t host_bits(const uint64_t* words, uint64_t o, uint32_t width) {
+    if (width == 0) return 0;
+    const uint64_t i = o >> 6;
+    const uint32_t sh = (uint32_t)(o & 63);
+    uint64_t v = words[i] >> sh;
+    if (sh + width > 64) v |= words[i + 1] << (64 - sh);
+    return width == 64 ? v : (v & ((1ull << width) - 1));
+}
+
+static phobic_status parse_export(const void* h_buf, size_t len, ParsedExport* pe) {
     if (!h_buf || len < kHeaderWords * 8 || (len & 7)) return PHOBIC_ERR_FORMAT;
     const uint64_t* w = static_cast<const uint64_t*>(h_buf);
     if (w[0] != kMagic || w[1] != kFormatVersion) return PHOBIC_ERR_FORMAT;
-    phobic_params p;
+    phobic_params& p = pe->p;
     phobic_params_init(&p);
     const uint64_t n = w[2], M = w[3], NP = w[4], B = w[5], P = w[6];
     std::memcpy(&p.lambda, &w[7], 8);
@@ -1325,7 +1347,7 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     if (P != p.partition_size || check_params(n, p) != PHOBIC_OK) return PHOBIC_ERR_FORMAT;
     if (NP != num_partitions(n, p.partition_size) || B != num_buckets(p.lambda, p.partition_size) || M < n)
         return PHOBIC_ERR_FORMAT;
-    uint64_t counts[7];
+    uint64_t* counts = pe->counts;
     uint64_t words = kHeaderWords;
     for (int i = 0; i < 7; i++) {
         counts[i] = w[16 + i];
@@ -1336,6 +1358,30 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     const uint64_t off_w = w[12];
     if (off_w > 64 || w[15] > 63) return PHOBIC_ERR_FORMAT;
     if (counts[0] < packed_words((NP + 1) * off_w)) return PHOBIC_ERR_FORMAT;
+    // offsets: T_j = floor(j Q / 2^32) + dmin + D_j runs from 0 to M without
+    // decreasing, every partition's table below 2^16 slots (as the search
+    // requires), so that a query's slot always lies in [0, M)
+    {
+        const uint64_t* ow = w + kHeaderWords;
+        uint64_t prev = 0;
+        for (uint64_t j = 0; j <= NP; j++) {
+            const uint64_t T = (uint64_t)(((unsigned __int128)j * w[13]) >> 32) + w[14] +
+                               host_bits(ow, j * off_w, (uint32_t)off_w);
+            if (j == 0 ? T != 0 : (T < prev || T - prev >= 65536)) return PHOBIC_ERR_FORMAT;
+            prev = T;
+        }
+        if (prev != M) return PHOBIC_ERR_FORMAT;
+    }
+    // Elias-Fano remap of slots [n, M): its three arrays have the sizes of N = M - n
+    // values with the low-bit count of the build, the high part holds exactly N
+    // ones and every sample is the position of its one
+    if (M > n) {
+        const uint64_t N = M - n, l = w[15];
+        if (l != ((n / N >= 1) ? bitlen64(n / N) - 1 : 0)) return PHOBIC_ERR_FORMAT;
+        const uint64_t hbits = N + (n >> l) + 1;
+        if (counts[4] != packed_words(N * l) || counts[5] != packed_words(hbits) || counts[6] != (N + 63) / 64)
+            return PHOBIC_ERR_FORMAT;
+    }
     // a mono encoder has the layout of its column encoder with one column of B N_P values
     const bool mono = p.encoder >= PHOBIC_ENC_MONO_C;
     const uint32_t enc = mono ? p.encoder - PHOBIC_ENC_MONO_C : p.encoder;
@@ -1391,30 +1437,103 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
             if (ones != nv) return PHOBIC_ERR_FORMAT;
         }
     }
+    // IC-D: every rank addresses a value of its column's dictionary (K values of
+    // dict_width bits from the column's dictionary base up to the next one's)
+    if (enc == PHOBIC_ENC_IC_D) {
+        const uint64_t* meta = w + kHeaderWords + counts[0];
+        const uint64_t* rk = w + kHeaderWords + counts[0] + counts[1];
+        const uint64_t dbits = (counts[3] - 1) * 64;
+        for (uint64_t b = 0; b < ncol; b++) {
+            const uint64_t rm = meta[2 * b], dm = meta[2 * b + 1];
+            const uint32_t rw = (uint32_t)(rm >> 56), dw = (uint32_t)(dm >> 56);
+            const uint64_t db = dm & ((1ull << 56) - 1);
+            const uint64_t de = b + 1 < ncol ? (meta[2 * b + 3] & ((1ull << 56) - 1)) : dbits;
+            if (de < db || de > dbits) return PHOBIC_ERR_FORMAT;
+            if (dw == 0) continue;  // every value is 0: nothing is read
+            const uint64_t K = (de - db) / dw;
+            for (uint64_t j = 0; j < nv; j++)
+                if (host_bits(rk, (rm & ((1ull << 56) - 1)) + j * rw, rw) >= K) return PHOBIC_ERR_FORMAT;
+        }
+    }
+    if (M > n) {
+        const uint64_t N = M - n;
+        const uint64_t hbits = N + (n >> w[15]) + 1;
+        const uint64_t* high = w + kHeaderWords + counts[0] + counts[1] + counts[2] + counts[3] + counts[4];
+        const uint64_t* samp = high + counts[5];
+        uint64_t ones = 0;
+        for (uint64_t bit = 0; bit < hbits; bit++) {
+            if (!((high[bit >> 6] >> (bit & 63)) & 1)) continue;
+            if (ones >= N) return PHOBIC_ERR_FORMAT;
+            if (ones % 64 == 0 && samp[ones / 64] != bit) return PHOBIC_ERR_FORMAT;
+            ones++;
+        }
+        if (ones != N) return PHOBIC_ERR_FORMAT;
+    }
+    pe->n = n;
+    pe->M = M;
+    pe->NP = NP;
+    pe->B = B;
+    pe->key_kind = key_kind;
+    pe->words = words;
+    pe->cmix = cmix;
+    pe->rice_sw = rice_sw;
+    pe->unary_enc = unary_enc;
+    return PHOBIC_OK;
+}
+
+// phobic_info of validated export bytes (no device memory)
+static void info_of_export(const ParsedExport& pe, const uint64_t* w, phobic_info* I) {
+    std::memset(I, 0, sizeof(*I));
+    I->n = pe.n;
+    I->M = pe.M;
+    I->num_partitions = pe.NP;
+    I->num_buckets = (uint32_t)pe.B;
+    I->partition_size = pe.p.partition_size;
+    I->lambda = pe.p.lambda;
+    I->alpha = pe.p.alpha;
+    I->epsilon = eps_of(pe.p.lambda, pe.p.partition_size);
+    I->encoder = pe.p.encoder;
+    I->pilot_mode = pe.p.pilot_mode;
+    I->seed = pe.p.seed;
+    I->bucket_function = pe.p.bucket_function;
+    I->compact_columns = (uint32_t)pe.cmix;
+    I->bits_header = w[23];
+    I->bits_offsets = w[24];
+    I->bits_pilots = w[25];
+    I->bits_remap = w[26];
+    I->bits_total = w[27];
+    I->device_bytes = (kTablePoints + 1) * 8 + 8 * (pe.words - kHeaderWords);
+}
+
+phobic_status phobic_inspect(const void* h_buf, size_t len, phobic_info* out) {
+    if (!out) return PHOBIC_ERR_INVALID_ARG;
+    ParsedExport pe;
+    const phobic_status st = parse_export(h_buf, len, &pe);
+    if (st != PHOBIC_OK) return st;
+    info_of_export(pe, static_cast<const uint64_t*>(h_buf), out);
+    return PHOBIC_OK;
+}
+
+phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t stream, phobic_handle** out) {
+    if (!out) return PHOBIC_ERR_INVALID_ARG;
+    *out = nullptr;
+    ParsedExport pe;
+    {
+        const phobic_status st = parse_export(h_buf, len, &pe);
+        if (st != PHOBIC_OK) return st;
+    }
+    const uint64_t* w = static_cast<const uint64_t*>(h_buf);
+    const phobic_params& p = pe.p;
+    const uint64_t n = pe.n, M = pe.M, NP = pe.NP, B = pe.B, words = pe.words, cmix = pe.cmix, rice_sw = pe.rice_sw;
+    const uint64_t* counts = pe.counts;
+    const uint32_t key_kind = pe.key_kind;
+    const bool unary_enc = pe.unary_enc;
+    const uint64_t off_w = w[12];
     (void)stream;  // the copies below are synchronous
     phobic_handle* h = new (std::nothrow) phobic_handle();
     if (!h) return PHOBIC_ERR_OOM;
     h->prm = p;
-    std::memset(&h->info, 0, sizeof(h->info));
-    phobic_info& I = h->info;
-    I.n = n;
-    I.M = M;
-    I.num_partitions = NP;
-    I.num_buckets = (uint32_t)B;
-    I.partition_size = p.partition_size;
-    I.lambda = p.lambda;
-    I.alpha = p.alpha;
-    I.epsilon = eps_of(p.lambda, p.partition_size);
-    I.encoder = p.encoder;
-    I.pilot_mode = p.pilot_mode;
-    I.seed = p.seed;
-    I.bucket_function = p.bucket_function;
-    I.compact_columns = (uint32_t)cmix;
-    I.bits_header = w[23];
-    I.bits_offsets = w[24];
-    I.bits_pilots = w[25];
-    I.bits_remap = w[26];
-    I.bits_total = w[27];
+    info_of_export(pe, w, &h->info);
     uint64_t** dst[7] = {&h->off_words, &h->col_meta, &h->pil_words, &h->dict_words,
                          &h->ef_low,    &h->ef_high,  &h->ef_samples};
     uint64_t* cnts[7] = {&h->n_off_words, &h->n_col_meta, &h->n_pil_words, &h->n_dict_words,
@@ -1479,7 +1598,6 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     v.small_bits = (h->n_pil_words < (1ull << 26) && h->n_dict_words < (1ull << 26)) ? 1 : 0;
     v.key_kind = key_kind;
     v.string_seed = p.seed;
-    I.device_bytes = (kTablePoints + 1) * 8 + 8 * (words - kHeaderWords);
     *out = h;
     return PHOBIC_OK;
 }

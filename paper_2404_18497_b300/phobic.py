@@ -139,6 +139,7 @@ _SIGS = [
     ("phobic_get_info", _INT, [_VP, ctypes.POINTER(phobic_info)]),
     ("phobic_export", _INT, [_VP, _VP, ctypes.POINTER(ctypes.c_size_t)]),
     ("phobic_import", _INT, [_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    ("phobic_inspect", _INT, [_VP, ctypes.c_size_t, ctypes.POINTER(phobic_info)]),
     ("phobic_copy_pilots", _INT, [_VP, _VP, _VP]),
     ("phobic_get_timings", _INT, [_VP, ctypes.POINTER(phobic_timings)]),
     ("phobic_kernel_launches", _U64, []),
@@ -523,6 +524,16 @@ def phobic_import(data: bytes, stream=None) -> Handle:
     h = ctypes.c_void_p()
     _check(lib().phobic_import(buf, len(data), _stream(stream), ctypes.byref(h)), "phobic_import")
     return Handle(h.value)
+
+
+def phobic_inspect(data: bytes) -> dict:
+    """Validates phobic_export bytes on the host (no device) and returns the
+    info the imported handle would report; raises PhobicError (FORMAT) when
+    phobic_import would refuse them."""
+    buf = ctypes.create_string_buffer(data, len(data))
+    i = phobic_info()
+    _check(lib().phobic_inspect(buf, len(data), ctypes.byref(i)), "phobic_inspect")
+    return {f[0].rstrip("_"): getattr(i, f[0]) for f in phobic_info._fields_}
 
 
 def phobic_copy_pilots(h: Handle, stream=None) -> torch.Tensor:

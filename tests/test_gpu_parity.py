@@ -229,6 +229,29 @@ def test_mono_encoder_parity(ph, orc, enc):
         h.free()
 
 
+@pytest.mark.parametrize("enc", list(range(9)))
+def test_import_of_oracle_written_files(ph, orc, enc):
+    """A structure the library never built: the oracle's arrays written in the
+    documented export layout.  Imported, the GPU query path answers every key
+    (and non-members) exactly as the oracle does, and exports the same bytes."""
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.dirname(__file__))
+    from oracle_export import oracle_export
+
+    keys = _keys(300_000 + enc, 120 + enc)
+    others = _keys(50_000, 999)
+    for alpha, mode, P in [(0.99, 0, 2500), (1.0, 1, 1000), (0.95, 0, 4096)]:
+        o = orc.Oracle(keys, lam=7.0, alpha=alpha, P=P, encoder=enc, mode=mode, compact_columns=9, seed=4, threads=0)
+        data = oracle_export(o)
+        h = ph.phobic_import(data)
+        assert np.array_equal(_host(h.query(_dev(keys))), o.query(keys))
+        assert np.array_equal(_host(h.query(_dev(others))), o.query(others))
+        assert ph.phobic_export(h) == data
+        h.free()
+
+
 def test_query_unaligned_and_odd_lengths(ph, orc):
     keys = _keys(30_001, 4)
     o = orc.Oracle(keys, lam=6.0, P=500, threads=0)
