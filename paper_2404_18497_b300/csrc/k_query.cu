@@ -63,6 +63,25 @@ __device__ __forceinline__ uint32_t div_u32(uint32_t p, uint32_t m) {
     return q;
 }
 
+// Position of the r-th (0-based) set bit of w, which has more than r set bits:
+// a binary search over halves, quarters, ... by popcount, in six fixed steps
+// (no loop whose length depends on r, so the lanes of a warp stay together)
+__device__ __forceinline__ uint32_t select_in_word(uint64_t w, uint32_t r) {
+    uint32_t pos = 0, c;
+    c = __popc((uint32_t)w);
+    if (r >= c) { r -= c; w >>= 32; pos += 32; }
+    c = __popc((uint32_t)w & 0xFFFFu);
+    if (r >= c) { r -= c; w >>= 16; pos += 16; }
+    c = __popc((uint32_t)w & 0xFFu);
+    if (r >= c) { r -= c; w >>= 8; pos += 8; }
+    c = __popc((uint32_t)w & 0xFu);
+    if (r >= c) { r -= c; w >>= 4; pos += 4; }
+    c = __popc((uint32_t)w & 0x3u);
+    if (r >= c) { r -= c; w >>= 2; pos += 2; }
+    if (r >= ((uint32_t)w & 1u)) pos += 1;
+    return pos;
+}
+
 // i-th value of the Elias-Fano sequence
 __device__ __forceinline__ uint64_t ef_access(const QueryView& v, uint64_t i) {
     uint64_t pos = __ldg(v.ef_samples + (i >> 6));
@@ -75,8 +94,7 @@ __device__ __forceinline__ uint64_t ef_access(const QueryView& v, uint64_t i) {
         need -= c;
         w = __ldg(v.ef_high + ++wi);
     }
-    for (uint32_t t = 0; t < need; t++) w &= w - 1;
-    uint64_t one = wi * 64 + (__ffsll((long long)w) - 1);
+    uint64_t one = wi * 64 + select_in_word(w, need);
     uint64_t low = read_bits(v.ef_low, i * v.ef_l, v.ef_l);
     return ((one - i) << v.ef_l) | low;
 }
@@ -122,8 +140,7 @@ __device__ __forceinline__ void unary_pair(const QueryView& v, uint32_t sc, uint
                 need -= cnt;
                 w = __ldg(high + ++wi);
             }
-            for (uint32_t t = 1; t < need; t++) w &= w - 1;
-            a = wi * 64 + (uint64_t)(__ffsll((long long)w) - 1);
+            a = wi * 64 + select_in_word(w, need - 1);
         }
         c = next_one(high, a + 1);
     }
