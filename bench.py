@@ -107,7 +107,7 @@ NCU_CAPTURES = {
                  "sha": "a3fcd6292c8f63e3", "n": 3e7, "warp_inst": 2110900855, "dram_bytes": 546543872 + 304698880,
                  "profile": "profiles/k_search_3e7.md"},
     "k_query": {"files": ["paper_2404_18497_b300/csrc/k_query.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-                "sha": "b0936cd21dc9e33f", "n": 3e7, "dram_bytes": 249967616 + 197720832,
+                "sha": "610b1261bfb50dd2", "n": 3e7, "dram_bytes": 249899520 + 197058560,
                 "profile": "profiles/k_query_3e7.md"},
     "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
                "sha": "8daadf6e1492f064", "n": 3e7, "dram_bytes": 243487744 + 197852672 + 243296000 + 196688640,
