@@ -954,6 +954,7 @@ def run_strings(a):
     torch.cuda.synchronize()
     clk = Clocks(0)
     clk.start()
+    l0 = phobic.phobic_kernel_launches()
     bms, qms, phases = [], [], []
     for _ in range(a.steps):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -969,6 +970,7 @@ def run_strings(a):
         bpk = h.bits_per_key()
         h.free()
     clocks = clk.stop()
+    launches = phobic.phobic_kernel_launches() - l0
     perm_ok = bool(torch.equal(torch.sort(out).values, torch.arange(n, device="cuda")))
     b_ms, q_ms = statistics.mean(bms), statistics.mean(qms)
     ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
@@ -985,8 +987,10 @@ def run_strings(a):
         "phase_ms": ph, "result_is_permutation": perm_ok, "clocks": clocks,
         "roofline": {"bound": "hbm", "kernel": "k_query_strings", "unit": "GB/s", "peak": hbm,
                      "achieved": (str_bytes + 8.0 * n) / (q_ms / 1e3) / 1e9,
-                     "algorithmic_bytes_per_launch": str_bytes + 8.0 * n, "peak_source": f"{src} hbm_gbs"},
-        "e2e": None, "gpu_launches": None, "cpu_baseline": None}))
+                     "frac": (str_bytes + 8.0 * n) / (q_ms / 1e3) / 1e9 / hbm,
+                     "algorithmic_bytes_per_launch": str_bytes + 8.0 * n, "peak_source": f"{src} hbm_gbs",
+                     "profile": "profiles/k_hash_strings_2e7.md"},
+        "e2e": None, "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps, "cpu_baseline": None}))
 
 
 def run_only(a):
