@@ -335,7 +335,9 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
  *   - for the unary encoders, each column's unary region holds exactly its
  *     number of ones, and every select sample is the position of its one.
  * Errors: FORMAT, INVALID_ARG (info NULL).  Safe on untrusted input: reads
- * stay within len. */
+ * stay within len, and the work is linear in len (checks whose loops the file
+ * does not pay for in bits, such as zero-width offsets or ranks, are made in
+ * closed form). */
 phobic_status phobic_inspect(const void* h_buf, size_t len, phobic_info* info);
 
 /* Copies the raw pilot matrix [B x N_P] (pilot of bucket b of partition j at

@@ -1361,7 +1361,14 @@ static phobic_status parse_export(const void* h_buf, size_t len, ParsedExport* p
     // offsets: T_j = floor(j Q / 2^32) + dmin + D_j runs from 0 to M without
     // decreasing, every partition's table below 2^16 slots (as the search
     // requires), so that a query's slot always lies in [0, M)
-    {
+    // (width 0: every D_j = 0, so T_j = floor(j Q / 2^32) + dmin is checked in
+    // closed form; otherwise the N_P + 1 stored values, which the file holds)
+    if (off_w == 0) {
+        const uint64_t Q = w[13];
+        const uint64_t step = (Q >> 32) + ((Q & 0xFFFFFFFFull) ? 1 : 0);  // largest T_{j+1} - T_j
+        if (w[14] != 0 || step >= 65536 || (uint64_t)(((unsigned __int128)NP * Q) >> 32) != M)
+            return PHOBIC_ERR_FORMAT;
+    } else {
         const uint64_t* ow = w + kHeaderWords;
         uint64_t prev = 0;
         for (uint64_t j = 0; j <= NP; j++) {
@@ -1451,6 +1458,8 @@ static phobic_status parse_export(const void* h_buf, size_t len, ParsedExport* p
             if (de < db || de > dbits) return PHOBIC_ERR_FORMAT;
             if (dw == 0) continue;  // every value is 0: nothing is read
             const uint64_t K = (de - db) / dw;
+            if (K == 0) return PHOBIC_ERR_FORMAT;
+            if (rw == 0) continue;  // every rank is 0 (and the ranks take no bits of the file)
             for (uint64_t j = 0; j < nv; j++)
                 if (host_bits(rk, (rm & ((1ull << 56) - 1)) + j * rw, rw) >= K) return PHOBIC_ERR_FORMAT;
         }

@@ -125,6 +125,32 @@ def test_corrupt_files_are_refused(ph, orc):
     bad = w.copy(); bad[nz] &= bad[nz] - np.uint64(1); _refused(ph, bad)
 
 
+def test_inspection_work_is_linear_in_the_file(ph, orc):
+    """A header may claim any number of keys; checks whose loops the file does
+    not pay for in bits (zero-width offsets, widths and ranks) are made in
+    closed form, so a tiny file claiming 2^40 keys is answered at once."""
+    import time
+
+    # one partition: every offset difference is 0, so the offsets have width 0
+    o = orc.Oracle(_keys(1_500, 95), lam=7.0, alpha=1.0, P=2500, encoder=0, threads=1)
+    w = _words(oracle_export(o))
+    assert w[12] == 0 and w[4] == 1
+    ph.phobic_inspect(w.tobytes())
+    bad = w.copy(); bad[13] += np.uint64(1 << 32); _refused(ph, bad)  # T_{N_P} != M in closed form
+    # the same file claiming 2^40 keys in 2^40 / 2500 partitions, every width 0
+    P, NP = 2500, (1 << 40) // 2500
+    big = w.copy()
+    big[2] = big[3] = NP * P          # n = M
+    big[4] = NP
+    big[13] = P << 32                 # Q: T_j = j P exactly
+    at = _offsets(big)
+    big[at[1]:at[2]] &= np.uint64((1 << 56) - 1)  # every column width 0
+    t = time.time()
+    info = ph.phobic_inspect(big.tobytes())  # a valid, degenerate structure: every pilot 0
+    assert time.time() - t < 1.0
+    assert info["n"] == NP * P and info["num_partitions"] == NP
+
+
 def test_fileinfo_tool(ph, orc, tmp_path, capsys):
     from paper_2404_18497_b300 import fileinfo
 
