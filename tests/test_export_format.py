@@ -151,6 +151,44 @@ def test_inspection_work_is_linear_in_the_file(ph, orc):
     assert info["n"] == NP * P and info["num_partitions"] == NP
 
 
+def test_inspection_survives_random_corruption(ph, orc):
+    """Random corruptions of valid files (bit flips anywhere, random words,
+    truncations, header fields) are each accepted or refused with FORMAT, and
+    never crash the process: the checks read only inside the buffer."""
+    rng = np.random.default_rng(2024)
+    keys = _keys(20_000, 97)
+    files = []
+    for enc, alpha in ((1, 0.97), (2, 0.97), (3, 1.0), (4, 0.97), (6, 0.97), (7, 1.0), (8, 0.97), (0, 0.97)):
+        o = orc.Oracle(keys, lam=6.5, alpha=alpha, P=1000, encoder=enc, compact_columns=7, threads=4)
+        files.append(_words(oracle_export(o)))
+    outcomes = {"OK": 0, "FORMAT": 0}
+    for w in files:
+        for t in range(250):
+            bad = w.copy()
+            kind = t % 5
+            if kind == 0:  # flip one bit anywhere
+                i = int(rng.integers(0, bad.size))
+                bad[i] ^= np.uint64(1 << int(rng.integers(0, 64)))
+            elif kind == 1:  # a random word anywhere
+                bad[int(rng.integers(0, bad.size))] = rng.integers(0, 2**64, dtype=np.uint64)
+            elif kind == 2:  # a header field set to a random small or huge value
+                i = int(rng.integers(2, 28))
+                bad[i] = np.uint64(int(rng.integers(0, 1 << 20)) if t % 2 else int(rng.integers(0, 2**63)))
+            elif kind == 3:  # truncated
+                bad = bad[: int(rng.integers(0, bad.size))]
+            else:  # several bit flips in the arrays
+                for _ in range(8):
+                    i = int(rng.integers(28, bad.size))
+                    bad[i] ^= np.uint64(1 << int(rng.integers(0, 64)))
+            try:
+                ph.phobic_inspect(bad.tobytes())
+                outcomes["OK"] += 1
+            except ph.PhobicError as e:
+                assert e.status == "FORMAT"
+                outcomes["FORMAT"] += 1
+    assert outcomes["FORMAT"] > 1000  # most corruptions are caught
+
+
 def test_fileinfo_tool(ph, orc, tmp_path, capsys):
     from paper_2404_18497_b300 import fileinfo
 
