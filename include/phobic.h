@@ -166,7 +166,8 @@ void phobic_params_init(phobic_params* p);
  * The call returns after the device work finishes (the structure's sizes
  * depend on device results), so it synchronises `stream`.
  * Errors: INVALID_ARG for n = 0, NULL pointers, lambda <= 0, alpha outside (0,1],
- * P = 0 or P > 16384; DUP_HASH for duplicate keys; SEARCH_LIMIT; OOM; CUDA.
+ * P = 0, P > 16384 or P < lambda (a partition smaller than one average bucket);
+ * DUP_HASH for duplicate keys; SEARCH_LIMIT; OOM; CUDA.
  */
 phobic_status phobic_build(const uint64_t* d_keys, uint64_t n, double lambda, double alpha,
                            uint32_t partition_size, uint64_t seed, phobic_stream_t stream,

@@ -352,6 +352,7 @@ static int check_params(uint64_t n, const or_params* p) {
     if (!(p->lambda > 0.0) || !isfinite(p->lambda)) return OR_ERR_INVALID_ARG;
     if (!(p->alpha > 0.0) || p->alpha > 1.0) return OR_ERR_INVALID_ARG;
     if (p->partition_size == 0) return OR_ERR_INVALID_ARG;
+    if ((double)p->partition_size < p->lambda) return OR_ERR_INVALID_ARG; /* P below one average bucket */
     if (p->encoder > OR_ENC_MONO_EF || p->pilot_mode > OR_PILOT_XOR) return OR_ERR_INVALID_ARG;
     if (p->bucket_fn > OR_BUCKET_UNIFORM) return OR_ERR_INVALID_ARG;
     return OR_OK;

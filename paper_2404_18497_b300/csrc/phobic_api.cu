@@ -263,6 +263,7 @@ phobic_status check_params(uint64_t n, const phobic_params& p) {
     if (!(p.lambda > 0.0) || !std::isfinite(p.lambda)) return PHOBIC_ERR_INVALID_ARG;
     if (!(p.alpha > 0.0) || p.alpha > 1.0) return PHOBIC_ERR_INVALID_ARG;
     if (p.partition_size == 0 || p.partition_size > kMaxPartitionSize) return PHOBIC_ERR_INVALID_ARG;
+    if ((double)p.partition_size < p.lambda) return PHOBIC_ERR_INVALID_ARG;  // fewer keys than one bucket
     if (p.encoder > PHOBIC_ENC_MONO_EF || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
     if (p.compact_columns >= (1u << 24)) return PHOBIC_ERR_INVALID_ARG;
     if (p.warps_per_partition != 0 && p.warps_per_partition != 1 && p.warps_per_partition != 2 &&

@@ -320,7 +320,7 @@ def test_errors(ph):
         with pytest.raises(ph.PhobicError) as e:
             ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, 1.0, 2500, warps_per_partition=wpp))
         assert e.value.status == "INVALID_ARG"
-    for kw in [dict(lam=0.0), dict(alpha=0.0), dict(alpha=1.5), dict(P=0), dict(P=100_000)]:
+    for kw in [dict(lam=0.0), dict(alpha=0.0), dict(alpha=1.5), dict(P=0), dict(P=100_000), dict(lam=9.0, P=8)]:
         args = dict(lam=7.0, alpha=1.0, P=2500)
         args.update(kw)
         with pytest.raises(ph.PhobicError) as e:

@@ -309,7 +309,7 @@ def test_errors(orc):
     with pytest.raises(orc.OracleError) as e:
         orc.Oracle(np.concatenate([keys, keys[:1]]), lam=5.0)
     assert e.value.code == orc.DUP_HASH
-    for kw in [dict(lam=0.0), dict(alpha=0.0), dict(alpha=1.5), dict(P=0)]:
+    for kw in [dict(lam=0.0), dict(alpha=0.0), dict(alpha=1.5), dict(P=0), dict(lam=9.0, P=8)]:
         with pytest.raises(orc.OracleError) as e:
             orc.Oracle(keys, **kw)
         assert e.value.code == orc.INVALID_ARG
