@@ -207,9 +207,10 @@ phobic_status phobic_build_batch(const uint64_t* d_keys, const uint64_t* h_set_o
  * process per device and (lambda, alpha, encoder, pilot_mode, s_max): per size
  * class for P, per power of two of the partition count for the search knobs.
  * The trials allocate device memory (keys for up to about 2^25 + one set) and
- * synchronize `stream`.  Errors: INVALID_ARG, OOM, CUDA, and any build error of
- * a trial.  Results of builds made with the outputs are exact PHOBIC
- * constructions with the chosen partition sizes.
+ * synchronize `stream`.  Partition sizes below lambda are never tried (lambda
+ * above 4096 leaves none: INVALID_ARG).  Errors: INVALID_ARG, OOM, CUDA, and any
+ * build error of a trial.  Results of builds made with the outputs are exact
+ * PHOBIC constructions with the chosen partition sizes.
  */
 #define PHOBIC_TUNE_P_CHOICES 3
 #define PHOBIC_TUNE_MAX_CLASSES 20

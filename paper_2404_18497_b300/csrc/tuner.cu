@@ -165,6 +165,9 @@ extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32
         return PHOBIC_ERR_INVALID_ARG;
     for (uint32_t s = 0; s < n_sets; s++)
         if (h_set_offsets[s + 1] <= h_set_offsets[s]) return PHOBIC_ERR_INVALID_ARG;
+    // a candidate partition size below lambda is not a valid build; none left: refuse
+    if (!(params->lambda > 0.0) || params->lambda > (double)kPChoices[PHOBIC_TUNE_P_CHOICES - 1])
+        return PHOBIC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PHOBIC_ERR_CUDA;
@@ -203,6 +206,10 @@ extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32
                 double sec = 0, bits = 0;
                 phobic_params p = base;
                 p.partition_size = kPChoices[i];
+                if ((double)kPChoices[i] < p.lambda) {  // never picked
+                    cr.ns_per_key[i] = cr.bits_per_key[i] = INFINITY;
+                    continue;
+                }
                 std::vector<uint32_t> Ps(sizes.size(), kPChoices[i]);
                 phobic_status s = time_build(sizes, Ps, p, st, &sec, &bits);
                 if (s != PHOBIC_OK) return s;

@@ -115,6 +115,9 @@ def test_invalid_arguments_without_gpu(libpath):
     off = (ctypes.c_uint64 * 3)(0, 5, 5)  # an empty set
     assert L.phobic_tune_batch(off, 2, ctypes.byref(p), None, ps, ctypes.byref(out), None) == 1
     assert L.phobic_tune_batch(None, 2, ctypes.byref(p), None, ps, ctypes.byref(out), None) == 1
+    big = phobic.make_params(5000.0, 1.0, 8192)  # every candidate partition size is below lambda
+    off2 = (ctypes.c_uint64 * 2)(0, 100)
+    assert L.phobic_tune_batch(off2, 1, ctypes.byref(big), None, ps, ctypes.byref(out), None) == 1
     # parameters are checked before the key pointer is used (a stand-in address here)
     small = phobic.make_params(9.0, 1.0, 8)  # P below lambda
     assert L.phobic_build_ex(ctypes.c_void_p(256), 100, ctypes.byref(small), None, ctypes.byref(h)) == 1
