@@ -168,6 +168,9 @@ void phobic_params_init(phobic_params* p);
  * Errors: INVALID_ARG for n = 0, NULL pointers, lambda <= 0, alpha outside (0,1],
  * P = 0, P > 16384 or P < lambda (a partition smaller than one average bucket);
  * DUP_HASH for duplicate keys; SEARCH_LIMIT; OOM; CUDA.
+ * The environment variable PHOBIC_KEYS_IN_SMEM=1 makes the search keep each
+ * partition's keys in shared memory instead of a bucket-sorted scratch array in
+ * global memory (slower on this hardware; the results are the same).
  */
 phobic_status phobic_build(const uint64_t* d_keys, uint64_t n, double lambda, double alpha,
                            uint32_t partition_size, uint64_t seed, phobic_stream_t stream,

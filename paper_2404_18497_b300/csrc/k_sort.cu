@@ -305,10 +305,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     }
 }
 
+// master hashes (or a copy) of n keys: 16-byte loads and stores of key pairs
+// when both arrays are 16-byte aligned, streaming past the caches
 __global__ void k_hash_copy(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t n, uint64_t kseed,
                             int hash_input) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = load_hk(in, i, kseed, hash_input);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0) {
+        const ulonglong2* in2 = reinterpret_cast<const ulonglong2*>(in);
+        ulonglong2* out2 = reinterpret_cast<ulonglong2*>(out);
+        for (uint64_t i = t0; i < n / 2; i += stride) {
+            ulonglong2 v = __ldcs(in2 + i);
+            if (hash_input) {
+                v.x = key_hash(v.x, kseed);
+                v.y = key_hash(v.y, kseed);
+            }
+            __stcs(out2 + i, v);
+        }
+        if ((n & 1) && t0 == 0) out[n - 1] = load_hk(in, n - 1, kseed, hash_input);
+    } else {
+        for (uint64_t i = t0; i < n; i += stride) out[i] = load_hk(in, i, kseed, hash_input);
+    }
 }
 
 // start[part_base_s + j] = first index of partition j of segment s in the

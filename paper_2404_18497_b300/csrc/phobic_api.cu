@@ -6,8 +6,10 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/phobic.h"
@@ -69,6 +71,27 @@ void make_table(double lambda, double alpha, uint32_t P, uint64_t* t, uint32_t f
         if (r > 4294967296LL) r = 4294967296LL;
         t[k] = (uint64_t)r;
     }
+}
+
+// The table of a parameter set, computed once per process (2049 evaluations of
+// gamma take tens of microseconds, and builds repeat their parameters)
+void cached_table(double lambda, double alpha, uint32_t P, uint32_t fn, uint64_t* t) {
+    static std::mutex mu;
+    static std::map<std::tuple<double, double, uint32_t, uint32_t>, std::vector<uint64_t>> cache;
+    const auto key = std::make_tuple(lambda, alpha, P, fn);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            std::memcpy(t, it->second.data(), it->second.size() * 8);
+            return;
+        }
+    }
+    std::vector<uint64_t> v(kTablePoints + 1);
+    make_table(lambda, alpha, P, v.data(), fn);
+    std::memcpy(t, v.data(), v.size() * 8);
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache.size() < 4096) cache.emplace(key, std::move(v));
 }
 
 uint32_t num_buckets(double lambda, uint32_t P) {
@@ -357,8 +380,8 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     const uint32_t ntab = (uint32_t)table_P.size();
     std::vector<uint64_t> tables((size_t)ntab * (kTablePoints + 1));
     for (uint32_t t = 0; t < ntab; t++)
-        make_table(prm.lambda, prm.alpha, table_P[t], tables.data() + (size_t)t * (kTablePoints + 1),
-                   prm.bucket_function);
+        cached_table(prm.lambda, prm.alpha, table_P[t], prm.bucket_function,
+                     tables.data() + (size_t)t * (kTablePoints + 1));
 
     PinnedBuf pin;
     CK(pin.alloc(4096 + (size_t)S * 48 + (size_t)cols_total * 12));

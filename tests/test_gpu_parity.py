@@ -81,6 +81,14 @@ def test_master_hash_parity(ph, orc):
     for seed in (0, 1, 0xDEADBEEF):
         got = _host(ph.phobic_hash_u64(_dev(keys), seed))
         assert (got == orc.key_hash(keys, seed)).all()
+    # 8- but not 16-byte aligned input and output (the kernel's scalar path), odd and tiny lengths
+    buf = torch.zeros(keys.size + 1, dtype=torch.int64, device="cuda")
+    buf[1:] = _dev(keys)
+    out = torch.zeros(keys.size + 1, dtype=torch.int64, device="cuda")
+    ph.phobic_hash_u64(buf[1:], 5, out[1:])
+    assert (_host(out[1:]) == orc.key_hash(keys, 5)).all()
+    for m in (1, 2, 3):
+        assert (_host(ph.phobic_hash_u64(_dev(keys[:m]), 5)) == orc.key_hash(keys[:m], 5)).all()
 
 
 def test_string_hash_parity(ph, orc):
