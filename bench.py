@@ -110,8 +110,11 @@ NCU_CAPTURES = {
                 "sha": "610b1261bfb50dd2", "n": 3e7, "dram_bytes": 249899520 + 197058560,
                 "profile": "profiles/k_query_3e7.md"},
     "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "8daadf6e1492f064", "n": 3e7, "dram_bytes": 243487744 + 197852672 + 243296000 + 196688640,
+               "sha": "0df6eed68fdd282c", "n": 3e7, "dram_bytes": 243519744 + 198288896 + 243346432 + 196616448,
                "profile": "profiles/k_sort_pass_3e7.md"},
+    "k_hash": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
+               "sha": "0df6eed68fdd282c", "n": 3e7, "dram_bytes": 240023040 + 192200704,
+               "profile": "profiles/k_hash_copy_3e7.md"},
 }
 ISSUE_SLOTS_PER_CLOCK = 148 * 4  # B300: 148 SMs x 4 warp schedulers, one warp instruction per clock each
 SM_MAX_MHZ = 2032.0
@@ -423,6 +426,8 @@ def run_ours(a):
                         "kernel": "k_hash_copy (phobic_hash_u64, 16-byte loads and stores)", "launch_ms": hash_ms,
                         "algorithmic_bytes_per_launch": 16.0 * n}
     roofline["hash"]["frac"] = roofline["hash"]["achieved"] / hbm
+    chh = capture("k_hash")
+    roofline["hash"]["traffic"] = (chh["dram_bytes"] / chh["n"] * n) if chh else None
     build_bytes = 8.3 * n
     roofline["build"] = {"bound": "hbm", "achieved": build_bytes / (b_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                          "kernel": "whole build", "algorithmic_bytes_per_launch": build_bytes}
