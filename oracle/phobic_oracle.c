@@ -29,8 +29,9 @@
  *
  * Readings where the paper is silent (hash functions, rounding of B and m_j,
  * bit layouts, bits/key accounting) follow one fixed written spec.  The CUDA
- * library implements the same spec independently.  The hash finaliser and
- * constants are "parity unpinned": nothing in the paper fixes them.
+ * library implements the same spec independently.  The hash constants are
+ * "parity unpinned": nothing in the paper fixes them (the mixer itself is
+ * SplitMix64's output function, pinned to that generator's known outputs).
  *
  * Floating point appears only in building the bucket table and in
  * ceil(n_j / alpha).  Compile with -ffp-contract=off so that no fused

@@ -225,8 +225,20 @@ def _unmix64(z: int) -> int:
     return unxorshift(z, 30)
 
 
+def test_mix64_is_splitmix64(orc):
+    """The 64-bit mixer is SplitMix64's output function: the generator's
+    published first outputs from state 0 (tests/golden/splitmix64_state0.json)."""
+    with open(os.path.join(GOLDEN, "splitmix64_state0.json")) as f:
+        g = json.load(f)
+    gamma = int(g["gamma"], 16)
+    L = orc.lib()
+    for k, want in enumerate(g["outputs"], 1):
+        assert L.or_mix64((k * gamma) % 2**64) == int(want, 16), k
+
+
 def test_mix64_is_bijective_and_avalanches(orc):
-    """parity unpinned (a hash choice): pinned by invertibility and avalanche"""
+    """the key, bucket and pilot hashes (own constants around SplitMix64's mixer):
+    invertibility and avalanche"""
     L = orc.lib()
     rng = np.random.default_rng(7)
     for x in rng.integers(0, 2**64, size=200, dtype=np.uint64):
