@@ -236,6 +236,14 @@ def test_mix64_is_splitmix64(orc):
         assert L.or_mix64((k * gamma) % 2**64) == int(want, 16), k
 
 
+def test_xxh64_of_the_empty_input(orc):
+    """XXH64's known answer for the empty input (tests/golden/xxh64_empty.json)."""
+    with open(os.path.join(GOLDEN, "xxh64_empty.json")) as f:
+        g = json.load(f)
+    h = orc.string_hashes(np.zeros(8, dtype=np.uint8), np.array([0, 0], dtype=np.uint64), g["seed"])
+    assert int(h[0]) == int(g["hash"], 16)
+
+
 def test_mix64_is_bijective_and_avalanches(orc):
     """the key, bucket and pilot hashes (own constants around SplitMix64's mixer):
     invertibility and avalanche"""
