@@ -626,6 +626,9 @@ def run_batch(a, phobic, workloads, torch):
                   "ns_per_key_by_decade": {f"1e{c}": ci["ns_per_key"] for c, ci in tinfo["classes"].items()},
                   "warps_per_partition": tinfo["warps_per_partition"], "candidate_width": tinfo["candidate_width"],
                   "launch_ns_per_key": tinfo["launch_ns_per_key"], "total_partitions": tinfo["total_partitions"],
+                  "search_schedule": {1: "one CTA per partition", 2: "persistent CTAs over the work queue"}.get(
+                      tinfo["search_schedule"], tinfo["search_schedule"]),
+                  "schedule_ns_per_key": tinfo["schedule_ns_per_key"],
                   "tune_s": tune_s, "tune_cached_s": tune_cached_s,
                   "cached_second_call": bool(tinfo2["cached_launch"])},
         "l2": "inputs larger than L2 (35.6 GB of keys vs 126 MB L2)",

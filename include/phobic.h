@@ -203,9 +203,11 @@ phobic_status phobic_build_batch(const uint64_t* d_keys, const uint64_t* h_set_o
  * current device: the expected partition size of every set, one of 1024, 2500,
  * 4096, per decade size class (the fastest, or within 3% of it the one with the
  * fewest bits per key); and warps_per_partition (1, 2, 4) and candidate_width
- * (32, 64) for the launch.  h_set_offsets as for phobic_build_batch (only the
- * sizes are read; no key is read).  Outputs: h_partition_sizes_out[n_sets],
- * *params_out = *params with the two search knobs set and search_schedule = 2;
+ * (32, 64) for the launch, then with those the search schedule (one CTA per
+ * partition, or persistent CTAs over the device work queue).  h_set_offsets as
+ * for phobic_build_batch (only the sizes are read; no key is read).  Outputs:
+ * h_partition_sizes_out[n_sets], *params_out = *params with the three search
+ * knobs set;
  * *info (may be NULL) reports the measurements.  Decisions are cached for the
  * process per device and (lambda, alpha, encoder, pilot_mode, s_max): per size
  * class for P, per power of two of the partition count for the search knobs.
@@ -231,6 +233,8 @@ typedef struct {
     uint64_t total_partitions;  /* of the batch with the chosen sizes */
     uint32_t cached_classes;    /* classes answered from the cache */
     uint32_t cached_launch;     /* 1: search knobs answered from the cache */
+    uint32_t search_schedule;   /* chosen: 1 one CTA per partition, 2 persistent CTAs over the work queue */
+    float schedule_ns_per_key[2]; /* trial time per key of schedules 1 and 2 with the chosen warps and width */
 } phobic_tune_info;
 phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32_t n_sets, const phobic_params* params,
                                 phobic_stream_t stream, uint32_t* h_partition_sizes_out,

@@ -70,8 +70,9 @@ struct ClassResult {
     float bits_per_key[PHOBIC_TUNE_P_CHOICES];
 };
 struct LaunchResult {
-    uint32_t warps, width;
+    uint32_t warps, width, schedule;
     float ns_per_key[6];
+    float schedule_ns_per_key[2];  // one CTA per partition, the work queue (chosen warps and width)
 };
 
 std::mutex g_mu;
@@ -277,6 +278,19 @@ extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32
                 }
                 k++;
             }
+        // the schedule, with the chosen knobs: one CTA per partition (1) or the
+        // persistent CTAs over the device work queue (2); the faster one is kept
+        for (int sc = 0; sc < 2; sc++) {
+            phobic_params p = base;
+            p.warps_per_partition = lr.warps;
+            p.candidate_width = lr.width;
+            p.search_schedule = sc + 1;
+            double sec = 0, bits = 0;
+            phobic_status s = time_build(sizes, Ps, p, st, &sec, &bits);
+            if (s != PHOBIC_OK) return s;
+            lr.schedule_ns_per_key[sc] = (float)(sec * 1e9 / (double)tot);
+        }
+        lr.schedule = lr.schedule_ns_per_key[0] < lr.schedule_ns_per_key[1] ? 1 : 2;
         it = g_launch.emplace(std::make_pair(pk, lk), lr).first;
     } else if (info) {
         info->cached_launch = 1;
@@ -284,10 +298,13 @@ extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32
     *params_out = *params;
     params_out->warps_per_partition = it->second.warps;
     params_out->candidate_width = it->second.width;
-    params_out->search_schedule = 2;
+    params_out->search_schedule = it->second.schedule;
     if (info) {
         info->warps_per_partition = it->second.warps;
         info->candidate_width = it->second.width;
+        info->search_schedule = it->second.schedule;
+        info->schedule_ns_per_key[0] = it->second.schedule_ns_per_key[0];
+        info->schedule_ns_per_key[1] = it->second.schedule_ns_per_key[1];
         for (int i = 0; i < 6; i++) info->launch_ns_per_key[i] = it->second.ns_per_key[i];
         info->total_partitions = total_parts;
     }

@@ -120,7 +120,8 @@ class phobic_tune_info(ctypes.Structure):
     _fields_ = [("classes", phobic_tune_class * TUNE_MAX_CLASSES),
                 ("warps_per_partition", ctypes.c_uint32), ("candidate_width", ctypes.c_uint32),
                 ("launch_ns_per_key", ctypes.c_float * 6), ("total_partitions", ctypes.c_uint64),
-                ("cached_classes", ctypes.c_uint32), ("cached_launch", ctypes.c_uint32)]
+                ("cached_classes", ctypes.c_uint32), ("cached_launch", ctypes.c_uint32),
+                ("search_schedule", ctypes.c_uint32), ("schedule_ns_per_key", ctypes.c_float * 2)]
 
 
 _VP, _U64, _U32, _DBL, _INT = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_int
@@ -331,7 +332,9 @@ def phobic_tune_batch(set_offsets, params: phobic_params, stream=None):
     d = dict(classes=classes, warps_per_partition=info.warps_per_partition, candidate_width=info.candidate_width,
              launch_ns_per_key={f"w{w}/c{cw}": float(v) for (w, cw), v in zip(combos, info.launch_ns_per_key)},
              total_partitions=int(info.total_partitions), cached_classes=info.cached_classes,
-             cached_launch=info.cached_launch)
+             cached_launch=info.cached_launch, search_schedule=info.search_schedule,
+             schedule_ns_per_key={"cta_per_partition": float(info.schedule_ns_per_key[0]),
+                                  "work_queue": float(info.schedule_ns_per_key[1])})
     return ps, pout, d
 
 

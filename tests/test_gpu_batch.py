@@ -61,7 +61,10 @@ def test_tuner_choices_cache_and_exactness(ph, orc):
     ph.phobic_tune_clear()
     Ps, p2, info = ph.phobic_tune_batch(off, prm)
     assert set(Ps.tolist()) <= {1024, 2500, 4096}
-    assert p2.warps_per_partition in (1, 2, 4) and p2.candidate_width in (32, 64) and p2.search_schedule == 2
+    assert p2.warps_per_partition in (1, 2, 4) and p2.candidate_width in (32, 64)
+    # the schedule: the faster of one CTA per partition (1) and the work queue (2)
+    sn = info["schedule_ns_per_key"]
+    assert p2.search_schedule == (1 if sn["cta_per_partition"] < sn["work_queue"] else 2) == info["search_schedule"]
     assert p2.lambda_ == prm.lambda_ and p2.alpha == prm.alpha and p2.encoder == 1 and p2.keep_pilots == 1
     for s in range(sizes.size):
         assert Ps[s] == info["classes"][_decade(sizes[s])]["partition_size"]
@@ -72,7 +75,8 @@ def test_tuner_choices_cache_and_exactness(ph, orc):
     # a second call is answered from the cache with the same choices
     Ps2, p3, info2 = ph.phobic_tune_batch(off, prm)
     assert np.array_equal(Ps, Ps2)
-    assert (p3.warps_per_partition, p3.candidate_width) == (p2.warps_per_partition, p2.candidate_width)
+    assert (p3.warps_per_partition, p3.candidate_width, p3.search_schedule) == (
+        p2.warps_per_partition, p2.candidate_width, p2.search_schedule)
     assert info2["cached_launch"] == 1 and info2["cached_classes"] == len(info["classes"])
 
     keys = workloads.stream_keys_torch(0, int(off[-1]), 5, "cuda")
