@@ -117,8 +117,10 @@ typedef struct {
     uint32_t record_timings;      /* nonzero: time the build phases with CUDA events on `stream` */
     uint32_t candidate_width;     /* search tuning: displacements per lane-window, 32 or 64 (0 = default 64);
                                      results do not depend on it */
-    uint32_t search_schedule;     /* search tuning: 0 auto, 1 one CTA per partition, 2 persistent CTAs taking
-                                     partitions from a device work queue; results do not depend on it */
+    uint32_t search_schedule;     /* search tuning: 0 auto (one CTA per partition, the faster on this
+                                     hardware for single builds and batches alike), 1 one CTA per
+                                     partition, 2 persistent CTAs taking partitions from a device work
+                                     queue; results do not depend on it */
     uint32_t bucket_function;     /* phobic_bucket_function: gamma of the bucket assignment (default 0) */
     uint32_t compact_columns;     /* PHOBIC_ENC_IC_CR: number of leading Compact columns (clamped to B) */
 } phobic_params;

@@ -540,8 +540,9 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     sl.work = work;
     sl.queue = queue;
     // schedule: 1 = one CTA per partition, 2 = persistent CTAs over the work queue;
-    // 0 (auto) = the queue for batches of several key sets
-    sl.use_queue = prm.search_schedule == 2 || (prm.search_schedule == 0 && S > 1) ? 1 : 0;
+    // 0 (auto) = one CTA per partition, which measured faster for single builds
+    // and for batches (the block scheduler balances uneven partitions for free)
+    sl.use_queue = prm.search_schedule == 2 ? 1 : 0;
     CK(ev.mark(3, st));
     CK(launch_search(sl, st));
     CK(ev.mark(4, st));

@@ -453,7 +453,8 @@ def test_batch_build_matches_single_builds(ph, orc, alpha, enc):
     keys = _keys(int(off[-1]), 51)
     Ps = rng.choice([1024, 2500, 4096], size=sizes.size).astype(np.uint32)
     prm = ph.make_params(7.0, alpha, 2500, seed=3, encoder=enc, keep_pilots=True,
-                         warps_per_partition=2 if enc else 1)
+                         warps_per_partition=2 if enc else 1,
+                         search_schedule=2 if enc % 2 == 0 else 1)  # the work queue, and one CTA per partition
     hs = ph.phobic_build_batch(_dev(keys), off, prm, partition_sizes=Ps)
     assert len(hs) == sizes.size
     for s, h in enumerate(hs):
