@@ -260,6 +260,24 @@ def test_import_of_oracle_written_files(ph, orc, enc):
         h.free()
 
 
+@pytest.mark.parametrize("enc", list(range(9)))
+def test_tiny_sets_every_encoder(ph, orc, enc):
+    """Degenerate sizes for every encoder (interleaved, mixture and mono): one
+    key, a handful, exactly one partition and one key more; both pilot forms,
+    with and without the Elias-Fano remap; bit-exact structure and queries."""
+    for n in (1, 2, 3, 2500, 2501):
+        keys = _keys(n, 500 + n + 10 * enc)
+        for mode, alpha in ((0, 1.0), (1, 0.97)):
+            o = orc.Oracle(keys, lam=7.0, alpha=alpha, P=2500, encoder=enc, mode=mode, compact_columns=3,
+                           threads=0)
+            h = ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, alpha, 2500, encoder=enc, mode=mode,
+                                                              compact_columns=3, keep_pilots=True))
+            assert np.array_equal(h.pilots().cpu().numpy().view(np.uint32), o.pilots), (n, mode)
+            compare_structure(ph, o, h, enc)
+            assert np.array_equal(_host(h.query(_dev(keys))), o.query(keys)), (n, mode)
+            h.free()
+
+
 def test_query_unaligned_and_odd_lengths(ph, orc):
     keys = _keys(30_001, 4)
     o = orc.Oracle(keys, lam=6.0, P=500, threads=0)
