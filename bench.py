@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
-    ap.add_argument("--only", choices=["batch", "serve", "lambda", "ablation", "encoders"], default=None,
+    ap.add_argument("--only", choices=["batch", "serve", "lambda", "ablation", "encoders", "table1"], default=None,
                     help="run one extra section alone (lambda: the large-lambda sweep; ablation: the bucket "
                          "functions of Fig. 3a)")
     return ap.parse_args()
@@ -684,6 +684,82 @@ def run_lambda_sweep(a, phobic, workloads, torch):
                              "its CPU share); not the same machine or input"}
 
 
+# ---------------------------------------------------------------- Table 1 ----
+# the paper's PHOBIC-GPU rows: (lambda, encoder, ns/key, bits/key), RTX 3090 through Vulkan
+PAPER_TABLE1 = [(9.0, 0, 28.0, 2.17), (9.0, 2, 27.0, 1.76), (13.0, 2, 560.0, 1.68), (14.0, 2, 1470.0, 1.67)]
+
+
+def run_table1(a, phobic, workloads, torch):
+    """The paper's own GPU workload (Table 1): 1e8 random strings, alpha = 1,
+    partition size 2500, at its lambda and encoder pairs.  Reports the build
+    with the strings resident on the device, the upload of the strings and
+    offsets from pinned host memory (the paper's times include the transfer), and
+    the space."""
+    stream = torch.cuda.current_stream()
+    n = 100_000_000
+    data, off = workloads.random_strings(n, 17)
+    hd = torch.from_numpy(data).pin_memory()
+    ho = torch.from_numpy(off.view(np.int64)).pin_memory()
+    dd = torch.empty_like(hd, device="cuda")
+    do = torch.empty_like(ho, device="cuda")
+    up = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dd.copy_(hd, non_blocking=True)
+        do.copy_(ho, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        up.append(e0.elapsed_time(e1))
+    up_ms = statistics.median(up)
+    del data
+    rows = []
+    for lam, enc, paper_ns, paper_bits in PAPER_TABLE1:
+        prm = phobic.make_params(lam, 1.0, 2500, seed=0, encoder=enc, record_timings=True)
+        seed, bms = 0, []
+        for it in range(2):
+            while True:
+                try:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    h = phobic.phobic_build_strings(dd, do, prm, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    break
+                except phobic.PhobicError as e:  # a 64-bit collision of two strings: take another seed
+                    if e.status != "DUP_HASH":
+                        raise
+                    seed += 1
+                    prm.seed = seed
+            bms.append(e0.elapsed_time(e1))
+            bpk = h.bits_per_key()
+            if it == 0:
+                h.free()
+        out = torch.empty(n, dtype=torch.int64, device="cuda")
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        phobic.phobic_query_strings(h, dd, do, out, stream)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        perm = bool(torch.equal(torch.sort(out).values, torch.arange(n, device="cuda")))
+        h.free()
+        del out
+        b_ms = bms[-1]
+        rows.append({"lambda": lam, "encoder": ["IC-C", "IC-D", "IC-R"][enc], "build_ms": b_ms,
+                     "build_ns_per_key": b_ms * 1e6 / n, "with_upload_ns_per_key": (b_ms + up_ms) * 1e6 / n,
+                     "bits_per_key": bpk, "query_ns_per_key": q0.elapsed_time(q1) * 1e6 / n,
+                     "permutation": perm, "paper_gpu_ns_per_key": paper_ns, "paper_bits_per_key": paper_bits,
+                     "speedup_vs_paper_incl_upload": paper_ns / ((b_ms + up_ms) * 1e6 / n)})
+    del dd, do
+    torch.cuda.empty_cache()
+    phobic.phobic_trim(0)
+    return {"workload": "the paper's Table 1 GPU workload: 1e8 random strings (lengths uniform in [10, 50] over "
+                        "[A-Za-z0-9], XXH64 on the device), alpha = 1, partition size 2500",
+            "upload_ms": up_ms, "upload_bytes": int(off[-1]) + 8 * (n + 1), "rows": rows,
+            "paper_context": "PHOBIC-GPU on an RTX 3090 through Vulkan with 8 CPU threads (Table 1); its times "
+                             "include the transfer of the input"}
+
+
 # ---------------------------------------------------------------- encoders ---
 def run_encoders(a, phobic, workloads, torch):
     """Figure 3b's comparison on this GPU: space and query rate of every pilot
@@ -1035,6 +1111,8 @@ def run_only(a):
         print(json.dumps({"ablation": run_ablation(a, phobic, workloads, torch)}))
     elif a.only == "encoders":
         print(json.dumps({"encoders": run_encoders(a, phobic, workloads, torch)}))
+    elif a.only == "table1":
+        print(json.dumps({"table1": run_table1(a, phobic, workloads, torch)}))
     else:
         print(json.dumps({"serve": run_serve(a, phobic, workloads, torch)}))
 
