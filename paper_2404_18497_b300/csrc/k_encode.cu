@@ -84,37 +84,49 @@ __device__ __forceinline__ void put_word(uint64_t* words, uint64_t word, uint64_
 }
 
 // ---------------------------------------------------------------- offsets ---
+__global__ void k_minmax_init(long long* __restrict__ mm, uint32_t nsets) {
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsets) {
+        mm[2 * s] = LLONG_MAX;
+        mm[2 * s + 1] = LLONG_MIN;
+    }
+}
+
+// min and max over j of D_j = T_j - T_0 - floor(j Q / 2^32) for every set.  The
+// blocks serve the sets round-robin (block b takes set b mod nsets), so that a
+// single large set is spread over the whole grid; partial results meet in mm
+// through 64-bit atomics (set up by k_minmax_init).
 __global__ void __launch_bounds__(256) k_offset_minmax(const uint64_t* __restrict__ T,
                                                        const OffDesc* __restrict__ sets, uint32_t nsets,
                                                        long long* __restrict__ mm) {
     __shared__ long long smin[8], smax[8];
-    for (uint32_t s = blockIdx.x; s < nsets; s += gridDim.x) {
-        const OffDesc d = sets[s];
-        const uint64_t T0 = T[d.part_base];
-        long long lo = LLONG_MAX, hi = LLONG_MIN;
-        for (uint64_t j = threadIdx.x; j <= d.np; j += blockDim.x) {
-            long long v = (long long)(T[d.part_base + j] - T0 - expectation(j, d.Q));
-            lo = min(lo, v);
-            hi = max(hi, v);
+    const uint32_t s = blockIdx.x % nsets;
+    const uint32_t part = blockIdx.x / nsets;
+    const uint32_t nparts = (gridDim.x - s + nsets - 1) / nsets;  // blocks that serve set s
+    const OffDesc d = sets[s];
+    const uint64_t T0 = T[d.part_base];
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
+    for (uint64_t j = (uint64_t)part * blockDim.x + threadIdx.x; j <= d.np; j += (uint64_t)nparts * blockDim.x) {
+        const long long v = (long long)(T[d.part_base + j] - T0 - expectation(j, d.Q));
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+    for (int o = 16; o; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smin[threadIdx.x >> 5] = lo;
+        smax[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; w++) {
+            lo = min(lo, smin[w]);
+            hi = max(hi, smax[w]);
         }
-        for (int o = 16; o; o >>= 1) {
-            lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
-            hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            smin[threadIdx.x >> 5] = lo;
-            smax[threadIdx.x >> 5] = hi;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < 8; w++) {
-                lo = min(lo, smin[w]);
-                hi = max(hi, smax[w]);
-            }
-            mm[2 * s] = lo;
-            mm[2 * s + 1] = hi;
-        }
-        __syncthreads();
+        atomicMin(mm + 2 * s, lo);
+        atomicMax(mm + 2 * s + 1, hi);
     }
 }
 
@@ -133,16 +145,27 @@ __global__ void k_offset_pack(const uint64_t* __restrict__ T, const OffDesc* __r
 }
 
 // ---------------------------------------------------------------- columns ---
+// Largest pilot (and sum) of every column.  A column is split into chunks of
+// kColChunk values, one block per (column, chunk), so that a few long columns
+// still fill the GPU; chunks meet in colmax / colsum through atomics (both
+// cleared before the launch).
+constexpr uint32_t kColChunk = 8192;
 __global__ void __launch_bounds__(256) k_column_max(const uint32_t* __restrict__ pilots,
                                                     const ColDesc* __restrict__ cols, uint32_t ncols,
-                                                    uint32_t* __restrict__ colmax, uint64_t* __restrict__ colsum) {
+                                                    uint32_t chunks, uint32_t* __restrict__ colmax,
+                                                    unsigned long long* __restrict__ colsum) {
     __shared__ uint32_t sm[8];
     __shared__ unsigned long long ss[8];
-    for (uint32_t c = blockIdx.x; c < ncols; c += gridDim.x) {
+    const uint64_t items = (uint64_t)ncols * chunks;
+    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const uint32_t c = (uint32_t)(it / chunks);
+        const uint64_t j0 = (it % chunks) * (uint64_t)kColChunk;
         const ColDesc d = cols[c];
+        if (j0 >= d.count) continue;  // the same for the whole block
+        const uint64_t j1 = d.count - j0 < kColChunk ? d.count : j0 + kColChunk;
         uint32_t mx = 0;
         unsigned long long sum = 0;
-        for (uint64_t j = threadIdx.x; j < d.count; j += blockDim.x) {
+        for (uint64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             const uint32_t v = __ldg(pilots + d.src + j);
             mx = max(mx, v);
             sum += v;
@@ -159,8 +182,8 @@ __global__ void __launch_bounds__(256) k_column_max(const uint32_t* __restrict__
                 mx = max(mx, sm[i]);
                 sum += ss[i];
             }
-            colmax[c] = mx;
-            if (colsum) colsum[c] = sum;
+            atomicMax(colmax + c, mx);
+            if (colsum) atomicAdd(colsum + c, sum);
         }
         __syncthreads();
     }
@@ -411,8 +434,11 @@ unsigned grid_items(uint64_t items) { return (unsigned)(items < 65535ull * 4 ? (
 
 cudaError_t launch_offset_minmax(const uint64_t* T, const OffDesc* sets, uint32_t nsets, long long* mm,
                                  cudaStream_t stream) {
-    k_offset_minmax<<<grid_items(nsets), 256, 0, stream>>>(T, sets, nsets, mm);
-    note_launches(1);
+    if (nsets == 0) return cudaSuccess;
+    k_minmax_init<<<(nsets + 255) / 256, 256, 0, stream>>>(mm, nsets);
+    const uint32_t grid = nsets > 1024 ? nsets : 1024;  // at least one block per set
+    k_offset_minmax<<<grid, 256, 0, stream>>>(T, sets, nsets, mm);
+    note_launches(2);
     return cudaGetLastError();
 }
 
@@ -423,9 +449,15 @@ cudaError_t launch_offset_pack(const uint64_t* T, const OffDesc* sets, uint32_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_column_max(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint32_t* colmax,
-                              uint64_t* colsum, cudaStream_t stream) {
-    k_column_max<<<grid_items(ncols), 256, 0, stream>>>(pilots, cols, ncols, colmax, colsum);
+cudaError_t launch_column_max(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t max_count,
+                              uint32_t* colmax, uint64_t* colsum, cudaStream_t stream) {
+    if (ncols == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(colmax, 0, (size_t)ncols * 4, stream);
+    if (e == cudaSuccess && colsum) e = cudaMemsetAsync(colsum, 0, (size_t)ncols * 8, stream);
+    if (e != cudaSuccess) return e;
+    const uint32_t chunks = (uint32_t)((max_count + kColChunk - 1) / kColChunk > 0 ? (max_count + kColChunk - 1) / kColChunk : 1);
+    k_column_max<<<grid_items((uint64_t)ncols * chunks), 256, 0, stream>>>(
+        pilots, cols, ncols, chunks, colmax, reinterpret_cast<unsigned long long*>(colsum));
     note_launches(1);
     return cudaGetLastError();
 }

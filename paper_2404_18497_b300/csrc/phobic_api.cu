@@ -586,7 +586,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     const bool unary = icr || icef || icmix;  // column layouts with a select-sampled unary part
     uint64_t* colsum = nullptr;
     if (unary) CK(tmp.alloc(&colsum, (size_t)cols_total * 8));
-    CK(launch_column_max(pilots, d_cd, (uint32_t)cols_total, colmax, colsum, st));
+    CK(launch_column_max(pilots, d_cd, (uint32_t)cols_total, max_np, colmax, colsum, st));
     CK(d2h(hmm, mm, 2 * (size_t)S, st));
     CK(d2h(hcolmax, colmax, cols_total, st));
     if (unary) CK(d2h(hK, colsum, cols_total, st));

@@ -135,8 +135,8 @@ cudaError_t launch_offset_minmax(const uint64_t* T, const OffDesc* sets, uint32_
 cudaError_t launch_offset_pack(const uint64_t* T, const OffDesc* sets, uint32_t nsets, const uint64_t* word_begin,
                                uint64_t total_words, uint64_t* arena, cudaStream_t stream);
 // colsum (may be null): sum of each column's pilots
-cudaError_t launch_column_max(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint32_t* colmax,
-                              uint64_t* colsum, cudaStream_t stream);
+cudaError_t launch_column_max(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t max_count,
+                              uint32_t* colmax, uint64_t* colsum, cudaStream_t stream);
 // IC-R: hlen[c] = sum over the column of (pilot >> width), i.e. its unary bits minus N_P
 cudaError_t launch_rice_unary_len(const uint32_t* pilots, const ColDesc* cols, uint32_t ncols, uint64_t* hlen,
                                   cudaStream_t stream);
