@@ -41,7 +41,8 @@ __device__ __forceinline__ uint64_t load_hk(const uint64_t* in, uint64_t i, uint
 // Digit histograms of every pass in one read of the input, per segment.  Each
 // block walks a contiguous range of tiles; each warp counts into its own
 // sub-histogram, which is flushed to the segment's global histogram when the
-// segment changes and at the end.
+// segment changes and at the end.  When the input needs hashing, the master
+// hashes are also written out (hashed_out), so that no pass hashes again.
 __device__ __forceinline__ uint32_t seg_of_tile(const SortSeg* __restrict__ segs, uint32_t nseg, uint64_t t) {
     uint32_t lo = 0, hi = nseg;  // largest s with first_tile[s] <= t
     while (hi - lo > 1) {
@@ -54,7 +55,8 @@ __device__ __forceinline__ uint32_t seg_of_tile(const SortSeg* __restrict__ segs
 __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ in, const SortSeg* __restrict__ segs,
                                                    uint32_t nseg, uint64_t tiles, uint64_t kseed, int hash_input,
                                                    uint32_t passes, uint32_t bits,
-                                                   unsigned long long* __restrict__ hist) {
+                                                   unsigned long long* __restrict__ hist,
+                                                   uint64_t* __restrict__ hashed_out) {
     extern __shared__ uint32_t sh_hist[];  // [kWarpsH][passes * R]
     constexpr int kWarpsH = 8;
     const uint32_t R = 1u << bits, mask = R - 1, PR = passes * R;
@@ -82,13 +84,17 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ 
             for (int u = 0; u < 4; u++) v[u] = __ldg(in + i + (uint64_t)u * blockDim.x);
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                const uint64_t j = partition_of(hash_input ? key_hash(v[u], kseed) : v[u], S.np);
+                const uint64_t hk = hash_input ? key_hash(v[u], kseed) : v[u];
+                if (hashed_out) hashed_out[i + (uint64_t)u * blockDim.x] = hk;
+                const uint64_t j = partition_of(hk, S.np);
                 for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
             }
         }
         for (; i < k1; i += blockDim.x) {
             const uint64_t v = __ldg(in + i);
-            const uint64_t j = partition_of(hash_input ? key_hash(v, kseed) : v, S.np);
+            const uint64_t hk = hash_input ? key_hash(v, kseed) : v;
+            if (hashed_out) hashed_out[i] = hk;
+            const uint64_t j = partition_of(hk, S.np);
             for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
         }
         __syncthreads();
@@ -420,15 +426,18 @@ cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint6
         uint64_t hblocks = tiles < (uint64_t)sms * 8 ? tiles : (uint64_t)sms * 8;
         if (hblocks == 0) hblocks = 1;
         if ((e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_sort_hist))) != cudaSuccess) return e;
+        // with hashing: the histogram pass also writes the master hashes, into the
+        // buffer that the first pass does not write, and the passes read those
+        uint64_t* hashed = hash_input ? ((passes & 1) ? alt : sorted) : nullptr;
         k_sort_hist<<<(unsigned)hblocks, 256, 8 * passes * R * 4, stream>>>(in, d_segs, nseg, tiles, kseed,
-                                                                            hash_input, passes, bits, hist);
+                                                                            hash_input, passes, bits, hist, hashed);
         note_launches(1);
         k_sort_hist_scan<<<nseg * passes, 512, 0, stream>>>(hist, d_segs, passes, bits);
         note_launches(1);
         size_t smem = sort_pass_smem(bits);
         if ((e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_sort_pass))) != cudaSuccess) return e;
-        const uint64_t* src = in;
-        int hash_now = hash_input;
+        const uint64_t* src = hashed ? hashed : in;
+        int hash_now = 0;
         // ping-pong so that the last pass lands in `sorted`
         uint64_t* dst = (passes & 1) ? sorted : alt;
         for (uint32_t ps = 0; ps < passes; ps++) {
