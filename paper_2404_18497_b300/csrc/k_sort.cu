@@ -155,7 +155,10 @@ struct PassArgs {
 // keys (order: item, lane): the lanes with equal digits are found as the AND,
 // over the digit's bits, of the ballots of the lanes that agree on that bit;
 // the leader of each group adds the group size to the warp's counter with one
-// shared atomicAdd and hands the old value to its peers, so ranks are stable.  Then
+// shared atomicAdd and hands the old value to its peers, so ranks are stable.
+// The first of several passes need not be stable (every later pass is, and
+// keeps its digit order; the order inside a partition is left unspecified): it
+// ranks each key with one shared atomicAdd on its digit's counter.  Then
 // per digit: prefix over warps, decoupled look-back for the tile's global
 // offset, a block scan for the tile-local digit starts, a shared-memory
 // reorder and a coalesced write-out.
@@ -190,6 +193,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     uint32_t dr[kItems];  // digit << 16 | rank within the warp's digit group
     const uint32_t lt = (1u << lane) - 1;
     uint32_t* myh = wh + warp * R;
+    if (a.pass == 0 && a.passes > 1) {
+        // the first of several passes need not be stable (the later ones keep its
+        // digit order): a key's rank is one shared atomic on its warp's counter
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+            const bool valid = wbase + (uint64_t)i * 32 + lane < seg_end;
+            const uint32_t dg = valid ? (uint32_t)((partition_of(k[i], S.np) >> a.shift) & mask) : R;
+            const uint32_t rank = valid ? atomicAdd(&myh[dg], 1u) : 0u;
+            dr[i] = (dg << 16) | rank;
+        }
+    } else
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
         const bool valid = wbase + (uint64_t)i * 32 + lane < seg_end;
