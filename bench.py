@@ -110,11 +110,11 @@ NCU_CAPTURES = {
                 "sha": "610b1261bfb50dd2", "n": 3e7, "dram_bytes": 249899520 + 197058560,
                 "profile": "profiles/k_query_3e7.md"},
     "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "c2f6b8579b6a7020", "n": 3e7,
-               "dram_bytes": (240055552 + 195964160) + (243367680 + 197179136) + (243356672 + 196539904),
+               "sha": "4b47def053d39f21", "n": 3e7,
+               "dram_bytes": (240048640 + 195887104) + (242551040 + 197579008) + (242448640 + 197109760),
                "profile": "profiles/k_sort_pass_3e7.md"},
     "k_hash": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "c2f6b8579b6a7020", "n": 3e7, "dram_bytes": 240023040 + 192200704,
+               "sha": "4b47def053d39f21", "n": 3e7, "dram_bytes": 240023040 + 192200704,
                "profile": "profiles/k_hash_copy_3e7.md"},
 }
 ISSUE_SLOTS_PER_CLOCK = 148 * 4  # B300: 148 SMs x 4 warp schedulers, one warp instruction per clock each
