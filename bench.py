@@ -107,7 +107,7 @@ NCU_CAPTURES = {
                  "sha": "a3fcd6292c8f63e3", "n": 3e7, "warp_inst": 2110900855, "dram_bytes": 546543872 + 304698880,
                  "profile": "profiles/k_search_3e7.md"},
     "k_query": {"files": ["paper_2404_18497_b300/csrc/k_query.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-                "sha": "610b1261bfb50dd2", "n": 3e7, "dram_bytes": 249899520 + 197058560,
+                "sha": "3f49bb2bc532d038", "n": 3e7, "dram_bytes": 249938176 + 197645568,
                 "profile": "profiles/k_query_3e7.md"},
     "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
                "sha": "4b47def053d39f21", "n": 3e7,

@@ -25,7 +25,9 @@ __device__ __forceinline__ uint64_t expectation(uint64_t j, uint64_t Q) {
 }
 
 // T_j and T_{j+1}: the two stored differences are adjacent (2w <= 62 bits), so
-// one 128-bit window of the packed words holds both
+// one 128-bit window of the packed words holds both.  kNarrow: read the second
+// word only when the pair runs into it.
+template <bool kNarrow>
 __device__ __forceinline__ void offsets_of(const QueryView& v, uint64_t j, uint64_t* Tj, uint64_t* Tj1) {
     const uint32_t w = v.off_w;
     uint64_t d0 = 0, d1 = 0;
@@ -33,8 +35,14 @@ __device__ __forceinline__ void offsets_of(const QueryView& v, uint64_t j, uint6
         const uint64_t o = j * w;
         const uint64_t i = o >> 6;
         const uint32_t sh = (uint32_t)(o & 63);
-        const uint64_t lo = __ldg(v.off_words + i);
-        const uint64_t x = sh ? (lo >> sh) | (__ldg(v.off_words + i + 1) << (64 - sh)) : lo;
+        uint64_t x;
+        if (kNarrow) {
+            x = __ldg(v.off_words + i) >> sh;
+            if (sh + 2 * w > 64) x |= __ldg(v.off_words + i + 1) << (64 - sh);  // sh > 0 here
+        } else {
+            const uint64_t lo = __ldg(v.off_words + i);
+            x = sh ? (lo >> sh) | (__ldg(v.off_words + i + 1) << (64 - sh)) : lo;
+        }
         const uint64_t mask = (1ull << w) - 1;
         d0 = x & mask;
         d1 = (x >> w) & mask;
@@ -45,6 +53,16 @@ __device__ __forceinline__ void offsets_of(const QueryView& v, uint64_t j, uint6
 
 __device__ __forceinline__ uint64_t offset_of(const QueryView& v, uint64_t j) {
     return expectation(j, v.off_Q) + (uint64_t)v.off_dmin + read_bits(v.off_words, j * v.off_w, v.off_w);
+}
+
+// read_bits32 for narrow fields: the 64-bit word holding bit o, and the next
+// word only when the field runs into it (for random o, with probability about
+// w/64), which spares the cache the second access of most random reads
+__device__ __forceinline__ uint32_t read_bits32_narrow(const uint64_t* __restrict__ words, uint32_t o, uint32_t w) {
+    const uint32_t i = o >> 6, sh = o & 63;
+    uint64_t x = __ldg(words + i) >> sh;
+    if (sh + w > 64) x |= __ldg(words + i + 1) << (64 - sh);  // sh > 0 here
+    return w >= 32 ? (uint32_t)x : ((uint32_t)x & ((1u << w) - 1));
 }
 
 // floor(p / m) for m >= 1 through a float reciprocal and an exact integer
@@ -195,22 +213,35 @@ __device__ __forceinline__ uint32_t mono_pilot(const QueryView& v, uint64_t i) {
 
 constexpr int kSeedTable = 64;  // pilot seeds mix64(s ^ C) for s < 64, per block
 
-// kMono: the handle uses a mono encoder (5..8).  The kernels are instantiated
-// for both, so that the interleaved encoders' code is not shaped by the other.
-template <bool kMono>
-__device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds);
+// Kinds of query kernel, one instantiation each, so that no encoder's code is
+// shaped by another's:
+//   kQInterleaved: the interleaved encoders (0..4), chosen at run time;
+//   kQMono: a mono encoder (5..8);
+//   kQDict: IC-D.  Its two dependent narrow reads (rank, then dictionary entry)
+//     leave the query bound by L1 accesses, so it reads a field's second word
+//     only when the field runs into it (about w/64 of random offsets).  The other
+//     encoders are bound by issue and keep the branch-free two-word reads.
+constexpr int kQInterleaved = 0, kQMono = 1, kQDict = 2;
 
-template <bool kMono>
-__device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key, const uint64_t* seeds) {
-    return query_hashed<kMono>(v, key_hash(key, v.kseed), seeds);
+__host__ __forceinline__ int query_kind(const QueryView& v) {
+    return v.encoder >= 5 ? kQMono : v.encoder == 1 ? kQDict : kQInterleaved;
 }
 
-template <bool kMono>
+template <int kKind>
+__device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds);
+
+template <int kKind>
+__device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key, const uint64_t* seeds) {
+    return query_hashed<kKind>(v, key_hash(key, v.kseed), seeds);
+}
+
+template <int kKind>
 __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds) {
+    constexpr bool kMono = kKind == kQMono, kNarrow = kKind == kQDict;
     const uint64_t j = partition_of(hk, v.NP);
     uint64_t Tj, Tj1;
     if (v.off_w <= 31) {
-        offsets_of(v, j, &Tj, &Tj1);
+        offsets_of<kNarrow>(v, j, &Tj, &Tj1);
     } else {
         Tj = offset_of(v, j);
         Tj1 = offset_of(v, j + 1);
@@ -242,8 +273,14 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
         } else {
             const uint64_t rm = __ldg(v.col_meta + 2 * b), dm = __ldg(v.col_meta + 2 * b + 1);
             const uint32_t rw = (uint32_t)(rm >> 56), dw = (uint32_t)(dm >> 56);
-            const uint32_t r = read_bits32(v.pil_words, (uint32_t)rm + jj * rw, rw);
-            p = read_bits32(v.dict_words, (uint32_t)dm + r * dw, dw);
+            uint32_t r;
+            if (kNarrow) {
+                r = read_bits32_narrow(v.pil_words, (uint32_t)rm + jj * rw, rw);
+                p = read_bits32_narrow(v.dict_words, (uint32_t)dm + r * dw, dw);
+            } else {
+                r = read_bits32(v.pil_words, (uint32_t)rm + jj * rw, rw);
+                p = read_bits32(v.dict_words, (uint32_t)dm + r * dw, dw);
+            }
         }
     } else if (v.encoder == 0) {
         uint64_t meta = __ldg(v.col_meta + b);
@@ -271,7 +308,7 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
     return g;
 }
 
-template <bool kMono>
+template <int kKind>
 __global__ void __launch_bounds__(256) k_query(const QueryView v, const uint64_t* __restrict__ keys,
                                                uint64_t* __restrict__ out, uint64_t m) {
     __shared__ uint64_t seeds[kSeedTable];
@@ -286,19 +323,19 @@ __global__ void __launch_bounds__(256) k_query(const QueryView v, const uint64_t
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < pairs; i += stride) {
             ulonglong2 k = __ldcs(k2 + i);
             ulonglong2 r;
-            r.x = query_one<kMono>(v, k.x, seeds);
-            r.y = query_one<kMono>(v, k.y, seeds);
+            r.x = query_one<kKind>(v, k.x, seeds);
+            r.y = query_one<kKind>(v, k.y, seeds);
             __stcs(o2 + i, r);
         }
-        if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[m - 1] = query_one<kMono>(v, keys[m - 1], seeds);
+        if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[m - 1] = query_one<kKind>(v, keys[m - 1], seeds);
     } else {
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += stride)
-            out[i] = query_one<kMono>(v, keys[i], seeds);
+            out[i] = query_one<kKind>(v, keys[i], seeds);
     }
 }
 
 // string keys: XXH64 master hash of each string (Section 5), then the same query
-template <bool kMono>
+template <int kKind>
 __global__ void __launch_bounds__(256) k_query_strings(const QueryView v, const uint8_t* __restrict__ bytes,
                                                        const uint64_t* __restrict__ offsets, uint64_t* __restrict__ out,
                                                        uint64_t m) {
@@ -307,7 +344,7 @@ __global__ void __launch_bounds__(256) k_query_strings(const QueryView v, const 
     __syncthreads();
     const uint64_t total = __ldg(offsets + m);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = query_hashed<kMono>(v, string_master_hash(bytes, offsets, total, i, v.string_seed), seeds);
+        out[i] = query_hashed<kKind>(v, string_master_hash(bytes, offsets, total, i, v.string_seed), seeds);
 }
 
 // Several query batches against different structures in one launch.  The
@@ -343,7 +380,10 @@ __global__ void __launch_bounds__(256) k_query_multi(const MultiQuery* __restric
             const MultiQuery* q = reqs + r;
             const uint64_t x = __ldcs(q->keys + (i - q->begin));
             // a handle's encoder is uniform over its request
-            const uint64_t y = q->v.encoder >= 5 ? query_one<true>(q->v, x, seeds) : query_one<false>(q->v, x, seeds);
+            const uint32_t enc = q->v.encoder;
+            const uint64_t y = enc >= 5   ? query_one<kQMono>(q->v, x, seeds)
+                               : enc == 1 ? query_one<kQDict>(q->v, x, seeds)
+                                          : query_one<kQInterleaved>(q->v, x, seeds);
             __stcs(q->out + (i - q->begin), y);
         }
     }
@@ -373,10 +413,11 @@ cudaError_t launch_query_strings(const QueryView& v, const uint8_t* bytes, const
     uint64_t want = (m + 255) / 256;
     uint64_t cap = (uint64_t)sms * 8;
     unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
-    if (v.encoder >= 5)
-        k_query_strings<true><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m);
-    else
-        k_query_strings<false><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m);
+    switch (query_kind(v)) {
+        case kQMono: k_query_strings<kQMono><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m); break;
+        case kQDict: k_query_strings<kQDict><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m); break;
+        default: k_query_strings<kQInterleaved><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m); break;
+    }
     note_launches(1);
     return cudaGetLastError();
 }
@@ -389,10 +430,11 @@ cudaError_t launch_query(const QueryView& v, const uint64_t* keys, uint64_t* out
     uint64_t want = (m / 2 + 255) / 256;
     uint64_t cap = (uint64_t)sms * 8;  // 8 resident blocks of 256 threads per SM
     unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
-    if (v.encoder >= 5)
-        k_query<true><<<grid, 256, 0, stream>>>(v, keys, out, m);
-    else
-        k_query<false><<<grid, 256, 0, stream>>>(v, keys, out, m);
+    switch (query_kind(v)) {
+        case kQMono: k_query<kQMono><<<grid, 256, 0, stream>>>(v, keys, out, m); break;
+        case kQDict: k_query<kQDict><<<grid, 256, 0, stream>>>(v, keys, out, m); break;
+        default: k_query<kQInterleaved><<<grid, 256, 0, stream>>>(v, keys, out, m); break;
+    }
     note_launches(1);
     return cudaGetLastError();
 }
