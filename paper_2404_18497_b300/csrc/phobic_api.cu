@@ -405,10 +405,15 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         if (p.B > cap_B) cap_B = p.B;
     }
     const uint32_t ntab = (uint32_t)table_P.size();
-    std::vector<uint64_t> tables((size_t)ntab * (kTablePoints + 1));
-    for (uint32_t t = 0; t < ntab; t++)
-        cached_table(prm.lambda, prm.alpha, table_P[t], prm.bucket_function,
-                     tables.data() + (size_t)t * (kTablePoints + 1));
+    // the device holds each table packed (kTablePoints words, bucket_of)
+    std::vector<uint64_t> tables((size_t)ntab * kTablePoints);
+    {
+        std::vector<uint64_t> t1(kTablePoints + 1);
+        for (uint32_t t = 0; t < ntab; t++) {
+            cached_table(prm.lambda, prm.alpha, table_P[t], prm.bucket_function, t1.data());
+            pack_bucket_table(t1.data(), tables.data() + (size_t)t * kTablePoints);
+        }
+    }
 
     PinnedBuf pin;
     CK(pin.alloc(4096 + (size_t)S * 48 + (size_t)cols_total * 12));
@@ -497,7 +502,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     std::vector<SearchSet> ss(S);
     for (uint32_t s = 0; s < S; s++)
         ss[s] = SearchSet{pl[s].part_base, pl[s].NP, pl[s].pilot_base,
-                          d_tables + (size_t)pl[s].table_idx * (kTablePoints + 1), pl[s].B, 0};
+                          d_tables + (size_t)pl[s].table_idx * kTablePoints, pl[s].B, 0};
     SearchSet* d_ss;
     uint32_t* pilots;
     uint32_t* taken = nullptr;
@@ -688,7 +693,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     }
 
     // ---- layouts and the arena
-    uint64_t aw = (uint64_t)ntab * (kTablePoints + 1);  // tables first
+    uint64_t aw = (uint64_t)ntab * kTablePoints;  // packed tables first
     std::vector<uint64_t> off_begin(S + 1, 0), col_begin(cols_total + 1, 0), remap_sets;
     std::vector<std::vector<uint64_t>> metas(S);
     for (uint32_t s = 0; s < S; s++) {
@@ -947,7 +952,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         h->prm.partition_size = p.P;
         h->prm.s_max = s_max;
         h->mem = mem;
-        h->table = arena + (size_t)p.table_idx * (kTablePoints + 1);
+        h->table = arena + (size_t)p.table_idx * kTablePoints;
         h->off_words = arena + p.a_off;
         h->n_off_words = p.n_off;
         h->col_meta = arena + p.a_meta;
@@ -986,7 +991,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         I.bits_pilots = p.bits_pilots;
         I.bits_remap = p.bits_remap;
         I.bits_total = p.bits_total;
-        I.device_bytes = 8 * ((kTablePoints + 1) + p.n_off + p.n_meta + p.n_pil + p.n_dict + p.n_low + p.n_high +
+        I.device_bytes = 8 * (kTablePoints + p.n_off + p.n_meta + p.n_pil + p.n_dict + p.n_low + p.n_high +
                               p.n_samp) + (prm.keep_pilots ? (uint64_t)p.B * p.NP * 4 : 0);
         QueryView& v = h->view;
         v.n = p.n;
@@ -1563,7 +1568,7 @@ static void info_of_export(const ParsedExport& pe, const uint64_t* w, phobic_inf
     I->bits_pilots = w[25];
     I->bits_remap = w[26];
     I->bits_total = w[27];
-    I->device_bytes = (kTablePoints + 1) * 8 + 8 * (pe.words - kHeaderWords);
+    I->device_bytes = kTablePoints * 8 + 8 * (pe.words - kHeaderWords);
 }
 
 phobic_status phobic_inspect(const void* h_buf, size_t len, phobic_info* out) {
@@ -1599,15 +1604,16 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
                          &h->ef_low,    &h->ef_high,  &h->ef_samples};
     uint64_t* cnts[7] = {&h->n_off_words, &h->n_col_meta, &h->n_pil_words, &h->n_dict_words,
                          &h->n_ef_low,    &h->n_ef_high,  &h->n_ef_samples};
-    std::vector<uint64_t> table(kTablePoints + 1);
-    make_table(p.lambda, p.alpha, p.partition_size, table.data(), p.bucket_function);
-    // one allocation: the table, then the seven arrays in file order
+    std::vector<uint64_t> table1(kTablePoints + 1), table(kTablePoints);
+    make_table(p.lambda, p.alpha, p.partition_size, table1.data(), p.bucket_function);
+    pack_bucket_table(table1.data(), table.data());
+    // one allocation: the packed table, then the seven arrays in file order
     SharedMem* mem = new (std::nothrow) SharedMem();
     if (!mem) {
         delete h;
         return PHOBIC_ERR_OOM;
     }
-    cudaError_t e = cudaMalloc(&mem->ptr, ((kTablePoints + 1) + (words - kHeaderWords)) * 8);
+    cudaError_t e = cudaMalloc(&mem->ptr, (kTablePoints + (words - kHeaderWords)) * 8);
     if (e != cudaSuccess) {
         delete mem;
         delete h;
@@ -1618,7 +1624,7 @@ phobic_status phobic_import(const void* h_buf, size_t len, phobic_stream_t strea
     uint64_t* arena = static_cast<uint64_t*>(mem->ptr);
     h->table = arena;
     e = cudaMemcpy(h->table, table.data(), table.size() * 8, cudaMemcpyHostToDevice);
-    uint64_t at = kHeaderWords, aw = kTablePoints + 1;
+    uint64_t at = kHeaderWords, aw = kTablePoints;
     for (int i = 0; i < 7 && e == cudaSuccess; i++) {
         *cnts[i] = counts[i];
         if (counts[i]) {

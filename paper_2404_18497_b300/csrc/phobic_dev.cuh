@@ -53,18 +53,26 @@ __device__ __forceinline__ uint32_t position_hash(uint64_t hk, uint64_t ps, uint
 __device__ __forceinline__ uint64_t partition_of(uint64_t hk, uint64_t np) { return mulhi64(hk, np); }
 
 // Section 3.1 / Appendix C: bucket of normalised hash x from the fixed-point
-// table of gamma, by linear interpolation between table[k] and table[k+1]:
+// table of gamma T_0..T_2048, by linear interpolation between T_k and T_{k+1}:
 // v = T_k + ((T_{k+1} - T_k) f >> 32), bucket = min(B - 1, v B >> 32).
-// The increments T_{k+1} - T_k are below 2^32, so the products are formed with
-// 32-bit multiplies; v >= 2^32 can only give bucket B - 1.
-__device__ __forceinline__ uint32_t bucket_of(uint64_t x, const uint64_t* __restrict__ table, uint32_t B) {
-    const uint32_t k = (uint32_t)(x >> 53);
-    const uint32_t f = (uint32_t)(x >> 21);
-    const uint64_t lo = __ldg(table + k), hi = __ldg(table + k + 1);
-    const uint64_t v = lo + __umulhi((uint32_t)(hi - lo), f);
+// The device holds the table packed, one word per interval (pack_bucket_table):
+// low half min(T_k, 2^32 - 1), high half T_{k+1} - T_k (below 2^32), so that a
+// lookup is one read.  The clamp changes no bucket: T_k = 2^32 gives v >= 2^32,
+// hence B - 1, and the clamped v >= 2^32 - 1 gives B - 1 too.
+__device__ __forceinline__ uint32_t bucket_of(uint64_t x, const uint64_t* __restrict__ qtable, uint32_t B) {
+    const uint64_t e = __ldg(qtable + (x >> 53));
+    const uint64_t v = (e & 0xFFFFFFFFull) + __umulhi((uint32_t)(e >> 32), (uint32_t)(x >> 21));
     if (v >> 32) return B - 1;
     const uint32_t b = __umulhi((uint32_t)v, B);
     return b > B - 1 ? B - 1 : b;
+}
+
+// T_0..T_2048 (kTablePoints + 1 words) -> the packed device form (kTablePoints words)
+__host__ __forceinline__ void pack_bucket_table(const uint64_t* t, uint64_t* q) {
+    for (int k = 0; k < kTablePoints; k++) {
+        const uint64_t lo = t[k] < 0xFFFFFFFFull ? t[k] : 0xFFFFFFFFull;
+        q[k] = lo | ((uint64_t)(uint32_t)(t[k + 1] - t[k]) << 32);
+    }
 }
 
 // number of bits of v (0 for 0)
@@ -112,7 +120,7 @@ struct QueryView {
     uint64_t kseed;      // mix64(seed ^ kSeedMix)
     uint64_t off_Q;
     int64_t off_dmin;
-    const uint64_t* table;     // 2049
+    const uint64_t* table;     // the packed bucket table (kTablePoints words, bucket_of)
     const uint64_t* off_words; // offsets, packed
     // IC-C: col_meta[b] = base | (width << 56); IC-D: col_meta[2b] = rank base | (rank width << 56),
     // col_meta[2b+1] = dict base | (dict width << 56)

@@ -67,7 +67,7 @@ cudaError_t launch_sizes(const uint64_t* start, uint64_t np, double alpha, uint6
 // pilots[pilot_base + b * np + j]
 struct SearchSet {
     uint64_t part_base, np, pilot_base;
-    const uint64_t* table;  // 2049-entry bucket table of this set's (lambda, alpha, P)
+    const uint64_t* table;  // packed bucket table of this set's (lambda, alpha, P) (bucket_of)
     uint32_t B, pad;
 };
 
