@@ -29,9 +29,13 @@
  *
  * Readings where the paper is silent (hash functions, rounding of B and m_j,
  * bit layouts, bits/key accounting) follow one fixed written spec.  The CUDA
- * library implements the same spec independently.  The hash constants are
- * "parity unpinned": nothing in the paper fixes them (the mixer itself is
- * SplitMix64's output function, pinned to that generator's known outputs).
+ * library implements the same spec independently.  The three hash constants
+ * below are "parity unpinned": nothing in the paper fixes them, so they are
+ * pinned only by their statistical effect.  The mixer around them is
+ * SplitMix64's output function, pinned to that generator's known outputs, and
+ * the string hash is XXH64, pinned to published known answers for every input
+ * path (tails, lanes, stripes, seeds).  The bits/key accounting is pinned by a
+ * term-by-term recount from independently derived sizes.
  *
  * Floating point appears only in building the bucket table and in
  * ceil(n_j / alpha).  Compile with -ffp-contract=off so that no fused

@@ -7,10 +7,10 @@
  * and is only ever loaded by the tests, by the smoke check and by the
  * benchmark's CPU-baseline leg.  It shares no code with the CUDA path.
  *
- * Parity status per function is stated in phobic_oracle.c.  The hash constants
- * are this implementation's own fixed spec and are "parity unpinned": they are
- * pinned only statistically (mix64, SplitMix64's output function, is pinned to
- * that generator's known outputs).
+ * Parity status per function is stated in phobic_oracle.c.  The three hash
+ * constants are this implementation's own fixed spec and are "parity unpinned":
+ * they are pinned only statistically (mix64, SplitMix64's output function, is
+ * pinned to that generator's known outputs; XXH64 to published known answers).
  */
 #ifndef PHOBIC_ORACLE_H
 #define PHOBIC_ORACLE_H

@@ -99,6 +99,17 @@ def test_string_hash_parity(ph, orc):
     assert (got == orc.string_hashes(data, off, 7)).all()
 
 
+def test_string_hash_known_answers(ph):
+    """The device XXH64 against published known answers (the same fixture that
+    pins the oracle), every path of the hash: tails of 1-7 bytes, 8-byte lanes,
+    one and several 32-byte stripes, nonzero seeds."""
+    from tests import xxh64_known
+
+    for seed, (data, offs, want) in xxh64_known.by_seed().items():
+        got = _host(ph.phobic_hash_strings(torch.from_numpy(data).cuda(), _dev(offs), seed))
+        assert [int(v) for v in got] == want, seed
+
+
 @pytest.mark.parametrize("n,P", [(1, 2500), (100, 2500), (2500, 2500), (1_000_000, 2500), (1_234_567, 1000),
                                  (300_000, 37), (5_000_000, 2500), (65_536, 1), (3_000_000, 24)])
 def test_partition_sort_parity(ph, orc, n, P):

@@ -236,12 +236,26 @@ def test_mix64_is_splitmix64(orc):
         assert L.or_mix64((k * gamma) % 2**64) == int(want, 16), k
 
 
-def test_xxh64_of_the_empty_input(orc):
-    """XXH64's known answer for the empty input (tests/golden/xxh64_empty.json)."""
-    with open(os.path.join(GOLDEN, "xxh64_empty.json")) as f:
-        g = json.load(f)
-    h = orc.string_hashes(np.zeros(8, dtype=np.uint8), np.array([0, 0], dtype=np.uint64), g["seed"])
-    assert int(h[0]) == int(g["hash"], 16)
+def test_xxh64_known_answers(orc):
+    """The string master hash is XXH64 (Section 5 hashes string keys with
+    xxHash).  Published known answers (tests/golden/xxh64_known_answers.json:
+    the xxHash tool's self-test table and two bindings' unit-test and README
+    values) reach the byte tail, the 4-byte tail, the 8-byte lanes, the 32-byte
+    stripe loop with its four-lane merge, and nonzero seeds; each is checked
+    one message at a time and as one packed array with offsets."""
+    from tests import xxh64_known
+
+    L = orc.lib()
+    lens = set()
+    for msg, seed, want in xxh64_known.cases():
+        a = np.frombuffer(msg + b"\0", dtype=np.uint8).copy()
+        assert L.or_string_hash(a.ctypes.data, len(msg), seed) == want, (len(msg), seed)
+        lens.add(len(msg))
+    # every tail length mod 32 class that matters: <4, 4..7, 8..31, >= 32 and >= 64
+    assert {1, 2, 3, 4, 6, 14, 39, 63, 222} <= lens
+    for seed, (data, offs, want) in xxh64_known.by_seed().items():
+        got = orc.string_hashes(data, offs, seed)
+        assert [int(v) for v in got] == want, seed
 
 
 def test_mix64_is_bijective_and_avalanches(orc):
