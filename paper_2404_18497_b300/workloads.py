@@ -7,9 +7,9 @@ numpy's PCG64 generator, sorting (to make keys distinct) and indexing.
 Workload recipes follow the paper's settings and the benchmark configurations:
 - uniform distinct 64-bit keys;
 - positive queries drawn uniformly from the key set;
-- Zipf(s = 1) query orders.  A rank r in [1, n] is drawn by inverting the
-  continuous 1/r law, r = floor((n + 1)^u) with u uniform in [0, 1), and mapped
-  to a key through a seeded permutation;
+- Zipf(s = 1) query orders: rank r in [1, n] with probability exactly
+  (1/r) / H_n, drawn by rejection-inversion (Hoermann and Derflinger 1996) and
+  mapped to a key through a seeded permutation;
 - random strings of length uniform in [10, 50] over [A-Za-z0-9] (Section 5's
   input);
 - batches of many key sets with log-uniform sizes, whose keys come from a
@@ -49,13 +49,39 @@ def uniform_queries(keys: np.ndarray, q: int, seed: int) -> np.ndarray:
     return keys[rng.integers(0, keys.size, size=q)]
 
 
+def zipf_ranks(n: int, q: int, rng: np.random.Generator) -> np.ndarray:
+    """q ranks in [1, n] with P(r) = (1/r) / H_n (Zipf, exponent 1), by
+    rejection-inversion (W. Hoermann, G. Derflinger, "Rejection-inversion to
+    generate variates from monotone discrete distributions", ACM TOMACS 6(3),
+    1996).
+
+    The hat is the continuous density 1/x with antiderivative H(x) = ln x.
+    Rank k owns the interval [H(k - 1/2), H(k + 1/2)), whose length
+    ln((k + 1/2) / (k - 1/2)) is at least 1/k because 1/x is convex; the top
+    1/k of it, [H(k + 1/2) - 1/k, H(k + 1/2)), is k's acceptance strip.  A
+    uniform u over [H(3/2) - 1, H(n + 1/2)) (from the start of rank 1's strip)
+    is inverted to x = e^u and rounded to k; u is kept when it lies in k's
+    strip and redrawn otherwise.  The kept u are uniform over the union of the
+    strips, so k is drawn with probability proportional to 1/k exactly (up to
+    double rounding at strip edges)."""
+    out = np.empty(q, dtype=np.int64)
+    lo, hi = np.log(1.5) - 1.0, np.log(n + 0.5)
+    todo = np.arange(q)
+    while todo.size:
+        u = lo + rng.random(todo.size) * (hi - lo)
+        k = np.clip(np.floor(np.exp(u) + 0.5), 1, n)
+        ok = u >= np.log(k + 0.5) - 1.0 / k
+        out[todo[ok]] = k[ok].astype(np.int64)
+        todo = todo[~ok]
+    return out
+
+
 def zipf_queries(keys: np.ndarray, q: int, seed: int) -> np.ndarray:
-    """Keys in a Zipf(s = 1) order: rank r has probability ~ 1/r."""
+    """Keys in a Zipf(s = 1) order: the key of rank r is drawn with probability
+    (1/r) / H_n; ranks are mapped to keys through a seeded permutation."""
     rng = np.random.default_rng(seed)
     n = keys.size
-    u = rng.random(q)
-    r = np.floor(np.exp(u * np.log(n + 1.0))).astype(np.int64)
-    r = np.clip(r, 1, n)
+    r = zipf_ranks(n, q, rng)
     perm = rng.permutation(n)
     return keys[perm[r - 1]]
 
