@@ -439,6 +439,74 @@ phobic_status phobic_selftest_sort_wait_timeout(const uint64_t* d_hk, uint64_t n
 phobic_status phobic_partition_sort_noalloc(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions,
                                             uint64_t* d_sorted, uint64_t* d_start, phobic_stream_t stream);
 
+/* ---- partition-sharded construction (Section 4: partitions are independent) ----
+ *
+ * One MPHF over n keys that are spread over several devices (one process per
+ * device).  Partition j = floor(hk N_P / 2^64) belongs to shard
+ * r = floor(j G / N_P) of G; a shard's partitions are the contiguous range
+ * [ceil(r N_P / G), ceil((r + 1) N_P / G)).  Each process hashes its keys
+ * (phobic_hash_u64) and groups them by partition (phobic_partition_sort with
+ * the build's N_P), sends every shard the hashes of its partitions, and groups
+ * what it receives again.  From the partition sizes of all shards it forms the
+ * build's partition starts, and phobic_table_offsets turns them into the slot
+ * offsets T.  phobic_search_partitions places the buckets of its own partitions
+ * into a zero-filled pilot matrix and occupancy bitmap of the whole build;
+ * summing those over the shards (their supports are disjoint, so the sum is the
+ * union) gives every shard the whole build's pilots and occupancy, from which
+ * phobic_assemble makes the same structure that phobic_build_ex makes from all
+ * n keys on one device.  The exchanges are the caller's (the Python binding's
+ * sharded_build does them with torch.distributed).
+ */
+
+/* Slot offsets from partition starts (Section 4: m_j = n_j for alpha = 1,
+ * else max(n_j, ceil(n_j / alpha)) in IEEE double; T is the exclusive prefix
+ * sum of m).  d_start: N_P + 1 partition starts (n_j = d_start[j+1] -
+ * d_start[j]), device.  Writes d_T[N_P + 1] (device, T[N_P] = M) and, when
+ * h_stats is not NULL, h_stats[0..2] = M, the largest n_j, the largest m_j.
+ * Synchronises `stream`.  Errors: INVALID_ARG (NULL pointers, N_P = 0, alpha
+ * outside (0, 1]), OOM, CUDA. */
+phobic_status phobic_table_offsets(const uint64_t* d_start, uint64_t num_partitions, double alpha, uint64_t* d_T,
+                                   uint64_t* h_stats, phobic_stream_t stream);
+
+/* Bucketing and pilot search (Sections 3 and 4) of partitions [j0, j1) of an
+ * n-key build with num_partitions = max(1, ceil(n / P)) partitions: one shard
+ * of a partition-sharded build.
+ *   d_sorted [n_local]: the master hashes of exactly those partitions, grouped
+ *     by partition ascending (phobic_partition_sort with num_partitions leaves
+ *     them so);
+ *   d_start [num_partitions + 1]: starts into d_sorted; entries j0..j1 are read;
+ *   d_T [num_partitions + 1]: the whole build's slot offsets
+ *     (phobic_table_offsets of the whole build's partition starts).
+ * Writes the pilot of bucket b of partition j, j0 <= j < j1, to
+ * d_pilots[b * num_partitions + j] (the caller zero-fills d_pilots: empty
+ * buckets are not written) and, when d_taken is not NULL, ORs the occupied
+ * slots of those partitions into d_taken, the occupancy bitmap of the whole
+ * build over its M slots (u32 words, bit g % 32 of word g / 32 = slot g,
+ * zero-filled by the caller, (M + 31) / 32 + 1 words).  Pilots are those a
+ * build of all n keys finds.  Synchronises `stream`.  Errors: INVALID_ARG (as
+ * phobic_build_ex, a partition count other than max(1, ceil(n / P)), j0 > j1,
+ * j1 > num_partitions, NULL pointers), PARTITION_TOO_LARGE, DUP_HASH,
+ * SEARCH_LIMIT, OOM, CUDA; j0 = j1 does nothing. */
+phobic_status phobic_search_partitions(const uint64_t* d_sorted, uint64_t n_local, const uint64_t* d_start,
+                                       const uint64_t* d_T, uint64_t n, uint64_t num_partitions, uint64_t j0,
+                                       uint64_t j1, const phobic_params* params, uint32_t* d_pilots, uint32_t* d_taken,
+                                       phobic_stream_t stream);
+
+/* The rest of a build from its partition starts and pilots: table sizes and
+ * offsets, offsets as differences to their expectation (Section 4),
+ * interleaved pilot encoding (Section 4.1) and, for alpha < 1, the Elias-Fano
+ * remap of slots >= n.  d_start [N_P + 1] (device): the whole build's
+ * partition starts, d_start[N_P] = n; d_pilots [B x N_P] (device): every
+ * pilot; d_taken (device): the occupancy bitmap as phobic_search_partitions
+ * leaves it summed over all shards (required when M > n, else may be NULL).
+ * The handle equals the one phobic_build_ex makes from the same n 64-bit keys
+ * with the same params (same export bytes, same answers); the inputs are
+ * borrowed for the call.  Synchronises `stream`.  Errors: INVALID_ARG (as
+ * phobic_build_ex, NULL pointers, starts that do not end at n, d_taken NULL
+ * with M > n), OOM, CUDA. */
+phobic_status phobic_assemble(const uint64_t* d_start, uint64_t n, const uint32_t* d_pilots, const uint32_t* d_taken,
+                              const phobic_params* params, phobic_stream_t stream, phobic_handle** out);
+
 /* Writes the 2049-entry fixed-point bucket table (Appendix C) to h_table. */
 phobic_status phobic_bucket_table(double lambda, double alpha, uint32_t partition_size, uint64_t* h_table);
 /* The same for any phobic_bucket_function. */

@@ -111,6 +111,8 @@ def lib():
         L.or_search_partitions.restype = ctypes.c_int
         L.or_search_partitions.argtypes = [vp, u64, P, vp, u64, ctypes.c_int, vp]
         L.or_verify_first_valid.restype = ctypes.c_int; L.or_verify_first_valid.argtypes = [vp, vp]
+        L.or_search_one_partition.restype = ctypes.c_int
+        L.or_search_one_partition.argtypes = [vp, u64, P, vp, vp]
         _lib = L
     return _lib
 
@@ -202,6 +204,21 @@ def string_hashes(data: np.ndarray, offsets: np.ndarray, seed: int) -> np.ndarra
     out = np.empty(o.size - 1, dtype=np.uint64)
     lib().or_string_hash_array(_ptr(d), _ptr(o), out.size, seed, _ptr(out))
     return out
+
+
+def search_one_partition(hk, lam, alpha, P, encoder=ENC_IC_C, mode=PILOT_ADDITIVE, s_max=0, bucket_fn=0):
+    """(pilots [B], taken [m] as bool) of one partition holding the hashes hk."""
+    L = lib()
+    k = _u64(hk)
+    prm = params(lam, alpha, P, encoder, mode, s_max, 0, bucket_fn)
+    B = L.or_num_buckets(float(lam), int(P))
+    m = L.or_table_size(k.size, float(alpha))
+    pil = np.zeros(B, dtype=np.uint32)
+    taken = np.zeros(m + 1, dtype=np.uint8)
+    st = L.or_search_one_partition(_ptr(k) if k.size else None, k.size, ctypes.byref(prm), _ptr(pil), _ptr(taken))
+    if st != OK:
+        raise OracleError(st, "search_one_partition")
+    return pil, taken[:m].astype(bool)
 
 
 def partition_sizes(hk, lam, alpha, P, seed=0) -> np.ndarray:

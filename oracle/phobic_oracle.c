@@ -1285,6 +1285,21 @@ int or_search_partitions(const uint64_t* hk, uint64_t n, const or_params* prm, c
     return status;
 }
 
+/* One partition alone (Section 4: partitions are searched independently):
+ * its nj master hashes, table size m = or_table_size(nj, alpha); pilots_out[B]
+ * and the final occupancy taken_out[m] (one byte per slot). */
+int or_search_one_partition(const uint64_t* hk, uint64_t nj, const or_params* prm, uint32_t* pilots_out,
+                            uint8_t* taken_out) {
+    int st = check_params(nj ? nj : 1, prm);
+    if (st != OR_OK) return st;
+    uint32_t B = or_num_buckets(prm->lambda, prm->partition_size);
+    uint64_t table[OR_TABLE_POINTS + 1];
+    or_bucket_table_fn(prm->lambda, prm->alpha, prm->partition_size, prm->bucket_fn, table);
+    uint64_t m = or_table_size(nj, prm->alpha);
+    search_stats loc = {0, 0, 0};
+    return search_partition(hk, nj, m, table, B, prm, pilots_out, taken_out, &loc);
+}
+
 /* ---- re-verification: replay every partition's buckets in order and check
  * that every pilot p' < p fails on the table state at that moment (Section 4.2:
  * the search returns the smallest working pilot). ---- */

@@ -111,6 +111,10 @@ int or_partition_sizes(const uint64_t* hk, uint64_t n, const or_params* prm, uin
 int or_search_partitions(const uint64_t* hk, uint64_t n, const or_params* prm,
                          const uint64_t* sel, uint64_t nsel, int threads, uint32_t* pilots_out);
 
+/* one partition's search from its own hashes: pilots_out[B], taken_out[m] */
+int or_search_one_partition(const uint64_t* hk, uint64_t nj, const or_params* prm, uint32_t* pilots_out,
+                            uint8_t* taken_out);
+
 /* ---- tiny-n re-verification helper: returns 1 if every p' < pilot fails ---- */
 int or_verify_first_valid(const or_mphf* h, const uint64_t* hk);
 

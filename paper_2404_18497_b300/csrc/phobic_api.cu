@@ -119,6 +119,7 @@ uint64_t num_partitions(uint64_t n, uint32_t P) {
     uint64_t np = (n + P - 1) / P;
     return np ? np : 1;
 }
+uint64_t num_partitions_of(uint64_t n, uint32_t P) { return num_partitions(n, P); }
 
 phobic_status from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return PHOBIC_OK;
@@ -365,8 +366,35 @@ cudaError_t wait_stream(cudaStream_t st) {
     return r;
 }
 
+// One shard's part of a partition-sharded build (Section 4: partitions are
+// independent, so a build can be split by partition ranges across devices).
+//   kShardSearch: bucketing and pilot search of partitions [j0, j1) only.  The
+//     master hashes of exactly those partitions are given grouped by partition
+//     (sorted, n_local of them; start: N_P + 1 entries indexing `sorted`, of
+//     which j0..j1 are read), with the build's global slot offsets T.  Pilots
+//     go to the global [B x N_P] matrix `pilots`, taken slots are ORed into the
+//     global occupancy bitmap `taken` (may be null); no handle is made.
+//   kShardAssemble: the rest of a build from the global partition starts
+//     (start, N_P + 1), the full pilot matrix and (M > n) the full occupancy
+//     bitmap: table sizes and offsets, encoding, remap, handle.  The result is
+//     the structure a single build of the same keys makes.
+// Either mode builds one set of sets[0].n keys (the whole build's n).
+enum { kShardNone = 0, kShardSearch = 1, kShardAssemble = 2 };
+struct ShardCtl {
+    int mode;
+    const uint64_t* sorted;
+    uint64_t n_local;
+    const uint64_t* start;
+    const uint64_t* T;
+    uint64_t j0, j1;
+    uint32_t* pilots;
+    uint32_t* taken;
+};
+
 phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<SetIn>& sets, const phobic_params& prm,
-                         cudaStream_t st, uint32_t key_kind, std::vector<phobic_handle*>* out) {
+                         cudaStream_t st, uint32_t key_kind, std::vector<phobic_handle*>* out,
+                         const ShardCtl* sc = nullptr) {
+    const int smode = sc ? sc->mode : kShardNone;
     ensure_pool();
     const uint32_t S = (uint32_t)sets.size();
     const uint64_t kseed = key_seed(prm.seed);
@@ -428,27 +456,48 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     std::vector<SortSeg> segs(S);
     for (uint32_t s = 0; s < S; s++) segs[s] = SortSeg{pl[s].key_base, pl[s].n, pl[s].NP, pl[s].part_base, pl[s].first_tile};
     SortSeg* d_segs;
-    uint64_t *d_tables, *sorted, *start, *T, *stats;
+    uint64_t *d_tables, *sorted = nullptr, *start = nullptr, *T = nullptr, *stats;
     uint32_t* status;
     void *sort_scratch, *sizes_scratch;
     CK(tmp.alloc(&d_segs, (size_t)S * sizeof(SortSeg)));
     CK(tmp.alloc(&d_tables, tables.size() * 8));
-    CK(tmp.alloc(&sorted, n_total * 8));
-    CK(tmp.alloc(&start, (NPT + 1) * 8));
-    CK(tmp.alloc(&T, (NPT + 1) * 8));
+    if (smode == kShardNone) {
+        CK(tmp.alloc(&sorted, n_total * 8));
+        CK(tmp.alloc(&start, (NPT + 1) * 8));
+    } else {
+        sorted = const_cast<uint64_t*>(sc->sorted);
+        start = const_cast<uint64_t*>(sc->start);
+    }
+    if (smode == kShardSearch)
+        T = const_cast<uint64_t*>(sc->T);
+    else
+        CK(tmp.alloc(&T, (NPT + 1) * 8));
     CK(tmp.alloc(&stats, 64));
     CK(tmp.alloc(&status, 64));
     CK(cudaMemsetAsync(status, 0, 64, st));
     CK(h2d(d_segs, segs.data(), S, st));
     CK(h2d(d_tables, tables.data(), tables.size(), st));
-    CK(tmp.alloc(&sort_scratch, sort_seg_scratch_bytes(n_total, tiles, S, max_np)));
     CK(ev.mark(0, st));
-    CK(launch_partition_sort_segs(in, hash_input, kseed, d_segs, S, n_total, tiles, max_np, NPT, sorted, start,
-                                  sort_scratch, status, st));
+    if (smode == kShardNone) {
+        CK(tmp.alloc(&sort_scratch, sort_seg_scratch_bytes(n_total, tiles, S, max_np)));
+        CK(launch_partition_sort_segs(in, hash_input, kseed, d_segs, S, n_total, tiles, max_np, NPT, sorted, start,
+                                      sort_scratch, status, st));
+        tmp.release(sort_scratch);
+    }
     CK(ev.mark(1, st));
-    tmp.release(sort_scratch);
-    CK(tmp.alloc(&sizes_scratch, sizes_scratch_bytes(NPT)));
-    CK(launch_sizes(start, NPT, prm.alpha, T, stats, sizes_scratch, st));
+    if (smode == kShardSearch) {
+        // the shard's largest n_j and m_j (stats[1], stats[2]) from its own partitions;
+        // M from the global offsets
+        uint64_t* Tloc;
+        const uint64_t np_loc = sc->j1 - sc->j0;
+        CK(tmp.alloc(&Tloc, (np_loc + 1) * 8));
+        CK(tmp.alloc(&sizes_scratch, sizes_scratch_bytes(np_loc)));
+        CK(launch_sizes(start + sc->j0, np_loc, prm.alpha, Tloc, stats, sizes_scratch, st));
+        CK(cudaMemcpyAsync(stats, T + NPT, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(tmp.alloc(&sizes_scratch, sizes_scratch_bytes(NPT)));
+        CK(launch_sizes(start, NPT, prm.alpha, T, stats, sizes_scratch, st));
+    }
     CK(ev.mark(2, st));
     {  // slot base of every set: T[part_base_s], s = 0..S
         std::vector<uint64_t> idx(S + 1);
@@ -463,9 +512,12 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     }
     CK(d2h(hst, stats, 3, st));
     CK(d2h(hstatus, status, 1, st));
+    if (smode == kShardAssemble) CK(d2h(hst + 16, start + NPT, 1, st));
     CK(wait_stream(st));
     if (hstatus[0] == kDevTimeout) return PHOBIC_ERR_TIMEOUT;
+    if (smode == kShardAssemble && hst[16] != n_total) return PHOBIC_ERR_INVALID_ARG;  // starts must end at n
     const uint64_t M_total = hst[0], max_n = hst[1], max_m = hst[2];
+    if (smode == kShardAssemble && M_total > n_total && !sc->taken) return PHOBIC_ERR_INVALID_ARG;
     for (uint32_t s = 0; s < S; s++) {
         pl[s].g0 = hTb[s];
         pl[s].M = hTb[s + 1] - hTb[s];
@@ -485,7 +537,7 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const double waves = (double)NPT / ((double)sms * 32.0);
+        const double waves = (double)(smode == kShardSearch ? sc->j1 - sc->j0 : NPT) / ((double)sms * 32.0);
         const double t = 0.3 * std::exp((prm.lambda - 7.0) / 1.5);
         wpp = waves <= t ? 4 : waves <= 2.0 * t ? 2 : 1;
         while (wpp > 1 && search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, cap_B, keys_in_smem, wpp) >
@@ -508,15 +560,25 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     uint32_t* taken = nullptr;
     uint64_t* bkeys = nullptr;
     unsigned long long *queue, *work = nullptr;
+    if (smode == kShardSearch) {  // partitions j0..j1-1: pilots at column offset j0, starts and offsets from j0
+        ss[0].pilot_base = sc->j0;
+        pilots = sc->pilots;
+        taken = sc->taken;
+    } else if (smode == kShardAssemble) {
+        pilots = sc->pilots;
+        taken = sc->taken;
+    } else {
+        CK(tmp.alloc(&pilots, pilots_total * 4));
+        CK(cudaMemsetAsync(pilots, 0, pilots_total * 4, st));
+        if (M_total > n_total) {
+            CK(tmp.alloc(&taken, ((M_total + 31) / 32 + 1) * 4));
+            CK(cudaMemsetAsync(taken, 0, ((M_total + 31) / 32 + 1) * 4, st));
+        }
+    }
     CK(tmp.alloc(&d_ss, (size_t)S * sizeof(SearchSet)));
     CK(h2d(d_ss, ss.data(), S, st));
-    CK(tmp.alloc(&pilots, pilots_total * 4));
-    CK(cudaMemsetAsync(pilots, 0, pilots_total * 4, st));
-    if (M_total > n_total) {
-        CK(tmp.alloc(&taken, ((M_total + 31) / 32 + 1) * 4));
-        CK(cudaMemsetAsync(taken, 0, ((M_total + 31) / 32 + 1) * 4, st));
-    }
-    if (!keys_in_smem) CK(tmp.alloc(&bkeys, n_total * 8));
+    if (!keys_in_smem && smode != kShardAssemble)
+        CK(tmp.alloc(&bkeys, (smode == kShardSearch ? sc->n_local : n_total) * 8));
     CK(tmp.alloc(&queue, 16));
     if (prm.record_timings) {
         CK(tmp.alloc(&work, 16));
@@ -524,11 +586,11 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     }
     SearchLaunch sl;
     sl.sorted = sorted;
-    sl.start = start;
-    sl.T = T;
+    sl.start = smode == kShardSearch ? start + sc->j0 : start;
+    sl.T = smode == kShardSearch ? T + sc->j0 : T;
     sl.sets = d_ss;
     sl.nsets = S;
-    sl.total_parts = NPT;
+    sl.total_parts = smode == kShardSearch ? sc->j1 - sc->j0 : NPT;
     sl.cap_B = cap_B;
     sl.mode = prm.pilot_mode;
     sl.s_max = s_max;
@@ -549,10 +611,20 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     // and for batches (the block scheduler balances uneven partitions for free)
     sl.use_queue = prm.search_schedule == 2 ? 1 : 0;
     CK(ev.mark(3, st));
-    CK(launch_search(sl, st));
+    if (smode != kShardAssemble) CK(launch_search(sl, st));
     CK(ev.mark(4, st));
-    tmp.release(sorted);
+    if (smode == kShardNone) tmp.release(sorted);
     if (bkeys) tmp.release(bkeys);
+    if (smode == kShardSearch) {
+        CK(d2h(hstatus, status, 1, st));
+        CK(wait_stream(st));
+        switch (hstatus[0]) {
+            case kDevOk: return PHOBIC_OK;
+            case kDevDupHash: return PHOBIC_ERR_DUP_HASH;
+            case kDevSearchLimit: return PHOBIC_ERR_SEARCH_LIMIT;
+            default: return PHOBIC_ERR_TIMEOUT;
+        }
+    }
 
     // ---- K5: offset differences; K6: column maxima (all sets)
     std::vector<OffDesc> od(S);
@@ -1126,6 +1198,58 @@ phobic_status phobic_build_host(const uint64_t* h_keys, uint64_t n, const phobic
     }
     s = build_impl(d, 1, n, *params, st, out);
     cudaFreeAsync(d, st);
+    return s;
+}
+
+phobic_status phobic_table_offsets(const uint64_t* d_start, uint64_t num_partitions, double alpha, uint64_t* d_T,
+                                   uint64_t* h_stats, phobic_stream_t stream) {
+    if (!d_start || !d_T || num_partitions == 0 || !(alpha > 0.0) || alpha > 1.0) return PHOBIC_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    ensure_pool();
+    Arena tmp(st);
+    uint64_t* stats;
+    void* scratch;
+    CK(tmp.alloc(&stats, 64));
+    CK(tmp.alloc(&scratch, sizes_scratch_bytes(num_partitions)));
+    CK(launch_sizes(d_start, num_partitions, alpha, d_T, stats, scratch, st));
+    uint64_t hs[3];
+    CK(d2h(hs, stats, 3, st));
+    CK(wait_stream(st));
+    CK(cudaGetLastError());
+    if (h_stats) std::memcpy(h_stats, hs, sizeof(hs));
+    return PHOBIC_OK;
+}
+
+phobic_status phobic_search_partitions(const uint64_t* d_sorted, uint64_t n_local, const uint64_t* d_start,
+                                       const uint64_t* d_T, uint64_t n, uint64_t num_partitions, uint64_t j0,
+                                       uint64_t j1, const phobic_params* params, uint32_t* d_pilots, uint32_t* d_taken,
+                                       phobic_stream_t stream) {
+    if (!params || !d_start || !d_T || !d_pilots) return PHOBIC_ERR_INVALID_ARG;
+    phobic_status s = check_params(n, *params);
+    if (s != PHOBIC_OK) return s;
+    if (num_partitions != num_partitions_of(n, params->partition_size) || j0 > j1 || j1 > num_partitions)
+        return PHOBIC_ERR_INVALID_ARG;
+    if (j0 == j1) return PHOBIC_OK;
+    if (!d_sorted && n_local) return PHOBIC_ERR_INVALID_ARG;
+    ShardCtl sc{kShardSearch, d_sorted, n_local, d_start, d_T, j0, j1, d_pilots, d_taken};
+    std::vector<phobic_handle*> hs;
+    return build_sets(nullptr, 0, {SetIn{0, n, params->partition_size}}, *params,
+                      reinterpret_cast<cudaStream_t>(stream), 0, &hs, &sc);
+}
+
+phobic_status phobic_assemble(const uint64_t* d_start, uint64_t n, const uint32_t* d_pilots, const uint32_t* d_taken,
+                              const phobic_params* params, phobic_stream_t stream, phobic_handle** out) {
+    if (!out) return PHOBIC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params || !d_start || !d_pilots) return PHOBIC_ERR_INVALID_ARG;
+    phobic_status s = check_params(n, *params);
+    if (s != PHOBIC_OK) return s;
+    ShardCtl sc{kShardAssemble, nullptr, 0, d_start, nullptr, 0, 0, const_cast<uint32_t*>(d_pilots),
+                const_cast<uint32_t*>(d_taken)};
+    std::vector<phobic_handle*> hs;
+    s = build_sets(nullptr, 0, {SetIn{0, n, params->partition_size}}, *params, reinterpret_cast<cudaStream_t>(stream), 0,
+                   &hs, &sc);
+    if (s == PHOBIC_OK) *out = hs[0];
     return s;
 }
 

@@ -168,6 +168,9 @@ _SIGS = [
     ("phobic_server_get_stats", _INT, [_VP, ctypes.POINTER(phobic_server_stats)]),
     ("phobic_server_destroy", None, [_VP]),
     ("phobic_pool_bytes", _INT, [ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
+    ("phobic_table_offsets", _INT, [_VP, _U64, _DBL, _VP, _VP, _VP]),
+    ("phobic_search_partitions", _INT, [_VP, _U64, _VP, _VP, _U64, _U64, _U64, _U64, _PP, _VP, _VP, _VP]),
+    ("phobic_assemble", _INT, [_VP, _U64, _VP, _VP, _PP, _VP, ctypes.POINTER(_VP)]),
 ]
 
 
@@ -550,6 +553,55 @@ def phobic_get_timings(h: Handle) -> dict:
     t = phobic_timings()
     _check(lib().phobic_get_timings(h.ptr, ctypes.byref(t)), "phobic_get_timings")
     return {f[0]: (float if f[1] is ctypes.c_float else int)(getattr(t, f[0])) for f in phobic_timings._fields_}
+
+
+def phobic_table_offsets(start: torch.Tensor, alpha: float, stream=None):
+    """Slot offsets T [N_P + 1] (int64) from partition starts [N_P + 1], and
+    (M, largest n_j, largest m_j)."""
+    st = _dev_u64(start, "start")
+    np_ = st.numel() - 1
+    T = torch.empty(max(np_ + 1, 1), dtype=torch.int64, device=st.device)
+    stats = (ctypes.c_uint64 * 3)()
+    _check(lib().phobic_table_offsets(st.data_ptr(), np_, float(alpha), T.data_ptr(), stats, _stream(stream)),
+           "phobic_table_offsets")
+    return T, (int(stats[0]), int(stats[1]), int(stats[2]))
+
+
+def _dev_u32(t: torch.Tensor, what: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype not in (torch.int32, torch.uint32):
+        raise TypeError(f"{what} must be a CUDA int32 or uint32 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t
+
+
+def phobic_search_partitions(sorted_hk: torch.Tensor, start: torch.Tensor, T: torch.Tensor, n: int,
+                             num_partitions: int, j0: int, j1: int, params: phobic_params, pilots: torch.Tensor,
+                             taken: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Pilot search of partitions [j0, j1) of an n-key build into the whole
+    build's pilot matrix `pilots` (int32, B x N_P) and occupancy bitmap `taken`
+    (int32 words, or None)."""
+    st, TT = _dev_u64(start, "start"), _dev_u64(T, "T")
+    srt = _dev_u64(sorted_hk, "sorted_hk") if sorted_hk.numel() else None
+    pl = _dev_u32(pilots, "pilots")
+    tk = None if taken is None else _dev_u32(taken, "taken")
+    _check(lib().phobic_search_partitions(None if srt is None else srt.data_ptr(), sorted_hk.numel(), st.data_ptr(),
+                                          TT.data_ptr(), int(n), int(num_partitions), int(j0), int(j1),
+                                          ctypes.byref(params), pl.data_ptr(), None if tk is None else tk.data_ptr(),
+                                          _stream(stream)), "phobic_search_partitions")
+
+
+def phobic_assemble(start: torch.Tensor, n: int, pilots: torch.Tensor, taken: Optional[torch.Tensor],
+                    params: phobic_params, stream=None) -> Handle:
+    """The structure of an n-key build from its partition starts, pilots and
+    occupancy bitmap."""
+    st = _dev_u64(start, "start")
+    pl = _dev_u32(pilots, "pilots")
+    tk = None if taken is None else _dev_u32(taken, "taken")
+    h = ctypes.c_void_p()
+    _check(lib().phobic_assemble(st.data_ptr(), int(n), pl.data_ptr(), None if tk is None else tk.data_ptr(),
+                                 ctypes.byref(params), _stream(stream), ctypes.byref(h)), "phobic_assemble")
+    return Handle(h.value)
 
 
 def phobic_kernel_launches() -> int:
