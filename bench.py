@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--sharded", action="store_true",
+                    help="one MPHF over the keys of all ranks, built partition-sharded (all-to-all of master "
+                         "hashes by partition owner; each rank holds --n keys)")
     ap.add_argument("--only", choices=["batch", "serve", "lambda", "ablation", "encoders", "table1"], default=None,
                     help="run one extra section alone (lambda: the large-lambda sweep; ablation: the bucket "
                          "functions of Fig. 3a)")
@@ -98,24 +101,20 @@ def workload(a):
     return w
 
 
-# Per-key counters from the ncu captures summarised in profiles/ (3e7-key case of
+# Per-key counters from ncu captures (the 3e7-key case of
 # this workload), valid only for the kernel sources they were taken on: each
 # entry names the source files and the sha256 (first 16 hex digits) of their
 # concatenation.  When a source changes, the counters are reported as null.
 NCU_CAPTURES = {
     "k_search": {"files": ["paper_2404_18497_b300/csrc/k_search.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-                 "sha": "727a759e01aea933", "n": 3e7, "warp_inst": 2106864120, "dram_bytes": 550261504 + 322606592,
-                 "profile": "profiles/k_search_3e7.md"},
+                 "sha": "727a759e01aea933", "n": 3e7, "warp_inst": 2106864120, "dram_bytes": 550261504 + 322606592},
     "k_query": {"files": ["paper_2404_18497_b300/csrc/k_query.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-                "sha": "a9701eb0d4c197a4", "n": 3e7, "dram_bytes": 250165504 + 198775296,
-                "profile": "profiles/k_query_3e7.md"},
+                "sha": "a9701eb0d4c197a4", "n": 3e7, "dram_bytes": 250165504 + 198775296},
     "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
                "sha": "22d85e6612ee39f3", "n": 3e7,
-               "dram_bytes": (240055040 + 195902464) + (242552320 + 197608192) + (242419456 + 196858880),
-               "profile": "profiles/k_sort_pass_3e7.md"},
+               "dram_bytes": (240055040 + 195902464) + (242552320 + 197608192) + (242419456 + 196858880)},
     "k_hash": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "22d85e6612ee39f3", "n": 3e7, "dram_bytes": 240021248 + 191719168,
-               "profile": "profiles/k_hash_copy_3e7.md"},
+               "sha": "22d85e6612ee39f3", "n": 3e7, "dram_bytes": 240021248 + 191719168},
 }
 ISSUE_SLOTS_PER_CLOCK = 148 * 4  # B300: 148 SMs x 4 warp schedulers, one warp instruction per clock each
 SM_MAX_MHZ = 2032.0
@@ -394,7 +393,8 @@ def run_ours(a):
                 "kernel": "k_search", "launch_ms": ph["search_ms"], "warp_inst_per_launch": inst,
                 "peak_source": "148 SMs x 4 schedulers x 1 warp-inst/clock x 2032 MHz (unit counts and max clock)",
                 "sm_mhz_measured": sm_mhz,
-                "counters": cs["profile"] if cs else "stale: kernel source changed since the ncu capture",
+                "counters": f"ncu capture at {cs['n']:.0e} keys, scaled per key" if cs else
+                            "stale: kernel source changed since the ncu capture",
                 "dominant_kernel_by_time": dom, "per_kernel_ms": kern}
     cq = capture("k_query")
     q_bytes = 16.0 * w["q_uniform"]
@@ -521,6 +521,139 @@ def run_ours(a):
         "serve": serve,
     }
     print(json.dumps(res_line))
+
+# ------------------------------------------------------ partition-sharded ---
+SHARDED = ("one MPHF over {total:.0e} distinct uint64 keys ({n:.0e} resident per GPU, counter-based stream), "
+           "lambda=7, alpha=0.99 with Elias-Fano remap, partition size 2500, IC-D, built partition-sharded over "
+           "{world} GPU(s); {n:.0e} uniform positive queries per GPU against the replicated structure")
+
+
+def run_sharded(a):
+    """The build of ONE MPHF whose keys are spread over all ranks (Section 4:
+    partitions are independent): each rank hashes and groups its own keys, one
+    all-to-all sends every partition's hashes to its owner, each rank searches
+    its partitions, and one all-reduce merges pilots and occupancy; every rank
+    then encodes the same structure.  Weak scaling: each rank holds n keys."""
+    import hashlib
+    import socket
+
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        with socket.socket() as so:
+            so.bind(("127.0.0.1", 0))
+            port = so.getsockname()[1]
+        dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1,
+                                device_id=torch.device("cuda", local))
+    from paper_2404_18497_b300 import build as libbuild
+
+    libbuild.build()
+    from paper_2404_18497_b300 import phobic, shard, workloads
+
+    n = int(a.n or 1e8)
+    keys = workloads.stream_keys_torch(rank * n, n, 2, "cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3 + 1000 * rank)
+    dq = keys[torch.randint(0, n, (n,), device="cuda", generator=g)]
+    out = torch.empty_like(dq)
+    prm = phobic.make_params(7.0, 0.99, 2500, seed=0, encoder="IC-D")
+    comm = shard.TorchComm(device=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        h = shard.sharded_build(keys, prm, comm)
+        e[1].record(stream)
+        phobic.phobic_query(h, dq, out, stream)
+        e[2].record(stream)
+        return h, e
+
+    for _ in range(a.warmup):
+        h, _ = step()
+        h.free()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = Clocks(local)
+    clk.start()
+    l0 = phobic.phobic_kernel_launches()
+    t0 = time.perf_counter()
+    recs = []
+    for _ in range(a.steps):
+        recs.append(step())
+    torch.cuda.synchronize()
+    barrier(world)
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    clocks = clk.stop()
+    launches = phobic.phobic_kernel_launches() - l0
+    b_ms = reduce_max(statistics.mean(e[0].elapsed_time(e[1]) for _, e in recs), world)
+    q_ms = reduce_max(statistics.mean(e[1].elapsed_time(e[2]) for _, e in recs), world)
+    ms_step = reduce_max(wall_ms / a.steps, world)
+    h = recs[-1][0]
+    digest = int(hashlib.sha256(h.export()).hexdigest()[:15], 16)
+    same_everywhere = len(set(comm.all_gather_int(digest))) == 1
+    srt = torch.sort(h.query(keys)).values  # this rank's keys get distinct positions below world * n
+    distinct = int((srt[1:] != srt[:-1]).sum().item()) + 1
+    ok_perm = distinct == n and int(srt[-1].item()) < world * n and int(srt[0].item()) >= 0
+    ok_perm = min(comm.all_gather_int(int(ok_perm))) == 1
+    del srt
+    bpk = h.bits_per_key()
+    single_equal = None
+    if world == 1:
+        ref = phobic.phobic_build_ex(keys, prm)
+        single_equal = ref.export() == h.export()
+        ref.free()
+    for hh, _ in recs:
+        hh.free()
+
+    e2e = None
+    if not a.no_e2e:
+        pin = keys.cpu().pin_memory()
+        dk2 = torch.empty_like(keys)
+        ts = []
+        for i in range(2 + min(a.steps, 3)):
+            torch.cuda.synchronize()
+            barrier(world)
+            t = time.perf_counter()
+            dk2.copy_(pin, non_blocking=True)
+            hh = shard.sharded_build(dk2, prm, comm)
+            torch.cuda.synchronize()
+            if i >= 2:
+                ts.append(time.perf_counter() - t)
+            hh.free()
+        e2e = {"value": world * n / reduce_max(statistics.mean(ts), world) / 1e6, "unit": "Mkeys/s",
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 0,
+               "note": "each rank's keys copied from pinned host memory inside the timed region, then the sharded build"}
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    hbm, src = peaks()
+    build_bytes = 8.3 * n
+    line = {
+        "metric": METRIC, "value": world * n / (b_ms / 1e3) / 1e6, "unit": "Mkeys/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": SHARDED.format(total=world * n, n=n, world=world), "n_total": world * n,
+                   "n_per_gpu": n, "lambda": 7.0, "alpha": 0.99, "P": 2500, "encoder": "IC-D",
+                   "parallelism": f"partition-sharded x{world} (NCCL all-to-all + all-reduce)",
+                   "l2": "inputs larger than L2 (8e8-byte key and query arrays vs 126 MB L2)",
+                   "gpu": torch.cuda.get_device_name(local)},
+        "build_ms": b_ms, "query_mkeys_s": world * n / (q_ms / 1e3) / 1e6, "bits_per_key": bpk,
+        "structure_identical_on_all_ranks": same_everywhere, "equals_single_build": single_equal,
+        "positions_distinct_per_rank": ok_perm, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": build_bytes / (b_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": build_bytes / (b_ms / 1e3) / 1e9 / hbm, "traffic": None,
+                     "kernel": "whole sharded build (8.3 B/key algorithmic)", "peak_source": f"{src} hbm_gbs"},
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+    dist.destroy_process_group()
+
 
 # ------------------------------------------------------------- XOR pilots ---
 def run_xor(a, phobic, torch, dk, dqu, out, w, n, world):
@@ -1092,8 +1225,7 @@ def run_strings(a):
         "roofline": {"bound": "hbm", "kernel": "k_query_strings", "unit": "GB/s", "peak": hbm,
                      "achieved": (str_bytes + 8.0 * n) / (q_ms / 1e3) / 1e9,
                      "frac": (str_bytes + 8.0 * n) / (q_ms / 1e3) / 1e9 / hbm,
-                     "algorithmic_bytes_per_launch": str_bytes + 8.0 * n, "peak_source": f"{src} hbm_gbs",
-                     "profile": "profiles/k_hash_strings_2e7.md"},
+                     "algorithmic_bytes_per_launch": str_bytes + 8.0 * n, "peak_source": f"{src} hbm_gbs"},
         "e2e": None, "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps, "cpu_baseline": None}))
 
 
@@ -1126,6 +1258,8 @@ def main():
         return run_only(a)
     if a.strings and a.impl != "reference":
         return run_strings(a)
+    if a.sharded and a.impl != "reference":
+        return run_sharded(a)
     if a.impl == "reference":
         run_reference(a)
     else:

@@ -430,11 +430,15 @@ phobic_status phobic_selftest_sort_wait_timeout(const uint64_t* d_hk, uint64_t n
  * Same inputs, outputs and results as phobic_partition_sort, for
  * n <= PHOBIC_NOALLOC_MAX_KEYS; a larger n (or a partition count whose digit
  * tables would not fit) returns PHOBIC_ERR_INVALID_ARG.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  All calls share the one array, so
- * calls whose work overlaps on the GPU (on different streams or threads)
- * race with each other: the caller must serialise them.  Synchronises
- * `stream`; calls no cudaMalloc, cudaFree or other allocating routine.
+ * The first call on a device looks up the array's device address and keeps
+ * it for the life of the process, so the library must not be used on a
+ * device after cudaDeviceReset (the array's address may change).  Every call
+ * synchronises `stream` and reads the sort's error word back to the host, so
+ * it must not be called while `stream` (or the legacy default stream) is
+ * being captured into a CUDA graph.  All calls share the one array, so calls
+ * whose work overlaps on the GPU (on different streams or threads) race with
+ * each other: the caller must serialise them.  Calls no cudaMalloc, cudaFree
+ * or other allocating routine.
  */
 phobic_status phobic_partition_sort_noalloc(const uint64_t* d_hk, uint64_t n, uint64_t num_partitions,
                                             uint64_t* d_sorted, uint64_t* d_start, phobic_stream_t stream);

@@ -7,8 +7,9 @@
 // 2022): one upfront pass computes every digit histogram, then each digit pass
 // ranks a tile in shared memory.  It finds the tile's global offset by decoupled
 // look-back over its predecessors and writes the tile out in digit order.  When
-// the input is raw 64-bit keys, the upfront pass and the first digit pass hash
-// them on the fly, so no separate array of hashes is written.
+// the input is raw 64-bit keys, the upfront pass hashes them and writes the
+// master hashes out (8 B per key more than the method needs), so that no digit
+// pass hashes again.
 //
 // Segments: the input may hold several independent key sets back to back (a
 // batched build).  Each set is a segment with its own partition count; tiles

@@ -130,3 +130,19 @@ def test_invalid_arguments_without_gpu(libpath):
     assert L.phobic_server_submit_release(None, 1, ctypes.byref(rid)) == 1
     assert L.phobic_server_create(None, None) == 1
     L.phobic_server_destroy(None)
+
+
+def test_noalloc_sort_rejects_sizes_on_the_host(libpath):
+    """phobic_partition_sort_noalloc refuses sizes beyond its fixed array before
+    it touches the device: more than PHOBIC_NOALLOC_MAX_KEYS keys, or (at the
+    maximum n) a partition count whose digit tables would not fit (2^36
+    partitions need four passes of 9-bit digits; the array holds three).  The
+    pointers are never dereferenced."""
+    from paper_2404_18497_b300 import phobic
+
+    L = phobic.lib()
+    fake = ctypes.c_void_p(16)
+    mx = phobic.NOALLOC_MAX_KEYS
+    assert L.phobic_partition_sort_noalloc(fake, mx + 1, 1, fake, fake, None) == 1
+    assert L.phobic_partition_sort_noalloc(fake, mx, 1 << 36, fake, fake, None) == 1
+    assert L.phobic_partition_sort_noalloc(fake, 0, 1, fake, fake, None) == 1

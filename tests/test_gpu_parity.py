@@ -363,6 +363,14 @@ def test_errors(ph):
         with pytest.raises(ph.PhobicError) as e:
             ph.phobic_build_ex(_dev(keys), ph.make_params(**args))
         assert e.value.status == "INVALID_ARG"
+    # a partition whose table reaches 2^16 slots (the search holds slots as u16):
+    # P = 16384 at alpha = 0.2 gives m_j = ceil(n_j / 0.2) ~ 81920; the build
+    # refuses it before any search launch (the oracle, with no such limit, builds it)
+    big = _keys(4 * 16384, 12)
+    for mode in (0, 1):
+        with pytest.raises(ph.PhobicError) as e:
+            ph.phobic_build_ex(_dev(big), ph.make_params(7.0, 0.2, 16384, mode=mode))
+        assert e.value.status == "PARTITION_TOO_LARGE", mode
     # the context is still usable after the errors
     h = ph.phobic_build(_dev(keys), 7.0, 1.0, 2500, 0)
     assert torch.unique(h.query(_dev(keys))).numel() == keys.size

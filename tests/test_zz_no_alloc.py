@@ -48,6 +48,23 @@ def test_noalloc_sort_matches_allocating_sort_twice(ph):
         assert torch.equal(out, ref_sorted)
 
 
+def test_noalloc_sort_at_its_maximum_size(ph):
+    """n = PHOBIC_NOALLOC_MAX_KEYS with 2^18 partitions: two digit passes of 9
+    bits (512 bins), the widest digits the fixed array is sized for, so the
+    scratch the sort needs is the array's full sort region."""
+    n = ph.NOALLOC_MAX_KEYS
+    NP = 1 << 18
+    for seed in (3, 4):
+        hk = _hashes(n, seed)
+        ref_sorted, ref_start = ph.phobic_partition_sort(hk, NP)
+        out = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+        start = torch.full((NP + 1,), -1, dtype=torch.int64, device="cuda")
+        ph.phobic_partition_sort_noalloc(hk, NP, out, start)
+        torch.cuda.synchronize()
+        assert torch.equal(start, ref_start)
+        assert torch.equal(out, ref_sorted)
+
+
 def test_noalloc_rejects_too_many_keys(ph):
     n = ph.NOALLOC_MAX_KEYS + 1
     hk = torch.zeros(n, dtype=torch.int64, device="cuda")
