@@ -17,6 +17,7 @@ problems: weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -59,6 +60,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the 1e6-key and 2e8-string configurations measured after the default one")
     ap.add_argument("--sharded", action="store_true",
                     help="one MPHF over the keys of all ranks, built partition-sharded (all-to-all of master "
                          "hashes by partition owner; each rank holds --n keys)")
@@ -478,6 +481,12 @@ def run_ours(a):
         if not a.no_serve:
             serve = run_serve(a, phobic, workloads, torch)
 
+    others = None
+    if world == 1 and not a.no_other_configs and a.impl == "ours" and n == int(1e8):
+        dk = dqu = dqz = out = None
+        torch.cuda.empty_cache()
+        others = run_other_configs(a, phobic, workloads, torch)
+
     if rank != 0:
         return
     cpu = None
@@ -519,8 +528,83 @@ def run_ours(a):
         "xor_mode": xor,
         "batch": batch,
         "serve": serve,
+        "other_configs": others,
     }
     print(json.dumps(res_line))
+
+
+def _time_build_query(phobic, torch, build, query, steps, warmup):
+    """Mean device ms of build() and of query(h) over `steps` after `warmup`,
+    CUDA events on the current stream; returns (build ms, query ms, last handle)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        h = build()
+        query(h)
+        h.free()
+    bms, qms = [], []
+    for i in range(steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        h = build()
+        e[1].record(stream)
+        query(h)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        bms.append(e[0].elapsed_time(e[1]))
+        qms.append(e[1].elapsed_time(e[2]))
+        if i + 1 < steps:
+            h.free()
+    return statistics.mean(bms), statistics.mean(qms), h
+
+
+def run_other_configs(a, phobic, workloads, torch):
+    """The two other single-GPU configurations on the same run, after the timed
+    region of the default one: C1 (1e6 u64 keys, lambda 7, alpha 1, IC-C, 1e7
+    uniform queries) and C3 (2e8 random strings of 10-50 characters, lambda
+    7.5, alpha 0.99, IC-D, every string queried once)."""
+    hbm, _ = peaks()
+    res = {}
+    keys = workloads.distinct_u64(1_000_000, 1)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dq = torch.from_numpy(workloads.uniform_queries(keys, 10_000_000, 3).view(np.int64)).cuda()
+    out = torch.empty_like(dq)
+    prm = phobic.make_params(7.0, 1.0, 2500, seed=0, encoder="IC-C")
+    b, q, h = _time_build_query(phobic, torch, lambda: phobic.phobic_build_ex(dk, prm),
+                                lambda hh: phobic.phobic_query(hh, dq, out), 10, 3)
+    res["C1"] = {"workload": SMALL, "build_ms": b, "build_mkeys_s": 1e6 / (b / 1e3) / 1e6, "query_ms": q,
+                 "query_mkeys_s": 1e7 / (q / 1e3) / 1e6, "query_hbm_frac": 16.0 * 1e7 / (q / 1e3) / 1e9 / hbm,
+                 "bits_per_key": h.bits_per_key(),
+                 "result_is_permutation": bool(torch.equal(torch.sort(h.query(dk)).values,
+                                                           torch.arange(1_000_000, device="cuda")))}
+    h.free()
+    del dk, dq, out
+    n = 200_000_000
+    data, off = workloads.random_strings_torch(n, 3, "cuda")
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    prm = phobic.make_params(7.5, 0.99, 2500, seed=0, encoder="IC-D")
+
+    def build_s():
+        while True:
+            try:
+                return phobic.phobic_build_strings(data, off, prm)
+            except phobic.PhobicError as e:  # two strings share a 64-bit hash: take another seed
+                if e.status != "DUP_HASH":
+                    raise
+                prm.seed += 1
+
+    b, q, h = _time_build_query(phobic, torch, build_s, lambda hh: phobic.phobic_query_strings(hh, data, off, out),
+                                5, 2)
+    str_bytes = float(off[-1].item()) + 8.0 * (n + 1)
+    res["C3"] = {"workload": STRINGS + " (strings drawn on the device with torch's generator)", "build_ms": b,
+                 "build_mkeys_s": n / (b / 1e3) / 1e6, "query_ms": q, "query_mkeys_s": n / (q / 1e3) / 1e6,
+                 "query_hbm_frac": (str_bytes + 8.0 * n) / (q / 1e3) / 1e9 / hbm, "bits_per_key": h.bits_per_key(),
+                 "seed": int(prm.seed),
+                 "result_is_permutation": bool(torch.equal(torch.sort(out).values,
+                                                           torch.arange(n, device="cuda")))}
+    h.free()
+    del data, off, out
+    torch.cuda.empty_cache()
+    return res
 
 # ------------------------------------------------------ partition-sharded ---
 SHARDED = ("one MPHF over {total:.0e} distinct uint64 keys ({n:.0e} resident per GPU, counter-based stream), "
@@ -988,11 +1072,11 @@ def _percentiles(x):
             "mean_ms": float(x.mean()), "max_ms": float(x.max())}
 
 
-def serve_trace(secs, brate, qrate, seed):
+def serve_trace(secs, brate, qrate, seed, build_sizes=(1e4, 5e7), query_sizes=(1e3, 1e6)):
     """Seeded open-loop trace: (arrival s, kind, size) sorted by arrival."""
     rng = np.random.default_rng(seed)
     ev = []
-    for kind, rate, lo, hi in ((0, brate, 1e4, 5e7), (1, qrate, 1e3, 1e6)):
+    for kind, rate, (lo, hi) in ((0, brate, build_sizes), (1, qrate, query_sizes)):
         t = 0.0
         while True:
             t += rng.exponential(1.0 / rate)
@@ -1003,7 +1087,7 @@ def serve_trace(secs, brate, qrate, seed):
     return ev
 
 
-def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_every=100):
+def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_every=100, budget=120 * 10**9):
     """Replays the trace against a server.  Latency is measured from each
     request's scheduled arrival (open loop: a late submission counts against
     it) to its completion, on the steady clock the library also uses.
@@ -1016,10 +1100,11 @@ def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_eve
     margin = 1 << 20
     rng = np.random.default_rng(seed)
     prm = phobic.make_params(7.0, 0.99, 2500, encoder=1)
-    srv = phobic.Server(hbm_budget_bytes=120 * 10**9, build_slots=2, serial=serial)
+    srv = phobic.Server(hbm_budget_bytes=budget, build_slots=2, serial=serial)
     ring = 1 << 27
     qout = torch.empty(ring, dtype=torch.int64, device="cuda")
     head = 0
+    pend_q = collections.deque()  # (request id, ring start, keys) of submitted queries, oldest first
     req = {}        # request id -> (kind, arrival ns, ...)
     resident = []   # (handle id, pool start, n), oldest first
     keep = set()    # handles kept for the final checks
@@ -1084,11 +1169,20 @@ def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_eve
             q0 = ps - mn if rng.integers(0, 2) else ps + n - mp
             if head + m > ring:
                 head = 0
-            # the output region must be free: wait for older requests that overlap it
-            while any(r[0] == 1 and r[2] < head + m and head < r[2] + r[3] for r in req.values()):
-                handle_completions()
+            # the output region must be free: wait while the oldest pending query's
+            # region overlaps it (regions are handed out in ring order, so when the
+            # oldest one does not overlap, no newer one does)
+            while pend_q:
+                r0, st0, m0 = pend_q[0]
+                if r0 not in req:
+                    pend_q.popleft()
+                elif st0 < head + m and head < st0 + m0:
+                    handle_completions()
+                else:
+                    break
             rid = srv.submit_query(hid, keys_pool[q0:q0 + m], qout[head:head + m])
             req[rid] = (1, arrival, head, m)
+            pend_q.append((rid, head, m))
             if len(samples) < 400 and rid % check_every == 0:
                 samples.append((hid, q0, m, rid))
                 outs[rid] = None
@@ -1148,12 +1242,58 @@ def run_serve(a, phobic, workloads, torch):
     del keys_pool
     torch.cuda.empty_cache()
     phobic.phobic_trim(0)
+    sweep = run_serve_sweep(phobic, torch, workloads, cap)
     return {"workload": SERVE.format(secs=secs, brate=brate, qrate=qrate, cap=cap),
             "offered": {"seconds": secs, "build_per_s": brate, "query_per_s": qrate,
                         "builds": sum(1 for e in trace if e[1] == 0), "queries": sum(1 for e in trace if e[1] == 1)},
             "continuous": cont, "serial": ser,
             "query_p99_speedup": (ser["query_latency"]["p99_ms"] / cont["query_latency"]["p99_ms"])
-            if cont["query_latency"]["p99_ms"] else None}
+            if cont["query_latency"]["p99_ms"] else None,
+            **sweep}
+
+
+SERVE_SWEEP = ("offered-load sweep: {secs:g} s per point, builds (sizes log-uniform in [1e4, 5e6]) at 20/s and small "
+               "query batches (sizes log-uniform in [1e3, 3e4], 90% members) at each offered rate, continuous "
+               "batching against one request at a time; budget point: builds of 1e7-5e7 keys at 100/s under a "
+               "4 GB HBM budget, so admission waits for memory")
+
+
+def _point(r):
+    return {"query_p50_ms": r["query_latency"]["p50_ms"], "query_p99_ms": r["query_latency"]["p99_ms"],
+            "build_p50_ms": r["build_latency"]["p50_ms"], "build_p99_ms": r["build_latency"]["p99_ms"],
+            "query_req_per_s": r["requests"]["queries"] / r["wall_s"], "query_mkeys_s": r["query_mkeys_s"],
+            "build_mkeys_s": r["build_mkeys_s"], "mean_requests_per_launch": r["mean_requests_per_launch"],
+            "submit_lag_s": r["submit_s"] - r["offered_s"], "builds_waited_for_memory": r["builds_waited_for_memory"],
+            "peak_accounted_gb": r["peak_accounted_gb"],
+            "equal_alone": r["check"]["queries_equal_alone"] and r["check"]["builds_equal_alone"]}
+
+
+def run_serve_sweep(phobic, torch, workloads, cap, secs=6.0, rates=(2000, 8000, 32000, 64000)):
+    """Throughput and p50/p99 per request type against offered query load, up
+    to the rate the submitting thread sustains, continuous against serial; and
+    one point where the HBM budget binds."""
+    keys_pool = workloads.stream_keys_torch(80_000_000_000, 1 << 28, 14, "cuda")
+    torch.cuda.synchronize()
+    points = []
+    for qr in rates:
+        trace = serve_trace(secs, 20.0, qr, 100 + qr, build_sizes=(1e4, 5e6), query_sizes=(1e3, 3e4))
+        pt = {"offered_query_per_s": qr}
+        for mode, serial in (("continuous", False), ("serial", True)):
+            r = run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, 7, check_every=500)
+            r["offered_s"] = secs
+            pt[mode] = _point(r)
+            phobic.phobic_trim(0)
+        points.append(pt)
+    trace = serve_trace(secs, 100.0, 500.0, 9, build_sizes=(1e7, 5e7), query_sizes=(1e3, 1e5))
+    budget = {"hbm_budget_gb": 4.0}
+    for mode, serial in (("continuous", False), ("serial", True)):
+        r = run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, 8, check_every=50, budget=4 * 10**9)
+        r["offered_s"] = secs
+        budget[mode] = _point(r)
+        phobic.phobic_trim(0)
+    del keys_pool
+    torch.cuda.empty_cache()
+    return {"sweep_workload": SERVE_SWEEP.format(secs=secs), "sweep": points, "budget_point": budget}
 
 
 def run_strings(a):

@@ -34,11 +34,6 @@ namespace phobic {
 
 namespace {
 
-__device__ __forceinline__ uint64_t expectation(uint64_t j, uint64_t Q) {
-    uint64_t lo = j * Q, hi = __umul64hi(j, Q);
-    return (hi << 32) | (lo >> 32);
-}
-
 // Assemble output word `word` (index inside the array) from values i in
 // [0, count) placed at bit base + i*w; value(i) supplies the value.  Only this
 // column's bits are produced.
@@ -107,7 +102,7 @@ __global__ void __launch_bounds__(256) k_offset_minmax(const uint64_t* __restric
     const uint64_t T0 = T[d.part_base];
     long long lo = LLONG_MAX, hi = LLONG_MIN;
     for (uint64_t j = (uint64_t)part * blockDim.x + threadIdx.x; j <= d.np; j += (uint64_t)nparts * blockDim.x) {
-        const long long v = (long long)(T[d.part_base + j] - T0 - expectation(j, d.Q));
+        const long long v = (long long)(T[d.part_base + j] - T0 - offset_expectation(j, d.Q));
         lo = min(lo, v);
         hi = max(hi, v);
     }
@@ -139,7 +134,7 @@ __global__ void k_offset_pack(const uint64_t* __restrict__ T, const OffDesc* __r
         const uint64_t word = t - word_begin[s];
         const uint64_t T0 = T[d.part_base];
         arena[d.dst_word + word] = gather_word(word, 0, d.width, d.np + 1, [&](uint64_t j) {
-            return (uint64_t)((long long)(T[d.part_base + j] - T0 - expectation(j, d.Q)) - d.dmin);
+            return (uint64_t)((long long)(T[d.part_base + j] - T0 - offset_expectation(j, d.Q)) - d.dmin);
         });
     }
 }

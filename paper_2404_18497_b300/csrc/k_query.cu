@@ -19,11 +19,6 @@ namespace {
 
 constexpr uint64_t kMeta = (1ull << 56) - 1;
 
-__device__ __forceinline__ uint64_t expectation(uint64_t j, uint64_t Q) {
-    uint64_t lo = j * Q, hi = __umul64hi(j, Q);
-    return (hi << 32) | (lo >> 32);
-}
-
 // T_j and T_{j+1}: the two stored differences are adjacent (2w <= 62 bits), so
 // one 128-bit window of the packed words holds both.  kNarrow: read the second
 // word only when the pair runs into it.
@@ -47,12 +42,12 @@ __device__ __forceinline__ void offsets_of(const QueryView& v, uint64_t j, uint6
         d0 = x & mask;
         d1 = (x >> w) & mask;
     }
-    *Tj = expectation(j, v.off_Q) + (uint64_t)v.off_dmin + d0;
-    *Tj1 = expectation(j + 1, v.off_Q) + (uint64_t)v.off_dmin + d1;
+    *Tj = offset_expectation(j, v.off_Q) + (uint64_t)v.off_dmin + d0;
+    *Tj1 = offset_expectation(j + 1, v.off_Q) + (uint64_t)v.off_dmin + d1;
 }
 
 __device__ __forceinline__ uint64_t offset_of(const QueryView& v, uint64_t j) {
-    return expectation(j, v.off_Q) + (uint64_t)v.off_dmin + read_bits(v.off_words, j * v.off_w, v.off_w);
+    return offset_expectation(j, v.off_Q) + (uint64_t)v.off_dmin + read_bits(v.off_words, j * v.off_w, v.off_w);
 }
 
 // read_bits32 for narrow fields: the 64-bit word holding bit o, and the next

@@ -36,9 +36,14 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 // floor(a * b / 2^64)
 __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
 
-// floor(h * m / 2^64) for m < 2^32: fastrange onto [0, m)
+// floor(h * m / 2^64) for m < 2^32: fastrange onto [0, m).  With h = hi 2^32 +
+// lo, h m / 2^32 = hi m + lo m / 2^32, and the fraction of lo m / 2^32 cannot
+// carry into bit 32 of the integer part, so the result is bits 32..63 of
+// hi m + floor(lo m / 2^32) (which stays below 2^64): one wide multiply-add and
+// one high multiply, where a general 64 x 64 high product needs several.
 __device__ __forceinline__ uint32_t fastrange32(uint64_t h, uint32_t m) {
-    return (uint32_t)__umul64hi(h, (uint64_t)m);
+    const uint64_t t = (uint64_t)(uint32_t)(h >> 32) * m + __umulhi((uint32_t)h, m);
+    return (uint32_t)(t >> 32);
 }
 
 __host__ __device__ __forceinline__ uint64_t key_seed(uint64_t seed) { return mix64(seed ^ kSeedMix); }
@@ -49,8 +54,14 @@ __device__ __forceinline__ uint32_t position_hash(uint64_t hk, uint64_t ps, uint
     return fastrange32(mix64(hk ^ ps), m);
 }
 
-// partition of a master hash
+// partition of a master hash, floor(hk N_P / 2^64)
 __device__ __forceinline__ uint64_t partition_of(uint64_t hk, uint64_t np) { return mulhi64(hk, np); }
+
+// Bits 32..95 of the 128-bit product j Q, mod 2^64: the offsets' expectation
+// floor(j Q / 2^32) (Section 4 stores offsets as differences to it)
+__device__ __forceinline__ uint64_t offset_expectation(uint64_t j, uint64_t Q) {
+    return (__umul64hi(j, Q) << 32) | ((j * Q) >> 32);
+}
 
 // Section 3.1 / Appendix C: bucket of normalised hash x from the fixed-point
 // table of gamma T_0..T_2048, by linear interpolation between T_k and T_{k+1}:

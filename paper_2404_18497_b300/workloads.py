@@ -106,6 +106,30 @@ def random_strings(n: int, seed: int, lmin: int = 10, lmax: int = 50):
     return data, offsets
 
 
+def random_strings_torch(n: int, seed: int, device, lmin: int = 10, lmax: int = 50):
+    """The same distribution as random_strings (lengths uniform in [lmin, lmax],
+    characters uniform over [A-Za-z0-9]), drawn on `device` with torch's
+    generator (another instance of the workload, generated in seconds).
+    Returns (bytes uint8[total], offsets int64[n + 1])."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    lens = torch.randint(lmin, lmax + 1, (n,), generator=g, device=device, dtype=torch.int64)
+    offsets = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    torch.cumsum(lens, 0, out=offsets[1:])
+    del lens
+    total = int(offsets[-1].item())
+    alnum = torch.from_numpy(ALNUM.copy()).to(device)
+    data = torch.empty(total + 8, dtype=torch.uint8, device=device)
+    chunk = 1 << 30
+    for c0 in range(0, total, chunk):
+        c1 = min(total, c0 + chunk)
+        data[c0:c1] = alnum[torch.randint(0, ALNUM.size, (c1 - c0,), generator=g, device=device)]
+    data[total:] = 0
+    return data, offsets
+
+
 _W = 0x9E3779B97F4A7C15
 _F1 = 0xFF51AFD7ED558CCD
 _F2 = 0xC4CEB9FE1A85EC53
