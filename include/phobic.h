@@ -213,7 +213,7 @@ phobic_status phobic_build_batch(const uint64_t* d_keys, const uint64_t* h_set_o
  * *info (may be NULL) reports the measurements.  Decisions are cached for the
  * process per device and (lambda, alpha, encoder, pilot_mode, s_max): per size
  * class for P, per power of two of the partition count for the search knobs.
- * The trials allocate device memory (keys for up to about 2^25 + one set) and
+ * The trials allocate device memory (keys for up to about 2^27 + one set) and
  * synchronize `stream`.  Partition sizes below lambda are never tried (lambda
  * above 4096 leaves none: INVALID_ARG).  Errors: INVALID_ARG, OOM, CUDA, and any
  * build error of a trial.  Results of builds made with the outputs are exact

@@ -21,8 +21,14 @@
 //      Each P is timed; the fastest wins, except that a P within kTieFrac of
 //      the fastest with fewer bits per key is preferred.
 //   2. With the chosen P per set, a deterministic subsample of the batch (every
-//      k-th set, at most kLaunchTrialKeys keys) is built with each of the six
-//      (warps, width) pairs and the fastest pair is kept.
+//      k-th set) is built with each of the six (warps, width) pairs and the
+//      fastest pair is kept, then with each search schedule.  Those knobs trade
+//      parallelism inside a partition against the number of partitions in
+//      flight, so the subsample keeps enough partitions to fill the GPU several
+//      times over (kLaunchTrialWaves waves of one-warp CTAs, or the whole batch
+//      when it has fewer), with at most kLaunchTrialMaxKeys keys.  A subsample
+//      of far fewer partitions than the batch favours several warps per
+//      partition, which the full batch, many waves deep, does not repay.
 // Decisions are cached per device and parameter set: per size class for P,
 // per power of two of the batch's partition count for (warps, width).
 // The paper has no counterpart; this is a deployment convenience.
@@ -41,7 +47,8 @@
 namespace {
 
 constexpr uint64_t kClassTrialKeys = 1ull << 23;
-constexpr uint64_t kLaunchTrialKeys = 1ull << 25;
+constexpr uint64_t kLaunchTrialWaves = 8;         // of 32 one-warp CTAs per SM
+constexpr uint64_t kLaunchTrialMaxKeys = 1ull << 27;
 constexpr double kTieFrac = 0.03;
 constexpr int kReps = 2;
 constexpr uint32_t kPChoices[PHOBIC_TUNE_P_CHOICES] = {1024, 2500, 4096};
@@ -250,7 +257,12 @@ extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32
     const int lk = log2_floor(total_parts);
     auto it = g_launch.find({pk, lk});
     if (it == g_launch.end()) {
-        const uint64_t stride = std::max<uint64_t>(1, (total + kLaunchTrialKeys - 1) / kLaunchTrialKeys);
+        int sms = 148;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const uint64_t want_parts = std::min<uint64_t>(total_parts, kLaunchTrialWaves * 32 * (uint64_t)sms);
+        // every stride-th set: about total_parts / stride partitions and total / stride keys
+        uint64_t stride = std::max<uint64_t>(1, total_parts / want_parts);
+        stride = std::max<uint64_t>(stride, (total + kLaunchTrialMaxKeys - 1) / kLaunchTrialMaxKeys);
         std::vector<uint64_t> sizes;
         std::vector<uint32_t> Ps;
         uint64_t tot = 0;
