@@ -568,7 +568,89 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
             // ===== PTHash XOR form: p = 0, 1, 2, ... =====
             const uint64_t limit = (uint64_t)min(a.s_max, 0xFFFFFFFFu / m) * m;  // pilots < 2^32
             uint32_t outcome = kOutNone, winner = 0;
-            if (k <= 32) {
+            // Expected candidates about q^-k (q the free fraction).  When they exceed
+            // what one step of the grouped scan below covers (floor(32 / k) pilots),
+            // the filter cascade takes the bucket instead.
+            const float xq = __fdividef((float)(m - placed), (float)m);
+            const bool cascade = k <= 32 && (float)k * -__log2f(xq) > __log2f((float)(32u / k));
+            if (cascade) {
+                // Filter cascade over windows of 32 consecutive pilots, one pilot per
+                // lane: every lane tests the bucket's key 0 under its pilot, then the
+                // lanes whose slot was free test key 1, and so on, while any lane's
+                // pilot still has all of its slots free.  On a filling table most
+                // pilots fail on their first keys, so a window costs about 1 / (1 - q)
+                // slot tests per pilot instead of k.  The surviving pilots are then
+                // checked for pairwise distinct slots in increasing order, so the first
+                // that passes is the smallest valid pilot of the window.
+                const uint64_t kv = lane < k ? keys[lane] : 0;  // key r on lane r
+                uint32_t mypos = 0;
+                for (uint64_t pb = 0;; pb += (uint64_t)kWarps * 32) {
+                    const uint64_t p0 = pb + (uint64_t)warp * 32;
+                    uint32_t my = kOutNone, myp = 0;
+                    if (p0 >= limit) {
+                        my = kOutLimit;
+                    } else if (p0 <= 8ull * m && 8ull * m < p0 + 32 && bucket_has_dup(keys, k, lane)) {
+                        my = kOutDup;  // the window holding pilot 8 m checks for duplicates
+                    } else {
+                        steps++;
+                        const uint64_t pc = p0 + lane;
+                        const uint64_t ps = pilot_seed(pc);
+                        bool alive = pc < limit;
+                        for (uint32_t r = 0; r < k; r++) {
+                            const uint64_t kr = __shfl_sync(kFull, kv, r);
+                            if (alive) {
+                                const uint32_t pos = position_hash(kr, ps, m);
+                                alive = (fw[pos >> 5] >> (pos & 31)) & 1;
+                            }
+                            if (!__any_sync(kFull, alive)) break;
+                        }
+                        uint32_t cand = __ballot_sync(kFull, alive);
+                        while (cand) {
+                            const uint32_t l = __ffs(cand) - 1;
+                            cand &= cand - 1;
+                            const uint32_t pos = position_hash(kv, __shfl_sync(kFull, ps, l), m);
+                            if (k > 1) {
+                                // pairwise distinct slots: mark them in the warp's scratch bitmap
+                                bool c = false;
+                                if (lane < k) {
+                                    const uint32_t bit = 1u << (pos & 31);
+                                    c = (atomicOr(&scr[pos >> 5], bit) & bit) != 0;
+                                }
+                                const bool coll = __any_sync(kFull, c);
+                                if (lane < k) scr[pos >> 5] = 0;
+                                __syncwarp();
+                                if (coll) continue;
+                            }
+                            my = kOutFound;
+                            myp = (uint32_t)(p0 + l);
+                            mypos = pos;
+                            break;
+                        }
+                    }
+                    if constexpr (kWarps == 1) {
+                        if (my != kOutNone) {
+                            outcome = my;
+                            p = myp;
+                            break;
+                        }
+                    } else {
+                        uint32_t wo = kOutNone, wv = 0;
+                        const uint32_t w = first_final<kWarps>(ctl, bank, warp, lane, my, myp, wo, wv);
+                        if (w < kWarps) {
+                            outcome = wo;
+                            p = wv;
+                            winner = w;
+                            break;
+                        }
+                    }
+                }
+                if (outcome != kOutFound) {
+                    local_err = outcome == kOutDup ? kDevDupHash : kDevSearchLimit;
+                    break;
+                }
+                if (warp == winner && lane < k) take_slot(fw, mypos, m);
+                placed += k;
+            } else if (k <= 32) {
                 // groups of k lanes test G = floor(32 / k) consecutive pilots per warp
                 // step (lanes g >= G idle): lane rr of group g hashes key rr with pilot
                 // p0 + g.  A group wins when its k slots are free and pairwise
