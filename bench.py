@@ -114,10 +114,10 @@ NCU_CAPTURES = {
     "k_query": {"files": ["paper_2404_18497_b300/csrc/k_query.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
                 "sha": "a00ad15a3316dba7", "n": 3e7, "dram_bytes": 249899264 + 197988864},
     "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "22d85e6612ee39f3", "n": 3e7,
-               "dram_bytes": (240055040 + 195902464) + (242552320 + 197608192) + (242419456 + 196858880)},
+               "sha": "33ef5becf6949207", "n": 3e7,
+               "dram_bytes": (240047872 + 196647936) + (242533888 + 198234880) + (242423808 + 196658432)},
     "k_hash": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "22d85e6612ee39f3", "n": 3e7, "dram_bytes": 240021248 + 191719168},
+               "sha": "33ef5becf6949207", "n": 3e7, "dram_bytes": 240025344 + 192023296},
 }
 ISSUE_SLOTS_PER_CLOCK = 148 * 4  # B300: 148 SMs x 4 warp schedulers, one warp instruction per clock each
 SM_MAX_MHZ = 2032.0
