@@ -34,6 +34,13 @@ from typing import List, Optional, Sequence
 import torch
 
 
+# When shards fail differently, all report the error a single build would: a
+# partition too large for the search is refused before any search, duplicate
+# keys take precedence over the search limit, which takes precedence over a
+# bounded wait that ran out (then any other failure).
+_ERROR_RANK = {5: 6, 3: 5, 4: 4, 7: 3}
+
+
 def shard_bounds(num_partitions: int, world: int) -> List[int]:
     """J_0 .. J_G: shard r owns partitions [J_r, J_{r+1}), J_r = ceil(r N_P / G),
     which is exactly the set of j with floor(j G / N_P) = r."""
@@ -187,7 +194,7 @@ def sharded_build(keys: torch.Tensor, params, comm, stages=None, stats_out: Opti
     pilots = st.zeros_u32(B * NP, gstart)
     taken = st.zeros_u32((M + 31) // 32 + 1, gstart) if M > n else None
     code = st.search(rsorted, rstart, T, n, NP, J[r], J[r + 1], params, pilots, taken)
-    worst = comm.all_reduce_max_int(code)
+    worst = comm.all_reduce_max_int((_ERROR_RANK.get(code, 1) << 8) | code if code else 0) & 0xFF
     if worst != 0:
         raise st.error(worst, "sharded search")
     del rsorted, rstart

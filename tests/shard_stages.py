@@ -24,8 +24,8 @@ def partition_ids(hk: np.ndarray, num_partitions: int) -> np.ndarray:
 
 
 class OracleStages:
-    def __init__(self, orc, lam, alpha, P, mode=0):
-        self.orc, self.lam, self.alpha, self.P, self.mode = orc, lam, alpha, P, mode
+    def __init__(self, orc, lam, alpha, P, mode=0, s_max=0):
+        self.orc, self.lam, self.alpha, self.P, self.mode, self.s_max = orc, lam, alpha, P, mode, s_max
         self.searched = []  # partitions this process searched
 
     def hash(self, keys, seed):
@@ -51,12 +51,13 @@ class OracleStages:
         h, st, TT = _u64(sorted_hk), start.numpy(), T.numpy()
         words = taken.numpy().view(np.uint32) if taken is not None else None
         pv = pilots.numpy().view(np.uint32)
-        for j in range(j0, j1):
+        for j in range(j0, j1):  # equal master hashes anywhere: DUP_HASH, whatever else fails
             if np.unique(h[st[j]:st[j + 1]]).size != st[j + 1] - st[j]:
-                return self.orc.DUP_HASH  # equal master hashes: DUP_HASH before any search
+                return self.orc.DUP_HASH
+        for j in range(j0, j1):
             try:
                 pil, tk = self.orc.search_one_partition(h[st[j]:st[j + 1]], self.lam, self.alpha, self.P,
-                                                        mode=self.mode)
+                                                        mode=self.mode, s_max=self.s_max)
             except self.orc.OracleError as e:
                 return e.code
             self.searched.append(j)

@@ -31,6 +31,7 @@ def _worker(rank, world, port, case, out_dir):
     from tests.shard_stages import OracleStages, remap_from_taken
 
     n, lam, alpha, P, mode, cuts_seed, dup = (case[k] for k in ("n", "lam", "alpha", "P", "mode", "cuts", "dup"))
+    s_max = case.get("s_max", 0)
     keys = workloads.distinct_u64(n, 11)
     if dup:
         keys[-1] = keys[0]  # a duplicate pair on two different ranks
@@ -40,7 +41,7 @@ def _worker(rank, world, port, case, out_dir):
         cuts = np.linspace(0, n, world + 1)[1:-1]
     cuts = np.concatenate([[0], cuts.astype(np.int64), [n]])
     mine = torch.from_numpy(keys[cuts[rank]:cuts[rank + 1]].view(np.int64).copy())
-    st = OracleStages(orc, lam, alpha, P, mode)
+    st = OracleStages(orc, lam, alpha, P, mode, s_max)
     prm = type("prm", (), dict(partition_size=P, lambda_=lam, alpha=alpha, seed=5))()
     res = {"rank": rank}
     stats = []
@@ -113,6 +114,27 @@ def test_sharded_build_duplicate_fails_on_every_rank(tmp_path):
     mp.spawn(_worker, args=(world, _free_port(), case, str(tmp_path)), nprocs=world, join=True)
     res = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(world)]
     assert [r.get("error") for r in res] == [3, 3]  # DUP_HASH on both ranks, no rank left waiting
+
+
+def test_sharded_build_reports_the_single_builds_error(tmp_path):
+    """One rank's partitions hit the search limit (s_max = 1 at lambda 12), another
+    rank holds a duplicate pair: every rank reports DUP_HASH, as a single build
+    would (duplicates take precedence over the search limit), and the oracle's
+    single build agrees."""
+    import torch.multiprocessing as mp
+    from oracle import oracle as orc
+    from paper_2404_18497_b300 import workloads
+
+    world = 2
+    case = dict(n=6_000, lam=12.0, alpha=1.0, P=500, mode=0, cuts=-1, dup=True, s_max=1)
+    mp.spawn(_worker, args=(world, _free_port(), case, str(tmp_path)), nprocs=world, join=True)
+    res = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(world)]
+    assert [r.get("error") for r in res] == [3, 3]
+    keys = workloads.distinct_u64(6_000, 11)
+    keys[-1] = keys[0]
+    with pytest.raises(orc.OracleError) as e:
+        orc.Oracle(keys, lam=12.0, alpha=1.0, P=500, s_max=1, seed=5, threads=1)
+    assert e.value.code == orc.DUP_HASH
 
 
 def test_shard_bounds_are_the_owner_map():
