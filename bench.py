@@ -1087,6 +1087,26 @@ def serve_trace(secs, brate, qrate, seed, build_sizes=(1e4, 5e7), query_sizes=(1
     return ev
 
 
+def _serve_warmup(srv, keys_pool, prm):
+    """One build per build slot, a query against each, then their release, all
+    waited for: the worker threads, the memory pool and the query path are warm
+    before the clock starts (a long-running server is)."""
+    n = 1_000_000
+    ids = []
+    for k in range(2):
+        ids.append(srv.submit_build(keys_pool[k * n:(k + 1) * n], prm))
+    srv.drain(600)
+    hids = [int(c["handle_id"]) for c in srv.poll() if int(c["kind"]) == 0 and int(c["status"]) == 0]
+    import torch
+    out = torch.empty(10_000, dtype=torch.int64, device=keys_pool.device)
+    for h in hids:
+        srv.submit_query(h, keys_pool[:10_000], out)
+        srv.drain(600)
+        srv.submit_release(h)
+    srv.drain(600)
+    srv.poll()
+
+
 def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_every=100, budget=120 * 10**9):
     """Replays the trace against a server.  Latency is measured from each
     request's scheduled arrival (open loop: a late submission counts against
@@ -1095,7 +1115,11 @@ def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_eve
     Every key set is a window [ps, ps + n) of a pool of distinct keys.  A query
     batch of m keys is one slice of the pool that covers 90% of it inside the
     set's window and 10% just outside it (keys of the pool that are not in the
-    set: random non-members), so no request needs a copy of its input."""
+    set: random non-members), so no request needs a copy of its input.
+
+    The client keeps its per-request records in arrays indexed by request id
+    and takes completions in vectorised batches, so that its own bookkeeping
+    does not limit the offered load."""
     P = keys_pool.numel()
     margin = 1 << 20
     rng = np.random.default_rng(seed)
@@ -1103,61 +1127,70 @@ def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_eve
     srv = phobic.Server(hbm_budget_bytes=budget, build_slots=2, serial=serial)
     ring = 1 << 27
     qout = torch.empty(ring, dtype=torch.int64, device="cuda")
-    head = 0
+    _serve_warmup(srv, keys_pool, prm)
+    cap_ids = 2 * len(trace) + 4096
+    arrival = np.zeros(cap_ids, dtype=np.int64)
+    pending = np.zeros(cap_ids, dtype=bool)
+    is_sample = np.zeros(cap_ids, dtype=bool)
+    qregion = {}    # sampled query id -> (ring start, keys)
+    binfo = {}      # build id -> (pool start, keys)
     pend_q = collections.deque()  # (request id, ring start, keys) of submitted queries, oldest first
-    req = {}        # request id -> (kind, arrival ns, ...)
     resident = []   # (handle id, pool start, n), oldest first
     keep = set()    # handles kept for the final checks
     samples = []    # (handle id, pool start, m, request id)
     outs = {}
-    lat = {0: [], 1: [], 2: []}
-    lat_srv = {0: [], 1: []}
-    keys_done = {0: 0, 1: 0}
-    batch_sizes = []
+    parts = []      # per poll: (kind, latency from arrival, latency from submission, batch requests, keys)
     checked_builds = []
+    tt = np.array([e[0] for e in trace], dtype=np.float64)
+    tk = np.array([e[1] for e in trace], dtype=np.int64)
+    ts = np.array([e[2] for e in trace], dtype=np.int64)
+    head = 0
     torch.cuda.synchronize()
 
     def handle_completions():
         comp = srv.poll()
-        for c in comp:
-            kind = int(c["kind"])
-            rid = int(c["request_id"])
-            r = req.pop(rid)
-            lat[kind].append(int(c["t_done_ns"]) - r[1])
-            if kind < 2:
-                lat_srv[kind].append(int(c["t_done_ns"]) - int(c["t_submit_ns"]))
-            if kind == 0:
-                _, _, ps, n = r
-                if int(c["status"]) == 0:
-                    resident.append((int(c["handle_id"]), ps, n))
-                    keys_done[0] += n
-                    if len(checked_builds) < 3 and n < 3_000_000:
-                        checked_builds.append((int(c["handle_id"]), ps, n))
-                        keep.add(int(c["handle_id"]))
-            elif kind == 1:
-                _, _, st, m = r
-                keys_done[1] += m
-                batch_sizes.append(int(c["batch_requests"]))
-                if rid in outs:
-                    outs[rid] = qout[st:st + m].clone()
+        if comp.size == 0:
+            return 0
+        rid = comp["request_id"].astype(np.int64)
+        kind = comp["kind"].astype(np.int64)
+        tdone = comp["t_done_ns"].astype(np.int64)
+        pending[rid] = False
+        parts.append((kind, tdone - arrival[rid], tdone - comp["t_submit_ns"].astype(np.int64),
+                      comp["batch_requests"].astype(np.int64), comp["keys"].astype(np.int64)))
+        for i in np.flatnonzero(kind == 0):  # builds: few
+            if int(comp["status"][i]) != 0:
+                continue
+            ps, n = binfo.pop(int(rid[i]))
+            hid = int(comp["handle_id"][i])
+            resident.append((hid, ps, n))
+            if len(checked_builds) < 3 and n < 3_000_000:
+                checked_builds.append((hid, ps, n))
+                keep.add(hid)
+        for i in np.flatnonzero(is_sample[rid]):  # sampled queries: their answers, for the final check
+            st0, m0 = qregion[int(rid[i])]
+            outs[int(rid[i])] = qout[st0:st0 + m0].clone()
         return comp.size
 
     t0 = time.monotonic_ns()
     i = 0
+    since_poll = 0
     while i < len(trace):
         now = time.monotonic_ns()
-        arrival = t0 + int(trace[i][0] * 1e9)
-        if arrival > now:
+        arr = t0 + int(tt[i] * 1e9)
+        if arr > now:
             if handle_completions() == 0:
-                time.sleep(min(2e-4, (arrival - now) / 1e9))
+                time.sleep(min(2e-4, (arr - now) / 1e9))
+            since_poll = 0
             continue
-        _, kind, size = trace[i]
+        kind, size = int(tk[i]), int(ts[i])
         i += 1
         if kind == 0:
             n = size
             ps = int(rng.integers(margin, P - n - margin))
             rid = srv.submit_build(keys_pool[ps:ps + n], prm)
-            req[rid] = (0, arrival, ps, n)
+            arrival[rid] = arr
+            pending[rid] = True
+            binfo[rid] = (ps, n)
         else:
             if not resident:
                 continue
@@ -1174,18 +1207,20 @@ def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_eve
             # oldest one does not overlap, no newer one does)
             while pend_q:
                 r0, st0, m0 = pend_q[0]
-                if r0 not in req:
+                if not pending[r0]:
                     pend_q.popleft()
                 elif st0 < head + m and head < st0 + m0:
                     handle_completions()
                 else:
                     break
             rid = srv.submit_query(hid, keys_pool[q0:q0 + m], qout[head:head + m])
-            req[rid] = (1, arrival, head, m)
+            arrival[rid] = arr
+            pending[rid] = True
             pend_q.append((rid, head, m))
             if len(samples) < 400 and rid % check_every == 0:
                 samples.append((hid, q0, m, rid))
-                outs[rid] = None
+                is_sample[rid] = True
+                qregion[rid] = (head, m)
                 keep.add(hid)
             head += m
         if len(resident) > cap:
@@ -1193,13 +1228,24 @@ def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_eve
                 if hid not in keep:
                     resident.pop(j)
                     rid = srv.submit_release(hid)
-                    req[rid] = (2, time.monotonic_ns())
+                    arrival[rid] = time.monotonic_ns()
+                    pending[rid] = True
                     break
+        since_poll += 1
+        if since_poll >= 256:  # keep completion batches small while the client runs flat out
+            handle_completions()
+            since_poll = 0
     submit_s = (time.monotonic_ns() - t0) / 1e9
     srv.drain(600)
     handle_completions()
     wall = (time.monotonic_ns() - t0) / 1e9
     st = srv.stats()
+    kind = np.concatenate([p[0] for p in parts]) if parts else np.zeros(0, dtype=np.int64)
+    lat = np.concatenate([p[1] for p in parts]) if parts else np.zeros(0, dtype=np.int64)
+    lat_srv = np.concatenate([p[2] for p in parts]) if parts else np.zeros(0, dtype=np.int64)
+    batch = np.concatenate([p[3] for p in parts]) if parts else np.zeros(0, dtype=np.int64)
+    keys = np.concatenate([p[4] for p in parts]) if parts else np.zeros(0, dtype=np.int64)
+    q, b = kind == 1, kind == 0
     # results in the mix equal the results alone (answered now, nothing else running)
     ok_q, n_q = True, 0
     for hid, q0, m, rid in samples:
@@ -1216,13 +1262,13 @@ def run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, seed, check_eve
     srv.close()
     del qout
     return {
-        "requests": {"builds": len(lat[0]), "queries": len(lat[1]), "releases": len(lat[2])},
-        "query_latency": _percentiles(lat[1]), "build_latency": _percentiles(lat[0]),
-        "query_latency_from_submit": _percentiles(lat_srv[1]), "build_latency_from_submit": _percentiles(lat_srv[0]),
-        "query_mkeys_s": keys_done[1] / wall / 1e6, "build_mkeys_s": keys_done[0] / wall / 1e6,
+        "requests": {"builds": int(b.sum()), "queries": int(q.sum()), "releases": int((kind == 2).sum())},
+        "query_latency": _percentiles(lat[q]), "build_latency": _percentiles(lat[b]),
+        "query_latency_from_submit": _percentiles(lat_srv[q]), "build_latency_from_submit": _percentiles(lat_srv[b]),
+        "query_mkeys_s": float(keys[q].sum()) / wall / 1e6, "build_mkeys_s": float(keys[b].sum()) / wall / 1e6,
         "wall_s": wall, "submit_s": submit_s,
         "query_launches": st["query_launches"],
-        "mean_requests_per_launch": float(np.mean(batch_sizes)) if batch_sizes else None,
+        "mean_requests_per_launch": float(batch[q].mean()) if q.any() else None,
         "max_requests_per_launch": st["max_batch_requests_seen"],
         "peak_accounted_gb": st["peak_accounted_bytes"] / 1e9,
         "builds_waited_for_memory": st["builds_waited_for_memory"],
@@ -1268,7 +1314,7 @@ def _point(r):
             "equal_alone": r["check"]["queries_equal_alone"] and r["check"]["builds_equal_alone"]}
 
 
-def run_serve_sweep(phobic, torch, workloads, cap, secs=6.0, rates=(2000, 8000, 32000, 64000)):
+def run_serve_sweep(phobic, torch, workloads, cap, secs=6.0, rates=(2000, 8000, 32000, 64000, 128000)):
     """Throughput and p50/p99 per request type against offered query load, up
     to the rate the submitting thread sustains, continuous against serial; and
     one point where the HBM budget binds."""
@@ -1282,7 +1328,6 @@ def run_serve_sweep(phobic, torch, workloads, cap, secs=6.0, rates=(2000, 8000, 
             r = run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, 7, check_every=500)
             r["offered_s"] = secs
             pt[mode] = _point(r)
-            phobic.phobic_trim(0)
         points.append(pt)
     trace = serve_trace(secs, 100.0, 500.0, 9, build_sizes=(1e7, 5e7), query_sizes=(1e3, 1e5))
     budget = {"hbm_budget_gb": 4.0}
@@ -1290,8 +1335,8 @@ def run_serve_sweep(phobic, torch, workloads, cap, secs=6.0, rates=(2000, 8000, 
         r = run_serve_mode(phobic, torch, trace, serial, keys_pool, cap, 8, check_every=50, budget=4 * 10**9)
         r["offered_s"] = secs
         budget[mode] = _point(r)
-        phobic.phobic_trim(0)
     del keys_pool
+    phobic.phobic_trim(0)
     torch.cuda.empty_cache()
     return {"sweep_workload": SERVE_SWEEP.format(secs=secs), "sweep": points, "budget_point": budget}
 

@@ -202,12 +202,15 @@ struct PinnedBuf {
         thread_local void* buf = nullptr;
         thread_local size_t cap = 0;
         if (cap < bytes) {
+            // grow in whole 64 KB steps: a pinned allocation (and its release)
+            // is slow and can stall other threads' CUDA calls
+            const size_t want = (bytes + 65535) & ~(size_t)65535;
             if (buf) cudaFreeHost(buf);
             buf = nullptr;
             cap = 0;
-            cudaError_t e = cudaMallocHost(&buf, bytes);
+            cudaError_t e = cudaMallocHost(&buf, want);
             if (e != cudaSuccess) return e;
-            cap = bytes;
+            cap = want;
         }
         p = buf;
         return cudaSuccess;
@@ -264,6 +267,13 @@ void handle_destroy(phobic_handle* h) {
 }  // namespace
 
 namespace phobic {
+// Allocates the calling thread's pinned read-back buffer ahead of its first
+// build (a server's build workers call it when they start).
+cudaError_t warm_build_thread() {
+    PinnedBuf pin;
+    return pin.alloc(65536);
+}
+
 // Frees a handle without synchronising the device: the caller guarantees that
 // no work that reads the handle is in flight.  Pool memory goes back to the
 // pool in stream order on `st`; cudaMalloc'ed memory is freed directly.
@@ -345,8 +355,20 @@ struct SetPlan {
 // where a blocking wait can add a scheduler round trip (measured: 0.3 ms per
 // 1e8-key build while an NVML client such as nvidia-smi is attached, and no
 // difference without one).  After kSpinWaitUs of polling it blocks instead, so
-// that long builds do not keep a core busy.
+// that long builds do not keep a core busy.  Between two polls the thread
+// pauses for about a microsecond without a system call: every poll is a driver
+// call, and back-to-back polls from several building threads (a server's build
+// slots) contend with the other threads' launches for the driver.
 constexpr double kSpinWaitUs = 50000.0;
+inline void pause_briefly() {
+    for (int i = 0; i < 64; i++) {
+#if defined(__x86_64__) || defined(__i386__)
+        __builtin_ia32_pause();
+#else
+        std::atomic_signal_fence(std::memory_order_seq_cst);
+#endif
+    }
+}
 cudaError_t wait_stream(cudaStream_t st) {
     cudaEvent_t e;
     cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
@@ -360,6 +382,7 @@ cudaError_t wait_stream(cudaStream_t st) {
                 r = cudaEventSynchronize(e);
                 break;
             }
+            pause_briefly();
         }
     }
     cudaEventDestroy(e);

@@ -192,4 +192,7 @@ cudaError_t launch_query(const QueryView& v, const uint64_t* keys, uint64_t* out
 cudaError_t launch_query_strings(const QueryView& v, const uint8_t* bytes, const uint64_t* offsets, uint64_t* out,
                                  uint64_t m, cudaStream_t stream);
 
+// the calling thread's pinned read-back buffer, allocated ahead of its first build
+cudaError_t warm_build_thread();
+
 }  // namespace phobic

@@ -17,17 +17,20 @@
 //     one kernel launch on a high-priority stream (up to max_batch_requests
 //     requests and max_batch_keys keys) while builds run.  Up to `launch_slots`
 //     coalesced launches are in flight; requests that arrive meanwhile form the
-//     next launch.  A host function enqueued after each launch timestamps its
-//     requests' completion.
+//     next launch.  An event recorded after each launch marks its completion;
+//     the scheduler thread polls the events of the launches in flight, in
+//     launch order, and completes their requests (no host callbacks: a
+//     callback thread taking the server's lock for every launch competed with
+//     the submitting threads).
 //   * A release waits until no queued or in-flight query reads the MPHF, then
 //     returns its memory in stream order (no device synchronisation).
 // Serial mode: one request at a time in arrival order, each as its own launch
 // sequence waited for to completion (the plain path to compare with).
 //
-// The scheduler never holds its mutex across a CUDA call that can block, and
-// the host functions take the mutex but make no CUDA call, so neither can wait
-// on the other.
+// The scheduler never holds its mutex across a CUDA call.  Submissions wake it
+// only while it sleeps; while launches are in flight it polls their events.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -102,6 +105,8 @@ struct phobic_server {
     std::vector<cudaStream_t> bstreams;
     int device = 0;
     bool stop = false;
+    bool sched_waiting = false;  // the scheduler sleeps on cv (submissions must wake it)
+    std::atomic<uint64_t> work_seq{0};  // bumped by every submission and finished build
     uint64_t next_id = 1, next_handle = 1, next_batch = 1;
     uint64_t pending = 0;
     uint32_t active_builds = 0;
@@ -115,6 +120,7 @@ struct Slot {
     phobic_server* srv = nullptr;
     phobic::MultiQuery* h_desc = nullptr;  // pinned
     phobic::MultiQuery* d_desc = nullptr;
+    cudaEvent_t done = nullptr;            // recorded after the launch
     std::vector<Req*> reqs;
     bool busy = false;
 };
@@ -144,18 +150,14 @@ void complete_locked(phobic_server* s, Req* r, phobic_status status) {
     if (s->pending == 0) s->cv_idle.notify_all();
 }
 
-void CUDART_CB on_launch_done(void* p) {
-    Slot* slot = static_cast<Slot*>(p);
-    phobic_server* s = slot->srv;
-    const int64_t t = now_ns();
-    std::lock_guard<std::mutex> lk(s->mu);
+// a launch's requests are done (caller holds the lock)
+void finish_slot_locked(phobic_server* s, Slot* slot, phobic_status status, int64_t t) {
     for (Req* r : slot->reqs) {
         r->t_done = t;
-        complete_locked(s, r, PHOBIC_OK);
+        complete_locked(s, r, status);
     }
     slot->reqs.clear();
     slot->busy = false;
-    s->cv.notify_all();
 }
 
 void account_peak(phobic_server* s) {
@@ -189,6 +191,7 @@ phobic_status run_build(Req* r, cudaStream_t bs, phobic_handle** h) {
 
 void build_worker(phobic_server* s, uint32_t w) {
     cudaSetDevice(s->device);
+    phobic::warm_build_thread();  // no pinned allocation inside the first request's build
     for (;;) {
         Req* r = nullptr;
         {
@@ -204,6 +207,7 @@ void build_worker(phobic_server* s, uint32_t w) {
         s->st.reserved_bytes -= r->est;
         s->active_builds--;
         finish_build_locked(s, r, status, h);
+        s->work_seq.fetch_add(1, std::memory_order_release);
         s->cv.notify_all();
     }
 }
@@ -299,24 +303,62 @@ cudaError_t launch_slot(phobic_server* s, Slot* sl) {
         if (e == cudaSuccess) e = phobic::launch_query_multi(sl->d_desc, k, begin, s->qstream);
         if (e != cudaSuccess) return e;
     }
-    return cudaLaunchHostFunc(s->qstream, on_launch_done, sl);
+    return cudaEventRecord(sl->done, s->qstream);
+}
+
+// pause of about a microsecond between two polls, without a system call
+inline void poll_pause() {
+    for (int i = 0; i < 64; i++) {
+#if defined(__x86_64__) || defined(__i386__)
+        __builtin_ia32_pause();
+#else
+        std::atomic_signal_fence(std::memory_order_seq_cst);
+#endif
+    }
 }
 
 void scheduler_continuous(phobic_server* s) {
     cudaSetDevice(s->device);
     std::vector<std::pair<Req*, phobic_handle*>> rel;
+    std::deque<Slot*> inflight;  // launched, in launch order (they finish in order on the query stream)
+    std::vector<std::pair<Slot*, phobic_status>> finished;
     for (;;) {
+        // launches that have finished, oldest first (polled without the lock)
+        while (!inflight.empty()) {
+            const cudaError_t q = cudaEventQuery(inflight.front()->done);
+            if (q == cudaErrorNotReady) break;
+            finished.emplace_back(inflight.front(), q == cudaSuccess ? PHOBIC_OK : PHOBIC_ERR_CUDA);
+            inflight.pop_front();
+        }
         Slot* sl = nullptr;
+        bool idle = false;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            for (;;) {
-                take_releases_locked(s, rel);
-                admit_locked(s);
-                if (!rel.empty()) break;
-                if ((sl = take_queries_locked(s)) != nullptr) break;
-                if (s->stop && s->pending == 0) return;
-                s->cv.wait_for(lk, std::chrono::milliseconds(2));
+            if (!finished.empty()) {
+                const int64_t t = now_ns();
+                for (auto& f : finished) finish_slot_locked(s, f.first, f.second, t);
+                finished.clear();
             }
+            take_releases_locked(s, rel);
+            admit_locked(s);
+            if (rel.empty()) sl = take_queries_locked(s);
+            if (rel.empty() && !sl) {
+                if (s->stop && s->pending == 0 && inflight.empty()) return;
+                if (inflight.empty()) {
+                    s->sched_waiting = true;
+                    s->cv.wait_for(lk, std::chrono::milliseconds(2));
+                    s->sched_waiting = false;
+                    continue;
+                }
+                idle = true;
+            }
+        }
+        if (idle) {  // launches in flight, nothing new: poll, without the lock, until one finishes or work arrives
+            const uint64_t seen = s->work_seq.load(std::memory_order_acquire);
+            while (cudaEventQuery(inflight.front()->done) == cudaErrorNotReady &&
+                   s->work_seq.load(std::memory_order_acquire) == seen)
+                poll_pause();
+            continue;
         }
         for (auto& pr : rel) {
             pr.first->t_start = now_ns();
@@ -324,16 +366,15 @@ void scheduler_continuous(phobic_server* s) {
             pr.first->t_done = now_ns();
             std::lock_guard<std::mutex> lk(s->mu);
             complete_locked(s, pr.first, PHOBIC_OK);
-            s->cv.notify_all();
         }
         rel.clear();
         if (sl) {
             const cudaError_t e = launch_slot(s, sl);
             if (e != cudaSuccess) {
                 std::lock_guard<std::mutex> lk(s->mu);
-                for (Req* r : sl->reqs) complete_locked(s, r, PHOBIC_ERR_CUDA);
-                sl->reqs.clear();
-                sl->busy = false;
+                finish_slot_locked(s, sl, PHOBIC_ERR_CUDA, now_ns());
+            } else {
+                inflight.push_back(sl);
             }
         }
     }
@@ -341,6 +382,7 @@ void scheduler_continuous(phobic_server* s) {
 
 void scheduler_serial(phobic_server* s) {
     cudaSetDevice(s->device);
+    phobic::warm_build_thread();
     for (;;) {
         Req* r = nullptr;
         {
@@ -407,7 +449,10 @@ phobic_status submit(phobic_server* s, Req* r, uint64_t* request_id) {
     } else {
         s->q_releases.push_back(r);
     }
-    s->cv.notify_all();
+    // the serial scheduler waits on cv for every request; the continuous one
+    // polls while launches are in flight and needs waking only when it sleeps
+    s->work_seq.fetch_add(1, std::memory_order_release);
+    if (s->cfg.serial || s->sched_waiting) s->cv.notify_all();
     return PHOBIC_OK;
 }
 
@@ -442,6 +487,7 @@ phobic_status phobic_server_create(const phobic_server_config* cfg, phobic_serve
         for (Slot* sl : s->slots) {
             if (sl->h_desc) cudaFreeHost(sl->h_desc);
             if (sl->d_desc) cudaFree(sl->d_desc);
+            if (sl->done) cudaEventDestroy(sl->done);
             delete sl;
         }
         for (cudaStream_t b : s->bstreams) cudaStreamDestroy(b);
@@ -469,6 +515,8 @@ phobic_status phobic_server_create(const phobic_server_config* cfg, phobic_serve
             const size_t bytes = (size_t)c.max_batch_requests * sizeof(phobic::MultiQuery);
             if (cudaMallocHost(&sl->h_desc, bytes) != cudaSuccess || cudaMalloc(&sl->d_desc, bytes) != cudaSuccess)
                 return fail(PHOBIC_ERR_OOM);
+            if (cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) != cudaSuccess)
+                return fail(PHOBIC_ERR_CUDA);
             sl->reqs.reserve(c.max_batch_requests);
         }
     }
@@ -592,6 +640,7 @@ void phobic_server_destroy(phobic_server* s) {
     for (Slot* sl : s->slots) {
         cudaFreeHost(sl->h_desc);
         cudaFree(sl->d_desc);
+        cudaEventDestroy(sl->done);
         delete sl;
     }
     for (cudaStream_t b : s->bstreams) cudaStreamDestroy(b);
