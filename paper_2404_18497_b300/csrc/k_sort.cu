@@ -159,7 +159,9 @@ struct PassArgs {
 // shared atomicAdd and hands the old value to its peers, so ranks are stable.
 // The first of several passes need not be stable (every later pass is, and
 // keeps its digit order; the order inside a partition is left unspecified): it
-// ranks each key with one shared atomicAdd on its digit's counter.  Then
+// ranks each key with one shared atomicAdd on its digit's counter.  The last
+// of two passes ranks the same way when its tile holds at most two first-pass
+// digits, with each digit's keys in two bins by that digit.  Then
 // per digit: prefix over warps, decoupled look-back for the tile's global
 // offset, a block scan for the tile-local digit starts, a shared-memory
 // reorder and a coalesced write-out.
@@ -167,15 +169,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t R = 1u << a.bits, mask = R - 1;
     uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);                      // kTile
-    uint32_t* wh = reinterpret_cast<uint32_t*>(keys_s + kTile);                // kWarps x R
-    uint32_t* tile_start = wh + kWarps * R;                                    // R
-    unsigned long long* gbase = reinterpret_cast<unsigned long long*>(tile_start + R + (R & 1)); // R
+    // per warp 2R counters: a digit's keys of the tile split by the previous
+    // pass's digit when the last pass ranks without ballots (below)
+    const uint32_t WS = 2 * R;
+    uint32_t* wh = reinterpret_cast<uint32_t*>(keys_s + kTile);                // kWarps x 2R
+    uint32_t* tile_start = wh + kWarps * WS;                                   // R
+    uint32_t* sub1 = tile_start + R;                                           // R
+    unsigned long long* gbase = reinterpret_cast<unsigned long long*>(sub1 + R);  // R
     __shared__ uint32_t tile_s;
     __shared__ uint32_t warp_tot[kWarps];
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) tile_s = atomicAdd(a.tile_counter, 1u);
-    for (uint32_t i = tid; i < kWarps * R; i += kThreads) wh[i] = 0;
+    for (uint32_t i = tid; i < kWarps * WS; i += kThreads) wh[i] = 0;
     __syncthreads();
     const uint64_t tile = tile_s;
     const uint32_t sg = seg_of_tile(a.segs, a.nseg, tile);
@@ -191,10 +197,42 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
         uint64_t idx = wbase + (uint64_t)i * 32 + lane;
         k[i] = idx < seg_end ? load_hk(a.in, idx, a.kseed, a.hash_input) : 0;
     }
-    uint32_t dr[kItems];  // digit << 16 | rank within the warp's digit group
+    uint32_t dr[kItems];  // digit (or bin) << 16 | rank within the warp's digit (bin) group
     const uint32_t lt = (1u << lane) - 1;
-    uint32_t* myh = wh + warp * R;
-    if (a.pass == 0 && a.passes > 1) {
+    uint32_t* myh = wh + warp * WS;
+    // The last of two passes must keep, inside each digit, the order of the
+    // first pass's digit.  Its input is grouped by that digit, so a tile holds a
+    // run of consecutive first-pass digits: when the run has at most two, the
+    // keys of digit d go to bin 2 d + (first-pass digit != the tile's first),
+    // and ranking within a bin needs no order (one shared atomic per key); the
+    // two bins of a digit are laid out one after the other.  Wider runs (few
+    // keys per digit) keep the stable ballot ranking.
+    bool split = false;
+    uint32_t lo_first = 0;
+    if (a.pass == 1 && a.passes == 2) {
+        const unsigned long long* db0 = a.digit_base + ((uint64_t)sg * a.passes) * R;
+        const uint64_t last = (seg_end - base < (uint64_t)kTile ? seg_end : base + kTile) - 1;
+        // first-pass digit of key index x: the largest d with db0[d] <= x
+        uint32_t lf = 0, ll = 0;
+        for (uint32_t st = R >> 1; st; st >>= 1) {
+            if (lf + st < R && __ldg(db0 + lf + st) <= base) lf += st;
+            if (ll + st < R && __ldg(db0 + ll + st) <= last) ll += st;
+        }
+        lo_first = lf;
+        split = ll - lf <= 1;
+    }
+    if (split) {
+        const uint64_t lomask = (1ull << a.bits) - 1;
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+            const bool valid = wbase + (uint64_t)i * 32 + lane < seg_end;
+            const uint64_t j = partition_of(k[i], S.np);
+            const uint32_t dg = (uint32_t)((j >> a.shift) & mask);
+            const uint32_t bin = valid ? 2 * dg + ((uint32_t)(j & lomask) != lo_first ? 1u : 0u) : WS;
+            const uint32_t rank = valid ? atomicAdd(&myh[bin], 1u) : 0u;
+            dr[i] = (bin << 16) | rank;
+        }
+    } else if (a.pass == 0 && a.passes > 1) {
         // the first of several passes need not be stable (the later ones keep its
         // digit order): a key's rank is one shared atomic on its warp's counter
 #pragma unroll
@@ -222,16 +260,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
         dr[i] = (dg << 16) | (old + __popc(peers & lt));
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps; tile count into tile_start
-    for (uint32_t d = tid; d < R; d += kThreads) {
-        uint32_t run = 0;
+    // per digit (per bin when split): exclusive prefix over warps; tile count into tile_start
+    if (split) {
+        for (uint32_t d = tid; d < R; d += kThreads) {
+            uint32_t run0 = 0, run1 = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; w++) {
-            uint32_t c = wh[w * R + d];
-            wh[w * R + d] = run;
-            run += c;
+            for (int w = 0; w < kWarps; w++) {
+                const uint32_t c0 = wh[w * WS + 2 * d], c1 = wh[w * WS + 2 * d + 1];
+                wh[w * WS + 2 * d] = run0;
+                wh[w * WS + 2 * d + 1] = run1;
+                run0 += c0;
+                run1 += c1;
+            }
+            sub1[d] = run0;  // the second bin of digit d starts after the first
+            tile_start[d] = run0 + run1;
         }
-        tile_start[d] = run;
+    } else {
+        for (uint32_t d = tid; d < R; d += kThreads) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; w++) {
+                uint32_t c = wh[w * WS + d];
+                wh[w * WS + d] = run;
+                run += c;
+            }
+            tile_start[d] = run;
+        }
     }
     __syncthreads();
     // decoupled look-back per digit (publish the aggregate first); each thread
@@ -309,10 +363,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     __syncthreads();
     for (uint32_t d = tid; d < R; d += kThreads) gbase[d] -= tile_start[d];
     // reorder in shared memory by digit
+    if (split) {
 #pragma unroll
-    for (int i = 0; i < kItems; i++) {
-        uint32_t d = dr[i] >> 16;
-        if (d < R) keys_s[tile_start[d] + wh[warp * R + d] + (dr[i] & 0xFFFFu)] = k[i];
+        for (int i = 0; i < kItems; i++) {
+            const uint32_t bin = dr[i] >> 16;
+            if (bin < WS) {
+                const uint32_t d = bin >> 1;
+                keys_s[tile_start[d] + ((bin & 1u) ? sub1[d] : 0u) + wh[warp * WS + bin] + (dr[i] & 0xFFFFu)] = k[i];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+            uint32_t d = dr[i] >> 16;
+            if (d < R) keys_s[tile_start[d] + wh[warp * WS + d] + (dr[i] & 0xFFFFu)] = k[i];
+        }
     }
     __syncthreads();
     // coalesced write-out: consecutive slots of one digit go to consecutive addresses
@@ -381,7 +446,7 @@ __global__ void k_partition_starts(const uint64_t* __restrict__ sorted, const So
 
 size_t sort_pass_smem(uint32_t bits) {
     uint32_t R = 1u << bits;
-    return (size_t)kTile * 8 + (size_t)kWarps * R * 4 + (size_t)(R + (R & 1)) * 4 + (size_t)R * 8;
+    return (size_t)kTile * 8 + (size_t)kWarps * 2 * R * 4 + (size_t)2 * R * 4 + (size_t)R * 8;
 }
 
 void sort_plan(uint64_t np, uint32_t* passes, uint32_t* bits) {
