@@ -178,12 +178,17 @@ def sharded_build(keys: torch.Tensor, params, comm, stages=None, stats_out: Opti
     srt, start = st.partition_sort(hk, NP)
     at = start[torch.tensor(J, dtype=torch.int64, device=start.device)].tolist()
     sent = [int(at[q + 1] - at[q]) for q in range(G)]
-    recv = comm.all_to_all(srt, sent)
-    del srt, hk, start
+    if G == 1:  # one shard: its hashes are already grouped, nothing to exchange
+        rsorted, rstart = srt, start
+        del hk
+    else:
+        recv = comm.all_to_all(srt, sent)
+        del srt, hk, start
+        # 3: group the received hashes (G runs, each grouped by partition)
+        rsorted, rstart = st.partition_sort(recv, NP)
+        del recv
 
-    # 3-4: group the received hashes; the whole build's partition starts and T
-    rsorted, rstart = st.partition_sort(recv, NP)
-    del recv
+    # 4: the whole build's partition starts and T
     held = comm.all_gather_int(rsorted.numel())
     own = rstart[J[r]:J[r + 1]] + sum(held[:r])
     gstart = comm.all_gather_v(own, [J[q + 1] - J[q] for q in range(G)])

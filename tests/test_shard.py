@@ -79,6 +79,7 @@ CASES = [
     (3, 15_000, 6.0, 1.0, 400, 0, 4),
     (2, 9_000, 5.0, 0.9, 300, 1, -1),
     (4, 600, 5.0, 0.97, 500, 0, 5),   # two partitions over four shards: two own none
+    (1, 8_000, 7.0, 0.99, 500, 0, -1),  # one shard: no exchange, no second grouping
 ]
 
 
