@@ -114,10 +114,10 @@ NCU_CAPTURES = {
     "k_query": {"files": ["paper_2404_18497_b300/csrc/k_query.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
                 "sha": "a00ad15a3316dba7", "n": 3e7, "dram_bytes": 249899264 + 197988864},
     "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "33ef5becf6949207", "n": 3e7,
-               "dram_bytes": (240047872 + 196647936) + (242533888 + 198234880) + (242423808 + 196658432)},
+               "sha": "927160e0248f0d62", "n": 3e7,
+               "dram_bytes": (240058624 + 197003776) + (243547648 + 195917312) + (243733760 + 195278592)},
     "k_hash": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "33ef5becf6949207", "n": 3e7, "dram_bytes": 240025344 + 192023296},
+               "sha": "927160e0248f0d62", "n": 3e7, "dram_bytes": 240020480 + 192098048},
 }
 ISSUE_SLOTS_PER_CLOCK = 148 * 4  # B300: 148 SMs x 4 warp schedulers, one warp instruction per clock each
 SM_MAX_MHZ = 2032.0
