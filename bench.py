@@ -112,7 +112,7 @@ NCU_CAPTURES = {
     "k_search": {"files": ["paper_2404_18497_b300/csrc/k_search.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
                  "sha": "8fd0d95e6fa61634", "n": 3e7, "warp_inst": 2107095390, "dram_bytes": 551496960 + 323245056},
     "k_query": {"files": ["paper_2404_18497_b300/csrc/k_query.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-                "sha": "a00ad15a3316dba7", "n": 3e7, "dram_bytes": 249899264 + 197988864},
+                "sha": "10e6fa277985462a", "n": 3e7, "dram_bytes": 249930240 + 198135296},
     "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
                "sha": "927160e0248f0d62", "n": 3e7,
                "dram_bytes": (240058624 + 197003776) + (243547648 + 195917312) + (243733760 + 195278592)},

@@ -61,7 +61,10 @@ __device__ __forceinline__ uint32_t read_bits32_narrow(const uint64_t* __restric
 }
 
 // floor(p / m) for m >= 1 through a float reciprocal and an exact integer
-// correction (the estimate is within one of the quotient for p < 2^32)
+// correction.  The float estimate has a relative error below 2^-21 (two
+// conversions and two round-toward-zero operations) plus the truncation, so the
+// loops run at most p / m 2^-21 + 2 times: once or twice for the pilots a build
+// makes, whose s stays far below 2^21.
 __device__ __forceinline__ uint32_t div_u32(uint32_t p, uint32_t m) {
     uint32_t q = __float2uint_rz(__fmul_rz((float)p, __frcp_rz((float)m)));
     int64_t r = (int64_t)p - (int64_t)q * m;
@@ -73,6 +76,24 @@ __device__ __forceinline__ uint32_t div_u32(uint32_t p, uint32_t m) {
         q++;
         r -= m;
     }
+    return q;
+}
+
+// floor(p / m) and p mod m for 1 <= m < 2^30, as div_u32 in 32-bit arithmetic:
+// |p - q m| <= p 2^-21 + m < 2^31 for the estimate q, so the remainder is exact
+// as a signed 32-bit value
+__device__ __forceinline__ uint32_t div_small(uint32_t p, uint32_t m, uint32_t& rem) {
+    uint32_t q = __float2uint_rz(__fmul_rz((float)p, __frcp_rz((float)m)));
+    int32_t r = (int32_t)(p - q * m);
+    while (r < 0) {
+        q--;
+        r += (int32_t)m;
+    }
+    while (r >= (int32_t)m) {
+        q++;
+        r -= (int32_t)m;
+    }
+    rem = (uint32_t)r;
     return q;
 }
 
@@ -222,26 +243,72 @@ __host__ __forceinline__ int query_kind(const QueryView& v) {
     return v.encoder >= 5 ? kQMono : v.encoder == 1 ? kQDict : kQInterleaved;
 }
 
-template <int kKind>
-__device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds);
-
-template <int kKind>
-__device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key, const uint64_t* seeds) {
-    return query_hashed<kKind>(v, key_hash(key, v.kseed), seeds);
+// Structures whose partition arithmetic fits 32 bits (every structure of up to
+// about 10^12 keys at the default partition size) take a second instantiation,
+// k32, with no 64-bit multiplies outside the hashes:
+//   - j = floor(hk N_P / 2^64) is fastrange onto N_P < 2^32 - 1;
+//   - the offsets' bit positions (N_P + 1) w stay below 2^32;
+//   - with Q = Qh 2^32 + Ql, the expectation floor(j Q / 2^32) is
+//     j Qh + floor(j Ql / 2^32) for j < 2^32: one wide multiply-add and one high
+//     multiply;
+//   - floor(p / m) and p mod m take 32-bit arithmetic (div_small): every
+//     m_j is below 2^16, since a build refuses larger partition tables and an
+//     import checks the decoded offsets for it;
+//   - the packed pilot arrays hold fewer than 2^32 bits (small_bits).
+// The instantiation is chosen once per launch, so no key takes a branch for it.
+__host__ __forceinline__ bool query_fast32(const QueryView& v) {
+    if (v.NP >= 0xFFFFFFFFull || v.off_w > 31 || !v.small_bits) return false;
+    return (v.NP + 1) * (uint64_t)v.off_w < (1ull << 32);
 }
 
-template <int kKind>
+template <int kKind, bool k32>
+__device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds);
+
+template <int kKind, bool k32>
+__device__ __forceinline__ uint64_t query_one(const QueryView& v, uint64_t key, const uint64_t* seeds) {
+    return query_hashed<kKind, k32>(v, key_hash(key, v.kseed), seeds);
+}
+
+template <int kKind, bool k32>
 __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk, const uint64_t* seeds) {
     constexpr bool kMono = kKind == kQMono, kNarrow = kKind == kQDict;
-    const uint64_t j = partition_of(hk, v.NP);
-    uint64_t Tj, Tj1;
-    if (v.off_w <= 31) {
-        offsets_of<kNarrow>(v, j, &Tj, &Tj1);
+    uint64_t j, Tj;
+    uint32_t m;
+    if constexpr (k32) {
+        const uint32_t j32 = fastrange32(hk, (uint32_t)v.NP);
+        const uint32_t w = v.off_w;
+        uint32_t d0 = 0, d1 = 0;
+        if (w) {
+            const uint32_t o = j32 * w, i = o >> 6, sh = o & 63;
+            uint64_t x;
+            if (kNarrow) {
+                x = __ldg(v.off_words + i) >> sh;
+                if (sh + 2 * w > 64) x |= __ldg(v.off_words + i + 1) << (64 - sh);  // sh > 0 here
+            } else {
+                const uint64_t lo = __ldg(v.off_words + i);
+                x = sh ? (lo >> sh) | (__ldg(v.off_words + i + 1) << (64 - sh)) : lo;
+            }
+            const uint32_t mask = (1u << w) - 1;
+            d0 = (uint32_t)x & mask;
+            d1 = (uint32_t)(x >> w) & mask;
+        }
+        const uint32_t Qh = (uint32_t)(v.off_Q >> 32), Ql = (uint32_t)v.off_Q;
+        const uint64_t e0 = (uint64_t)j32 * Qh + __umulhi(j32, Ql);
+        const uint32_t e1 = (j32 + 1) * Qh + __umulhi(j32 + 1, Ql);  // low 32 bits of E(j + 1)
+        Tj = e0 + (uint64_t)v.off_dmin + d0;
+        m = e1 - (uint32_t)e0 + d1 - d0;
+        j = j32;
     } else {
-        Tj = offset_of(v, j);
-        Tj1 = offset_of(v, j + 1);
+        j = partition_of(hk, v.NP);
+        uint64_t Tj1;
+        if (v.off_w <= 31) {
+            offsets_of<kNarrow>(v, j, &Tj, &Tj1);
+        } else {
+            Tj = offset_of(v, j);
+            Tj1 = offset_of(v, j + 1);
+        }
+        m = (uint32_t)(Tj1 - Tj);
     }
-    const uint32_t m = (uint32_t)(Tj1 - Tj);
     if (m == 0) return 0;  // only a key outside the set can land in an empty partition
     const uint32_t b = bucket_of(bucket_hash(hk), v.table, v.B);
     uint32_t p;
@@ -259,7 +326,7 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
         } else {
             p = rice_pilot(v, b, j);
         }
-    } else if (v.small_bits) {
+    } else if (k32 || v.small_bits) {
         const uint32_t jj = (uint32_t)j;
         if (v.encoder == 0) {
             const uint64_t meta = __ldg(v.col_meta + b);
@@ -289,8 +356,13 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
     }
     uint32_t local;
     if (v.pilot_mode == 0) {
-        const uint32_t s = div_u32(p, m);
-        const uint32_t d = p - s * m;
+        uint32_t s, d;
+        if constexpr (k32) {
+            s = div_small(p, m, d);
+        } else {
+            s = div_u32(p, m);
+            d = p - s * m;
+        }
         const uint64_t ps = s < kSeedTable ? seeds[s] : pilot_seed(s);
         local = position_hash(hk, ps, m) + d;
         if (local >= m) local -= m;
@@ -303,7 +375,7 @@ __device__ __forceinline__ uint64_t query_hashed(const QueryView& v, uint64_t hk
     return g;
 }
 
-template <int kKind>
+template <int kKind, bool k32>
 __global__ void __launch_bounds__(256) k_query(const QueryView v, const uint64_t* __restrict__ keys,
                                                uint64_t* __restrict__ out, uint64_t m) {
     __shared__ uint64_t seeds[kSeedTable];
@@ -318,19 +390,19 @@ __global__ void __launch_bounds__(256) k_query(const QueryView v, const uint64_t
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < pairs; i += stride) {
             ulonglong2 k = __ldcs(k2 + i);
             ulonglong2 r;
-            r.x = query_one<kKind>(v, k.x, seeds);
-            r.y = query_one<kKind>(v, k.y, seeds);
+            r.x = query_one<kKind, k32>(v, k.x, seeds);
+            r.y = query_one<kKind, k32>(v, k.y, seeds);
             __stcs(o2 + i, r);
         }
-        if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[m - 1] = query_one<kKind>(v, keys[m - 1], seeds);
+        if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[m - 1] = query_one<kKind, k32>(v, keys[m - 1], seeds);
     } else {
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += stride)
-            out[i] = query_one<kKind>(v, keys[i], seeds);
+            out[i] = query_one<kKind, k32>(v, keys[i], seeds);
     }
 }
 
 // string keys: XXH64 master hash of each string (Section 5), then the same query
-template <int kKind>
+template <int kKind, bool k32>
 __global__ void __launch_bounds__(256) k_query_strings(const QueryView v, const uint8_t* __restrict__ bytes,
                                                        const uint64_t* __restrict__ offsets, uint64_t* __restrict__ out,
                                                        uint64_t m) {
@@ -339,7 +411,7 @@ __global__ void __launch_bounds__(256) k_query_strings(const QueryView v, const 
     __syncthreads();
     const uint64_t total = __ldg(offsets + m);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = query_hashed<kKind>(v, string_master_hash(bytes, offsets, total, i, v.string_seed), seeds);
+        out[i] = query_hashed<kKind, k32>(v, string_master_hash(bytes, offsets, total, i, v.string_seed), seeds);
 }
 
 // Several query batches against different structures in one launch.  The
@@ -376,9 +448,9 @@ __global__ void __launch_bounds__(256) k_query_multi(const MultiQuery* __restric
             const uint64_t x = __ldcs(q->keys + (i - q->begin));
             // a handle's encoder is uniform over its request
             const uint32_t enc = q->v.encoder;
-            const uint64_t y = enc >= 5   ? query_one<kQMono>(q->v, x, seeds)
-                               : enc == 1 ? query_one<kQDict>(q->v, x, seeds)
-                                          : query_one<kQInterleaved>(q->v, x, seeds);
+            const uint64_t y = enc >= 5   ? query_one<kQMono, false>(q->v, x, seeds)
+                               : enc == 1 ? query_one<kQDict, false>(q->v, x, seeds)
+                                          : query_one<kQInterleaved, false>(q->v, x, seeds);
             __stcs(q->out + (i - q->begin), y);
         }
     }
@@ -408,10 +480,21 @@ cudaError_t launch_query_strings(const QueryView& v, const uint8_t* bytes, const
     uint64_t want = (m + 255) / 256;
     uint64_t cap = (uint64_t)sms * 8;
     unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
+    const bool f32 = query_fast32(v);
     switch (query_kind(v)) {
-        case kQMono: k_query_strings<kQMono><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m); break;
-        case kQDict: k_query_strings<kQDict><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m); break;
-        default: k_query_strings<kQInterleaved><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m); break;
+        case kQMono: k_query_strings<kQMono, false><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m); break;
+        case kQDict:
+            if (f32)
+                k_query_strings<kQDict, true><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m);
+            else
+                k_query_strings<kQDict, false><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m);
+            break;
+        default:
+            if (f32)
+                k_query_strings<kQInterleaved, true><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m);
+            else
+                k_query_strings<kQInterleaved, false><<<grid, 256, 0, stream>>>(v, bytes, offsets, out, m);
+            break;
     }
     note_launches(1);
     return cudaGetLastError();
@@ -425,10 +508,21 @@ cudaError_t launch_query(const QueryView& v, const uint64_t* keys, uint64_t* out
     uint64_t want = (m / 2 + 255) / 256;
     uint64_t cap = (uint64_t)sms * 8;  // 8 resident blocks of 256 threads per SM
     unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
+    const bool f32 = query_fast32(v);
     switch (query_kind(v)) {
-        case kQMono: k_query<kQMono><<<grid, 256, 0, stream>>>(v, keys, out, m); break;
-        case kQDict: k_query<kQDict><<<grid, 256, 0, stream>>>(v, keys, out, m); break;
-        default: k_query<kQInterleaved><<<grid, 256, 0, stream>>>(v, keys, out, m); break;
+        case kQMono: k_query<kQMono, false><<<grid, 256, 0, stream>>>(v, keys, out, m); break;
+        case kQDict:
+            if (f32)
+                k_query<kQDict, true><<<grid, 256, 0, stream>>>(v, keys, out, m);
+            else
+                k_query<kQDict, false><<<grid, 256, 0, stream>>>(v, keys, out, m);
+            break;
+        default:
+            if (f32)
+                k_query<kQInterleaved, true><<<grid, 256, 0, stream>>>(v, keys, out, m);
+            else
+                k_query<kQInterleaved, false><<<grid, 256, 0, stream>>>(v, keys, out, m);
+            break;
     }
     note_launches(1);
     return cudaGetLastError();

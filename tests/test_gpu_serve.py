@@ -38,6 +38,10 @@ def _negatives(n, seed):
 
 
 def test_query_multi_equals_separate_queries(ph):
+    # phobic_query_multi decodes with the 64-bit partition arithmetic and
+    # phobic_query, at these sizes, with the 32-bit one: this also checks the two
+    # query instantiations against each other, for five encoders, both pilot
+    # forms, members and non-members
     hs, keysets = [], []
     cfgs = [(7.0, 1.0, 2500, 0, 0), (7.0, 0.99, 2500, 1, 0), (6.0, 0.97, 1024, 1, 1), (8.0, 0.99, 4096, 0, 0),
             (7.0, 0.99, 2500, 2, 0), (7.0, 0.99, 2500, 7, 1), (7.0, 1.0, 2500, 6, 0)]
