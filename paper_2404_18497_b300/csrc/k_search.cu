@@ -15,13 +15,13 @@
 //      ADDITIVE mode (Section 4, "Hash Function"): p = s m + d.  For each s the
 //      warp computes h(x, s) once per key.  Equal values among the keys rule
 //      out this s (a shift by d moves them together).  Otherwise d is found by
-//      scanning 32-slot windows of the free-slot bitmap.  The bitmap is stored
-//      twice in a row, so (h + d) mod m reads linearly.  A window is the AND,
-//      over the bucket's keys, of 32 free bits starting at h + 32w.  Lanes
-//      split into groups: each group covers one window and its lanes cover the
-//      keys.  A ballot picks the first window with a set bit, and __ffs picks
-//      its smallest d.  That is the smallest valid d, so p matches a sequential
-//      scan exactly.
+//      scanning windows of 64 (or 32) displacements of the free-slot bitmap.
+//      The bitmap is stored twice in a row, so (h + d) mod m reads linearly.  A
+//      window is the AND, over the bucket's keys, of the free bits starting at
+//      h + 64w.  Lanes split into groups: each group covers one window and its
+//      lanes cover the keys.  A ballot picks the first window with a set bit,
+//      and __ffs picks its smallest d.  That is the smallest valid d, so p
+//      matches a sequential scan exactly.
 //      XOR mode (PTHash): groups of lanes test consecutive pilots p, one key
 //      per lane.  A slot must be free and unshared within its group.
 //   4. Write the pilots (column-major, i.e. interleaved order) and, when a
@@ -148,7 +148,9 @@ __device__ __forceinline__ uint32_t choose_lanes_log2(uint32_t k, uint32_t free_
 // per window (32 >> LG windows per warp step): lane rr of group g ANDs the
 // windows of keys rr, rr + 2^LG, ... for window w0 + g, the group reduces by
 // AND, and a ballot over the group leaders takes the first window that still
-// has a set bit; its lowest bit is the smallest valid displacement.
+// has a set bit; its lowest bit is the smallest valid displacement.  With one
+// lane per window and 2048 < m <= 3072, the lanes take 96-bit windows instead,
+// so that one step covers all m displacements.
 template <int W, int LG>
 __device__ __forceinline__ bool scan_windows(const uint32_t* fw, const uint16_t* hb, uint32_t k, uint32_t m,
                                              uint32_t nw, uint32_t lane, uint32_t& d, unsigned long long& steps) {
@@ -156,6 +158,51 @@ __device__ __forceinline__ bool scan_windows(const uint32_t* fw, const uint16_t*
     using WT = typename Wn::T;
     constexpr uint32_t Lw = 1u << LG, G = 32u >> LG;
     const uint32_t g = lane >> LG, rr = lane & (Lw - 1);
+    if constexpr (W == 64 && LG == 0) {
+        if (nw > 32 && m <= 96 * 32) {
+            // 2048 < m <= 3072 (a partition of about 2500 keys): 64-bit windows
+            // would take two steps, the second with most lanes idle.  One step of
+            // 96-bit windows (lane g: displacements 96 g .. 96 g + 95; four loads
+            // and three funnel shifts per key) covers every displacement instead.
+            steps++;
+            const uint32_t base = 96 * lane;
+            uint32_t a0 = 0, a1 = 0, a2 = 0;
+            if (base < m) {
+                const uint32_t rem = m - base;
+                a0 = rem >= 32 ? kFull : (1u << rem) - 1;
+                a1 = rem >= 64 ? kFull : rem <= 32 ? 0u : (1u << (rem - 32)) - 1;
+                a2 = rem >= 96 ? kFull : rem <= 64 ? 0u : (1u << (rem - 64)) - 1;
+                uint32_t i = 0;
+                for (; i + 1 < k && (a0 | a1 | a2); i += 2) {
+                    const uint32_t q = (uint32_t)hb[i] + base, r = (uint32_t)hb[i + 1] + base;
+                    const uint32_t* x = fw + (q >> 5);
+                    const uint32_t* y = fw + (r >> 5);
+                    const uint32_t sq = q & 31, sr = r & 31;
+                    const uint32_t x0 = x[0], x1 = x[1], x2 = x[2], x3 = x[3];
+                    const uint32_t y0 = y[0], y1 = y[1], y2 = y[2], y3 = y[3];
+                    a0 &= __funnelshift_r(x0, x1, sq) & __funnelshift_r(y0, y1, sr);
+                    a1 &= __funnelshift_r(x1, x2, sq) & __funnelshift_r(y1, y2, sr);
+                    a2 &= __funnelshift_r(x2, x3, sq) & __funnelshift_r(y2, y3, sr);
+                }
+                if (i < k && (a0 | a1 | a2)) {
+                    const uint32_t q = (uint32_t)hb[i] + base;
+                    const uint32_t* x = fw + (q >> 5);
+                    const uint32_t sq = q & 31;
+                    const uint32_t x0 = x[0], x1 = x[1], x2 = x[2], x3 = x[3];
+                    a0 &= __funnelshift_r(x0, x1, sq);
+                    a1 &= __funnelshift_r(x1, x2, sq);
+                    a2 &= __funnelshift_r(x2, x3, sq);
+                }
+            }
+            const uint32_t win = __ballot_sync(kFull, (a0 | a1 | a2) != 0);
+            if (!win) return false;
+            const uint32_t fl = __ffs(win) - 1;
+            const uint32_t b0 = __shfl_sync(kFull, a0, fl), b1 = __shfl_sync(kFull, a1, fl),
+                           b2 = __shfl_sync(kFull, a2, fl);
+            d = 96 * fl + (b0 ? __ffs(b0) - 1 : b1 ? 31 + __ffs(b1) : 63 + __ffs(b2));
+            return true;
+        }
+    }
     for (uint32_t w0 = 0; w0 < nw; w0 += G) {
         steps++;
         const uint32_t w = w0 + g;

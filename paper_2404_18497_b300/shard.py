@@ -68,21 +68,31 @@ class ShardStats:
 
 class TorchComm:
     """The exchanges over a torch.distributed process group.  Tensors live on
-    `device` (CUDA for NCCL, CPU for gloo)."""
+    `device` (CUDA for NCCL, CPU for gloo).  `cpu_group` (optional, a gloo
+    group over the same processes) carries the integer metadata (key counts,
+    status codes): those values are on the host already, and sending them over
+    a device group would cost a device synchronisation each."""
 
-    def __init__(self, group=None, device=None):
+    def __init__(self, group=None, device=None, cpu_group=None):
         import torch.distributed as dist
 
         self.dist = dist
         self.group = group
+        self.cpu_group = cpu_group
         self.rank = dist.get_rank(group)
         self.world = dist.get_world_size(group)
         self.device = torch.device(device) if device is not None else torch.device("cpu")
 
+    def _int_exchange(self):
+        if self.cpu_group is not None:
+            return self.cpu_group, torch.device("cpu")
+        return self.group, self.device
+
     def all_gather_int(self, v: int) -> List[int]:
-        t = torch.tensor([int(v)], dtype=torch.int64, device=self.device)
+        grp, dev = self._int_exchange()
+        t = torch.tensor([int(v)], dtype=torch.int64, device=dev)
         out = [torch.empty_like(t) for _ in range(self.world)]
-        self.dist.all_gather(out, t, group=self.group)
+        self.dist.all_gather(out, t, group=grp)
         return [int(x.item()) for x in out]
 
     def all_to_all(self, send: torch.Tensor, send_counts: Sequence[int]) -> torch.Tensor:
@@ -104,14 +114,16 @@ class TorchComm:
         self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM, group=self.group)
 
     def all_reduce_max_int(self, v: int) -> int:
-        t = torch.tensor([int(v)], dtype=torch.int64, device=self.device)
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX, group=self.group)
+        grp, dev = self._int_exchange()
+        t = torch.tensor([int(v)], dtype=torch.int64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX, group=grp)
         return int(t.item())
 
     def _exchange_counts(self, send_counts: Sequence[int]) -> List[int]:
-        s = torch.tensor(list(send_counts), dtype=torch.int64, device=self.device)
+        grp, dev = self._int_exchange()
+        s = torch.tensor(list(send_counts), dtype=torch.int64, device=dev)
         r = torch.empty_like(s)
-        self.dist.all_to_all_single(r, s, group=self.group)
+        self.dist.all_to_all_single(r, s, group=grp)
         return [int(x) for x in r.tolist()]
 
 

@@ -46,7 +46,10 @@ def _worker(rank, world, port, case, out_dir):
     res = {"rank": rank}
     stats = []
     try:
-        out = shard.sharded_build(mine, prm, shard.TorchComm(), st, stats_out=stats)
+        # optionally a second gloo group for the integer metadata, as bench.py
+        # passes one beside its NCCL group
+        comm = shard.TorchComm(cpu_group=dist.new_group(backend="gloo") if case.get("cpu_group") else None)
+        out = shard.sharded_build(mine, prm, comm, st, stats_out=stats)
     except orc.OracleError as e:
         res["error"] = e.code
     else:
@@ -85,9 +88,20 @@ CASES = [
 
 @pytest.mark.parametrize("world,n,lam,alpha,P,mode,cuts", CASES)
 def test_sharded_build_equals_single_build(tmp_path, world, n, lam, alpha, P, mode, cuts):
+    _check_equals_single_build(tmp_path, world, dict(n=n, lam=lam, alpha=alpha, P=P, mode=mode, cuts=cuts, dup=False))
+
+
+@pytest.mark.parametrize("world", [1, 3])
+def test_sharded_build_with_a_metadata_group(tmp_path, world):
+    """Counts and status codes over a separate gloo group give the same build."""
+    case = dict(n=12_000, lam=7.0, alpha=0.99, P=500, mode=0, cuts=6, dup=False, cpu_group=True)
+    _check_equals_single_build(tmp_path, world, case)
+
+
+def _check_equals_single_build(tmp_path, world, case):
     import torch.multiprocessing as mp
 
-    case = dict(n=n, lam=lam, alpha=alpha, P=P, mode=mode, cuts=cuts, dup=False)
+    n, alpha = case["n"], case["alpha"]
     mp.spawn(_worker, args=(world, _free_port(), case, str(tmp_path)), nprocs=world, join=True)
     res = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(world)]
     for r in res:
