@@ -453,42 +453,53 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
         if (kMode == 0) {
             // ===== additive displacement =====
             if (k == 1) {
-                // the remaining buckets are singletons: warp 0 places them alone
+                // Every bucket from here on holds one key (buckets come in size
+                // order): s = 0 always succeeds, and d is the distance from h to
+                // the next free slot.  Warp 0 hashes 32 of these keys at a time,
+                // one per lane, then places them one after another.
                 if (kWarps > 1 && warp != 0) break;
-                // one key: s = 0 always works (free slots remain); d is the
-                // distance from h to the first free slot at or after it
-                // only lane 0 holds the key; every lane scans from its h
-                const uint32_t h1 =
-                    __shfl_sync(kFull, position_hash(mykey, __shfl_sync(kFull, ps_lane, 0), m), 0);
-                s_tries++;
-                uint32_t d1 = 0;
-                for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
-                    steps++;
-                    const uint32_t w = w0 + lane;
-                    WT acc = 0;
-                    if (w < nw) acc = Wn::valid(w, m) & Wn::load(fw, h1 + kW * w);
-                    uint32_t win = __ballot_sync(kFull, acc != 0);
-                    if (win) {
-                        uint32_t fl = __ffs(win) - 1;
-                        d1 = kW * (w0 + fl) + Wn::first(Wn::shfl(acc, fl));
-                        found = true;
-                        break;
+                const uint64_t ps0 = __shfl_sync(kFull, ps_lane, 0);
+                for (uint32_t r1 = r; r1 < nb && local_err == kDevOk; r1 += 32) {
+                    const uint32_t cnt = min(32u, nb - r1);
+                    uint32_t bl = 0, hl = 0, dl = 0;
+                    if (lane < cnt) {
+                        bl = order[r1 + lane];
+                        hl = position_hash(hk[bend[bl] - 1], ps0, m);
                     }
+                    for (uint32_t i = 0; i < cnt; i++) {
+                        const uint32_t h1 = __shfl_sync(kFull, hl, i);
+                        s_tries++;
+                        bool got = false;
+                        uint32_t d1 = 0;
+                        for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
+                            steps++;
+                            const uint32_t w = w0 + lane;
+                            WT acc = 0;
+                            if (w < nw) acc = Wn::valid(w, m) & Wn::load(fw, h1 + kW * w);
+                            const uint32_t win = __ballot_sync(kFull, acc != 0);
+                            if (win) {
+                                const uint32_t fl = __ffs(win) - 1;
+                                d1 = kW * (w0 + fl) + Wn::first(Wn::shfl(acc, fl));
+                                got = true;
+                                break;
+                            }
+                        }
+                        if (!got) {  // unreachable while the counts are consistent
+                            local_err = kDevSearchLimit;
+                            break;
+                        }
+                        if (lane == i) dl = d1;
+                        if (lane == 0) {
+                            uint32_t pos = h1 + d1;
+                            if (pos >= m) pos -= m;
+                            take_slot(fw, pos, m);
+                        }
+                        __syncwarp();
+                    }
+                    if (local_err == kDevOk && lane < cnt) pil[(uint64_t)bl * S.np] = dl;
+                    placed += cnt;
                 }
-                if (!found) {  // unreachable while the counts are consistent
-                    local_err = kDevSearchLimit;
-                    break;
-                }
-                p = d1;
-                if (lane == 0) {
-                    uint32_t pos = h1 + d1;
-                    if (pos >= m) pos -= m;
-                    take_slot(fw, pos, m);
-                }
-                placed += 1;
-                __syncwarp();
-                if (lane == 0) pil[(uint64_t)b * S.np] = p;
-                continue;
+                break;
             }
             uint32_t d = 0;
             uint32_t sb = 0;           // first s of this round
