@@ -164,6 +164,8 @@ __device__ __forceinline__ bool scan_windows(const uint32_t* fw, const uint16_t*
             // would take two steps, the second with most lanes idle.  One step of
             // 96-bit windows (lane g: displacements 96 g .. 96 g + 95; four loads
             // and three funnel shifts per key) covers every displacement instead.
+            // Four keys at a time, so that their loads are in flight together: a
+            // warp here waits mostly on its own loads, not for issue slots.
             steps++;
             const uint32_t base = 96 * lane;
             uint32_t a0 = 0, a1 = 0, a2 = 0;
@@ -173,6 +175,21 @@ __device__ __forceinline__ bool scan_windows(const uint32_t* fw, const uint16_t*
                 a1 = rem >= 64 ? kFull : rem <= 32 ? 0u : (1u << (rem - 32)) - 1;
                 a2 = rem >= 96 ? kFull : rem <= 64 ? 0u : (1u << (rem - 64)) - 1;
                 uint32_t i = 0;
+                for (; i + 3 < k && (a0 | a1 | a2); i += 4) {
+                    const uint32_t q = (uint32_t)hb[i] + base, r = (uint32_t)hb[i + 1] + base;
+                    const uint32_t u = (uint32_t)hb[i + 2] + base, v = (uint32_t)hb[i + 3] + base;
+                    const uint32_t* x = fw + (q >> 5);
+                    const uint32_t* y = fw + (r >> 5);
+                    const uint32_t* z = fw + (u >> 5);
+                    const uint32_t* t = fw + (v >> 5);
+                    const uint32_t sq = q & 31, sr = r & 31, su = u & 31, sv = v & 31;
+                    a0 &= __funnelshift_r(x[0], x[1], sq) & __funnelshift_r(y[0], y[1], sr) &
+                          __funnelshift_r(z[0], z[1], su) & __funnelshift_r(t[0], t[1], sv);
+                    a1 &= __funnelshift_r(x[1], x[2], sq) & __funnelshift_r(y[1], y[2], sr) &
+                          __funnelshift_r(z[1], z[2], su) & __funnelshift_r(t[1], t[2], sv);
+                    a2 &= __funnelshift_r(x[2], x[3], sq) & __funnelshift_r(y[2], y[3], sr) &
+                          __funnelshift_r(z[2], z[3], su) & __funnelshift_r(t[2], t[3], sv);
+                }
                 for (; i + 1 < k && (a0 | a1 | a2); i += 2) {
                     const uint32_t q = (uint32_t)hb[i] + base, r = (uint32_t)hb[i + 1] + base;
                     const uint32_t* x = fw + (q >> 5);
@@ -448,7 +465,6 @@ __device__ __forceinline__ void search_partition(const SearchLaunch& a, const Se
             const uint32_t bn = order[r + 1], bsn = bn ? bend[bn - 1] : 0;
             pre = lane < bend[bn] - bsn ? hk[bsn + lane] : 0;
         }
-        bool found = false;
         uint32_t p = 0;
         if (kMode == 0) {
             // ===== additive displacement =====
