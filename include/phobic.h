@@ -202,7 +202,9 @@ phobic_status phobic_build_batch(const uint64_t* d_keys, const uint64_t* h_set_o
 /*
  * Autotuner for phobic_build_batch (the paper has no counterpart).  From the
  * set sizes alone it picks, by timing trial batches of synthetic keys on the
- * current device: the expected partition size of every set, one of 1024, 2500,
+ * current device (steady-state time per key: each trial and its first half are
+ * built, and their difference is timed, so that a launch's fixed costs
+ * cancel): the expected partition size of every set, one of 1024, 2500,
  * 4096, per decade size class (the fastest, or within 3% of it the one with the
  * fewest bits per key); and warps_per_partition (1, 2, 4) and candidate_width
  * (32, 64) for the launch, then with those the search schedule (one CTA per
@@ -224,7 +226,7 @@ phobic_status phobic_build_batch(const uint64_t* d_keys, const uint64_t* h_set_o
 typedef struct {
     uint32_t sets;           /* sets of the batch in this class (0: none) */
     uint32_t partition_size; /* chosen expected partition size */
-    float ns_per_key[PHOBIC_TUNE_P_CHOICES];   /* trial time per key for P = 1024, 2500, 4096 */
+    float ns_per_key[PHOBIC_TUNE_P_CHOICES];   /* steady-state trial time per key for P = 1024, 2500, 4096 */
     float bits_per_key[PHOBIC_TUNE_P_CHOICES]; /* trial bits per key for the same */
 } phobic_tune_class;
 typedef struct {

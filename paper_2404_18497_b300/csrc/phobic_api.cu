@@ -549,20 +549,24 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
     const bool keys_in_smem = ks && ks[0] == '1';
     // warps per partition: as asked, or (0) chosen from the partition count and
     // lambda.  The build ends with its slowest partitions, and the spread of
-    // per-partition search work grows like e^lambda, so 2 or 4 warps (testing
+    // per-partition search work grows like e^lambda, so 4 warps (testing
     // consecutive candidate ranges of a bucket at once) pay off while there are
     // few waves of partitions per resident one-warp CTA slot (32 per SM), the
-    // more so at large lambda; with many waves one warp per partition wastes
-    // the fewest issue slots.  Measured crossovers: lambda 7: 4 warps at 0.08
-    // waves, 1 at 0.84; lambda 9-14: 4 warps at 0.84 waves; lambda 10: 1 at 8.4.
+    // more so at large lambda; with more waves one warp per partition wastes
+    // the fewest issue slots.  Measured (search ms, 1 / 2 / 4 warps): lambda 7,
+    // alpha 0.99: 0.084 waves 0.84 / 0.76 / 0.67, 0.15 waves 0.83 / 0.79 / 0.80,
+    // 0.25 waves 0.82 / 0.81 / 1.03, 0.5 waves 1.15 / 1.28 / 1.86; lambda 9,
+    // alpha 1: 0.3 waves 2.81 / 2.41 / 2.38, 0.84 waves 4.87 / 5.61 / 5.29;
+    // lambda 11: 0.84 waves 27.8 / 27.8 / 23.4.  Two warps never win by more
+    // than a few percent, so the choice is between one and four.
     uint32_t wpp = prm.warps_per_partition;
     if (wpp == 0) {
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const double waves = (double)(smode == kShardSearch ? sc->j1 - sc->j0 : NPT) / ((double)sms * 32.0);
-        const double t = 0.3 * std::exp((prm.lambda - 7.0) / 1.5);
-        wpp = waves <= t ? 4 : waves <= 2.0 * t ? 2 : 1;
+        const double t = 0.15 * std::exp(0.6 * (prm.lambda - 7.0));
+        wpp = waves <= t ? 4 : 1;
         while (wpp > 1 && search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, cap_B, keys_in_smem, wpp) >
                               search_smem_limit())
             wpp /= 2;

@@ -16,10 +16,9 @@
 // timed on the host around the call, which is host-synchronous.
 //   1. Sets are grouped into decade size classes [10^c, 10^(c+1)).  For each
 //      class, a trial batch repeats the class's own set sizes until it holds
-//      at least kClassTrialKeys keys (enough partitions to fill the GPU, so the
-//      time per key is the throughput the class gets inside a large batch).
-//      Each P is timed; the fastest wins, except that a P within kTieFrac of
-//      the fastest with fewer bits per key is preferred.
+//      at least kClassTrialKeys keys.  Each P is timed; the fastest wins,
+//      except that a P within kTieFrac of the fastest with fewer bits per key
+//      is preferred.
 //   2. With the chosen P per set, a deterministic subsample of the batch (every
 //      k-th set) is built with each of the six (warps, width) pairs and the
 //      fastest pair is kept, then with each search schedule.  Those knobs trade
@@ -29,6 +28,13 @@
 //      when it has fewer), with at most kLaunchTrialMaxKeys keys.  A subsample
 //      of far fewer partitions than the batch favours several warps per
 //      partition, which the full batch, many waves deep, does not repay.
+// Every time is a slope: a trial batch and its first half are both built, and
+// their difference in time over their difference in keys is the time per key.
+// A launch ends with its last wave of partitions draining, which costs about
+// one partition's lifetime whatever the launch's size; in a trial of a few
+// waves that drain would decide between knobs that differ in per-partition
+// latency rather than in throughput, which is what a batch of hundreds of
+// waves sees.  The difference cancels it (and the host's fixed costs).
 // Decisions are cached per device and parameter set: per size class for P,
 // per power of two of the batch's partition count for (warps, width).
 // The paper has no counterpart; this is a deployment convenience.
@@ -46,7 +52,7 @@
 
 namespace {
 
-constexpr uint64_t kClassTrialKeys = 1ull << 23;
+constexpr uint64_t kClassTrialKeys = 1ull << 24;
 constexpr uint64_t kLaunchTrialWaves = 8;         // of 32 one-warp CTAs per SM
 constexpr uint64_t kLaunchTrialMaxKeys = 1ull << 27;
 constexpr double kTieFrac = 0.03;
@@ -163,6 +169,35 @@ phobic_status time_build(const std::vector<uint64_t>& sizes, const std::vector<u
     return PHOBIC_OK;
 }
 
+// Steady-state seconds per key of a batched build: the time of `sizes` minus
+// that of its first half, over the keys the second half adds (one set: its
+// time over its keys).  Bits per key of the whole trial in *bits.
+phobic_status time_slope(const std::vector<uint64_t>& sizes, const std::vector<uint32_t>& Ps,
+                         const phobic_params& prm, cudaStream_t st, double* sec_per_key, double* bits) {
+    double full = 0;
+    phobic_status s = time_build(sizes, Ps, prm, st, &full, bits);
+    if (s != PHOBIC_OK) return s;
+    const size_t h = sizes.size() / 2;
+    uint64_t keys_all = 0, keys_second = 0;
+    for (size_t i = 0; i < sizes.size(); i++) {
+        keys_all += sizes[i];
+        if (i >= h) keys_second += sizes[i];
+    }
+    if (h == 0) {
+        *sec_per_key = full / (double)keys_all;
+        return PHOBIC_OK;
+    }
+    const std::vector<uint64_t> s1(sizes.begin(), sizes.begin() + h);
+    const std::vector<uint32_t> p1(Ps.begin(), Ps.begin() + h);
+    double half = 0, bits_half = 0;
+    s = time_build(s1, p1, prm, st, &half, &bits_half);
+    if (s != PHOBIC_OK) return s;
+    // a difference below a tenth of the full time is noise: fall back to the full time
+    const double d = full - half;
+    *sec_per_key = d > 0.1 * full ? d / (double)keys_second : full / (double)keys_all;
+    return PHOBIC_OK;
+}
+
 }  // namespace
 
 extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32_t n_sets,
@@ -186,7 +221,7 @@ extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32
     base.record_timings = 0;
     base.warps_per_partition = 1;
     base.candidate_width = 64;
-    base.search_schedule = 2;
+    base.search_schedule = 1;
     if (info) *info = phobic_tune_info{};
 
     std::lock_guard<std::mutex> lock(g_mu);
@@ -219,9 +254,9 @@ extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32
                     continue;
                 }
                 std::vector<uint32_t> Ps(sizes.size(), kPChoices[i]);
-                phobic_status s = time_build(sizes, Ps, p, st, &sec, &bits);
+                phobic_status s = time_slope(sizes, Ps, p, st, &sec, &bits);
                 if (s != PHOBIC_OK) return s;
-                cr.ns_per_key[i] = (float)(sec * 1e9 / (double)tot);
+                cr.ns_per_key[i] = (float)(sec * 1e9);
                 cr.bits_per_key[i] = (float)bits;
                 best = std::min(best, (double)cr.ns_per_key[i]);
             }
@@ -280,9 +315,9 @@ extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32
                 p.warps_per_partition = w;
                 p.candidate_width = cw;
                 double sec = 0, bits = 0;
-                phobic_status s = time_build(sizes, Ps, p, st, &sec, &bits);
+                phobic_status s = time_slope(sizes, Ps, p, st, &sec, &bits);
                 if (s != PHOBIC_OK) return s;
-                lr.ns_per_key[k] = (float)(sec * 1e9 / (double)tot);
+                lr.ns_per_key[k] = (float)(sec * 1e9);
                 if (lr.ns_per_key[k] < best) {
                     best = lr.ns_per_key[k];
                     lr.warps = w;
@@ -298,9 +333,9 @@ extern "C" phobic_status phobic_tune_batch(const uint64_t* h_set_offsets, uint32
             p.candidate_width = lr.width;
             p.search_schedule = sc + 1;
             double sec = 0, bits = 0;
-            phobic_status s = time_build(sizes, Ps, p, st, &sec, &bits);
+            phobic_status s = time_slope(sizes, Ps, p, st, &sec, &bits);
             if (s != PHOBIC_OK) return s;
-            lr.schedule_ns_per_key[sc] = (float)(sec * 1e9 / (double)tot);
+            lr.schedule_ns_per_key[sc] = (float)(sec * 1e9);
         }
         lr.schedule = lr.schedule_ns_per_key[0] < lr.schedule_ns_per_key[1] ? 1 : 2;
         it = g_launch.emplace(std::make_pair(pk, lk), lr).first;
