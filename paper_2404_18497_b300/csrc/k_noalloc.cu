@@ -24,7 +24,7 @@ constexpr size_t kErrorBytes = 256;
 // look-back tile states, tile counters), plus one error word
 constexpr size_t kMaxTiles = (PHOBIC_NOALLOC_MAX_KEYS + phobic::kSortTileKeys - 1) / phobic::kSortTileKeys;
 constexpr size_t kSortBytes =
-    (size_t)PHOBIC_NOALLOC_MAX_KEYS * 8 + 3 * 512 * 8 + 64 + kMaxTiles * 512 * 8 + 64 + 256 + 64;
+    (size_t)PHOBIC_NOALLOC_MAX_KEYS * 8 + 3 * 512 * 8 + 64 + 256 + (kMaxTiles + 2) * 512 * 8 + 64 + 256 + 64;
 constexpr size_t kScratchBytes = (kSortBytes + 255) / 256 * 256 + kErrorBytes;
 
 // Held by every GPU that loads this library, until the process exits.

@@ -33,6 +33,8 @@ constexpr uint64_t kFlagPre = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kLookWin = 2;    // predecessors' states read per look-back poll
+constexpr uint64_t kStatusPad = 2;  // unused tile rows before the states (a poll's window may start at tile -1)
 
 __device__ __forceinline__ uint64_t load_hk(const uint64_t* in, uint64_t i, uint64_t kseed, int hash_input) {
     uint64_t v = __ldg(in + i);
@@ -43,7 +45,8 @@ __device__ __forceinline__ uint64_t load_hk(const uint64_t* in, uint64_t i, uint
 // block walks a contiguous range of tiles; each warp counts into its own
 // sub-histogram, which is flushed to the segment's global histogram when the
 // segment changes and at the end.  When the input needs hashing, the master
-// hashes are also written out (hashed_out), so that no pass hashes again.
+// hashes are also written out (hashed_out, with streaming stores: the first
+// pass reads them only after the whole input), so that no pass hashes again.
 __device__ __forceinline__ uint32_t seg_of_tile(const SortSeg* __restrict__ segs, uint32_t nseg, uint64_t t) {
     uint32_t lo = 0, hi = nseg;  // largest s with first_tile[s] <= t
     while (hi - lo > 1) {
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ 
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const uint64_t hk = hash_input ? key_hash(v[u], kseed) : v[u];
-                if (hashed_out) hashed_out[i + (uint64_t)u * blockDim.x] = hk;
+                if (hashed_out) __stcs(hashed_out + i + (uint64_t)u * blockDim.x, hk);  // read again only by the first pass
                 const uint64_t j = partition_of(hk, S.np);
                 for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
             }
@@ -94,7 +97,7 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ 
         for (; i < k1; i += blockDim.x) {
             const uint64_t v = __ldg(in + i);
             const uint64_t hk = hash_input ? key_hash(v, kseed) : v;
-            if (hashed_out) hashed_out[i] = hk;
+            if (hashed_out) __stcs(hashed_out + i, hk);
             const uint64_t j = partition_of(hk, S.np);
             for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
         }
@@ -145,7 +148,7 @@ struct PassArgs {
     int hash_input;
     uint32_t shift, bits;
     const unsigned long long* digit_base; // [seg][pass][R]: exclusive scans of the histograms
-    unsigned long long* status;            // [tiles x R]: flag | value
+    unsigned long long* status;            // [kStatusPad + tiles][R]: flag | value
     uint32_t* tile_counter;
     uint32_t* error;
     uint32_t spin_limit;  // polls of an unpublished predecessor before the wait gives up
@@ -161,10 +164,10 @@ struct PassArgs {
 // keeps its digit order; the order inside a partition is left unspecified): it
 // ranks each key with one shared atomicAdd on its digit's counter.  The last
 // of two passes ranks the same way when its tile holds at most two first-pass
-// digits, with each digit's keys in two bins by that digit.  Then
-// per digit: prefix over warps, decoupled look-back for the tile's global
-// offset, a block scan for the tile-local digit starts, a shared-memory
-// reorder and a coalesced write-out.
+// digits, with each digit's keys in two bins by that digit.  Then per digit:
+// prefix over warps and publication of the tile's counts, a block scan for
+// the tile-local digit starts, a shared-memory reorder, decoupled look-back
+// for the tile's global offset, and a coalesced write-out.
 __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t R = 1u << a.bits, mask = R - 1;
@@ -288,49 +291,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
         }
     }
     __syncthreads();
-    // decoupled look-back per digit (publish the aggregate first); each thread
-    // reads up to 8 predecessors' states at once, so a long chain of
-    // aggregates costs one L2 round trip per 8 tiles instead of one per tile
-    for (uint32_t d = tid; d < R; d += kThreads) {
-        const uint64_t cnt = tile_start[d];
-        volatile unsigned long long* st = a.status;
-        uint64_t excl = 0;
-        const bool publish = tile != a.mute_tile;
-        if (tile == first) {
-            if (publish) st[tile * R + d] = kFlagPre | cnt;
-        } else {
-            if (publish) st[tile * R + d] = kFlagAgg | cnt;
-            int64_t t = (int64_t)tile - 1;  // next predecessor to account for
-            uint32_t spins = 0;
-            bool done = false;
-            while (!done) {
-                unsigned long long v[8];
+    // Publish the tile's digit counts at once (the aggregate; the inclusive
+    // prefix for a segment's first tile), so that successors can sum past this
+    // tile while it scans and reorders.  Thread tid owns digits tid and
+    // tid + kThreads (R <= 512 < 2 kThreads) and keeps their counts for its
+    // look-back below.
+    volatile unsigned long long* st = a.status;
+    const bool publish = tile != a.mute_tile;
+    uint32_t cnt_own[2] = {0, 0};
 #pragma unroll
-                for (int u = 0; u < 8; u++)
-                    v[u] = (t - u >= (int64_t)first) ? st[(uint64_t)(t - u) * R + d] : (kFlagPre | 0ull);
-                int u = 0;
-                for (; u < 8; u++) {
-                    const uint64_t flag = v[u] & ~kValMask;
-                    if (flag == 0) break;  // not published yet: poll again from here
-                    excl += v[u] & kValMask;
-                    if (flag == kFlagPre) {
-                        done = true;
-                        break;
-                    }
-                }
-                if (done) break;
-                t -= u;
-                if (u == 0) {
-                    if (++spins > a.spin_limit) {
-                        atomicMax(a.error, kDevTimeout);
-                        break;
-                    }
-                    if (spins > 32) __nanosleep(64);
-                }
-            }
-            if (publish) st[tile * R + d] = kFlagPre | (excl + cnt);
+    for (int u = 0; u < 2; u++) {
+        const uint32_t d = tid + u * kThreads;
+        if (d < R) {
+            cnt_own[u] = tile_start[d];
+            if (publish) st[(tile + kStatusPad) * R + d] = (tile == first ? kFlagPre : kFlagAgg) | cnt_own[u];
         }
-        gbase[d] = a.digit_base[((uint64_t)sg * a.passes + a.pass) * R + d] + excl;
     }
     // block-wide exclusive scan of the tile counts over digits: each thread
     // owns R / kThreads consecutive digits (1 or 2)
@@ -361,8 +336,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
         }
     }
     __syncthreads();
-    for (uint32_t d = tid; d < R; d += kThreads) gbase[d] -= tile_start[d];
-    // reorder in shared memory by digit
+    // reorder in shared memory by digit (tile-local offsets only)
     if (split) {
 #pragma unroll
         for (int i = 0; i < kItems; i++) {
@@ -378,6 +352,60 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
             uint32_t d = dr[i] >> 16;
             if (d < R) keys_s[tile_start[d] + wh[warp * WS + d] + (dr[i] & 0xFFFFu)] = k[i];
         }
+    }
+    // Decoupled look-back per digit, after the reorder: the predecessors have
+    // had that much longer to publish.  Each poll reads the states of two
+    // predecessors; reading more per poll was measured slower, because the
+    // polls of all tiles share the L2 lines that the tiles publish to.
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const uint32_t d = tid + u * kThreads;
+        if (d >= R) continue;
+        uint64_t excl = 0;
+        if (tile != first) {
+            // states of tile x for digit d at (x + kStatusPad) R + d; the tile rows
+            // start 256-byte aligned
+            const volatile unsigned long long* col = st + kStatusPad * R + d;
+            int64_t e = (int64_t)tile;  // predecessors [first, e) are not accounted yet
+            const int64_t lo = (int64_t)first;
+            uint32_t spins = 0;
+            bool done = false;
+            while (!done) {
+                const int64_t s0 = e - (int64_t)kLookWin;  // >= -1, inside the padding
+                unsigned long long v[kLookWin];
+#pragma unroll
+                for (int q = 0; q < (int)kLookWin; q++) v[q] = col[(s0 + q) * (int64_t)R];
+                const int64_t e0 = e;
+                bool stop = false;
+#pragma unroll
+                for (int q = (int)kLookWin - 1; q >= 0; q--) {
+                    const int64_t x = s0 + q;  // nearest first
+                    if (stop) continue;
+                    if (x < lo) {  // past the segment's first tile: everything is accounted
+                        done = stop = true;
+                        continue;
+                    }
+                    const uint64_t flag = v[q] & ~kValMask;
+                    if (flag == 0) {  // not published yet: poll again from here
+                        stop = true;
+                        continue;
+                    }
+                    excl += v[q] & kValMask;
+                    e = x;
+                    if (flag == kFlagPre) done = stop = true;
+                }
+                if (done) break;
+                if (e == e0) {
+                    if (++spins > a.spin_limit) {
+                        atomicMax(a.error, kDevTimeout);
+                        break;
+                    }
+                    if (spins > 32) __nanosleep(64);
+                }
+            }
+            if (publish) st[(tile + kStatusPad) * R + d] = kFlagPre | (excl + cnt_own[u]);
+        }
+        gbase[d] = a.digit_base[((uint64_t)sg * a.passes + a.pass) * R + d] + excl - tile_start[d];
     }
     __syncthreads();
     // coalesced write-out: consecutive slots of one digit go to consecutive addresses
@@ -465,7 +493,7 @@ size_t sort_seg_scratch_bytes(uint64_t n_total, uint64_t tiles, uint32_t nseg, u
     size_t s = 0;
     s += (size_t)n_total * 8;                          // ping-pong buffer
     s += (size_t)nseg * (passes ? passes : 1) * R * 8 + 64;  // histograms / digit bases
-    s += (size_t)tiles * R * 8 + 64;                   // look-back status
+    s += 256 + (size_t)(tiles + kStatusPad) * R * 8 + 64;  // look-back states, 256-byte aligned
     s += 64 * 4;                                       // tile counters
     return s;
 }
@@ -486,8 +514,10 @@ cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint6
     p += (size_t)n_total * 8;
     unsigned long long* hist = reinterpret_cast<unsigned long long*>(p);
     p += (size_t)nseg * (passes ? passes : 1) * R * 8 + 64;
+    p = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 255) & ~uintptr_t(255));
     unsigned long long* status = reinterpret_cast<unsigned long long*>(p);
-    p += (size_t)tiles * R * 8 + 64;
+    const size_t status_bytes = (size_t)(tiles + kStatusPad) * R * 8;
+    p += status_bytes + 64;
     uint32_t* counters = reinterpret_cast<uint32_t*>(p);
     cudaError_t e;
 
@@ -521,7 +551,7 @@ cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint6
         // ping-pong so that the last pass lands in `sorted`
         uint64_t* dst = (passes & 1) ? sorted : alt;
         for (uint32_t ps = 0; ps < passes; ps++) {
-            if ((e = cudaMemsetAsync(status, 0, (size_t)tiles * R * 8, stream)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(status, 0, status_bytes, stream)) != cudaSuccess) return e;
             PassArgs a;
             a.in = src;
             a.out = dst;
