@@ -114,10 +114,10 @@ NCU_CAPTURES = {
     "k_query": {"files": ["paper_2404_18497_b300/csrc/k_query.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
                 "sha": "10e6fa277985462a", "n": 3e7, "dram_bytes": 249930240 + 198135296},
     "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "927160e0248f0d62", "n": 3e7,
-               "dram_bytes": (240058624 + 197003776) + (243547648 + 195917312) + (243733760 + 195278592)},
+               "sha": "94cab6432812081e", "n": 3e7,
+               "dram_bytes": (240018944 + 187418880) + (240089344 + 196672768) + (240083712 + 195541760)},
     "k_hash": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "927160e0248f0d62", "n": 3e7, "dram_bytes": 240020480 + 192098048},
+               "sha": "94cab6432812081e", "n": 3e7, "dram_bytes": 240024064 + 192360448},
 }
 ISSUE_SLOTS_PER_CLOCK = 148 * 4  # B300: 148 SMs x 4 warp schedulers, one warp instruction per clock each
 SM_MAX_MHZ = 2032.0
