@@ -36,6 +36,39 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kLookWin = 2;    // predecessors' states read per look-back poll
 constexpr uint64_t kStatusPad = 2;  // unused tile rows before the states (a poll's window may start at tile -1)
 
+// The digit of each pass: bits [shift[p], shift[p] + bits[p]) of the partition
+// id.  ceil(log2 N_P) bits split into as few passes of at most 9 bits as
+// possible; when they do not split evenly, the first passes take one bit less
+// (17 bits: 8 + 9, where equal widths would run two 512-digit passes, one of
+// them with half its digits empty).  Histogram rows, digit bases and look-back
+// states keep the widest pass's stride.
+constexpr uint32_t kMaxPasses = 8;
+struct DigitPlan {
+    uint32_t passes, max_bits;
+    uint32_t bits[kMaxPasses], shift[kMaxPasses];
+    __device__ __forceinline__ uint32_t digit(uint64_t j, uint32_t p) const {
+        return (uint32_t)(j >> shift[p]) & ((1u << bits[p]) - 1);
+    }
+};
+
+DigitPlan make_digit_plan(uint64_t np) {
+    DigitPlan d{};
+    uint32_t bits_max = 0;
+    sort_plan(np, &d.passes, &bits_max);
+    d.max_bits = bits_max;
+    const uint32_t total = np > 1 ? bitlen64(np - 1) : 0;
+    if (d.passes) {
+        const uint32_t base = total / d.passes, extra = total % d.passes;
+        uint32_t sh = 0;
+        for (uint32_t p = 0; p < d.passes; p++) {
+            d.bits[p] = base + (p >= d.passes - extra ? 1u : 0u);
+            d.shift[p] = sh;
+            sh += d.bits[p];
+        }
+    }
+    return d;
+}
+
 __device__ __forceinline__ uint64_t load_hk(const uint64_t* in, uint64_t i, uint64_t kseed, int hash_input) {
     uint64_t v = __ldg(in + i);
     return hash_input ? key_hash(v, kseed) : v;
@@ -58,12 +91,11 @@ __device__ __forceinline__ uint32_t seg_of_tile(const SortSeg* __restrict__ segs
 
 __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ in, const SortSeg* __restrict__ segs,
                                                    uint32_t nseg, uint64_t tiles, uint64_t kseed, int hash_input,
-                                                   uint32_t passes, uint32_t bits,
-                                                   unsigned long long* __restrict__ hist,
+                                                   DigitPlan dp, unsigned long long* __restrict__ hist,
                                                    uint64_t* __restrict__ hashed_out) {
-    extern __shared__ uint32_t sh_hist[];  // [kWarpsH][passes * R]
+    extern __shared__ uint32_t sh_hist[];  // [kWarpsH][passes * R], R = 2^(widest digit)
     constexpr int kWarpsH = 8;
-    const uint32_t R = 1u << bits, mask = R - 1, PR = passes * R;
+    const uint32_t passes = dp.passes, R = 1u << dp.max_bits, PR = passes * R;
     const uint64_t per = (tiles + gridDim.x - 1) / gridDim.x;
     const uint64_t t0 = (uint64_t)blockIdx.x * per;
     const uint64_t t1 = t0 + per < tiles ? t0 + per : tiles;
@@ -91,7 +123,9 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ 
                 const uint64_t hk = hash_input ? key_hash(v[u], kseed) : v[u];
                 if (hashed_out) __stcs(hashed_out + i + (uint64_t)u * blockDim.x, hk);  // read again only by the first pass
                 const uint64_t j = partition_of(hk, S.np);
-                for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
+#pragma unroll
+                for (uint32_t p = 0; p < kMaxPasses; p++)
+                    if (p < passes) atomicAdd(&mine[p * R + dp.digit(j, p)], 1u);
             }
         }
         for (; i < k1; i += blockDim.x) {
@@ -99,7 +133,9 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ 
             const uint64_t hk = hash_input ? key_hash(v, kseed) : v;
             if (hashed_out) __stcs(hashed_out + i, hk);
             const uint64_t j = partition_of(hk, S.np);
-            for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + ((j >> (p * bits)) & mask)], 1u);
+#pragma unroll
+            for (uint32_t p = 0; p < kMaxPasses; p++)
+                if (p < passes) atomicAdd(&mine[p * R + dp.digit(j, p)], 1u);
         }
         __syncthreads();
         unsigned long long* gh = hist + (uint64_t)sg * PR;
@@ -146,8 +182,10 @@ struct PassArgs {
     uint32_t nseg, passes, pass;
     uint64_t kseed;
     int hash_input;
-    uint32_t shift, bits;
-    const unsigned long long* digit_base; // [seg][pass][R]: exclusive scans of the histograms
+    uint32_t shift, bits;   // this pass's digit: bits [shift, shift + bits) of the partition id
+    uint32_t bits0;         // the first pass's digit width
+    uint32_t rstride;       // digits per (segment, pass) row of digit_base: 2^(widest digit)
+    const unsigned long long* digit_base; // [seg][pass][rstride]: exclusive scans of the histograms
     unsigned long long* status;            // [kStatusPad + tiles][R]: flag | value
     uint32_t* tile_counter;
     uint32_t* error;
@@ -213,19 +251,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     bool split = false;
     uint32_t lo_first = 0;
     if (a.pass == 1 && a.passes == 2) {
-        const unsigned long long* db0 = a.digit_base + ((uint64_t)sg * a.passes) * R;
+        const unsigned long long* db0 = a.digit_base + ((uint64_t)sg * a.passes) * a.rstride;
+        const uint32_t R0 = 1u << a.bits0;
         const uint64_t last = (seg_end - base < (uint64_t)kTile ? seg_end : base + kTile) - 1;
         // first-pass digit of key index x: the largest d with db0[d] <= x
         uint32_t lf = 0, ll = 0;
-        for (uint32_t st = R >> 1; st; st >>= 1) {
-            if (lf + st < R && __ldg(db0 + lf + st) <= base) lf += st;
-            if (ll + st < R && __ldg(db0 + ll + st) <= last) ll += st;
+        for (uint32_t st = R0 >> 1; st; st >>= 1) {
+            if (lf + st < R0 && __ldg(db0 + lf + st) <= base) lf += st;
+            if (ll + st < R0 && __ldg(db0 + ll + st) <= last) ll += st;
         }
         lo_first = lf;
         split = ll - lf <= 1;
     }
     if (split) {
-        const uint64_t lomask = (1ull << a.bits) - 1;
+        const uint64_t lomask = (1ull << a.bits0) - 1;
 #pragma unroll
         for (int i = 0; i < kItems; i++) {
             const bool valid = wbase + (uint64_t)i * 32 + lane < seg_end;
@@ -405,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
             }
             if (publish) st[(tile + kStatusPad) * R + d] = kFlagPre | (excl + cnt_own[u]);
         }
-        gbase[d] = a.digit_base[((uint64_t)sg * a.passes + a.pass) * R + d] + excl - tile_start[d];
+        gbase[d] = a.digit_base[((uint64_t)sg * a.passes + a.pass) * a.rstride + d] + excl - tile_start[d];
     }
     __syncthreads();
     // coalesced write-out: consecutive slots of one digit go to consecutive addresses
@@ -506,8 +545,8 @@ cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint6
                                        uint32_t nseg, uint64_t n_total, uint64_t tiles, uint64_t max_np,
                                        uint64_t total_parts, uint64_t* sorted, uint64_t* start, void* scratch,
                                        uint32_t* d_error, cudaStream_t stream, const SortWaitTest* wait_test) {
-    uint32_t passes, bits;
-    sort_plan(max_np, &passes, &bits);
+    const DigitPlan dp = make_digit_plan(max_np);
+    const uint32_t passes = dp.passes, bits = dp.max_bits;
     const uint32_t R = 1u << bits;
     unsigned char* p = static_cast<unsigned char*>(scratch);
     uint64_t* alt = reinterpret_cast<uint64_t*>(p);
@@ -540,11 +579,10 @@ cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint6
         // buffer that the first pass does not write, and the passes read those
         uint64_t* hashed = hash_input ? ((passes & 1) ? alt : sorted) : nullptr;
         k_sort_hist<<<(unsigned)hblocks, 256, 8 * passes * R * 4, stream>>>(in, d_segs, nseg, tiles, kseed,
-                                                                            hash_input, passes, bits, hist, hashed);
+                                                                            hash_input, dp, hist, hashed);
         note_launches(1);
         k_sort_hist_scan<<<nseg * passes, 512, 0, stream>>>(hist, d_segs, passes, bits);
         note_launches(1);
-        size_t smem = sort_pass_smem(bits);
         if ((e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_sort_pass))) != cudaSuccess) return e;
         const uint64_t* src = hashed ? hashed : in;
         int hash_now = 0;
@@ -561,15 +599,17 @@ cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint6
             a.pass = ps;
             a.kseed = kseed;
             a.hash_input = hash_now;
-            a.shift = ps * bits;
-            a.bits = bits;
+            a.shift = dp.shift[ps];
+            a.bits = dp.bits[ps];
+            a.bits0 = dp.bits[0];
+            a.rstride = R;
             a.digit_base = hist;
             a.status = status;
             a.tile_counter = counters + ps;
             a.error = d_error;
             a.spin_limit = wait_test ? wait_test->spin_limit : kSpinLimit;
             a.mute_tile = wait_test ? wait_test->mute_tile : ~0ull;
-            k_sort_pass<<<(unsigned)tiles, kThreads, smem, stream>>>(a);
+            k_sort_pass<<<(unsigned)tiles, kThreads, sort_pass_smem(dp.bits[ps]), stream>>>(a);
             note_launches(1);
             src = dst;
             hash_now = 0;

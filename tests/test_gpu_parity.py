@@ -111,7 +111,8 @@ def test_string_hash_known_answers(ph):
 
 
 @pytest.mark.parametrize("n,P", [(1, 2500), (100, 2500), (2500, 2500), (1_000_000, 2500), (1_234_567, 1000),
-                                 (300_000, 37), (5_000_000, 2500), (65_536, 1), (3_000_000, 24)])
+                                 (300_000, 37), (5_000_000, 2500), (65_536, 1), (3_000_000, 24),
+                                 (1_000_000, 1), (2_000_000, 3)])
 def test_partition_sort_parity(ph, orc, n, P):
     """Section 4: keys grouped by partition j = floor(hk N_P / 2^64), partitions
     ascending.  j is monotone in hk, so sorting each partition's segment must give
