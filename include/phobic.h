@@ -107,12 +107,12 @@ typedef struct {
                                      32-bit pilot: in every partition s < floor((2^32-1)/m_j), which also
                                      caps any other value */
     uint64_t seed;                /* master-hash seed */
-    uint32_t warps_per_partition; /* search tuning: warps sharing one partition, 1, 2 or 4; 0 = chosen from
-                                     the partition count and lambda (w = partitions / (32 x SMs); 4 warps
-                                     while w <= 0.3 e^((lambda-7)/1.5), 2 up to twice that, then 1).
-                                     Several warps test consecutive candidate ranges of a bucket at once and
-                                     the first success in enumeration order is kept, so results do not
-                                     depend on it */
+    uint32_t warps_per_partition; /* search tuning: warps sharing one partition, 1, 2, 4 or 8; 0 = chosen
+                                     from the partition count and lambda (w = partitions / (32 x SMs);
+                                     4 warps while w <= 0.15 e^(0.6 (lambda - 7)), 8 of them when also
+                                     lambda >= 12 and w <= 1, else 1).  Several warps test consecutive
+                                     candidate ranges of a bucket at once and the first success in
+                                     enumeration order is kept, so results do not depend on it */
     uint32_t keep_pilots;         /* nonzero: keep the raw pilot matrix for phobic_copy_pilots */
     uint32_t record_timings;      /* nonzero: time the build phases with CUDA events on `stream` */
     uint32_t candidate_width;     /* search tuning: displacements per lane-window, 32 or 64 (0 = default 64);

@@ -1021,9 +1021,12 @@ SearchKernel pick_kernel(const SearchLaunch& a) {
 
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t stream) {
     const uint32_t wp = a.warps;
-    if (wp != 1 && wp != 2 && wp != 4) return cudaErrorInvalidValue;
+    if (wp != 1 && wp != 2 && wp != 4 && wp != 8) return cudaErrorInvalidValue;
     const size_t smem = search_smem_bytes(a.cap_n, a.cap_m, a.cap_B, a.keys_in_smem != 0, wp);
-    const SearchKernel kern = wp == 1 ? pick_kernel<1>(a) : wp == 2 ? pick_kernel<2>(a) : pick_kernel<4>(a);
+    const SearchKernel kern = wp == 1   ? pick_kernel<1>(a)
+                              : wp == 2 ? pick_kernel<2>(a)
+                              : wp == 4 ? pick_kernel<4>(a)
+                                        : pick_kernel<8>(a);
     const bool q = a.use_queue != 0;
     cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
     if (e != cudaSuccess) return e;

@@ -302,7 +302,7 @@ phobic_status check_params(uint64_t n, const phobic_params& p) {
     if (p.encoder > PHOBIC_ENC_MONO_EF || p.pilot_mode > PHOBIC_PILOT_XOR) return PHOBIC_ERR_INVALID_ARG;
     if (p.compact_columns >= (1u << 24)) return PHOBIC_ERR_INVALID_ARG;
     if (p.warps_per_partition != 0 && p.warps_per_partition != 1 && p.warps_per_partition != 2 &&
-        p.warps_per_partition != 4)
+        p.warps_per_partition != 4 && p.warps_per_partition != 8)
         return PHOBIC_ERR_INVALID_ARG;
     if (p.candidate_width != 0 && p.candidate_width != 32 && p.candidate_width != 64) return PHOBIC_ERR_INVALID_ARG;
     if (p.search_schedule > 2) return PHOBIC_ERR_INVALID_ARG;
@@ -567,6 +567,13 @@ phobic_status build_sets(const uint64_t* in, int hash_input, const std::vector<S
         const double waves = (double)(smode == kShardSearch ? sc->j1 - sc->j0 : NPT) / ((double)sms * 32.0);
         const double t = 0.15 * std::exp(0.6 * (prm.lambda - 7.0));
         wpp = waves <= t ? 4 : 1;
+        // Eight warps from lambda 12, while the partitions fill at most one wave:
+        // a bucket then tries so many seeds that eight at a time pay for the
+        // CTAs they take.  Measured (search ms, 4 / 8 warps, IC-R, alpha 1):
+        // 1e7 keys (0.84 waves) lambda 11: 23.2 / 24.0, 12: 62.3 / 60.9,
+        // 13: 169.1 / 157.5, 14: 486 / 437; 1e8 keys (8.4 waves) lambda 14:
+        // 3502 / 3684; lambda 7, 1e6 keys: 0.62 / 0.74.
+        if (wpp == 4 && prm.lambda >= 12.0 && waves <= 1.0) wpp = 8;
         while (wpp > 1 && search_smem_bytes((uint32_t)max_n, (uint32_t)max_m, cap_B, keys_in_smem, wpp) >
                               search_smem_limit())
             wpp /= 2;

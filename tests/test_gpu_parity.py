@@ -346,7 +346,7 @@ def test_errors(ph):
     # every search variant reports the same errors (several warps per partition
     # keep the first final outcome in enumeration order)
     for mode in (0, 1):
-        for wpp in (1, 2, 4):
+        for wpp in (1, 2, 4, 8):
             with pytest.raises(ph.PhobicError) as e:
                 ph.phobic_build_ex(_dev(dup), ph.make_params(7.0, 1.0, 2500, mode=mode, warps_per_partition=wpp))
             assert e.value.status == "DUP_HASH", (mode, wpp)
@@ -354,7 +354,7 @@ def test_errors(ph):
                 ph.phobic_build_ex(_dev(keys), ph.make_params(12.0, 1.0, 2500, mode=mode, s_max=1,
                                                               warps_per_partition=wpp))
             assert e.value.status == "SEARCH_LIMIT", (mode, wpp)
-    for wpp in (3, 8):
+    for wpp in (3, 16):
         with pytest.raises(ph.PhobicError) as e:
             ph.phobic_build_ex(_dev(keys), ph.make_params(7.0, 1.0, 2500, warps_per_partition=wpp))
         assert e.value.status == "INVALID_ARG"
@@ -389,7 +389,7 @@ def test_search_limit_matches_oracle(ph, orc, mode):
         except orc.OracleError as e:
             assert e.code == orc.SEARCH_LIMIT
             o_ok = False
-        for wpp in (1, 2, 4):
+        for wpp in (1, 2, 4, 8):
             try:
                 ph.phobic_build_ex(_dev(keys), ph.make_params(9.0, 1.0, 2500, mode=mode, s_max=s_max,
                                                               warps_per_partition=wpp)).free()
@@ -426,7 +426,7 @@ def test_search_variants_agree(ph, orc, mode, lam, P, monkeypatch):
         monkeypatch.setenv("PHOBIC_KEYS_IN_SMEM", in_smem)
         for width in (32, 64):
             for sched in (1, 2):
-                for wpp in (1, 2, 4):
+                for wpp in (1, 2, 4, 8):
                     h = ph.phobic_build_ex(_dev(keys), ph.make_params(lam, 0.99, P, mode=mode, keep_pilots=True,
                                                                       candidate_width=width, search_schedule=sched,
                                                                       warps_per_partition=wpp))
