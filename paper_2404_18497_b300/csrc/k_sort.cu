@@ -89,13 +89,16 @@ __device__ __forceinline__ uint32_t seg_of_tile(const SortSeg* __restrict__ segs
     return lo;
 }
 
+// kPasses = dp.passes, so that the per-key loop over the passes unrolls exactly.
+template <uint32_t kPasses>
 __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ in, const SortSeg* __restrict__ segs,
                                                    uint32_t nseg, uint64_t tiles, uint64_t kseed, int hash_input,
                                                    DigitPlan dp, unsigned long long* __restrict__ hist,
                                                    uint64_t* __restrict__ hashed_out) {
     extern __shared__ uint32_t sh_hist[];  // [kWarpsH][passes * R], R = 2^(widest digit)
     constexpr int kWarpsH = 8;
-    const uint32_t passes = dp.passes, R = 1u << dp.max_bits, PR = passes * R;
+    constexpr uint32_t passes = kPasses;
+    const uint32_t R = 1u << dp.max_bits, PR = passes * R;
     const uint64_t per = (tiles + gridDim.x - 1) / gridDim.x;
     const uint64_t t0 = (uint64_t)blockIdx.x * per;
     const uint64_t t1 = t0 + per < tiles ? t0 + per : tiles;
@@ -124,8 +127,7 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ 
                 if (hashed_out) __stcs(hashed_out + i + (uint64_t)u * blockDim.x, hk);  // read again only by the first pass
                 const uint64_t j = partition_of(hk, S.np);
 #pragma unroll
-                for (uint32_t p = 0; p < kMaxPasses; p++)
-                    if (p < passes) atomicAdd(&mine[p * R + dp.digit(j, p)], 1u);
+                for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + dp.digit(j, p)], 1u);
             }
         }
         for (; i < k1; i += blockDim.x) {
@@ -134,8 +136,7 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint64_t* __restrict__ 
             if (hashed_out) __stcs(hashed_out + i, hk);
             const uint64_t j = partition_of(hk, S.np);
 #pragma unroll
-            for (uint32_t p = 0; p < kMaxPasses; p++)
-                if (p < passes) atomicAdd(&mine[p * R + dp.digit(j, p)], 1u);
+            for (uint32_t p = 0; p < passes; p++) atomicAdd(&mine[p * R + dp.digit(j, p)], 1u);
         }
         __syncthreads();
         unsigned long long* gh = hist + (uint64_t)sg * PR;
@@ -251,17 +252,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort_pass(PassArgs a) {
     bool split = false;
     uint32_t lo_first = 0;
     if (a.pass == 1 && a.passes == 2) {
-        const unsigned long long* db0 = a.digit_base + ((uint64_t)sg * a.passes) * a.rstride;
-        const uint32_t R0 = 1u << a.bits0;
+        // the run of first-pass digits: those of the tile's first and last keys
         const uint64_t last = (seg_end - base < (uint64_t)kTile ? seg_end : base + kTile) - 1;
-        // first-pass digit of key index x: the largest d with db0[d] <= x
-        uint32_t lf = 0, ll = 0;
-        for (uint32_t st = R0 >> 1; st; st >>= 1) {
-            if (lf + st < R0 && __ldg(db0 + lf + st) <= base) lf += st;
-            if (ll + st < R0 && __ldg(db0 + ll + st) <= last) ll += st;
-        }
-        lo_first = lf;
-        split = ll - lf <= 1;
+        const uint32_t m0 = (1u << a.bits0) - 1;
+        lo_first = (uint32_t)partition_of(load_hk(a.in, base, a.kseed, a.hash_input), S.np) & m0;
+        const uint32_t ll = (uint32_t)partition_of(load_hk(a.in, last, a.kseed, a.hash_input), S.np) & m0;
+        split = ll - lo_first <= 1;
     }
     if (split) {
         const uint64_t lomask = (1ull << a.bits0) - 1;
@@ -574,12 +570,19 @@ cudaError_t launch_partition_sort_segs(const uint64_t* in, int hash_input, uint6
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         uint64_t hblocks = tiles < (uint64_t)sms * 8 ? tiles : (uint64_t)sms * 8;
         if (hblocks == 0) hblocks = 1;
-        if ((e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_sort_hist))) != cudaSuccess) return e;
+        using HistKernel = void (*)(const uint64_t*, const SortSeg*, uint32_t, uint64_t, uint64_t, int, DigitPlan,
+                                    unsigned long long*, uint64_t*);
+        static const HistKernel hist_kernels[kMaxPasses] = {k_sort_hist<1>, k_sort_hist<2>, k_sort_hist<3>,
+                                                            k_sort_hist<4>, k_sort_hist<5>, k_sort_hist<6>,
+                                                            k_sort_hist<7>, k_sort_hist<8>};
+        if (passes > kMaxPasses) return cudaErrorInvalidValue;
+        const HistKernel hk = hist_kernels[passes - 1];
+        if ((e = allow_max_dynamic_smem(reinterpret_cast<const void*>(hk))) != cudaSuccess) return e;
         // with hashing: the histogram pass also writes the master hashes, into the
         // buffer that the first pass does not write, and the passes read those
         uint64_t* hashed = hash_input ? ((passes & 1) ? alt : sorted) : nullptr;
-        k_sort_hist<<<(unsigned)hblocks, 256, 8 * passes * R * 4, stream>>>(in, d_segs, nseg, tiles, kseed,
-                                                                            hash_input, dp, hist, hashed);
+        hk<<<(unsigned)hblocks, 256, 8 * passes * R * 4, stream>>>(in, d_segs, nseg, tiles, kseed, hash_input, dp,
+                                                                   hist, hashed);
         note_launches(1);
         k_sort_hist_scan<<<nseg * passes, 512, 0, stream>>>(hist, d_segs, passes, bits);
         note_launches(1);
