@@ -114,10 +114,10 @@ NCU_CAPTURES = {
     "k_query": {"files": ["paper_2404_18497_b300/csrc/k_query.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
                 "sha": "10e6fa277985462a", "n": 3e7, "dram_bytes": 249930240 + 198135296},
     "k_sort": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "ae4d3944ce2140ca", "n": 3e7,
-               "dram_bytes": (240018176 + 186698752) + (240127232 + 196268288) + (240125184 + 195954176)},
+               "sha": "5ad006ea5cf8bbe5", "n": 3e7,
+               "dram_bytes": (240013824 + 186941952) + (240104192 + 196000512) + (240187392 + 195732736)},
     "k_hash": {"files": ["paper_2404_18497_b300/csrc/k_sort.cu", "paper_2404_18497_b300/csrc/phobic_dev.cuh"],
-               "sha": "ae4d3944ce2140ca", "n": 3e7, "dram_bytes": 240024576 + 192365568},
+               "sha": "5ad006ea5cf8bbe5", "n": 3e7, "dram_bytes": 240025856 + 192203008},
 }
 ISSUE_SLOTS_PER_CLOCK = 148 * 4  # B300: 148 SMs x 4 warp schedulers, one warp instruction per clock each
 SM_MAX_MHZ = 2032.0
