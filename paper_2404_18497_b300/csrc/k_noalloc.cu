@@ -21,7 +21,9 @@ namespace {
 constexpr size_t kErrorBytes = 256;
 // the sort's scratch for PHOBIC_NOALLOC_MAX_KEYS keys at the widest digit
 // (512 bins) and up to three passes (ping-pong keys, digit histograms,
-// look-back tile states, tile counters), plus one error word
+// look-back tile states with two rows of padding and up to 256 bytes of
+// alignment, tile counters), plus one error word; the same layout as
+// sort_scratch_bytes, which each call checks against this size
 constexpr size_t kMaxTiles = (PHOBIC_NOALLOC_MAX_KEYS + phobic::kSortTileKeys - 1) / phobic::kSortTileKeys;
 constexpr size_t kSortBytes =
     (size_t)PHOBIC_NOALLOC_MAX_KEYS * 8 + 3 * 512 * 8 + 64 + 256 + (kMaxTiles + 2) * 512 * 8 + 64 + 256 + 64;
