@@ -51,7 +51,8 @@ def test_noalloc_sort_matches_allocating_sort_twice(ph):
 def test_noalloc_sort_at_its_maximum_size(ph):
     """n = PHOBIC_NOALLOC_MAX_KEYS with 2^18 partitions: two digit passes of 9
     bits (512 bins), the widest digits the fixed array is sized for, so the
-    scratch the sort needs is the array's full sort region."""
+    sort uses all of the array's key, look-back and counter regions (only the
+    histogram region keeps room for a third pass)."""
     n = ph.NOALLOC_MAX_KEYS
     NP = 1 << 18
     for seed in (3, 4):
